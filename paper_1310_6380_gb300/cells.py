@@ -1,0 +1,247 @@
+"""Seeded synthetic unit cells and wavevector lists.
+
+This module makes the inputs that every consumer (tests, the benchmark,
+the smoke run, the oracle) feeds to the band-structure method: a lattice
+(h1, h2), a pixel phase map, a per-phase table of Lame constants and
+density, and lists of fractional wavevectors Q (k = Q1 q1 + Q2 q2).  It
+holds none of the method's arithmetic: no form factors, no matrices, no
+eigenvalues.  Everything is a deterministic function of its arguments.
+
+Conventions (Sec. "Statement of the problem" of the paper):
+  * phase[p, q]: p indexes pixels along h1, q along h2; pixel (p, q) covers
+    fractional coordinates [p/P, (p+1)/P) x [q/P, (q+1)/P) and its centroid
+    is H = ((p + 1/2)/P, (q + 1/2)/P), x = H1 h1 + H2 h2.
+  * lam, mu are the Lame constants and rho the density of each phase.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Cell", "square", "hexagonal", "homogeneous_cell", "circle_cell",
+    "bilayer_cell", "voronoi_cell", "ellipse_cell", "steel_epoxy_hex_cell",
+    "ibz_path", "config0", "config1", "config3_cell", "CONFIGS",
+]
+
+
+@dataclass
+class Cell:
+    """A pixelated multi-phase 2-D unit cell."""
+
+    h1: np.ndarray            # (2,) first unit-cell vector, Cartesian
+    h2: np.ndarray            # (2,) second unit-cell vector
+    phase: np.ndarray         # (P, P) uint16 phase index per pixel
+    lam: np.ndarray           # (nphase,) Lame lambda per phase
+    mu: np.ndarray            # (nphase,) Lame mu (shear modulus) per phase
+    rho: np.ndarray           # (nphase,) density per phase
+    name: str = "cell"
+    lattice: str = "square"   # "square" or "hex": selects the IBZ path
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def P(self) -> int:
+        return int(self.phase.shape[0])
+
+    @property
+    def nphase(self) -> int:
+        return int(self.lam.shape[0])
+
+    def shifted(self, s1: int, s2: int) -> "Cell":
+        """The same cell translated by whole pixels (circular shift)."""
+        return Cell(self.h1.copy(), self.h2.copy(),
+                    np.roll(self.phase, (s1, s2), axis=(0, 1)).copy(),
+                    self.lam.copy(), self.mu.copy(), self.rho.copy(),
+                    self.name + f"+shift({s1},{s2})", self.lattice, dict(self.meta))
+
+    def with_props(self, lam=None, mu=None, rho=None, h_scale: float = 1.0) -> "Cell":
+        return Cell(self.h1 * h_scale, self.h2 * h_scale, self.phase.copy(),
+                    self.lam.copy() if lam is None else np.asarray(lam, np.float64),
+                    self.mu.copy() if mu is None else np.asarray(mu, np.float64),
+                    self.rho.copy() if rho is None else np.asarray(rho, np.float64),
+                    self.name, self.lattice, dict(self.meta))
+
+
+def square(a: float = 1.0):
+    return np.array([a, 0.0]), np.array([0.0, a])
+
+
+def hexagonal(a: float = 1.0):
+    return np.array([a, 0.0]), np.array([0.5 * a, np.sqrt(3.0) / 2.0 * a])
+
+
+def _centroids(h1, h2, P):
+    """Cartesian centroids (P, P, 2) of the pixels."""
+    f = (np.arange(P) + 0.5) / P
+    H1, H2 = np.meshgrid(f, f, indexing="ij")
+    return H1[..., None] * h1 + H2[..., None] * h2
+
+
+def _min_image_dist2(h1, h2, pts, centre):
+    """Squared Cartesian distance from pts (..., 2) to the nearest periodic
+    image of `centre` (2,), over the 9 neighbouring images."""
+    best = None
+    for i in (-1, 0, 1):
+        for j in (-1, 0, 1):
+            c = centre + i * h1 + j * h2
+            d2 = np.sum((pts - c) ** 2, axis=-1)
+            best = d2 if best is None else np.minimum(best, d2)
+    return best
+
+
+def homogeneous_cell(P=16, lam=4.0, mu=1.5, rho=1.2, lattice="square", a=1.0):
+    h1, h2 = square(a) if lattice == "square" else hexagonal(a)
+    return Cell(h1, h2, np.zeros((P, P), np.uint16), np.array([lam], float),
+                np.array([mu], float), np.array([rho], float), "homogeneous", lattice)
+
+
+def circle_cell(P=32, r=0.3, matrix=(4.0, 1.5, 1.2), inclusion=(110.0, 80.0, 7.8),
+                lattice="square", a=1.0, name="circle"):
+    """One circular inclusion of radius r*a centred in the cell; a pixel is
+    in the inclusion iff its centroid lies within r*a of the cell centre
+    (fractional (1/2, 1/2))."""
+    h1, h2 = square(a) if lattice == "square" else hexagonal(a)
+    x = _centroids(h1, h2, P)
+    centre = 0.5 * h1 + 0.5 * h2
+    inside = _min_image_dist2(h1, h2, x, centre) <= (r * a) ** 2
+    phase = inside.astype(np.uint16)
+    lam, mu, rho = (np.array([matrix[i], inclusion[i]], float) for i in range(3))
+    return Cell(h1, h2, phase, lam, mu, rho, name, lattice)
+
+
+def bilayer_cell(P=64, n1=None, layer1=(4.0, 1.5, 1.2), layer2=(110.0, 80.0, 7.8), a=1.0):
+    """Square cell of two layers normal to x1 (uniform along x2): pixels with
+    p < n1 are phase 0, the rest phase 1.  Layer thicknesses are n1*a/P and
+    (P-n1)*a/P, so the interfaces fall on pixel edges."""
+    if n1 is None:
+        n1 = P // 2
+    h1, h2 = square(a)
+    phase = np.zeros((P, P), np.uint16)
+    phase[n1:, :] = 1
+    lam, mu, rho = (np.array([layer1[i], layer2[i]], float) for i in range(3))
+    return Cell(h1, h2, phase, lam, mu, rho, "bilayer", "square", {"n1": n1})
+
+
+def _draw_props(rng, nphase, lam_rng=(2.0, 120.0), mu_rng=(1.0, 80.0), rho_rng=(1.0, 8.0)):
+    """Per phase, in the order lambda, mu, rho (rows of a (nphase, 3) draw)."""
+    u = rng.random((nphase, 3))
+    lam = lam_rng[0] + (lam_rng[1] - lam_rng[0]) * u[:, 0]
+    mu = mu_rng[0] + (mu_rng[1] - mu_rng[0]) * u[:, 1]
+    rho = rho_rng[0] + (rho_rng[1] - rho_rng[0]) * u[:, 2]
+    return lam, mu, rho
+
+
+def voronoi_cell(P=256, nseeds=1132, seed=1310, lattice="square", a=1.0, name="voronoi"):
+    """Periodic Voronoi tessellation: seeds uniform in the cell (fractional),
+    each pixel takes the index of the nearest seed under the minimum-image
+    Cartesian metric over the 9 neighbouring images."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    h1, h2 = square(a) if lattice == "square" else hexagonal(a)
+    frac = rng.random((nseeds, 2))
+    lam, mu, rho = _draw_props(rng, nseeds)
+    pts = frac[:, :1] * h1 + frac[:, 1:] * h2
+    images = np.concatenate([pts + i * h1 + j * h2 for i in (-1, 0, 1) for j in (-1, 0, 1)])
+    tree = cKDTree(images)
+    x = _centroids(h1, h2, P).reshape(-1, 2)
+    _, idx = tree.query(x)
+    phase = (idx % nseeds).astype(np.uint16).reshape(P, P)
+    return Cell(h1, h2, phase, lam, mu, rho, name, lattice, {"seed": seed, "nseeds": nseeds})
+
+
+def ellipse_cell(P=64, nellipse=3, seed=0, lattice="square", a=1.0, name="ellipses"):
+    """A matrix (phase 0) holding `nellipse` random ellipses; ellipse i is
+    phase i+1 and later ellipses cover earlier ones.  Centres uniform in the
+    cell, semi-axes uniform in [0.05a, 0.25a], orientation uniform."""
+    rng = np.random.default_rng(seed)
+    h1, h2 = square(a) if lattice == "square" else hexagonal(a)
+    x = _centroids(h1, h2, P)
+    phase = np.zeros((P, P), np.uint16)
+    geo = rng.random((nellipse, 5))
+    for i in range(nellipse):
+        c = geo[i, 0] * h1 + geo[i, 1] * h2
+        ax, bx = (0.05 + 0.2 * geo[i, 2]) * a, (0.05 + 0.2 * geo[i, 3]) * a
+        th = np.pi * geo[i, 4]
+        rot = np.array([[np.cos(th), np.sin(th)], [-np.sin(th), np.cos(th)]])
+        inside = np.zeros((P, P), bool)
+        for s in (-1, 0, 1):
+            for t in (-1, 0, 1):
+                d = (x - (c + s * h1 + t * h2)) @ rot.T
+                inside |= (d[..., 0] / ax) ** 2 + (d[..., 1] / bx) ** 2 <= 1.0
+        phase[inside] = i + 1
+    lam, mu, rho = _draw_props(rng, nellipse + 1)
+    return Cell(h1, h2, phase, lam, mu, rho, name, lattice, {"seed": seed})
+
+
+def steel_epoxy_hex_cell(P=64):
+    """Steel cylinders (diameter 4 mm) in epoxy on a hexagonal lattice of
+    constant 6.023 mm, SI units (Sec. "Example: hexagonal unit cell").
+    Plane strain uses mu = C44 and lambda = C11 - 2 C44."""
+    a = 6.023e-3
+    steel = (264e9 - 2 * 81e9, 81e9, 7780.0)
+    epoxy = (7.54e9 - 2 * 1.48e9, 1.48e9, 1142.0)
+    return circle_cell(P, r=2.0e-3 / a, matrix=epoxy, inclusion=steel, lattice="hex",
+                       a=a, name="steel_epoxy_hex")
+
+
+# High-symmetry points in fractional coordinates Q (k = Q1 q1 + Q2 q2).
+_PATHS = {
+    "square": [(0.0, 0.0), (0.5, 0.0), (0.5, 0.5), (0.0, 0.0)],          # G-X-M-G
+    "hex": [(0.0, 0.0), (0.5, 0.0), (2.0 / 3.0, 1.0 / 3.0), (0.0, 0.0)],  # G-M-K-G
+}
+
+
+def ibz_path(lattice: str, nk: int, h1=None, h2=None) -> np.ndarray:
+    """nk fractional wavevectors (nk, 2) uniform in Cartesian arc length
+    along the closed IBZ boundary; the first and last are both Gamma."""
+    if nk < 2:
+        raise ValueError("nk must be >= 2")
+    if h1 is None:
+        h1, h2 = square() if lattice == "square" else hexagonal()
+    A = np.array([h1, h2], float)
+    qmat = 2.0 * np.pi * np.linalg.inv(A)      # column i is q^i
+    corners = np.array(_PATHS[lattice], float)
+    kc = corners @ qmat.T
+    seg = np.linalg.norm(np.diff(kc, axis=0), axis=1)
+    cum = np.concatenate([[0.0], np.cumsum(seg)])
+    out = np.empty((nk, 2))
+    for i in range(nk):
+        s = cum[-1] * i / (nk - 1)
+        j = min(int(np.searchsorted(cum, s, side="right")) - 1, len(seg) - 1)
+        t = 0.0 if seg[j] == 0 else (s - cum[j]) / seg[j]
+        out[i] = corners[j] + min(max(t, 0.0), 1.0) * (corners[j + 1] - corners[j])
+    return out
+
+
+def config0():
+    """32x32 circle r=0.3a, square a=1, M=3, 30 k on G-X-M-G, 8 bands."""
+    cell = circle_cell(32, 0.3)
+    return dict(cell=cell, M=3, Q=ibz_path("square", 30), nbands=8)
+
+
+def config1():
+    """256x256 periodic Voronoi with 1132 phases (seed 1310), square, M=10,
+    90 k on G-X-M-G, 18 bands."""
+    cell = voronoi_cell(256, 1132, 1310)
+    return dict(cell=cell, M=10, Q=ibz_path("square", 90), nbands=18)
+
+
+def config3_cell(i: int, P: int = 64):
+    """Cell i of the ragged batch: seed 6380+i; square or hexagonal lattice
+    with probability 1/2; half ellipse maps, half Voronoi; 2..16 phases;
+    truncation M uniform in {5..8}; 30 k on its lattice's path; 10 bands."""
+    rng = np.random.default_rng(6380 + i)
+    lattice = "square" if rng.random() < 0.5 else "hex"
+    nphase = int(rng.integers(2, 17))
+    M = int(rng.integers(5, 9))
+    sub = int(rng.integers(0, 2**31 - 1))
+    if rng.random() < 0.5:
+        cell = ellipse_cell(P, nphase - 1, sub, lattice, name=f"c3_{i}_ellipses")
+    else:
+        cell = voronoi_cell(P, nphase, sub, lattice, name=f"c3_{i}_voronoi")
+    return dict(cell=cell, M=M, Q=ibz_path(lattice, 30, cell.h1, cell.h2), nbands=10)
+
+
+CONFIGS = {"c0": config0, "c1": config1}
