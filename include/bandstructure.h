@@ -1,0 +1,169 @@
+/*
+ * bandstructure.h - C ABI of the GB300 mixed-variational band-structure
+ * library (libbs.so).
+ *
+ * The library computes phononic band structures of 2-D pixelated
+ * multi-phase unit cells with the mixed-variational (Nemat-Nasser)
+ * formulation of Srivastava, "Fast phononic band-structure calculations
+ * through a GPU accelerated mixed-variational formulation":
+ *
+ *   assembly  : density and compliance form factors of the cell
+ *               (Eqs. (eo), (ep); centroid quadrature of Sec. III),
+ *   per-k     : H(k) of Eq. (eh), the Cholesky factors of the compliance
+ *               Gram matrix Phi and of Omega, and the reduced Hermitian
+ *               matrix C(k) = L_Omega^-1 H Phi^-1 H^* L_Omega^-dagger,
+ *   eigensolve: lowest eigenvalues lambda = omega^2 of
+ *               H Phi^-1 H^* U = lambda Omega U (Eq. (eigenvalueproblem)).
+ *
+ * Conventions shared by every call
+ *   - Every function returns an int status: BS_OK (0) or a negative
+ *     BS_E* code.  No C++ exception crosses this boundary.  After an
+ *     error, bs_last_error() returns a message for the calling thread.
+ *   - Pointers may be host or device pointers unless stated otherwise;
+ *     the library finds out with cudaPointerGetAttributes.  The caller
+ *     keeps ownership of every array it passes in.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that return results into host memory synchronise
+ *     the stream before returning; calls whose outputs are all device
+ *     pointers are asynchronous on `stream`.
+ *   - A bs_cell handle is not thread-safe: one thread (and one stream)
+ *     at a time per handle.  Different handles are independent.
+ *   - Wavevectors are fractional: k = Q1 q^1 + Q2 q^2, with the
+ *     reciprocal vectors q^i of Eq. (1).
+ */
+#ifndef BANDSTRUCTURE_H
+#define BANDSTRUCTURE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BS_OK        0
+#define BS_EINVAL   -1   /* bad argument: mu <= 0, lam + mu <= 0, rho <= 0, NaN,
+                            P < 2M+1, nbands > 2(2M+1)^2, nk < 0, ...          */
+#define BS_ENOTPD   -2   /* a Gram matrix (Phi or Omega block) is not positive
+                            definite: Cholesky failed                          */
+#define BS_ENOCONV  -3   /* an iteration reached its cap; per-k status is set  */
+#define BS_ENOMEM   -4   /* device allocation failed                           */
+#define BS_ECUDA    -5   /* any other CUDA runtime error                       */
+#define BS_ESTATE   -6   /* call out of order (e.g. solve before assemble)     */
+
+/* arithmetic of the eigen path */
+#define BS_PREC_FP64   0  /* every step in float64                             */
+#define BS_PREC_MIXED  1  /* FP32 reduction + FP64 Rayleigh-Ritz refinement    */
+
+/* IBZ boundary paths for bs_bands (fractional corner points) */
+#define BS_PATH_SQUARE_GXMG 0  /* G(0,0) - X(1/2,0) - M(1/2,1/2) - G              */
+#define BS_PATH_HEX_GMKG    1  /* G(0,0) - M(1/2,0) - K(2/3,1/3) - G (h2 at 60 deg) */
+
+typedef struct bs_cell bs_cell;
+
+/*
+ * Description of one unit cell.
+ *   h1, h2  : unit-cell vectors h^1, h^2 in Cartesian coordinates (Sec. II).
+ *   P       : pixels per side; pixel (p, q) covers fractional coordinates
+ *             [p/P,(p+1)/P) x [q/P,(q+1)/P) and its centroid
+ *             ((p+1/2)/P) h^1 + ((q+1/2)/P) h^2 is the quadrature point of
+ *             Sec. III, with weight V/P^2, V = |h^1 x h^2|.
+ *   phase   : P*P uint16 phase indices, p-major (phase[p*P + q]).
+ *   nphase  : number of phases; every phase index must be < nphase.
+ *   lam, mu, rho : per-phase Lame constants and density (isotropic plane
+ *             strain, Sec. IV); need mu > 0, lam + mu > 0, rho > 0.
+ *   M       : plane-wave truncation, alpha, beta in [-M, M]
+ *             (Eq. (approximation2d)); N = (2M+1)^2 waves, eigen dimension
+ *             n = 2N; requires 2M+1 <= P.
+ *   precision : BS_PREC_FP64 or BS_PREC_MIXED.
+ */
+typedef struct bs_cell_desc {
+    double h1[2];
+    double h2[2];
+    int32_t P;
+    const uint16_t* phase;
+    int32_t nphase;
+    const double* lam;
+    const double* mu;
+    const double* rho;
+    int32_t M;
+    int32_t precision;
+} bs_cell_desc;
+
+/*
+ * bs_create_cell - validate a cell description and copy it into
+ * device-owned storage.  Allocates the cell's device workspace.
+ * Errors: BS_EINVAL (any constraint above), BS_ENOMEM, BS_ECUDA.
+ * On success *out owns the cell until bs_destroy_cell.
+ * Synchronous.
+ */
+int bs_create_cell(const bs_cell_desc* desc, bs_cell** out);
+
+/*
+ * bs_assemble - everything that does not depend on k, on `stream`:
+ *   material fields 1/(lam+mu), 1/mu, rho per pixel (Sec. IV, the
+ *   compliance D_jkmn), their form factors ghat(d) = sum_i g_i V_i
+ *   exp(-i G_d . x_i) for d in [-2M, 2M]^2 (Eqs. (eo), (ep) with the
+ *   centroid rule of Sec. III), the plane-wave (Toeplitz) Gram blocks,
+ *   their Cholesky factors, and the six k-monomial coefficient matrices
+ *   of C(k).  Asynchronous; a failed Cholesky is reported by the next
+ *   call that synchronises (bs_solve_k / bs_bands with host output, or
+ *   bs_sync) as BS_ENOTPD.
+ */
+int bs_assemble(bs_cell* cell, void* stream);
+
+/*
+ * bs_solve_k - lowest `nbands` angular frequencies at `nk` wavevectors.
+ *   Q        : nk*2 doubles (Q1, Q2) per wavevector, host or device.
+ *   omega_out: nk*nbands doubles, ascending per k, omega = sqrt(max(lambda,0))
+ *              (Eq. (eigenvalueproblem)); host or device.
+ *   status_out: nk ints (0 = converged) or NULL; host or device.
+ * Requires bs_assemble first (BS_ESTATE otherwise); 1 <= nbands <= 2N.
+ * Asynchronous when every output is a device pointer.
+ */
+int bs_solve_k(bs_cell* cell, const double* Q, int nk, int nbands,
+               double* omega_out, int* status_out, void* stream);
+
+/*
+ * bs_bands - generate `nk` wavevectors uniform in Cartesian arc length
+ * along the closed IBZ boundary `path` (first and last are Gamma), write
+ * them to Q_out (nk*2, host or device, may be NULL) and solve them as
+ * bs_solve_k does.  Requires nk >= 2.
+ */
+int bs_bands(bs_cell* cell, int path, int nk, int nbands,
+             double* Q_out, double* omega_out, void* stream);
+
+/*
+ * bs_form_factors - copy the assembled form factors to `out`
+ * (host or device): 3 fields (1/(lam+mu), 1/mu, rho) x D x D complex
+ * (interleaved re, im), D = 4M+1, index [f][da+2M][db+2M].
+ * Synchronises `stream` when `out` is a host pointer.
+ */
+int bs_form_factors(bs_cell* cell, double* out, void* stream);
+
+/*
+ * bs_reduced_matrix - the reduced Hermitian matrix
+ * C(k) = L^-1 H(k) Phi^-1 H(k)^* L^-dagger (L = Cholesky factor of
+ * Omega) at one wavevector Q (2 doubles), written to `out` as an n x n
+ * complex column-major matrix (interleaved re, im; n = 2N).  Only the
+ * lower triangle is defined.  Host or device pointers.
+ */
+int bs_reduced_matrix(bs_cell* cell, const double* Q, double* out, void* stream);
+
+/* bs_cell_dims - N (plane waves) and n = 2N (eigen dimension). */
+int bs_cell_dims(const bs_cell* cell, int* N, int* n);
+
+/* bs_sync - synchronise `stream` and report any deferred error. */
+int bs_sync(bs_cell* cell, void* stream);
+
+/* bs_destroy_cell - free the cell and its device storage.  NULL is a no-op. */
+int bs_destroy_cell(bs_cell* cell);
+
+/* bs_last_error - message of the last error on the calling thread ("" if none). */
+const char* bs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BANDSTRUCTURE_H */

@@ -1,0 +1,163 @@
+"""Thin Python binding of libbs.so (argument marshalling only).
+
+Each function here has the name of the C entry point it calls and does
+nothing but convert arguments: numpy arrays become host pointers, CUDA
+torch tensors become device pointers, a torch stream becomes a
+cudaStream_t.  All of the computation happens in the library's CUDA
+kernels.  Importing this module fails loudly when the library has not
+been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BS_OK, BS_EINVAL, BS_ENOTPD, BS_ENOCONV, BS_ENOMEM, BS_ECUDA, BS_ESTATE = 0, -1, -2, -3, -4, -5, -6
+BS_PREC_FP64, BS_PREC_MIXED = 0, 1
+BS_PATH_SQUARE_GXMG, BS_PATH_HEX_GMKG = 0, 1
+_NAMES = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOTPD", -3: "BS_ENOCONV", -4: "BS_ENOMEM",
+          -5: "BS_ECUDA", -6: "BS_ESTATE"}
+
+LIB_PATH = _build.LIB
+
+
+class BSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class bs_cell_desc(ctypes.Structure):
+    _fields_ = [("h1", ctypes.c_double * 2), ("h2", ctypes.c_double * 2), ("P", ctypes.c_int32),
+                ("phase", ctypes.c_void_p), ("nphase", ctypes.c_int32),
+                ("lam", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("M", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbs.so is not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+    sig = {
+        "bs_create_cell": [ctypes.POINTER(bs_cell_desc), ctypes.POINTER(vp)],
+        "bs_assemble": [vp, vp],
+        "bs_solve_k": [vp, dp, i32, i32, dp, dp, vp],
+        "bs_bands": [vp, i32, i32, i32, dp, dp, vp],
+        "bs_form_factors": [vp, dp, vp],
+        "bs_reduced_matrix": [vp, dp, dp, vp],
+        "bs_cell_dims": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "bs_sync": [vp, vp],
+        "bs_destroy_cell": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.bs_last_error.argtypes = []
+    lib.bs_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+#: every symbol the C header declares (checked by the tests)
+EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_factors",
+            "bs_reduced_matrix", "bs_cell_dims", "bs_sync", "bs_destroy_cell", "bs_last_error"]
+
+
+def bs_last_error() -> str:
+    return _lib.bs_last_error().decode()
+
+
+def _check(code: int):
+    if code != BS_OK:
+        raise BSError(code, bs_last_error())
+
+
+def _ptr(x, dtype):
+    """Pointer of a contiguous numpy array or torch tensor of `dtype`."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        tdt = {np.float64: torch.float64, np.uint16: torch.uint16, np.int32: torch.int32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous {tdt} tensor")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream      # torch.cuda.Stream
+
+
+def bs_create_cell(h1, h2, phase, lam, mu, rho, M: int, precision: int = BS_PREC_FP64):
+    """Handle of a new cell (see bs_cell_desc in include/bandstructure.h)."""
+    P = int(phase.shape[0])
+    d = bs_cell_desc()
+    d.h1[0], d.h1[1] = float(h1[0]), float(h1[1])
+    d.h2[0], d.h2[1] = float(h2[0]), float(h2[1])
+    d.P, d.M, d.precision = P, int(M), int(precision)
+    d.nphase = int(lam.shape[0])
+    d.phase = _ptr(phase, np.uint16)
+    d.lam, d.mu, d.rho = _ptr(lam, np.float64), _ptr(mu, np.float64), _ptr(rho, np.float64)
+    out = ctypes.c_void_p()
+    _check(_lib.bs_create_cell(ctypes.byref(d), ctypes.byref(out)))
+    return out
+
+
+def bs_assemble(cell, stream=None):
+    _check(_lib.bs_assemble(cell, _stream(stream)))
+
+
+def bs_solve_k(cell, Q, nbands: int, omega_out, status_out=None, stream=None):
+    nk = int(Q.shape[0])
+    _check(_lib.bs_solve_k(cell, _ptr(Q, np.float64), nk, int(nbands),
+                           _ptr(omega_out, np.float64), _ptr(status_out, np.int32),
+                           _stream(stream)))
+    return omega_out
+
+
+def bs_bands(cell, path: int, nk: int, nbands: int, Q_out, omega_out, stream=None):
+    _check(_lib.bs_bands(cell, int(path), int(nk), int(nbands), _ptr(Q_out, np.float64),
+                         _ptr(omega_out, np.float64), _stream(stream)))
+    return Q_out, omega_out
+
+
+def bs_form_factors(cell, out, stream=None):
+    _check(_lib.bs_form_factors(cell, _ptr(out, np.float64), _stream(stream)))
+    return out
+
+
+def bs_reduced_matrix(cell, Q, out, stream=None):
+    _check(_lib.bs_reduced_matrix(cell, _ptr(Q, np.float64), _ptr(out, np.float64),
+                                  _stream(stream)))
+    return out
+
+
+def bs_cell_dims(cell):
+    N, n = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.bs_cell_dims(cell, ctypes.byref(N), ctypes.byref(n)))
+    return N.value, n.value
+
+
+def bs_sync(cell, stream=None):
+    _check(_lib.bs_sync(cell, _stream(stream)))
+
+
+def bs_destroy_cell(cell):
+    _check(_lib.bs_destroy_cell(cell))

@@ -1,0 +1,446 @@
+// C ABI of libbs: validation, device storage of a cell and the host-side
+// orchestration of the assembly, per-k build and eigensolve kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bs_internal.h"
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+void bs_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int bs_cuda_status(cudaError_t e, const char* where) {
+  bs_set_error("%s: %s", where, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? BS_ENOMEM : BS_ECUDA;
+}
+
+#define CK(call, where)                                    \
+  do {                                                     \
+    cudaError_t e__ = (call);                              \
+    if (e__ != cudaSuccess) return bs_cuda_status(e__, where); \
+  } while (0)
+
+#define TRY(expr)          \
+  do {                     \
+    int r__ = (expr);      \
+    if (r__) return r__;   \
+  } while (0)
+
+extern "C" const char* bs_last_error(void) { return g_err; }
+
+// ------------------------------------------------------------------ helpers
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return BS_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    bs_set_error("cudaMalloc(%s, %zu bytes) failed: %s", what, count * sizeof(T),
+                 cudaGetErrorString(e));
+    return BS_ENOMEM;
+  }
+  return BS_OK;
+}
+
+// copy `bytes` from a host or device pointer into host memory
+static int fetch_to_host(void* dst, const void* src, size_t bytes) {
+  if (is_device_ptr(src)) {
+    CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost), "fetch");
+  } else {
+    memcpy(dst, src, bytes);
+  }
+  return BS_OK;
+}
+
+static int copy_in(void* ddst, const void* src, size_t bytes, cudaStream_t s) {
+  CK(cudaMemcpyAsync(ddst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice
+                                                           : cudaMemcpyHostToDevice, s),
+     "copy in");
+  return BS_OK;
+}
+
+static void free_workspace(bs_cell* c) {
+  cudaFree(c->d_C);
+  cudaFree(c->d_vec);
+  cudaFree(c->d_part);
+  cudaFree(c->d_de);
+  cudaFree(c->d_tau);
+  cudaFree(c->d_count);
+  cudaFree(c->d_Q);
+  cudaFree(c->d_w);
+  cudaFree(c->d_stat);
+  c->d_C = nullptr;
+  c->d_vec = c->d_part = nullptr;
+  c->d_de = c->d_tau = c->d_Q = c->d_w = nullptr;
+  c->d_count = nullptr;
+  c->d_stat = nullptr;
+  c->kcap = 0;
+  c->wcap = 0;
+}
+
+// per-k workspace for `kb` matrices and `nb` bands
+static int ensure_workspace(bs_cell* c, int kb, int nb) {
+  if (kb <= c->kcap && nb <= c->wcap) return BS_OK;
+  kb = std::max(kb, c->kcap);
+  nb = std::max(nb, c->wcap);
+  free_workspace(c);
+  const int n = c->n;
+  TRY(dalloc(&c->d_C, (size_t)kb * n * n, "C(k)"));
+  TRY(dalloc(&c->d_vec, (size_t)kb * bs_tridiag_vec_elems(n), "tridiag vectors"));
+  TRY(dalloc(&c->d_part, (size_t)kb * bs_tridiag_part_elems(n), "tridiag partials"));
+  TRY(dalloc(&c->d_de, (size_t)kb * 2 * n, "tridiagonal"));
+  TRY(dalloc(&c->d_tau, (size_t)kb, "tau"));
+  TRY(dalloc(&c->d_count, (size_t)kb, "counters"));
+  TRY(dalloc(&c->d_Q, (size_t)kb * 2, "Q"));
+  TRY(dalloc(&c->d_w, (size_t)kb * nb, "omega"));
+  TRY(dalloc(&c->d_stat, (size_t)kb, "status"));
+  c->kcap = kb;
+  c->wcap = nb;
+  return BS_OK;
+}
+
+// largest k batch whose C(k) workspace stays under ~4 GiB
+static int k_batch_cap(const bs_cell* c) {
+  const size_t per = (size_t)c->n * c->n * sizeof(zd);
+  size_t cap = ((size_t)4 << 30) / per;
+  return (int)std::max<size_t>(1, std::min<size_t>(cap, 4096));
+}
+
+// ------------------------------------------------------------------ create
+extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
+  if (!d || !out) {
+    bs_set_error("bs_create_cell: NULL argument");
+    return BS_EINVAL;
+  }
+  *out = nullptr;
+  const int P = d->P, M = d->M, np = d->nphase;
+  if (P < 1 || P > 4096 || M < 0 || M > 16 || 2 * M + 1 > P || np < 1 || np > 65536 ||
+      !d->phase || !d->lam || !d->mu || !d->rho) {
+    bs_set_error("bs_create_cell: need 1 <= P <= 4096, 0 <= M <= 16, 2M+1 <= P, 1 <= nphase "
+                 "<= 65536 and non-NULL arrays (P=%d M=%d nphase=%d)", P, M, np);
+    return BS_EINVAL;
+  }
+  if (d->precision != BS_PREC_FP64 && d->precision != BS_PREC_MIXED) {
+    bs_set_error("bs_create_cell: unknown precision %d", d->precision);
+    return BS_EINVAL;
+  }
+  const double det = d->h1[0] * d->h2[1] - d->h1[1] * d->h2[0];
+  if (!(fabs(det) > 0.0) || !isfinite(det)) {
+    bs_set_error("bs_create_cell: h1, h2 are not a basis");
+    return BS_EINVAL;
+  }
+  std::vector<double> raw(3 * (size_t)np);
+  TRY(fetch_to_host(raw.data(), d->lam, np * sizeof(double)));
+  TRY(fetch_to_host(raw.data() + np, d->mu, np * sizeof(double)));
+  TRY(fetch_to_host(raw.data() + 2 * np, d->rho, np * sizeof(double)));
+  for (int i = 0; i < np; ++i) {
+    const double lam = raw[i], mu = raw[np + i], rho = raw[2 * np + i];
+    if (!isfinite(lam) || !isfinite(mu) || !isfinite(rho) || !(mu > 0.0) || !(lam + mu > 0.0) ||
+        !(rho > 0.0)) {
+      bs_set_error("bs_create_cell: phase %d has lam=%g mu=%g rho=%g (need mu > 0, "
+                   "lam + mu > 0, rho > 0, finite)", i, lam, mu, rho);
+      return BS_EINVAL;
+    }
+  }
+  std::vector<uint16_t> ph((size_t)P * P);
+  TRY(fetch_to_host(ph.data(), d->phase, ph.size() * sizeof(uint16_t)));
+  for (size_t i = 0; i < ph.size(); ++i)
+    if (ph[i] >= np) {
+      bs_set_error("bs_create_cell: pixel %zu has phase %u >= nphase %d", i, ph[i], np);
+      return BS_EINVAL;
+    }
+
+  bs_cell* c = new bs_cell;
+  memset(c, 0, sizeof(*c));
+  c->P = P;
+  c->M = M;
+  c->N = (2 * M + 1) * (2 * M + 1);
+  c->n = 2 * c->N;
+  c->D = 4 * M + 1;
+  c->nphase = np;
+  c->precision = d->precision;
+  for (int i = 0; i < 2; ++i) {
+    c->h1[i] = d->h1[i];
+    c->h2[i] = d->h2[i];
+  }
+  c->V = fabs(det);
+  // reciprocal basis of Eq. (1) in 2-D: q^1 = 2 pi (h2y, -h2x)/det, q^2 = 2 pi (-h1y, h1x)/det
+  c->q1[0] = 2.0 * M_PI * d->h2[1] / det;
+  c->q1[1] = -2.0 * M_PI * d->h2[0] / det;
+  c->q2[0] = -2.0 * M_PI * d->h1[1] / det;
+  c->q2[1] = 2.0 * M_PI * d->h1[0] / det;
+
+  const size_t NN = (size_t)c->N * c->N, nn = (size_t)c->n * c->n;
+  int r = BS_OK;
+  if (!r) r = dalloc(&c->d_phase, (size_t)P * P, "phase");
+  if (!r) r = dalloc(&c->d_table, 6 * (size_t)np, "table");
+  if (!r) r = dalloc(&c->d_E, (size_t)c->D * P, "E");
+  if (!r) r = dalloc(&c->d_Y, 3 * (size_t)P * c->D, "Y");
+  if (!r) r = dalloc(&c->d_ghat, 3 * (size_t)c->D * c->D, "ghat");
+  if (!r) r = dalloc(&c->d_T, 3 * NN, "T");
+  if (!r) r = dalloc(&c->d_Linv, 3 * NN, "Linv");
+  if (!r) r = dalloc(&c->d_G, 2 * (size_t)c->N, "G");
+  if (!r) r = dalloc(&c->d_F, 6 * NN, "F");
+  if (!r) r = dalloc(&c->d_Pp, 12 * NN, "P");
+  if (!r) r = dalloc(&c->d_Cm, 6 * nn, "Cm");
+  if (!r) r = dalloc(&c->d_info, 4, "info");
+  if (r) {
+    bs_destroy_cell(c);
+    return r;
+  }
+  std::vector<double> G(2 * (size_t)c->N);
+  for (int a = 0; a < c->N; ++a) {
+    const int al = a / (2 * M + 1) - M, be = a % (2 * M + 1) - M;
+    G[a] = al * c->q1[0] + be * c->q2[0];
+    G[c->N + a] = al * c->q1[1] + be * c->q2[1];
+  }
+  cudaError_t e = cudaMemcpy(c->d_phase, ph.data(), ph.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_table + 3 * np, raw.data(), raw.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_G, G.data(), G.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_info, 0, 4 * sizeof(int));
+  if (e != cudaSuccess) {
+    r = bs_cuda_status(e, "bs_create_cell upload");
+    bs_destroy_cell(c);
+    return r;
+  }
+  *out = c;
+  return BS_OK;
+}
+
+extern "C" int bs_destroy_cell(bs_cell* c) {
+  if (!c) return BS_OK;
+  free_workspace(c);
+  cudaFree(c->d_phase);
+  cudaFree(c->d_table);
+  cudaFree(c->d_E);
+  cudaFree(c->d_Y);
+  cudaFree(c->d_ghat);
+  cudaFree(c->d_T);
+  cudaFree(c->d_Linv);
+  cudaFree(c->d_G);
+  cudaFree(c->d_F);
+  cudaFree(c->d_Pp);
+  cudaFree(c->d_Cm);
+  cudaFree(c->d_info);
+  delete c;
+  return BS_OK;
+}
+
+extern "C" int bs_cell_dims(const bs_cell* c, int* N, int* n) {
+  if (!c) {
+    bs_set_error("bs_cell_dims: NULL cell");
+    return BS_EINVAL;
+  }
+  if (N) *N = c->N;
+  if (n) *n = c->n;
+  return BS_OK;
+}
+
+// ------------------------------------------------------------------ assemble
+extern "C" int bs_assemble(bs_cell* c, void* stream) {
+  if (!c) {
+    bs_set_error("bs_assemble: NULL cell");
+    return BS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t NN = (size_t)c->N * c->N;
+  CK(cudaMemsetAsync(c->d_info, 0, sizeof(int), s), "bs_assemble");
+  TRY(bs_launch_assembly(c, s));                                   // a1 + a2
+  TRY(bs_launch_toeplitz(c, s));                                   // a3 expansion
+  TRY(bs_launch_cholesky(c->d_T, c->N, 3, (long)NN, c->d_info, s)); // a3 factors
+  TRY(bs_launch_trinv(c->d_T, c->d_Linv, c->N, 3, (long)NN, s));
+  TRY(bs_launch_monomials(c, s));                                  // a3/a4 coefficients
+  c->assembled = true;
+  return BS_OK;
+}
+
+static int check_info(bs_cell* c, cudaStream_t s) {
+  int info = 0;
+  CK(cudaMemcpyAsync(&info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, s), "info");
+  CK(cudaStreamSynchronize(s), "sync");
+  if (info) {
+    bs_set_error("Cholesky of a Gram matrix failed (not positive definite)");
+    return BS_ENOTPD;
+  }
+  return BS_OK;
+}
+
+extern "C" int bs_sync(bs_cell* c, void* stream) {
+  if (!c) {
+    bs_set_error("bs_sync: NULL cell");
+    return BS_EINVAL;
+  }
+  return check_info(c, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ solve
+// Solve a chunk of kb wavevectors already in c->d_Q; results in c->d_w / d_stat.
+static int solve_chunk(bs_cell* c, int kb, int nbands, cudaStream_t s) {
+  TRY(bs_launch_builder(c->d_Cm, c->n, c->d_Q, kb, c->q1[0], c->q1[1], c->q2[0], c->q2[1], c->d_C,
+                        s));
+  TRY(bs_launch_tridiag(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau, c->d_count, s));
+  TRY(bs_launch_bisect(c->d_de, c->n, kb, nbands, c->d_w, c->d_stat, s));
+  return BS_OK;
+}
+
+extern "C" int bs_solve_k(bs_cell* c, const double* Q, int nk, int nbands, double* omega_out,
+                          int* status_out, void* stream) {
+  if (!c || !Q || !omega_out || nk < 0) {
+    bs_set_error("bs_solve_k: NULL argument or nk < 0");
+    return BS_EINVAL;
+  }
+  if (!c->assembled) {
+    bs_set_error("bs_solve_k: call bs_assemble first");
+    return BS_ESTATE;
+  }
+  if (nbands < 1 || nbands > c->n) {
+    bs_set_error("bs_solve_k: nbands=%d outside [1, %d]", nbands, c->n);
+    return BS_EINVAL;
+  }
+  if (nk == 0) return BS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool q_dev = is_device_ptr(Q), w_dev = is_device_ptr(omega_out);
+  const bool st_dev = status_out && is_device_ptr(status_out);
+  const int cap = k_batch_cap(c);
+  TRY(ensure_workspace(c, std::min(nk, cap), nbands));
+  for (int k0 = 0; k0 < nk; k0 += cap) {
+    const int kb = std::min(cap, nk - k0);
+    CK(cudaMemcpyAsync(c->d_Q, Q + 2 * (size_t)k0, 2 * kb * sizeof(double),
+                       q_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+       "bs_solve_k Q");
+    TRY(solve_chunk(c, kb, nbands, s));
+    CK(cudaMemcpyAsync(omega_out + (size_t)k0 * nbands, c->d_w, (size_t)kb * nbands * sizeof(double),
+                       w_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+       "bs_solve_k omega");
+    if (status_out)
+      CK(cudaMemcpyAsync(status_out + k0, c->d_stat, kb * sizeof(int),
+                         st_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+         "bs_solve_k status");
+  }
+  if (!w_dev || (status_out && !st_dev)) {
+    TRY(check_info(c, s));
+    if (status_out && !st_dev)
+      for (int k = 0; k < nk; ++k)
+        if (status_out[k]) {
+          bs_set_error("bs_solve_k: wavevector %d did not converge", k);
+          return BS_ENOCONV;
+        }
+  }
+  return BS_OK;
+}
+
+// IBZ boundary path, uniform in Cartesian arc length
+static int make_path(const bs_cell* c, int path, int nk, std::vector<double>& Q) {
+  static const double sq[4][2] = {{0, 0}, {0.5, 0}, {0.5, 0.5}, {0, 0}};
+  static const double hx[4][2] = {{0, 0}, {0.5, 0}, {2.0 / 3.0, 1.0 / 3.0}, {0, 0}};
+  const double(*pc)[2];
+  if (path == BS_PATH_SQUARE_GXMG) pc = sq;
+  else if (path == BS_PATH_HEX_GMKG) pc = hx;
+  else {
+    bs_set_error("bs_bands: unknown path %d", path);
+    return BS_EINVAL;
+  }
+  double seg[3], cum[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 3; ++i) {
+    const double dq1 = pc[i + 1][0] - pc[i][0], dq2 = pc[i + 1][1] - pc[i][1];
+    const double kx = dq1 * c->q1[0] + dq2 * c->q2[0], ky = dq1 * c->q1[1] + dq2 * c->q2[1];
+    seg[i] = sqrt(kx * kx + ky * ky);
+    cum[i + 1] = cum[i] + seg[i];
+  }
+  Q.resize(2 * (size_t)nk);
+  for (int i = 0; i < nk; ++i) {
+    const double sarc = cum[3] * i / (nk - 1);
+    int j = 0;
+    while (j < 2 && sarc >= cum[j + 1]) ++j;
+    double t = seg[j] == 0 ? 0.0 : (sarc - cum[j]) / seg[j];
+    t = std::min(std::max(t, 0.0), 1.0);
+    Q[2 * i] = pc[j][0] + t * (pc[j + 1][0] - pc[j][0]);
+    Q[2 * i + 1] = pc[j][1] + t * (pc[j + 1][1] - pc[j][1]);
+  }
+  return BS_OK;
+}
+
+extern "C" int bs_bands(bs_cell* c, int path, int nk, int nbands, double* Q_out,
+                        double* omega_out, void* stream) {
+  if (!c || !omega_out || nk < 2) {
+    bs_set_error("bs_bands: NULL argument or nk < 2");
+    return BS_EINVAL;
+  }
+  std::vector<double> Q;
+  TRY(make_path(c, path, nk, Q));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (Q_out) {
+    CK(cudaMemcpyAsync(Q_out, Q.data(), Q.size() * sizeof(double),
+                       is_device_ptr(Q_out) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s),
+       "bs_bands Q_out");
+  }
+  int r = bs_solve_k(c, Q.data(), nk, nbands, omega_out, nullptr, stream);
+  if (r) return r;
+  CK(cudaStreamSynchronize(s), "bs_bands sync");   // Q lives on this host stack
+  return BS_OK;
+}
+
+// ------------------------------------------------------------------ diagnostics
+extern "C" int bs_form_factors(bs_cell* c, double* out, void* stream) {
+  if (!c || !out) {
+    bs_set_error("bs_form_factors: NULL argument");
+    return BS_EINVAL;
+  }
+  if (!c->assembled) {
+    bs_set_error("bs_form_factors: call bs_assemble first");
+    return BS_ESTATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool dev = is_device_ptr(out);
+  CK(cudaMemcpyAsync(out, c->d_ghat, 3 * (size_t)c->D * c->D * sizeof(zd),
+                     dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+     "bs_form_factors");
+  if (!dev) CK(cudaStreamSynchronize(s), "bs_form_factors sync");
+  return BS_OK;
+}
+
+extern "C" int bs_reduced_matrix(bs_cell* c, const double* Q, double* out, void* stream) {
+  if (!c || !Q || !out) {
+    bs_set_error("bs_reduced_matrix: NULL argument");
+    return BS_EINVAL;
+  }
+  if (!c->assembled) {
+    bs_set_error("bs_reduced_matrix: call bs_assemble first");
+    return BS_ESTATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_workspace(c, 1, 1));
+  TRY(copy_in(c->d_Q, Q, 2 * sizeof(double), s));
+  TRY(bs_launch_builder(c->d_Cm, c->n, c->d_Q, 1, c->q1[0], c->q1[1], c->q2[0], c->q2[1], c->d_C, s));
+  const bool dev = is_device_ptr(out);
+  CK(cudaMemcpyAsync(out, c->d_C, (size_t)c->n * c->n * sizeof(zd),
+                     dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+     "bs_reduced_matrix");
+  if (!dev) TRY(check_info(c, s));
+  return BS_OK;
+}

@@ -1,0 +1,397 @@
+// Dense FP64 complex linear algebra of the k-independent part of the
+// method: Cholesky factors of the Gram matrices Phi (isotropic blocks
+// T[1/(lam+mu)], T[1/mu]) and Omega (T[rho]) (Eqs. (ep), (eo)), their
+// triangular inverses, and the six k-monomial coefficient matrices of the
+// reduced matrix C(k) = L^-1 H(k) Phi^-1 H(k)^* L^-dagger.
+//
+// With the rotated stress basis (s11 +- s22)/sqrt2, s12 the isotropic Phi
+// is block diagonal, diag(T_k/2, T_m/2, T_m) (T_k = T[1/(lam+mu)],
+// T_m = T[1/mu]), and H of Eq. (eh) is diagonal per plane wave with
+// entries i V K_a, K_a = k + G_a.  Writing T_X^-1 = Z_X Z_X^dagger
+// (Z_X = L_X^-dagger) and W_{X,i}(k) = L_R^-1 diag(K_i) Z_X = k_i F_X^0 + F_X^i
+// with F_X^0 = L_R^-1 Z_X and F_X^i = L_R^-1 diag(G_i) Z_X, the blocks of C are
+//   C11 = V^2 (W_k1 W_k1^+ + W_m1 W_m1^+ + W_m2 W_m2^+)
+//   C22 = V^2 (W_k2 W_k2^+ + W_m2 W_m2^+ + W_m1 W_m1^+)
+//   C12 = V^2 (W_k1 W_k2^+ - W_m1 W_m2^+ + W_m2 W_m1^+)
+// so C(k) is a quadratic polynomial in the Cartesian k whose six matrix
+// coefficients are sums of the products P_X^{ab} = F_X^a F_X^b^dagger.
+#include <math.h>
+
+#include "bs_internal.h"
+
+namespace {
+
+constexpr int NB = 32;   // block size of the blocked factorisations
+
+// ---------------------------------------------------------------- Cholesky
+// Factor the diagonal block of panel j0 in shared memory (every CTA of the
+// panel does it); the CTA with blockIdx.x == 0 stores it, the others solve
+// their block row X := A_ij L_jj^-dagger.
+__global__ void chol_panel_kernel(zd* __restrict__ A, int n, long stride, int j0,
+                                  int* __restrict__ info) {
+  __shared__ zd L[NB][NB + 1];
+  __shared__ zd X[NB][NB + 1];
+  zd* a = A + (size_t)blockIdx.y * stride;
+  const int tid = threadIdx.x;
+  const int jb = min(NB, n - j0);
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int r = e % NB, c = e / NB;
+    L[r][c] = (r < jb && c < jb && r >= c) ? a[(size_t)(j0 + r) + (size_t)(j0 + c) * n]
+                                           : zmake(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int c = 0; c < jb; ++c) {
+    if (tid == 0) {
+      double piv = L[c][c].x;
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        if (blockIdx.x == 0) atomicOr(info, 1);
+        piv = 1.0;
+      }
+      L[c][c] = zmake(sqrt(piv), 0.0);
+    }
+    __syncthreads();
+    const double inv = 1.0 / L[c][c].x;
+    for (int r = c + 1 + tid; r < jb; r += blockDim.x) L[r][c] = zscale(L[r][c], inv);
+    __syncthreads();
+    const int m = jb - c - 1;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      int r = c + 1 + e % m, s = c + 1 + e / m;
+      if (r >= s) L[r][s] = zfnmac(L[r][c], L[s][c], L[r][s]);
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      int r = e % NB, c = e / NB;
+      if (r < jb && c < jb && r >= c) a[(size_t)(j0 + r) + (size_t)(j0 + c) * n] = L[r][c];
+    }
+    return;
+  }
+  const int i0 = j0 + NB * blockIdx.x;
+  if (i0 >= n) return;
+  const int ib = min(NB, n - i0);
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int r = e % NB, c = e / NB;
+    X[r][c] = (r < ib && c < jb) ? a[(size_t)(i0 + r) + (size_t)(j0 + c) * n] : zmake(0.0, 0.0);
+  }
+  __syncthreads();
+  // X L^dagger = A_ij: column c of X from columns t < c
+  if (tid < ib) {
+    const int r = tid;
+    for (int c = 0; c < jb; ++c) {
+      zd x = X[r][c];
+      for (int t = 0; t < c; ++t) x = zfnmac(X[r][t], L[c][t], x);
+      X[r][c] = zscale(x, 1.0 / L[c][c].x);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int r = e % NB, c = e / NB;
+    if (r < ib && c < jb) a[(size_t)(i0 + r) + (size_t)(j0 + c) * n] = X[r][c];
+  }
+}
+
+__device__ __forceinline__ void tri_index(int l, int& bi, int& bk) {
+  int r = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+  while ((r + 1) * (r + 2) / 2 <= l) ++r;
+  while (r * (r + 1) / 2 > l) --r;
+  bi = r;
+  bk = l - r * (r + 1) / 2;
+}
+
+// Trailing update A_ik -= L_ij L_kj^dagger for block rows i >= k > j.
+__global__ void chol_update_kernel(zd* __restrict__ A, int n, long stride, int j0) {
+  __shared__ zd Li[NB][NB + 1];
+  __shared__ zd Lk[NB][NB + 1];
+  zd* a = A + (size_t)blockIdx.y * stride;
+  int bi, bk;
+  tri_index(blockIdx.x, bi, bk);
+  const int t0 = j0 / NB + 1;
+  const int i0 = (t0 + bi) * NB, k0 = (t0 + bk) * NB;
+  const int jb = min(NB, n - j0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int r = e % NB, c = e / NB;
+    bool ok = c < jb;
+    Li[r][c] = (ok && i0 + r < n) ? a[(size_t)(i0 + r) + (size_t)(j0 + c) * n] : zmake(0.0, 0.0);
+    Lk[r][c] = (ok && k0 + r < n) ? a[(size_t)(k0 + r) + (size_t)(j0 + c) * n] : zmake(0.0, 0.0);
+  }
+  __syncthreads();
+  const int r = tid % NB;
+  for (int cc = tid / NB; cc < NB; cc += blockDim.x / NB) {
+    zd acc = zmake(0.0, 0.0);
+    for (int t = 0; t < jb; ++t) acc = zfmac(Li[r][t], Lk[cc][t], acc);
+    if (i0 + r < n && k0 + cc < n) {
+      size_t o = (size_t)(i0 + r) + (size_t)(k0 + cc) * n;
+      a[o] = zsub(a[o], acc);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- inverse
+// X_ii = L_ii^-1 for every diagonal block; zero X above the diagonal blocks.
+__global__ void trinv_diag_kernel(const zd* __restrict__ Lg, zd* __restrict__ Xg, int n,
+                                  long stride) {
+  __shared__ zd L[NB][NB + 1];
+  __shared__ zd X[NB][NB + 1];
+  const zd* l = Lg + (size_t)blockIdx.y * stride;
+  zd* x = Xg + (size_t)blockIdx.y * stride;
+  const int i0 = blockIdx.x * NB, ib = min(NB, n - i0), tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int r = e % NB, c = e / NB;
+    L[r][c] = (r < ib && c < ib && r >= c) ? l[(size_t)(i0 + r) + (size_t)(i0 + c) * n]
+                                           : zmake(0.0, 0.0);
+  }
+  __syncthreads();
+  if (tid < ib) {
+    const int c = tid;
+    for (int r = 0; r < ib; ++r) {
+      if (r < c) {
+        X[r][c] = zmake(0.0, 0.0);
+        continue;
+      }
+      zd s = zmake(r == c ? 1.0 : 0.0, 0.0);
+      for (int t = c; t < r; ++t) s = zsub(s, zmul(L[r][t], X[t][c]));
+      X[r][c] = zscale(s, 1.0 / L[r][r].x);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int r = e % NB, c = e / NB;
+    if (r < ib && c < ib) x[(size_t)(i0 + r) + (size_t)(i0 + c) * n] = X[r][c];
+  }
+  // zero the part of block row i to the right of the diagonal block
+  const int cols = n - (i0 + ib);
+  for (int e = tid; e < ib * cols; e += blockDim.x) {
+    int r = e % ib, c = i0 + ib + e / ib;
+    x[(size_t)(i0 + r) + (size_t)c * n] = zmake(0.0, 0.0);
+  }
+}
+
+// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj for block diagonal i - j = d.
+__global__ void trinv_off_kernel(const zd* __restrict__ Lg, zd* __restrict__ Xg, int n,
+                                 long stride, int d) {
+  __shared__ zd As[NB][NB + 1];
+  __shared__ zd Bs[NB][NB + 1];
+  const zd* l = Lg + (size_t)blockIdx.y * stride;
+  zd* x = Xg + (size_t)blockIdx.y * stride;
+  const int bi = d + blockIdx.x, bj = blockIdx.x;
+  const int i0 = bi * NB, j0 = bj * NB;
+  const int ib = min(NB, n - i0);
+  const int tid = threadIdx.x, r = tid % NB, c0 = tid / NB, cs = blockDim.x / NB;
+  zd acc[NB / 8];
+#pragma unroll
+  for (int u = 0; u < NB / 8; ++u) acc[u] = zmake(0.0, 0.0);
+  for (int bk = bj; bk < bi; ++bk) {
+    const int k0 = bk * NB;
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      int rr = e % NB, cc = e / NB;
+      As[rr][cc] = (rr < ib) ? l[(size_t)(i0 + rr) + (size_t)(k0 + cc) * n] : zmake(0.0, 0.0);
+      Bs[rr][cc] = (j0 + cc < n) ? x[(size_t)(k0 + rr) + (size_t)(j0 + cc) * n] : zmake(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NB / 8; ++u) {
+      int c = c0 + u * cs;
+      for (int t = 0; t < NB; ++t) acc[u] = zfma(As[r][t], Bs[t][c], acc[u]);
+    }
+  }
+  __syncthreads();
+  // As <- X_ii, Bs <- S
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int rr = e % NB, cc = e / NB;
+    As[rr][cc] = (rr < ib && cc < ib) ? x[(size_t)(i0 + rr) + (size_t)(i0 + cc) * n]
+                                      : zmake(0.0, 0.0);
+  }
+#pragma unroll
+  for (int u = 0; u < NB / 8; ++u) Bs[r][c0 + u * cs] = acc[u];
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < NB / 8; ++u) {
+    int c = c0 + u * cs;
+    zd s = zmake(0.0, 0.0);
+    for (int t = 0; t < NB; ++t) s = zfma(As[r][t], Bs[t][c], s);
+    if (r < ib && j0 + c < n) x[(size_t)(i0 + r) + (size_t)(j0 + c) * n] = zmake(-s.x, -s.y);
+  }
+}
+
+// ---------------------------------------------------------------- GEMM
+// C = alpha * opA(A) * diag(sc) * opB(B), column-major; 32 x 32 tile per CTA.
+template <bool CA, bool CB>
+__global__ void zgemm_kernel(int m, int nn, int k, zd alpha, const zd* __restrict__ A, int lda,
+                             long sA, const zd* __restrict__ B, int ldb, long sB,
+                             const double* __restrict__ sc, long sS, zd* __restrict__ C, int ldc,
+                             long sC, int tri) {
+  constexpr int BM = 32, BN = 32, BK = 16;
+  __shared__ zd As[BK][BM + 1];
+  __shared__ zd Bs[BN][BK + 1];
+  const int b = blockIdx.z;
+  A += (size_t)b * sA;
+  B += (size_t)b * sB;
+  C += (size_t)b * sC;
+  if (sc) sc += (size_t)b * sS;
+  const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
+  const int tid = threadIdx.x, tx = tid % 32, ty = tid / 32;
+  int kend = k;
+  if (tri & 1) kend = min(kend, r0 + BM);
+  if (tri & 2) kend = min(kend, c0 + BN);
+  zd acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = zmake(0.0, 0.0);
+  for (int k0 = 0; k0 < kend; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      int r, kk;
+      if (!CA) { r = e % BM; kk = e / BM; } else { kk = e % BK; r = e / BK; }
+      int gr = r0 + r, gk = k0 + kk;
+      zd v = zmake(0.0, 0.0);
+      if (gr < m && gk < k) v = CA ? zconj(A[(size_t)gk + (size_t)gr * lda]) : A[(size_t)gr + (size_t)gk * lda];
+      As[kk][r] = v;
+    }
+    for (int e = tid; e < BN * BK; e += 256) {
+      int c, kk;
+      if (!CB) { kk = e % BK; c = e / BK; } else { c = e % BN; kk = e / BN; }
+      int gc = c0 + c, gk = k0 + kk;
+      zd v = zmake(0.0, 0.0);
+      if (gc < nn && gk < k) {
+        v = CB ? zconj(B[(size_t)gc + (size_t)gk * ldb]) : B[(size_t)gk + (size_t)gc * ldb];
+        if (sc) v = zscale(v, sc[gk]);
+      }
+      Bs[c][kk] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      zd a = As[kk][tx];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = zfma(a, Bs[ty + 8 * i][kk], acc[i]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gr = r0 + tx, gc = c0 + ty + 8 * i;
+    if (gr < m && gc < nn) C[(size_t)gr + (size_t)gc * ldc] = zmul(alpha, acc[i]);
+  }
+}
+
+// ---------------------------------------------------------------- monomials
+// P_X^{ab} for a <= b is stored at Pp[(X*6 + pidx(a,b)) * N*N]
+__device__ __forceinline__ int pidx(int a, int b) {
+  // (0,0)=0 (0,1)=1 (0,2)=2 (1,1)=3 (1,2)=4 (2,2)=5
+  return a == 0 ? b : (a == 1 ? 2 + b : 5);
+}
+__device__ __forceinline__ zd getP(const zd* __restrict__ Pp, int N, int X, int a, int b, int i,
+                                   int j) {
+  size_t NN = (size_t)N * N;
+  if (a <= b) return Pp[(size_t)(X * 6 + pidx(a, b)) * NN + i + (size_t)j * N];
+  return zconj(Pp[(size_t)(X * 6 + pidx(b, a)) * NN + j + (size_t)i * N]);
+}
+
+__global__ void monomial_kernel(const zd* __restrict__ Pp, int N, double V2, zd* __restrict__ Cm) {
+  const int n = 2 * N;
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * n) return;
+  const int r = (int)(e % n), c = (int)(e / n);
+  if (r < c) return;   // lower triangle only
+  const int I = r / N, J = c / N, i = r % N, j = c % N;
+  const int K = 0, Mu = 1;
+  zd m[6];
+  const zd z = zmake(0.0, 0.0);
+#define PP(X, a, b) getP(Pp, N, X, a, b, i, j)
+  if (I == 0 && J == 0) {
+    m[0] = zadd(zadd(PP(K, 1, 1), PP(Mu, 1, 1)), PP(Mu, 2, 2));
+    m[1] = zadd(zadd(PP(K, 0, 1), PP(K, 1, 0)), zadd(PP(Mu, 0, 1), PP(Mu, 1, 0)));
+    m[2] = zadd(PP(Mu, 0, 2), PP(Mu, 2, 0));
+    m[3] = zadd(PP(K, 0, 0), PP(Mu, 0, 0));
+    m[4] = z;
+    m[5] = PP(Mu, 0, 0);
+  } else if (I == 1 && J == 1) {
+    m[0] = zadd(zadd(PP(K, 2, 2), PP(Mu, 2, 2)), PP(Mu, 1, 1));
+    m[1] = zadd(PP(Mu, 0, 1), PP(Mu, 1, 0));
+    m[2] = zadd(zadd(PP(K, 0, 2), PP(K, 2, 0)), zadd(PP(Mu, 0, 2), PP(Mu, 2, 0)));
+    m[3] = PP(Mu, 0, 0);
+    m[4] = z;
+    m[5] = zadd(PP(K, 0, 0), PP(Mu, 0, 0));
+  } else {   // I == 1, J == 0: C21 = C12^dagger
+    m[0] = zadd(zsub(PP(K, 2, 1), PP(Mu, 2, 1)), PP(Mu, 1, 2));
+    m[1] = zadd(zsub(PP(K, 2, 0), PP(Mu, 2, 0)), PP(Mu, 0, 2));
+    m[2] = zadd(zsub(PP(K, 0, 1), PP(Mu, 0, 1)), PP(Mu, 1, 0));
+    m[3] = z;
+    m[4] = PP(K, 0, 0);
+    m[5] = z;
+  }
+#undef PP
+  const size_t nn = (size_t)n * n;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) Cm[t * nn + e] = zscale(m[t], V2);
+}
+
+}  // namespace
+
+int bs_launch_cholesky(zd* A, int n, int batch, long stride, int* info, cudaStream_t s) {
+  const int nt = (n + NB - 1) / NB;
+  for (int j = 0; j < nt; ++j) {
+    chol_panel_kernel<<<dim3(nt - j, batch), 256, 0, s>>>(A, n, stride, j * NB, info);
+    BS_CHECK_LAUNCH("chol_panel_kernel");
+    const int rem = nt - j - 1;
+    if (rem > 0) {
+      chol_update_kernel<<<dim3(rem * (rem + 1) / 2, batch), 256, 0, s>>>(A, n, stride, j * NB);
+      BS_CHECK_LAUNCH("chol_update_kernel");
+    }
+  }
+  return BS_OK;
+}
+
+int bs_launch_trinv(const zd* L, zd* X, int n, int batch, long stride, cudaStream_t s) {
+  const int nt = (n + NB - 1) / NB;
+  trinv_diag_kernel<<<dim3(nt, batch), 256, 0, s>>>(L, X, n, stride);
+  BS_CHECK_LAUNCH("trinv_diag_kernel");
+  for (int d = 1; d < nt; ++d) {
+    trinv_off_kernel<<<dim3(nt - d, batch), 256, 0, s>>>(L, X, n, stride, d);
+    BS_CHECK_LAUNCH("trinv_off_kernel");
+  }
+  return BS_OK;
+}
+
+int bs_launch_zgemm(bool conjA, bool conjB, int m, int nn, int k, zd alpha, const zd* A, int lda,
+                    long sA, const zd* B, int ldb, long sB, const double* sc, long sS, zd* C,
+                    int ldc, long sC, int batch, int tri, cudaStream_t s) {
+  dim3 grid((m + 31) / 32, (nn + 31) / 32, batch);
+  if (!conjA && !conjB)
+    zgemm_kernel<false, false><<<grid, 256, 0, s>>>(m, nn, k, alpha, A, lda, sA, B, ldb, sB, sc, sS, C, ldc, sC, tri);
+  else if (!conjA && conjB)
+    zgemm_kernel<false, true><<<grid, 256, 0, s>>>(m, nn, k, alpha, A, lda, sA, B, ldb, sB, sc, sS, C, ldc, sC, tri);
+  else if (conjA && !conjB)
+    zgemm_kernel<true, false><<<grid, 256, 0, s>>>(m, nn, k, alpha, A, lda, sA, B, ldb, sB, sc, sS, C, ldc, sC, tri);
+  else
+    zgemm_kernel<true, true><<<grid, 256, 0, s>>>(m, nn, k, alpha, A, lda, sA, B, ldb, sB, sc, sS, C, ldc, sC, tri);
+  BS_CHECK_LAUNCH("zgemm_kernel");
+  return BS_OK;
+}
+
+int bs_launch_monomials(bs_cell* c, cudaStream_t s) {
+  const int N = c->N;
+  const size_t NN = (size_t)N * N;
+  const zd one = zmake(1.0, 0.0);
+  const zd* LinvR = c->d_Linv + 2 * NN;
+  // F_X^a = L_R^-1 diag(s_a) L_X^-dagger for X in {kappa, mu} (batched), a = 0, 1, 2
+  for (int a = 0; a < 3; ++a) {
+    const double* sc = a == 0 ? nullptr : c->d_G + (size_t)(a - 1) * N;
+    int r = bs_launch_zgemm(false, true, N, N, N, one, LinvR, N, 0, c->d_Linv, N, (long)NN, sc, 0,
+                            c->d_F + (size_t)a * NN, N, (long)(3 * NN), 2, 3, s);
+    if (r) return r;
+  }
+  // P_X^{ab} = F_X^a F_X^b^dagger, a <= b
+  const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+  for (int t = 0; t < 6; ++t) {
+    int r = bs_launch_zgemm(false, true, N, N, N, one, c->d_F + (size_t)pa[t] * NN, N, (long)(3 * NN),
+                            c->d_F + (size_t)pb[t] * NN, N, (long)(3 * NN), nullptr, 0,
+                            c->d_Pp + (size_t)t * NN, N, (long)(6 * NN), 2, 0, s);
+    if (r) return r;
+  }
+  const size_t tot = (size_t)c->n * c->n;
+  monomial_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->d_Pp, N, c->V * c->V, c->d_Cm);
+  BS_CHECK_LAUNCH("monomial_kernel");
+  return BS_OK;
+}
