@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""k-point solves per second of the mixed-variational band structure.
+
+One step = the whole hot path over one cell: bs_assemble (material fields,
+form factors, Gram Cholesky factors, k-monomials) and bs_solve_k over the
+workload's wavevectors (per-k builder, Householder tridiagonalisation,
+bisection).  Inputs are resident in HBM when the timed region starts; L2
+is flushed (a 256 MiB write) between timed steps, outside the timed
+events.  Each step is timed with CUDA events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1|c0]
+                  [--impl ours|reference] [--no-cpu-baseline]
+
+For N > 1 (torchrun, one process per GPU) every rank runs an independent
+replica of the workload (the method needs no exchange between GPUs);
+value = all ranks' k-solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Nominal FP64 peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
+# (An FMA-loop probe measured 1.19 TFLOP/s at 2.0 GHz.)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+METRIC = "k-point solves/sec at <=1e-6 rel omega err vs FP64 oracle"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="c1", choices=["c0", "c1"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-k", type=int, default=6)
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1310_6380_gb300 import cells
+    cfg = cells.config1() if name == "c1" else cells.config0()
+    cell = cfg["cell"]
+    N = (2 * cfg["M"] + 1) ** 2
+    desc = {
+        "c1": "256x256 periodic Voronoi, 1132 phases (seed 1310), square a=1",
+        "c0": "32x32 circle r=0.3a, two phases, square a=1",
+    }[name]
+    config = {
+        "workload": f"{name}: {desc}, M={cfg['M']} ({N} plane waves, n={2 * N}), "
+                    f"{len(cfg['Q'])} k on G-X-M-G, lowest {cfg['nbands']} branches, FP64 path",
+        "cells": 1, "k_points": len(cfg["Q"]), "plane_waves": N, "n": 2 * N,
+        "nbands": cfg["nbands"], "precision": "fp64",
+        "l2": "flushed between timed steps (256 MiB write, untimed)",
+    }
+    return cfg, config
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            if self.bus_id and self.bus_id.lower() not in f[1].lower():
+                continue
+            rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        if not self.bus_id:                    # keep the first GPU listed
+            idx0 = rows[0][0]
+            rows = [r for r in rows if r[0] == idx0]
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][3]) if rows[0][3].replace(".", "").isdigit() else None,
+                "power_w_max": max(float(r[4]) for r in rows if r[4].replace(".", "").isdigit())
+                if any(r[4].replace(".", "").isdigit() for r in rows) else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def device_bus_id(torch):
+    try:
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}"
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- helpers
+def traffic_record(kernel):
+    """DRAM bytes per step of `kernel` from the committed ncu summary, if the
+    kernel's source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1310_6380_gb300", "csrc", rec["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["sha256_16"]:
+        return None
+    return rec["dram_bytes_per_step"]
+
+
+def cpu_oracle_sample(cfg, nk_sample):
+    """The FP64 oracle as it stands on this host: cell set-up plus a sample
+    of wavevectors; returns (solves/s extrapolated to the full k list,
+    sampled indices, sampled omegas, description)."""
+    from oracle import mixed_variational as mv
+    Q = cfg["Q"]
+    idx = np.linspace(0, len(Q) - 1, nk_sample).round().astype(int)
+    t0 = time.perf_counter()
+    oc = mv.OracleCell(cfg["cell"], cfg["M"])
+    t1 = time.perf_counter()
+    ws = [oc.omega(Q[i], cfg["nbands"]) for i in idx]
+    t2 = time.perf_counter()
+    per_k = (t2 - t1) / len(idx)
+    total = (t1 - t0) + len(Q) * per_k
+    desc = (f"oracle cell set-up ({t1 - t0:.1f} s) + {len(idx)} of {len(Q)} wavevectors "
+            f"({per_k:.2f} s each); value extrapolated to all {len(Q)}")
+    return len(Q) / total, idx, np.array(ws), desc, t2 - t0
+
+
+def rel_err(w, ref, cell):
+    A = np.array([cell.h1, cell.h2])
+    qm = 2 * np.pi * np.linalg.inv(A)
+    floor = np.sqrt(np.min(cell.mu / cell.rho)) * min(np.linalg.norm(qm[:, 0]),
+                                                       np.linalg.norm(qm[:, 1])) / 2
+    return np.abs(w ** 2 - ref ** 2) / (2 * np.maximum(ref ** 2, floor ** 2))
+
+
+# ---------------------------------------------------------------- arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg, config = workload(args.config)
+    cores = len(os.sched_getaffinity(0))
+    times, vals = [], []
+    for i in range(args.warmup + args.steps):
+        v, _, _, desc, secs = cpu_oracle_sample(cfg, 2)
+        if i >= args.warmup:
+            times.append(secs)
+            vals.append(v)
+    value = statistics.mean(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "k-solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": "k-solves/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step: " + desc},
+        "e2e": {"value": value, "unit": "k-solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1310_6380_gb300 import binding as bs
+
+    cfg, config = workload(args.config)
+    cell, M, nb = cfg["cell"], cfg["M"], cfg["nbands"]
+    Q = np.ascontiguousarray(cfg["Q"])
+    nk = len(Q)
+    n = 2 * (2 * M + 1) ** 2
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    h = bs.bs_create_cell(cell.h1, cell.h2, dev(cell.phase.astype(np.uint16)), dev(cell.lam),
+                          dev(cell.mu), dev(cell.rho), M)
+    bs.bs_set_profiling(h, True)
+    stream = torch.cuda.current_stream()
+    Qd = dev(Q)
+    w = torch.empty((nk, nb), dtype=torch.float64, device="cuda")
+    st = torch.empty(nk, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        bs.bs_assemble(h, stream)
+        bs.bs_solve_k(h, Qd, nb, w, st, stream)
+
+    for _ in range(args.warmup):
+        step()
+    bs.bs_sync(h, stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(device_bus_id(torch))
+    step_ms, phases = [], []
+    barrier()
+    launches0 = bs.bs_launch_count()
+    sampler.start()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        phases.append(bs.bs_phase_times(h))
+    t_wall = time.perf_counter() - t_wall
+    barrier()
+    clocks = sampler.stop()
+    launches = bs.bs_launch_count() - launches0 - 0
+    bs.bs_sync(h, stream)
+    assert not st.cpu().numpy().any(), "a wavevector did not converge"
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nk / (ms / 1e3)
+    omega = w.cpu().numpy()
+
+    # dominant kernel: the Householder tridiagonalisation
+    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+    trid_flops = nk * 16.0 / 3.0 * n ** 3
+    achieved = trid_flops / (ph["tridiag"] / 1e3) / 1e12
+    traffic = traffic_record("tridiag_step_kernel")
+    roofline = {"bound": "alu", "kernel": "tridiag_step_kernel (all launches of one step)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}"}
+
+    # end to end through the public API with host (pinned) buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hp, hl, hm, hr = pin(cell.phase.astype(np.uint16)), pin(cell.lam), pin(cell.mu), pin(cell.rho)
+    hQ = pin(Q)
+    hw = torch.empty((nk, nb), dtype=torch.float64).pin_memory()
+    hs = torch.empty(nk, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        c = bs.bs_create_cell(cell.h1, cell.h2, hp, hl, hm, hr, M)
+        try:
+            bs.bs_assemble(c, stream)
+            bs.bs_solve_k(c, hQ, nb, hw, hs, stream)
+        finally:
+            bs.bs_destroy_cell(c)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = hp.numel() * 2 + 3 * hl.numel() * 8 + hQ.numel() * 8
+    d2h = hw.numel() * 8 + hs.numel() * 4
+    e2e = {"value": world * nk / e2e_s, "unit": "k-solves/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h,
+           "api": "bs_create_cell + bs_assemble + bs_solve_k + bs_destroy_cell, pinned host buffers"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config, "e2e": e2e, "gpu_launches": launches,
+        "gpu_launches_per_step": launches // max(1, args.steps), "roofline": roofline,
+        "phases_ms": {k: round(v, 3) for k, v in ph.items()},
+        "wall_s_timed_region": t_wall, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, idx, ws, desc, _ = cpu_oracle_sample(cfg, args.cpu_sample_k)
+        out["cpu_baseline"] = {"value": v, "unit": "k-solves/s",
+                               "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                               "sample": desc}
+        out["max_rel_err_vs_oracle"] = float(rel_err(omega[idx], ws, cell).max())
+        out["oracle_sampled_k"] = idx.tolist()
+    bs.bs_destroy_cell(h)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -150,8 +150,46 @@ int bs_form_factors(bs_cell* cell, double* out, void* stream);
  */
 int bs_reduced_matrix(bs_cell* cell, const double* Q, double* out, void* stream);
 
+/*
+ * bs_tridiag_eigenvalues - the eigen step on its own: the lowest `nbands`
+ * eigenvalues lambda (ascending) of `batch` real symmetric tridiagonal
+ * matrices, by the same Sturm-sequence multisection that finishes
+ * bs_solve_k (the matrices Householder reduction leaves behind when the
+ * reduced Hermitian matrix of Eq. (eigenvalueproblem) is tridiagonalised).
+ *   d       : batch x n diagonals (row-major), host or device.
+ *   e       : batch x (n-1) off-diagonals (row-major), host or device;
+ *             only |e| matters.  May be NULL when n == 1.
+ *   lam_out : batch x nbands eigenvalues, host or device.
+ * Accuracy: absolute error <= 4 eps max(||T||, |lambda|).  Allocates and
+ * frees its own device scratch; synchronises `stream` before returning.
+ */
+int bs_tridiag_eigenvalues(const double* d, const double* e, int n, int batch, int nbands,
+                           double* lam_out, void* stream);
+
 /* bs_cell_dims - N (plane waves) and n = 2N (eigen dimension). */
 int bs_cell_dims(const bs_cell* cell, int* N, int* n);
+
+/*
+ * bs_set_profiling - when `on` is non-zero, bs_assemble and bs_solve_k
+ * record CUDA events on their stream around each phase; bs_phase_times
+ * then returns the elapsed milliseconds of the most recent call (the last
+ * k batch of a multi-batch solve), synchronising on those events:
+ *   ms[0] assembly (material table, exponential table, two contractions)
+ *   ms[1] Gram blocks (Toeplitz expansion, Cholesky, triangular inverses)
+ *   ms[2] k-monomial coefficient matrices
+ *   ms[3] per-k builder of C(k)
+ *   ms[4] Householder tridiagonalisation
+ *   ms[5] bisection and omega
+ * Phases that did not run in the last call report 0.
+ */
+int bs_set_profiling(bs_cell* cell, int on);
+int bs_phase_times(bs_cell* cell, double ms[6]);
+
+/*
+ * bs_launch_count - number of CUDA kernels this library has launched in
+ * the process so far (all cells, all threads).
+ */
+int bs_launch_count(long long* out);
 
 /* bs_sync - synchronise `stream` and report any deferred error. */
 int bs_sync(bs_cell* cell, void* stream);

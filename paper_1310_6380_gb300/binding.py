@@ -54,6 +54,10 @@ def _load():
         "bs_cell_dims": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "bs_sync": [vp, vp],
         "bs_destroy_cell": [vp],
+        "bs_set_profiling": [vp, i32],
+        "bs_phase_times": [vp, dp],
+        "bs_launch_count": [ctypes.POINTER(ctypes.c_longlong)],
+        "bs_tridiag_eigenvalues": [dp, dp, i32, i32, i32, dp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -68,7 +72,8 @@ _lib = _load()
 
 #: every symbol the C header declares (checked by the tests)
 EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_factors",
-            "bs_reduced_matrix", "bs_cell_dims", "bs_sync", "bs_destroy_cell", "bs_last_error"]
+            "bs_reduced_matrix", "bs_cell_dims", "bs_sync", "bs_destroy_cell", "bs_last_error",
+            "bs_set_profiling", "bs_phase_times", "bs_launch_count", "bs_tridiag_eigenvalues"]
 
 
 def bs_last_error() -> str:
@@ -149,6 +154,14 @@ def bs_reduced_matrix(cell, Q, out, stream=None):
     return out
 
 
+def bs_tridiag_eigenvalues(d, e, nbands: int, lam_out, stream=None):
+    """d: (batch, n), e: (batch, n-1) float64; lam_out: (batch, nbands)."""
+    batch, n = int(d.shape[0]), int(d.shape[1])
+    _check(_lib.bs_tridiag_eigenvalues(_ptr(d, np.float64), _ptr(e, np.float64), n, batch,
+                                       int(nbands), _ptr(lam_out, np.float64), _stream(stream)))
+    return lam_out
+
+
 def bs_cell_dims(cell):
     N, n = ctypes.c_int(), ctypes.c_int()
     _check(_lib.bs_cell_dims(cell, ctypes.byref(N), ctypes.byref(n)))
@@ -157,6 +170,25 @@ def bs_cell_dims(cell):
 
 def bs_sync(cell, stream=None):
     _check(_lib.bs_sync(cell, _stream(stream)))
+
+
+def bs_set_profiling(cell, on: bool):
+    _check(_lib.bs_set_profiling(cell, int(bool(on))))
+
+
+PHASES = ("assembly", "gram", "monomials", "builder", "tridiag", "bisect")
+
+
+def bs_phase_times(cell) -> dict:
+    ms = np.zeros(6)
+    _check(_lib.bs_phase_times(cell, ms.ctypes.data))
+    return dict(zip(PHASES, ms.tolist()))
+
+
+def bs_launch_count() -> int:
+    v = ctypes.c_longlong()
+    _check(_lib.bs_launch_count(ctypes.byref(v)))
+    return v.value
 
 
 def bs_destroy_cell(cell):

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "bs_internal.h"
@@ -38,6 +39,31 @@ int bs_cuda_status(cudaError_t e, const char* where) {
   } while (0)
 
 extern "C" const char* bs_last_error(void) { return g_err; }
+
+// ------------------------------------------------------------------ profiling
+static std::atomic<long long> g_launches{0};
+
+void bs_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" int bs_launch_count(long long* out) {
+  if (!out) {
+    bs_set_error("bs_launch_count: NULL argument");
+    return BS_EINVAL;
+  }
+  *out = g_launches.load();
+  return BS_OK;
+}
+
+void bs_phase_begin(bs_cell* c, int ph, cudaStream_t s) {
+  if (c->prof) cudaEventRecord(c->ev[ph][0], s);
+}
+
+void bs_phase_end(bs_cell* c, int ph, cudaStream_t s) {
+  if (c->prof) {
+    cudaEventRecord(c->ev[ph][1], s);
+    c->prof_ready[ph] = true;
+  }
+}
 
 // ------------------------------------------------------------------ helpers
 static bool is_device_ptr(const void* p) {
@@ -234,6 +260,7 @@ extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
 
 extern "C" int bs_destroy_cell(bs_cell* c) {
   if (!c) return BS_OK;
+  bs_set_profiling(c, 0);
   free_workspace(c);
   cudaFree(c->d_phase);
   cudaFree(c->d_table);
@@ -270,11 +297,18 @@ extern "C" int bs_assemble(bs_cell* c, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const size_t NN = (size_t)c->N * c->N;
   CK(cudaMemsetAsync(c->d_info, 0, sizeof(int), s), "bs_assemble");
+  for (int i = 0; i < 6; ++i) c->prof_ready[i] = false;
+  bs_phase_begin(c, PH_ASM, s);
   TRY(bs_launch_assembly(c, s));                                   // a1 + a2
+  bs_phase_end(c, PH_ASM, s);
+  bs_phase_begin(c, PH_GRAM, s);
   TRY(bs_launch_toeplitz(c, s));                                   // a3 expansion
   TRY(bs_launch_cholesky(c->d_T, c->N, 3, (long)NN, c->d_info, s)); // a3 factors
   TRY(bs_launch_trinv(c->d_T, c->d_Linv, c->N, 3, (long)NN, s));
+  bs_phase_end(c, PH_GRAM, s);
+  bs_phase_begin(c, PH_MONO, s);
   TRY(bs_launch_monomials(c, s));                                  // a3/a4 coefficients
+  bs_phase_end(c, PH_MONO, s);
   c->assembled = true;
   return BS_OK;
 }
@@ -301,10 +335,16 @@ extern "C" int bs_sync(bs_cell* c, void* stream) {
 // ------------------------------------------------------------------ solve
 // Solve a chunk of kb wavevectors already in c->d_Q; results in c->d_w / d_stat.
 static int solve_chunk(bs_cell* c, int kb, int nbands, cudaStream_t s) {
+  bs_phase_begin(c, PH_BUILD, s);
   TRY(bs_launch_builder(c->d_Cm, c->n, c->d_Q, kb, c->q1[0], c->q1[1], c->q2[0], c->q2[1], c->d_C,
                         s));
+  bs_phase_end(c, PH_BUILD, s);
+  bs_phase_begin(c, PH_TRID, s);
   TRY(bs_launch_tridiag(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau, c->d_count, s));
+  bs_phase_end(c, PH_TRID, s);
+  bs_phase_begin(c, PH_BISECT, s);
   TRY(bs_launch_bisect(c->d_de, c->n, kb, nbands, c->d_w, c->d_stat, s));
+  bs_phase_end(c, PH_BISECT, s);
   return BS_OK;
 }
 
@@ -405,7 +445,83 @@ extern "C" int bs_bands(bs_cell* c, int path, int nk, int nbands, double* Q_out,
   return BS_OK;
 }
 
+extern "C" int bs_set_profiling(bs_cell* c, int on) {
+  if (!c) {
+    bs_set_error("bs_set_profiling: NULL cell");
+    return BS_EINVAL;
+  }
+  if (on && !c->prof) {
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 2; ++j) CK(cudaEventCreate(&c->ev[i][j]), "bs_set_profiling");
+  }
+  if (!on && c->prof) {
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 2; ++j) cudaEventDestroy(c->ev[i][j]);
+  }
+  c->prof = on != 0;
+  for (int i = 0; i < 6; ++i) c->prof_ready[i] = false;
+  return BS_OK;
+}
+
+extern "C" int bs_phase_times(bs_cell* c, double ms[6]) {
+  if (!c || !ms) {
+    bs_set_error("bs_phase_times: NULL argument");
+    return BS_EINVAL;
+  }
+  for (int i = 0; i < 6; ++i) {
+    ms[i] = 0.0;
+    if (!c->prof || !c->prof_ready[i]) continue;
+    CK(cudaEventSynchronize(c->ev[i][1]), "bs_phase_times");
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->ev[i][0], c->ev[i][1]), "bs_phase_times");
+    ms[i] = t;
+  }
+  return BS_OK;
+}
+
 // ------------------------------------------------------------------ diagnostics
+extern "C" int bs_tridiag_eigenvalues(const double* d, const double* e, int n, int batch,
+                                      int nbands, double* lam_out, void* stream) {
+  if (!d || (!e && n > 1) || !lam_out || n < 1 || batch < 1 || nbands < 1 || nbands > n ||
+      n > 100000) {
+    bs_set_error("bs_tridiag_eigenvalues: need non-NULL arrays, n >= 1, batch >= 1, "
+                 "1 <= nbands <= n");
+    return BS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* de = nullptr;
+  double* out = nullptr;
+  int* st = nullptr;
+  int r = dalloc(&de, (size_t)batch * 2 * n, "tridiagonals");
+  const bool odev = is_device_ptr(lam_out);
+  if (!r && !odev) r = dalloc(&out, (size_t)batch * nbands, "eigenvalues");
+  if (!r) r = dalloc(&st, (size_t)batch, "status");
+  auto kind = [](const void* p) {
+    return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  };
+  cudaError_t ce = cudaSuccess;
+  if (!r) ce = cudaMemset2DAsync(de + n, 2 * n * sizeof(double), 0, n * sizeof(double), batch, s);
+  if (!r && ce == cudaSuccess)
+    ce = cudaMemcpy2DAsync(de, 2 * n * sizeof(double), d, n * sizeof(double), n * sizeof(double),
+                           batch, kind(d), s);
+  if (!r && ce == cudaSuccess && n > 1)
+    ce = cudaMemcpy2DAsync(de + n, 2 * n * sizeof(double), e, (n - 1) * sizeof(double),
+                           (n - 1) * sizeof(double), batch, kind(e), s);
+  if (!r && ce != cudaSuccess) r = bs_cuda_status(ce, "bs_tridiag_eigenvalues copy");
+  if (!r) r = bs_launch_bisect(de, n, batch, nbands, odev ? lam_out : out, st, s, false);
+  if (!r && !odev) {
+    ce = cudaMemcpyAsync(lam_out, out, (size_t)batch * nbands * sizeof(double),
+                         cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) r = bs_cuda_status(ce, "bs_tridiag_eigenvalues copy out");
+  }
+  if (odev) cudaStreamSynchronize(s);   // the scratch below is freed on return
+  cudaFree(de);
+  cudaFree(out);
+  cudaFree(st);
+  return r;
+}
+
 extern "C" int bs_form_factors(bs_cell* c, double* out, void* stream) {
   if (!c || !out) {
     bs_set_error("bs_form_factors: NULL argument");

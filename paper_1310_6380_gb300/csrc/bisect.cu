@@ -1,11 +1,21 @@
 // Lowest eigenvalues of the real symmetric tridiagonal matrices left by the
-// Householder reduction, by Sturm-sequence bisection (FP64), and the
-// angular frequencies omega = sqrt(max(lambda, 0)) of Eq. (eigenvalueproblem).
+// Householder reduction, by Sturm-sequence multisection, and the angular
+// frequencies omega = sqrt(max(lambda, 0)) of Eq. (eigenvalueproblem).
 //
-// One thread per (matrix, eigenvalue index i): the interval [lo, hi] keeps
-// count(lo) <= i < count(hi), where count(x) is the number of negative
-// pivots of T - x I (Sylvester inertia), until it is as narrow as FP64
-// allows relative to the Gershgorin bound of the matrix.
+// count(x) = number of non-positive pivots of the LDL^T factorisation of
+// T - x I (Sylvester inertia) = number of eigenvalues <= x.  Each eigenvalue
+// index i keeps a bracket lo < lambda_i <= hi with count(lo) <= i < count(hi);
+// a group of L lanes evaluates count at L interior points per sweep.
+//
+// GB300 executes FP64 (and above all FP64 division) far slower than FP32,
+// so the bracket is first narrowed with FP32 counts to a width of
+// 64 eps32 ||T|| (an FP32 count is exact for a matrix within a few eps32
+// ||T|| of T), then widened by that margin, verified with FP64 counts and
+// finished in FP64 to 4 eps64 max(||T||, |lambda|).  In the FP64 pivot
+// recurrence q_k = (d_k - x) - e_k^2 / q_{k-1} the reciprocal of q is an
+// FP32 seed refined by two Newton-Raphson steps r <- r + r (1 - q r)
+// (relative error squares each step: ~2^-23 -> 2^-46 -> below 2^-53),
+// with an exact division when q lies outside the FP32 normal range.
 #include <float.h>
 #include <math.h>
 
@@ -13,35 +23,87 @@
 
 namespace {
 
-__device__ __forceinline__ int sturm_count(const double* __restrict__ d,
-                                           const double* __restrict__ e2, int n, double x,
-                                           double pivmin) {
+constexpr int L = 4;        // lanes per eigenvalue
+constexpr int NTB = 128;    // threads per block
+
+__device__ __forceinline__ double rcp64(double q) {
+  const double aq = fabs(q);
+  if (aq > 1e-36 && aq < 1e36) {
+    double r = (double)__frcp_rn((float)q);
+    r = fma(r, fma(-q, r, 1.0), r);
+    r = fma(r, fma(-q, r, 1.0), r);
+    return r;
+  }
+  return 1.0 / q;
+}
+
+__device__ int count64(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                       double x, double pivmin) {
   double q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
   int cnt = q <= 0.0;
   for (int k = 1; k < n; ++k) {
-    q = (d[k] - x) - e2[k - 1] / q;
+    q = fma(-e2[k - 1], rcp64(q), d[k] - x);
     if (fabs(q) < pivmin) q = -pivmin;
     cnt += q <= 0.0;
   }
   return cnt;
 }
 
-__global__ void bisect_kernel(const double* __restrict__ de, int n, int nbands,
-                              double* __restrict__ omega, int* __restrict__ stat) {
+__device__ int count32(const float* __restrict__ d, const float* __restrict__ e2, int n, float x,
+                       float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = q <= 0.0f;
+  for (int k = 1; k < n; ++k) {
+    q = (d[k] - x) - e2[k - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q <= 0.0f;
+  }
+  return cnt;
+}
+
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+
+// one multisection sweep of the group: lanes evaluate L interior points
+template <typename T, typename CountFn>
+__device__ void sweep(T& lo, T& hi, int i, int l, unsigned mask, CountFn cnt) {
+  const T x = lo + (hi - lo) * (T)(l + 1) / (T)(L + 1);
+  const int c = cnt(x);
+  T xl = c <= i ? x : lo;
+  T xh = c > i ? x : hi;
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1) {
+    xl = vmax(xl, __shfl_xor_sync(mask, xl, o, L));
+    xh = vmin(xh, __shfl_xor_sync(mask, xh, o, L));
+  }
+  lo = xl;
+  hi = xh;
+}
+
+__global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ de, int n,
+                                                     int nbands, double* __restrict__ omega,
+                                                     int* __restrict__ stat, int want_omega) {
   extern __shared__ double sm[];
   double* d = sm;
   double* e2 = sm + n;
-  __shared__ double red[3];
-  const int b = blockIdx.x;
+  float* d32 = reinterpret_cast<float*>(sm + 2 * n);
+  float* e32 = d32 + n;
+  __shared__ double red[4];
+  const int b = blockIdx.x, tid = threadIdx.x;
   const double* dg = de + (size_t)b * 2 * n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  for (int k = tid; k < n; k += NTB) {
     d[k] = dg[k];
     const double e = k + 1 < n ? dg[n + k] : 0.0;
     e2[k] = e * e;
+    d32[k] = (float)d[k];
+    e32[k] = (float)e2[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double gl = d[0], gu = d[0], emax = 0.0;
     for (int k = 0; k < n; ++k) {
       const double el = k > 0 ? sqrt(e2[k - 1]) : 0.0, er = k + 1 < n ? sqrt(e2[k]) : 0.0;
@@ -55,39 +117,62 @@ __global__ void bisect_kernel(const double* __restrict__ de, int n, int nbands,
     red[0] = gl;
     red[1] = gu;
     red[2] = DBL_MIN * fmax(1.0, emax);
+    red[3] = tnorm;
   }
   __syncthreads();
-  const double gl = red[0], gu = red[1], pivmin = red[2];
-  const double atol = 4.0 * DBL_EPSILON * fmax(fabs(gl), fabs(gu));
+  const double gl = red[0], gu = red[1], pivmin = red[2], tnorm = red[3];
+  const double atol = 4.0 * DBL_EPSILON * tnorm;
+  // FP32 counts need the matrix inside the FP32 range with headroom
+  const bool use32 = tnorm < 1e18 && tnorm > 1e-18;
+  const float pivmin32 = FLT_MIN * fmaxf(1.0f, (float)(tnorm * tnorm));
+  const double w32 = 64.0 * FLT_EPSILON * tnorm;
+
+  const int lane = tid & 31, l = tid % L;
+  const unsigned mask = 0xFu << (lane & ~(L - 1));
+  auto c64 = [&](double x) { return count64(d, e2, n, x, pivmin); };
+  auto c32 = [&](float x) { return count32(d32, e32, n, x, pivmin32); };
   int bad = 0;
-  for (int i = threadIdx.x; i < nbands; i += blockDim.x) {
+  for (int i = tid / L; i < nbands; i += NTB / L) {
     double lo = gl, hi = gu;
-    for (int it = 0; it < 256; ++it) {
+    if (use32) {
+      float flo = (float)gl, fhi = (float)gu;
+      flo = fminf(flo, (float)gl - (float)w32);
+      fhi = fmaxf(fhi, (float)gu + (float)w32);
+      for (int it = 0; it < 64 && (double)fhi - (double)flo > w32; ++it) sweep(flo, fhi, i, l, mask, c32);
+      // widen by the FP32 count margin and verify in FP64
+      double vlo = fmax(gl, (double)flo - w32), vhi = fmin(gu, (double)fhi + w32);
+      const double x = l == 0 ? vlo : vhi;
+      const int c = (l < 2) ? c64(x) : 0;
+      const int clo = __shfl_sync(mask, c, 0, L), chi = __shfl_sync(mask, c, 1, L);
+      if (clo <= i && chi > i) {
+        lo = vlo;
+        hi = vhi;
+      }
+    }
+    for (int it = 0; it < 128; ++it) {
       const double tol = fmax(atol, 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)));
       if (hi - lo <= tol) break;
-      const double mid = 0.5 * (lo + hi);
-      if (sturm_count(d, e2, n, mid, pivmin) > i) hi = mid;
-      else lo = mid;
+      sweep(lo, hi, i, l, mask, c64);
     }
     const double lam = 0.5 * (lo + hi);
     if (!isfinite(lam)) bad = 1;
-    omega[(size_t)b * nbands + i] = sqrt(fmax(lam, 0.0));
+    if (l == 0) omega[(size_t)b * nbands + i] = want_omega ? sqrt(fmax(lam, 0.0)) : lam;
   }
   bad = __syncthreads_or(bad);
-  if (threadIdx.x == 0 && stat) stat[b] = bad ? BS_ENOCONV : 0;
+  if (tid == 0 && stat) stat[b] = bad ? BS_ENOCONV : 0;
 }
 
 }  // namespace
 
 int bs_launch_bisect(const double* de, int n, int batch, int nbands, double* omega, int* stat,
-                     cudaStream_t s) {
-  const size_t smem = 2 * (size_t)n * sizeof(double);
+                     cudaStream_t s, bool want_omega) {
+  const size_t smem = 2 * (size_t)n * sizeof(double) + 2 * (size_t)n * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return bs_cuda_status(e, "bisect smem");
   }
-  bisect_kernel<<<batch, 64, smem, s>>>(de, n, nbands, omega, stat);
+  bisect_kernel<<<batch, NTB, smem, s>>>(de, n, nbands, omega, stat, want_omega ? 1 : 0);
   BS_CHECK_LAUNCH("bisect_kernel");
   return BS_OK;
 }

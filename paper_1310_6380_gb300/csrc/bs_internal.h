@@ -83,7 +83,18 @@ struct bs_cell {
   double* d_w;         // kcap x nbands_cap output
   int* d_stat;         // kcap
   int wcap;            // capacity of d_w per k
+
+  // profiling: events around each phase of the last call
+  bool prof;
+  bool prof_ready[6];
+  cudaEvent_t ev[6][2];
 };
+
+// phase indices of bs_phase_times
+enum { PH_ASM = 0, PH_GRAM = 1, PH_MONO = 2, PH_BUILD = 3, PH_TRID = 4, PH_BISECT = 5 };
+void bs_phase_begin(bs_cell* c, int ph, cudaStream_t s);
+void bs_phase_end(bs_cell* c, int ph, cudaStream_t s);
+void bs_count_launch();
 
 // ------------------------------------------------------------------ errors
 void bs_set_error(const char* fmt, ...);
@@ -91,6 +102,7 @@ int bs_cuda_status(cudaError_t e, const char* where);
 
 #define BS_CHECK_LAUNCH(where)                                   \
   do {                                                           \
+    bs_count_launch();                                           \
     cudaError_t e__ = cudaGetLastError();                        \
     if (e__ != cudaSuccess) return bs_cuda_status(e__, where);   \
   } while (0)
@@ -121,5 +133,7 @@ int bs_launch_tridiag(zd* A, int n, int batch, zd* vec, zd* part, double* de, do
                       unsigned* count, cudaStream_t s);
 
 // bisect.cu
+// lowest nbands eigenvalues of batch tridiagonals packed as [b][d(n) | e(n-1), pad];
+// writes omega = sqrt(max(lambda, 0)) when want_omega, else lambda
 int bs_launch_bisect(const double* de, int n, int batch, int nbands, double* omega, int* stat,
-                     cudaStream_t s);
+                     cudaStream_t s, bool want_omega = true);

@@ -6,7 +6,7 @@
 // v[j+1] = 1) needs p = tau B v on the trailing block B = A[j+1:, j+1:],
 // w = p - (tau/2)(v^dagger p) v and the rank-2 update B -= v w^dagger + w v^dagger.
 // One launch per step does, for every matrix of the batch, the rank-2
-// update of step j-1 fused with p of step j over 32 x 32 tiles of the
+// update of step j-1 fused with p of step j over 64 x 64 tiles of the
 // lower triangle (each element is read and written once per step), and
 // the last tile of each matrix to finish (an arrival counter, no waiting)
 // reduces the tile partials, forms w, applies the update to column j+1
@@ -16,7 +16,7 @@
 
 namespace {
 
-constexpr int TS = 32;    // tile edge
+constexpr int TS = 64;    // tile edge
 constexpr int NT = 256;   // threads per CTA (8 warps)
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -101,19 +101,24 @@ __device__ __forceinline__ void tri_index(int l, int& bi, int& bk) {
   bk = l - r * (r + 1) / 2;
 }
 
-__global__ void __launch_bounds__(NT) tridiag_step_kernel(zd* __restrict__ A, int n, int j,
-                                                          zd* __restrict__ vec,
-                                                          zd* __restrict__ part,
-                                                          double* __restrict__ de,
-                                                          double* __restrict__ tau,
-                                                          unsigned* __restrict__ count, int ntl) {
+__global__ void __launch_bounds__(NT, 2) tridiag_step_kernel(zd* __restrict__ A, int n, int j,
+                                                             zd* __restrict__ vec,
+                                                             zd* __restrict__ part,
+                                                             double* __restrict__ de,
+                                                             double* __restrict__ tau,
+                                                             unsigned* __restrict__ count,
+                                                             int ntl) {
+  // Thread (tx, ty) owns rows R*TS + tx + 16v and columns S*TS + ty + 16u,
+  // u, v = 0..3: its 16 elements give 4 row and 4 column partials of p,
+  // reduced once per tile through shared memory.
   __shared__ zd vpS[TS], wpS[TS], vcS[TS];
-  __shared__ zd rowred[NT / 32][TS];
-  __shared__ zd colsum[TS];
+  __shared__ zd rowred[TS / 4][TS];   // [ty][row]
+  __shared__ zd colred[TS / 4][TS];   // [tx][col]
   __shared__ double sh[NT / 32 + 1];
   __shared__ int is_last;
 
-  const int b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.y, tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
   const int nt = (n + TS - 1) / TS, t0 = (j + 1) / TS, r0 = j + 1;
   zd* a = A + (size_t)b * n * n;
   zd* vb = vec + (size_t)b * 3 * n;
@@ -125,55 +130,71 @@ __global__ void __launch_bounds__(NT) tridiag_step_kernel(zd* __restrict__ A, in
   int bi, bk;
   tri_index(blockIdx.x, bi, bk);
   const int R = t0 + bi, S = t0 + bk;
+  const int rbase = R * TS, sbase = S * TS;
 
-  // column vectors of this tile
   if (tid < TS) {
-    const int s = S * TS + tid;
+    const int s = sbase + tid;
     const bool ok = s < n && s >= r0;
     vpS[tid] = ok ? vprev[s] : zmake(0.0, 0.0);
     wpS[tid] = ok ? w[s] : zmake(0.0, 0.0);
     vcS[tid] = ok ? vcur[s] : zmake(0.0, 0.0);
   }
-  const int r = R * TS + lane;
-  const bool rok = r < n && r >= r0;
-  const zd vpr = rok ? vprev[r] : zmake(0.0, 0.0);
-  const zd wpr = rok ? w[r] : zmake(0.0, 0.0);
-  const zd vcr = rok ? vcur[r] : zmake(0.0, 0.0);
+  zd vpr[4], wpr[4], vcr[4], racc[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int r = rbase + tx + 16 * v;
+    const bool ok = r < n && r >= r0;
+    vpr[v] = ok ? vprev[r] : zmake(0.0, 0.0);
+    wpr[v] = ok ? w[r] : zmake(0.0, 0.0);
+    vcr[v] = ok ? vcur[r] : zmake(0.0, 0.0);
+    racc[v] = zmake(0.0, 0.0);
+  }
   __syncthreads();
 
-  zd racc = zmake(0.0, 0.0);
 #pragma unroll
-  for (int i = 0; i < TS / (NT / 32); ++i) {
-    const int sl = warp + (NT / 32) * i;
-    const int s = S * TS + sl;
+  for (int u = 0; u < 4; ++u) {
+    const int sl = ty + 16 * u, s = sbase + sl;
+    const zd vps = vpS[sl], wps = wpS[sl], vcs = vcS[sl];
     zd cacc = zmake(0.0, 0.0);
-    if (rok && s >= r0 && r >= s) {
-      zd* ap = a + r + (size_t)s * n;
-      zd x = *ap;
-      x = zfnmac(vpr, wpS[sl], x);
-      x = zfnmac(wpr, vpS[sl], x);
-      if (r == s) x.y = 0.0;
-      *ap = x;
-      racc = zfma(x, vcS[sl], racc);
-      if (r != s) cacc = zfma(zconj(x), vcr, cacc);
-    }
-    cacc.x = warp_sum(cacc.x);
-    cacc.y = warp_sum(cacc.y);
-    if (lane == 0) colsum[sl] = cacc;
-  }
-  rowred[warp][lane] = racc;
-  __syncthreads();
-  if (tid < TS) {
-    zd rs = rowred[0][tid];
+    const bool sok = s >= r0;
 #pragma unroll
-    for (int u = 1; u < NT / 32; ++u) rs = zadd(rs, rowred[u][tid]);
-    const int ir = R * TS + tid, is = S * TS + tid;
-    if (R == S) {
-      if (ir < n) pt[(size_t)R * n + ir] = zadd(rs, colsum[tid]);
-    } else {
-      if (ir < n) pt[(size_t)S * n + ir] = rs;
-      pt[(size_t)R * n + is] = colsum[tid];
+    for (int v = 0; v < 4; ++v) {
+      const int r = rbase + tx + 16 * v;
+      if (sok && r < n && r >= s) {
+        zd* ap = a + r + (size_t)s * n;
+        zd x = *ap;
+        x = zfnmac(vpr[v], wps, x);
+        x = zfnmac(wpr[v], vps, x);
+        if (r == s) x.y = 0.0;
+        *ap = x;
+        racc[v] = zfma(x, vcs, racc[v]);
+        if (r != s) cacc = zfma(zconj(x), vcr[v], cacc);
+      }
     }
+    colred[tx][sl] = cacc;
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) rowred[ty][tx + 16 * v] = racc[v];
+  __syncthreads();
+  if (tid < 2 * TS) {
+    const bool isrow = tid < TS;
+    const int l = isrow ? tid : tid - TS;
+    zd acc = zmake(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < TS / 4; ++q) acc = zadd(acc, isrow ? rowred[q][l] : colred[q][l]);
+    if (R == S) {
+      // diagonal tile: row and column partials of the same index meet here
+      if (isrow) rowred[0][l] = acc;
+      else colred[0][l] = acc;
+    } else if (isrow) {
+      if (rbase + l < n) pt[(size_t)S * n + rbase + l] = acc;
+    } else {
+      pt[(size_t)R * n + sbase + l] = acc;
+    }
+  }
+  if (R == S) {
+    __syncthreads();
+    if (tid < TS && rbase + tid < n) pt[(size_t)R * n + rbase + tid] = zadd(rowred[0][tid], colred[0][tid]);
   }
   __threadfence();
   __syncthreads();
