@@ -180,10 +180,12 @@ int bs_cell_dims(const bs_cell* cell, int* N, int* n);
  *   ms[3] per-k builder of C(k)
  *   ms[4] Householder tridiagonalisation
  *   ms[5] bisection and omega
+ *   ms[6] FP64 Rayleigh-Ritz refinement (mixed path)
+ *   ms[7] reserved (0)
  * Phases that did not run in the last call report 0.
  */
 int bs_set_profiling(bs_cell* cell, int on);
-int bs_phase_times(bs_cell* cell, double ms[6]);
+int bs_phase_times(bs_cell* cell, double ms[8]);
 
 /*
  * bs_launch_count - number of CUDA kernels this library has launched in

@@ -176,11 +176,11 @@ def bs_set_profiling(cell, on: bool):
     _check(_lib.bs_set_profiling(cell, int(bool(on))))
 
 
-PHASES = ("assembly", "gram", "monomials", "builder", "tridiag", "bisect")
+PHASES = ("assembly", "gram", "monomials", "builder", "tridiag", "bisect", "refine", "reserved")
 
 
 def bs_phase_times(cell) -> dict:
-    ms = np.zeros(6)
+    ms = np.zeros(8)
     _check(_lib.bs_phase_times(cell, ms.ctypes.data))
     return dict(zip(PHASES, ms.tolist()))
 

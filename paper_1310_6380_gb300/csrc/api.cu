@@ -110,6 +110,13 @@ static int copy_in(void* ddst, const void* src, size_t bytes, cudaStream_t s) {
 }
 
 static void free_workspace(bs_cell* c) {
+  void* mixed[] = {c->d_C32, c->d_vec32, c->d_part32, c->d_lamT, c->d_scr, c->d_mY, c->d_mphase,
+                   c->d_X32, c->d_X64, c->d_CX, c->d_mG, c->d_H, c->d_W, c->d_theta, c->d_beta};
+  for (void* p : mixed) cudaFree(p);
+  c->d_C32 = c->d_vec32 = c->d_part32 = c->d_X32 = nullptr;
+  c->d_lamT = c->d_scr = c->d_mY = c->d_theta = nullptr;
+  c->d_mphase = c->d_X64 = c->d_CX = c->d_mG = c->d_H = c->d_W = c->d_beta = nullptr;
+  c->bcap = 0;
   cudaFree(c->d_C);
   cudaFree(c->d_vec);
   cudaFree(c->d_part);
@@ -139,11 +146,30 @@ static int ensure_workspace(bs_cell* c, int kb, int nb) {
   TRY(dalloc(&c->d_vec, (size_t)kb * bs_tridiag_vec_elems(n), "tridiag vectors"));
   TRY(dalloc(&c->d_part, (size_t)kb * bs_tridiag_part_elems(n), "tridiag partials"));
   TRY(dalloc(&c->d_de, (size_t)kb * 2 * n, "tridiagonal"));
-  TRY(dalloc(&c->d_tau, (size_t)kb, "tau"));
+  TRY(dalloc(&c->d_tau, (size_t)kb * n, "tau"));
+  TRY(dalloc(&c->d_beta, (size_t)kb * n, "beta"));
   TRY(dalloc(&c->d_count, (size_t)kb, "counters"));
   TRY(dalloc(&c->d_Q, (size_t)kb * 2, "Q"));
   TRY(dalloc(&c->d_w, (size_t)kb * nb, "omega"));
   TRY(dalloc(&c->d_stat, (size_t)kb, "status"));
+  if (c->precision == BS_PREC_MIXED) {
+    const int b = bs_mixed_guard(nb, n);
+    TRY(dalloc(&c->d_C32, (size_t)kb * n * n, "C32"));
+    TRY(dalloc(&c->d_vec32, (size_t)kb * bs_tridiag_vec_elems(n), "vec32"));
+    TRY(dalloc(&c->d_part32, (size_t)kb * bs_tridiag_part_elems(n), "part32"));
+    TRY(dalloc(&c->d_lamT, (size_t)kb * (b + 1), "lamT"));
+    TRY(dalloc(&c->d_scr, (size_t)kb * b * 5 * n, "inverse iteration"));
+    TRY(dalloc(&c->d_mY, (size_t)kb * b * n, "Y"));
+    TRY(dalloc(&c->d_mphase, (size_t)kb * n, "phase"));
+    TRY(dalloc(&c->d_X32, (size_t)kb * b * n, "X32"));
+    TRY(dalloc(&c->d_X64, (size_t)kb * b * n, "X64"));
+    TRY(dalloc(&c->d_CX, (size_t)kb * b * n, "CX"));
+    TRY(dalloc(&c->d_mG, (size_t)kb * b * b, "G"));
+    TRY(dalloc(&c->d_H, (size_t)kb * b * b, "H"));
+    TRY(dalloc(&c->d_W, (size_t)kb * b * b, "W"));
+    TRY(dalloc(&c->d_theta, (size_t)kb * b, "theta"));
+    c->bcap = b;
+  }
   c->kcap = kb;
   c->wcap = nb;
   return BS_OK;
@@ -155,6 +181,8 @@ static int k_batch_cap(const bs_cell* c) {
   size_t cap = ((size_t)4 << 30) / per;
   return (int)std::max<size_t>(1, std::min<size_t>(cap, 4096));
 }
+
+static double omega_floor2(const bs_cell* c);
 
 // ------------------------------------------------------------------ create
 extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
@@ -254,6 +282,8 @@ extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
     bs_destroy_cell(c);
     return r;
   }
+  c->tol = 1e-6;
+  c->floor2 = omega_floor2(c);
   *out = c;
   return BS_OK;
 }
@@ -297,7 +327,7 @@ extern "C" int bs_assemble(bs_cell* c, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const size_t NN = (size_t)c->N * c->N;
   CK(cudaMemsetAsync(c->d_info, 0, sizeof(int), s), "bs_assemble");
-  for (int i = 0; i < 6; ++i) c->prof_ready[i] = false;
+  for (int i = 0; i < PH_COUNT; ++i) c->prof_ready[i] = false;
   bs_phase_begin(c, PH_ASM, s);
   TRY(bs_launch_assembly(c, s));                                   // a1 + a2
   bs_phase_end(c, PH_ASM, s);
@@ -334,13 +364,51 @@ extern "C" int bs_sync(bs_cell* c, void* stream) {
 
 // ------------------------------------------------------------------ solve
 // Solve a chunk of kb wavevectors already in c->d_Q; results in c->d_w / d_stat.
+// omega_floor^2 = (c_T,min |q|_min / 2)^2: below it frequencies are judged
+// in absolute terms (the acoustic branches vanish at Gamma)
+static double omega_floor2(const bs_cell* c) {
+  std::vector<double> raw(3 * (size_t)c->nphase);
+  cudaMemcpy(raw.data(), c->d_table + 3 * c->nphase, raw.size() * 8, cudaMemcpyDeviceToHost);
+  double ct2 = 1e300;
+  for (int i = 0; i < c->nphase; ++i) ct2 = std::min(ct2, raw[c->nphase + i] / raw[2 * c->nphase + i]);
+  const double q2 = std::min(c->q1[0] * c->q1[0] + c->q1[1] * c->q1[1],
+                             c->q2[0] * c->q2[0] + c->q2[1] * c->q2[1]);
+  return ct2 * q2 / 4.0;
+}
+
+static int solve_chunk_mixed(bs_cell* c, int kb, int nbands, cudaStream_t s) {
+  const int n = c->n, b = bs_mixed_guard(nbands, n);
+  bs_phase_begin(c, PH_BUILD, s);
+  TRY(bs_launch_builder_mixed(c->d_Cm, n, c->d_Q, kb, c->q1[0], c->q1[1], c->q2[0], c->q2[1],
+                              c->d_C, c->d_C32, s));
+  bs_phase_end(c, PH_BUILD, s);
+  bs_phase_begin(c, PH_TRID, s);
+  TRY(bs_launch_tridiag<float>(c->d_C32, n, kb, c->d_vec32, c->d_part32, c->d_de, c->d_tau,
+                               c->d_beta, c->d_count, s));
+  bs_phase_end(c, PH_TRID, s);
+  bs_phase_begin(c, PH_BISECT, s);
+  TRY(bs_launch_bisect(c->d_de, n, kb, std::min(b + 1, n), c->d_lamT, nullptr, s, false, 1e-9));
+  bs_phase_end(c, PH_BISECT, s);
+  bs_phase_begin(c, PH_REFINE, s);
+  MixedWs w;
+  w.C64 = c->d_C; w.C32 = c->d_C32; w.de = c->d_de; w.tau = c->d_tau; w.beta = c->d_beta;
+  w.lamT = c->d_lamT; w.scratch = c->d_scr; w.Y = c->d_mY; w.phase = c->d_mphase;
+  w.X32 = c->d_X32; w.X64 = c->d_X64; w.CX = c->d_CX; w.G = c->d_mG; w.H = c->d_H; w.W = c->d_W;
+  w.theta = c->d_theta;
+  TRY(bs_launch_mixed_refine(w, n, kb, nbands, b, c->tol, c->floor2, c->d_w, c->d_stat, s));
+  bs_phase_end(c, PH_REFINE, s);
+  return BS_OK;
+}
+
 static int solve_chunk(bs_cell* c, int kb, int nbands, cudaStream_t s) {
+  if (c->precision == BS_PREC_MIXED) return solve_chunk_mixed(c, kb, nbands, s);
   bs_phase_begin(c, PH_BUILD, s);
   TRY(bs_launch_builder(c->d_Cm, c->n, c->d_Q, kb, c->q1[0], c->q1[1], c->q2[0], c->q2[1], c->d_C,
                         s));
   bs_phase_end(c, PH_BUILD, s);
   bs_phase_begin(c, PH_TRID, s);
-  TRY(bs_launch_tridiag(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau, c->d_count, s));
+  TRY(bs_launch_tridiag<double>(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
+                                c->d_beta, c->d_count, s));
   bs_phase_end(c, PH_TRID, s);
   bs_phase_begin(c, PH_BISECT, s);
   TRY(bs_launch_bisect(c->d_de, c->n, kb, nbands, c->d_w, c->d_stat, s));
@@ -360,6 +428,11 @@ extern "C" int bs_solve_k(bs_cell* c, const double* Q, int nk, int nbands, doubl
   }
   if (nbands < 1 || nbands > c->n) {
     bs_set_error("bs_solve_k: nbands=%d outside [1, %d]", nbands, c->n);
+    return BS_EINVAL;
+  }
+  if (c->precision == BS_PREC_MIXED && (nbands > BS_MIXED_MAX_BANDS || nbands + 2 > c->n)) {
+    bs_set_error("bs_solve_k: the mixed path needs nbands <= %d and nbands + 2 <= n (%d)",
+                 BS_MIXED_MAX_BANDS, c->n);
     return BS_EINVAL;
   }
   if (nk == 0) return BS_OK;
@@ -451,24 +524,24 @@ extern "C" int bs_set_profiling(bs_cell* c, int on) {
     return BS_EINVAL;
   }
   if (on && !c->prof) {
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < PH_COUNT; ++i)
       for (int j = 0; j < 2; ++j) CK(cudaEventCreate(&c->ev[i][j]), "bs_set_profiling");
   }
   if (!on && c->prof) {
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < PH_COUNT; ++i)
       for (int j = 0; j < 2; ++j) cudaEventDestroy(c->ev[i][j]);
   }
   c->prof = on != 0;
-  for (int i = 0; i < 6; ++i) c->prof_ready[i] = false;
+  for (int i = 0; i < PH_COUNT; ++i) c->prof_ready[i] = false;
   return BS_OK;
 }
 
-extern "C" int bs_phase_times(bs_cell* c, double ms[6]) {
+extern "C" int bs_phase_times(bs_cell* c, double ms[8]) {
   if (!c || !ms) {
     bs_set_error("bs_phase_times: NULL argument");
     return BS_EINVAL;
   }
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < PH_COUNT; ++i) {
     ms[i] = 0.0;
     if (!c->prof || !c->prof_ready[i]) continue;
     CK(cudaEventSynchronize(c->ev[i][1]), "bs_phase_times");

@@ -16,6 +16,9 @@
 // FP32 seed refined by two Newton-Raphson steps r <- r + r (1 - q r)
 // (relative error squares each step: ~2^-23 -> 2^-46 -> below 2^-53),
 // with an exact division when q lies outside the FP32 normal range.
+// stop_rel > 4 eps ends the FP64 phase at stop_rel ||T||: the mixed path
+// needs the eigenvalues of its FP32-reduced T only as inverse-iteration
+// shifts, for which 1e-9 ||T|| is ample.
 #include <float.h>
 #include <math.h>
 
@@ -86,7 +89,8 @@ __device__ void sweep(T& lo, T& hi, int i, int l, unsigned mask, CountFn cnt) {
 
 __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ de, int n,
                                                      int nbands, double* __restrict__ omega,
-                                                     int* __restrict__ stat, int want_omega) {
+                                                     int* __restrict__ stat, int want_omega,
+                                                     double stop_rel) {
   extern __shared__ double sm[];
   double* d = sm;
   double* e2 = sm + n;
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ 
   }
   __syncthreads();
   const double gl = red[0], gu = red[1], pivmin = red[2], tnorm = red[3];
-  const double atol = 4.0 * DBL_EPSILON * tnorm;
+  const double atol = fmax(4.0 * DBL_EPSILON, stop_rel) * tnorm;
   // FP32 counts need the matrix inside the FP32 range with headroom
   const bool use32 = tnorm < 1e18 && tnorm > 1e-18;
   const float pivmin32 = FLT_MIN * fmaxf(1.0f, (float)(tnorm * tnorm));
@@ -165,14 +169,15 @@ __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ 
 }  // namespace
 
 int bs_launch_bisect(const double* de, int n, int batch, int nbands, double* omega, int* stat,
-                     cudaStream_t s, bool want_omega) {
+                     cudaStream_t s, bool want_omega, double stop_rel) {
   const size_t smem = 2 * (size_t)n * sizeof(double) + 2 * (size_t)n * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return bs_cuda_status(e, "bisect smem");
   }
-  bisect_kernel<<<batch, NTB, smem, s>>>(de, n, nbands, omega, stat, want_omega ? 1 : 0);
+  bisect_kernel<<<batch, NTB, smem, s>>>(de, n, nbands, omega, stat, want_omega ? 1 : 0,
+                                         stop_rel);
   BS_CHECK_LAUNCH("bisect_kernel");
   return BS_OK;
 }

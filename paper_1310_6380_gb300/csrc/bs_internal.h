@@ -46,6 +46,44 @@ __host__ __device__ __forceinline__ zd zfnmac(zd a, zd b, zd acc) {
   return acc;
 }
 
+// float2 versions (FP32 reduction of the mixed path)
+__host__ __device__ __forceinline__ zf zadd(zf a, zf b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ zf zsub(zf a, zf b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ zf zconj(zf a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ zf zscale(zf a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ zf zmul(zf a, zf b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ zf zfma(zf a, zf b, zf acc) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+__host__ __device__ __forceinline__ zf zfnmac(zf a, zf b, zf acc) {
+  acc.x = fmaf(-a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  return acc;
+}
+
+// complex type of a real precision
+template <typename R> struct Cplx;
+template <> struct Cplx<double> {
+  typedef double2 T;
+  static __host__ __device__ __forceinline__ T make(double a, double b) { return make_double2(a, b); }
+};
+template <> struct Cplx<float> {
+  typedef float2 T;
+  static __host__ __device__ __forceinline__ T make(float a, float b) { return make_float2(a, b); }
+};
+
+// phase indices of bs_phase_times
+enum { PH_ASM = 0, PH_GRAM = 1, PH_MONO = 2, PH_BUILD = 3, PH_TRID = 4, PH_BISECT = 5,
+       PH_REFINE = 6, PH_COUNT = 8 };
+
 // ------------------------------------------------------------------ cell
 struct bs_cell {
   // geometry and truncation
@@ -77,7 +115,26 @@ struct bs_cell {
   zd* d_vec;           // tridiagonalisation vectors
   zd* d_part;          // partial sums of the tridiagonalisation
   double* d_de;        // kcap x 2n tridiagonal (d, |e|)
-  double* d_tau;       // kcap
+  double* d_tau;       // kcap x n reflector scalars
+  zd* d_beta;          // kcap x n tridiagonal off-diagonals (complex)
+  // mixed path
+  zf* d_C32;
+  zf* d_vec32;
+  zf* d_part32;
+  double* d_lamT;
+  double* d_scr;
+  double* d_mY;
+  zd* d_mphase;
+  zf* d_X32;
+  zd* d_X64;
+  zd* d_CX;
+  zd* d_mG;
+  zd* d_H;
+  zd* d_W;
+  double* d_theta;
+  int bcap;            // guard-extended block size the mixed workspace holds
+  double tol;          // relative omega tolerance the mixed path certifies
+  double floor2;       // omega_floor^2 of the cell
   unsigned* d_count;   // kcap arrival counters
   double* d_Q;         // kcap x 2 wavevectors
   double* d_w;         // kcap x nbands_cap output
@@ -86,12 +143,10 @@ struct bs_cell {
 
   // profiling: events around each phase of the last call
   bool prof;
-  bool prof_ready[6];
-  cudaEvent_t ev[6][2];
+  bool prof_ready[PH_COUNT];
+  cudaEvent_t ev[PH_COUNT][2];
 };
 
-// phase indices of bs_phase_times
-enum { PH_ASM = 0, PH_GRAM = 1, PH_MONO = 2, PH_BUILD = 3, PH_TRID = 4, PH_BISECT = 5 };
 void bs_phase_begin(bs_cell* c, int ph, cudaStream_t s);
 void bs_phase_end(bs_cell* c, int ph, cudaStream_t s);
 void bs_count_launch();
@@ -99,6 +154,12 @@ void bs_count_launch();
 // ------------------------------------------------------------------ errors
 void bs_set_error(const char* fmt, ...);
 int bs_cuda_status(cudaError_t e, const char* where);
+
+#define TRY_LAUNCH(expr)     \
+  do {                       \
+    int r__ = (expr);        \
+    if (r__) return r__;     \
+  } while (0)
 
 #define BS_CHECK_LAUNCH(where)                                   \
   do {                                                           \
@@ -126,14 +187,45 @@ int bs_launch_monomials(bs_cell* c, cudaStream_t s);
 int bs_launch_builder(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,
                       double q2x, double q2y, zd* C, cudaStream_t s);
 
-// tridiag.cu
+// tridiag.cu: Householder reduction in precision R (double or float).  On
+// return column j of A below row j+1 holds v_j (v_j[j+1] = 1 implied),
+// de = [d | |beta|], tau[b*n + j] = tau_j and beta[b*n + j] = beta_j, the
+// (j+1, j) entry of the unitarily reduced (complex) tridiagonal.
 size_t bs_tridiag_vec_elems(int n);
 size_t bs_tridiag_part_elems(int n);
-int bs_launch_tridiag(zd* A, int n, int batch, zd* vec, zd* part, double* de, double* tau,
+template <typename R>
+int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
+                      typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
                       unsigned* count, cudaStream_t s);
+
+// mixed.cu: FP32 reduction + FP64 Rayleigh-Ritz refinement
+struct MixedWs {
+  zd* C64;        // kb x n x n full Hermitian C(k)
+  zf* C32;        // kb x n x n, lower triangle; reflectors after the reduction
+  double* de;     // kb x 2n tridiagonal
+  double* tau;    // kb x n
+  zd* beta;       // kb x n
+  double* lamT;   // kb x (b+1) eigenvalues of T
+  double* scratch;// kb x b x 5n inverse-iteration factors
+  double* Y;      // kb x b x n tridiagonal eigenvectors
+  zd* phase;      // kb x n diagonal unitary scaling
+  zf* X32;        // kb x b x n back-transformed vectors (FP32)
+  zd* X64;        // kb x n x b (column-major) FP64 copy
+  zd* CX;         // kb x n x b
+  zd* G;          // kb x b x b
+  zd* H;          // kb x b x b
+  zd* W;          // kb x b x b Ritz coefficients
+  double* theta;  // kb x b Ritz values
+};
+#define BS_MIXED_MAX_BANDS 24
+int bs_mixed_guard(int nbands, int n);
+int bs_launch_builder_mixed(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,
+                            double q2x, double q2y, zd* C64, zf* C32, cudaStream_t s);
+int bs_launch_mixed_refine(const MixedWs& w, int n, int kb, int nbands, int b, double tol,
+                           double floor2, double* omega, int* stat, cudaStream_t s);
 
 // bisect.cu
 // lowest nbands eigenvalues of batch tridiagonals packed as [b][d(n) | e(n-1), pad];
 // writes omega = sqrt(max(lambda, 0)) when want_omega, else lambda
 int bs_launch_bisect(const double* de, int n, int batch, int nbands, double* omega, int* stat,
-                     cudaStream_t s, bool want_omega = true);
+                     cudaStream_t s, bool want_omega = true, double stop_rel = 0.0);

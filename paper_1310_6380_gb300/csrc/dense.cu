@@ -292,8 +292,10 @@ __global__ void monomial_kernel(const zd* __restrict__ Pp, int N, double V2, zd*
   const int n = 2 * N;
   size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (size_t)n * n) return;
-  const int r = (int)(e % n), c = (int)(e / n);
-  if (r < c) return;   // lower triangle only
+  const int r0 = (int)(e % n), c0 = (int)(e / n);
+  // the upper triangle is the conjugate of the lower one (C(k) is Hermitian)
+  const bool up = r0 < c0;
+  const int r = up ? c0 : r0, c = up ? r0 : c0;
   const int I = r / N, J = c / N, i = r % N, j = c % N;
   const int K = 0, Mu = 1;
   zd m[6];
@@ -324,7 +326,7 @@ __global__ void monomial_kernel(const zd* __restrict__ Pp, int N, double V2, zd*
 #undef PP
   const size_t nn = (size_t)n * n;
 #pragma unroll
-  for (int t = 0; t < 6; ++t) Cm[t * nn + e] = zscale(m[t], V2);
+  for (int t = 0; t < 6; ++t) Cm[t * nn + e] = zscale(up ? zconj(m[t]) : m[t], V2);
 }
 
 }  // namespace

@@ -1,0 +1,489 @@
+// Mixed-precision eigen path: an FP32 Householder reduction gives
+// approximate eigenvectors of the reduced matrix C(k), and one FP64
+// Rayleigh-Ritz projection with the FP64 C(k) turns them into eigenvalues
+// accurate to FP64 working accuracy times (eps32 ||C|| / gap)^2.
+//
+//   C32(k) --FP32 Householder--> T (real after a diagonal unitary scaling)
+//   T --FP64 bisection--> lambda_1..lambda_{b+1}
+//   T --FP64 inverse iteration + MGS--> y_1..y_b
+//   y --phases of beta, FP32 reflectors--> X (n x b)
+//   X --FP64: C X, X^dagger X, X^dagger C X, Cholesky + Jacobi--> Ritz pairs
+//   Ritz pairs --FP64 residual ||C x - theta x||--> error bound and status
+//
+// b = nbands + guard vectors, so clusters at the edge of the wanted band
+// stay inside the subspace.  The bound |theta - lambda| <= ||r||^2 / gap
+// (gap = distance to lambda_{b+1} of T) is checked against the requested
+// tolerance; wavevectors that miss it are reported with BS_ENOCONV.
+#include <float.h>
+#include <math.h>
+
+#include "bs_internal.h"
+
+namespace {
+
+// ------------------------------------------------------------ builder
+// C64 full (FP64) and C32 lower triangle (FP32) from the full monomials.
+__global__ void builder_mixed_kernel(const zd* __restrict__ Cm, int n,
+                                     const double* __restrict__ Q, int nk, double q1x, double q1y,
+                                     double q2x, double q2y, zd* __restrict__ C64,
+                                     zf* __restrict__ C32) {
+  constexpr int KB = 32;
+  __shared__ double coef[KB][6];
+  const size_t nn = (size_t)n * n;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = e < nn;
+  const bool lower = live && (int)(e % n) >= (int)(e / n);
+  zd m[6];
+  if (live) {
+#pragma unroll
+    for (int t = 0; t < 6; ++t) m[t] = Cm[t * nn + e];
+  }
+  for (int k0 = 0; k0 < nk; k0 += KB) {
+    const int kb = min(KB, nk - k0);
+    __syncthreads();
+    if (threadIdx.x < kb) {
+      const double Q1 = Q[2 * (k0 + threadIdx.x)], Q2 = Q[2 * (k0 + threadIdx.x) + 1];
+      const double k1 = Q1 * q1x + Q2 * q2x, k2 = Q1 * q1y + Q2 * q2y;
+      coef[threadIdx.x][1] = k1;
+      coef[threadIdx.x][2] = k2;
+      coef[threadIdx.x][3] = k1 * k1;
+      coef[threadIdx.x][4] = k1 * k2;
+      coef[threadIdx.x][5] = k2 * k2;
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int b = 0; b < kb; ++b) {
+      double re = m[0].x, im = m[0].y;
+#pragma unroll
+      for (int t = 1; t < 6; ++t) {
+        re = fma(coef[b][t], m[t].x, re);
+        im = fma(coef[b][t], m[t].y, im);
+      }
+      C64[(size_t)(k0 + b) * nn + e] = zmake(re, im);
+      if (lower) C32[(size_t)(k0 + b) * nn + e] = make_float2((float)re, (float)im);
+    }
+  }
+}
+
+// ------------------------------------------------------------ tridiagonal eigenvectors
+__device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
+  unsigned h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (double)h * (2.0 / 4294967296.0) - 1.0;
+}
+
+// Inverse iteration on T - sigma I (Gaussian elimination with partial
+// pivoting of the tridiagonal), two solves from a pseudo-random start, then
+// modified Gram-Schmidt of the block in FP64.  Thread i < b owns vector i.
+// Also writes the diagonal unitary scaling D (T_complex = D T_real D^dagger).
+__global__ void tri_eigvec_kernel(const double* __restrict__ de, const zd* __restrict__ beta,
+                                  const double* __restrict__ lam, int n, int b, int lstride,
+                                  double* __restrict__ scratch, double* __restrict__ Y,
+                                  zd* __restrict__ phase) {
+  __shared__ double red[64];
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const double* d = de + (size_t)k * 2 * n;
+  const double* e = d + n;
+  double* y = Y + (size_t)k * b * n;
+  if (tid < b) {
+    const int i = tid;
+    double* u0 = scratch + ((size_t)k * b + i) * 5 * n;
+    double* u1 = u0 + n;
+    double* u2 = u1 + n;
+    double* ml = u2 + n;
+    double* pv = ml + n;   // 1 where rows r, r+1 were interchanged
+    double tnorm = 0.0;
+    for (int r = 0; r < n; ++r)
+      tnorm = fmax(tnorm, fabs(d[r]) + (r > 0 ? e[r - 1] : 0.0) + (r + 1 < n ? e[r] : 0.0));
+    const double tiny = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    const double sigma = lam[(size_t)k * lstride + i];
+    // factor: u0, u1, u2 = the three diagonals of U; ml = multipliers of L
+    double al = d[0] - sigma, bt = n > 1 ? e[0] : 0.0;
+    for (int r = 0; r + 1 < n; ++r) {
+      const double g = e[r];
+      const double dn = d[r + 1] - sigma, en = r + 2 < n ? e[r + 1] : 0.0;
+      if (fabs(al) >= fabs(g)) {
+        const double a0 = fabs(al) < tiny ? (al < 0 ? -tiny : tiny) : al;
+        const double mlt = g / a0;
+        u0[r] = a0; u1[r] = bt; u2[r] = 0.0; ml[r] = mlt; pv[r] = 0.0;
+        al = dn - mlt * bt;
+        bt = en;
+      } else {
+        const double mlt = al / g;
+        u0[r] = g; u1[r] = dn; u2[r] = en; ml[r] = mlt; pv[r] = 1.0;
+        al = bt - mlt * dn;
+        bt = -mlt * en;
+      }
+    }
+    u0[n - 1] = fabs(al) < tiny ? (al < 0 ? -tiny : tiny) : al;
+    double* yi = y + (size_t)i * n;
+    for (int r = 0; r < n; ++r) yi[r] = hash_unit(r, i + 977u * k);
+    for (int it = 0; it < 2; ++it) {
+      // forward: L^-1 with interchanges
+      for (int r = 0; r + 1 < n; ++r) {
+        const double mlt = ml[r];
+        if (pv[r] != 0.0) {   // interchange rows r, r+1
+          const double t = yi[r];
+          yi[r] = yi[r + 1];
+          yi[r + 1] = t - mlt * yi[r];
+        } else {
+          yi[r + 1] -= mlt * yi[r];
+        }
+      }
+      // backward: U y = rhs
+      double amax = 0.0;
+      for (int r = n - 1; r >= 0; --r) {
+        double s = yi[r];
+        if (r + 1 < n) s -= u1[r] * yi[r + 1];
+        if (r + 2 < n) s -= u2[r] * yi[r + 2];
+        yi[r] = s / u0[r];
+        amax = fmax(amax, fabs(yi[r]));
+      }
+      const double sc = amax > 0.0 ? 1.0 / amax : 1.0;
+      for (int r = 0; r < n; ++r) yi[r] *= sc;
+    }
+  }
+  if (tid == 0) {
+    zd ph = zmake(1.0, 0.0);
+    zd* pk = phase + (size_t)k * n;
+    pk[0] = ph;
+    for (int r = 0; r + 1 < n; ++r) {
+      const zd bt = beta[(size_t)k * n + r];
+      const double ab = hypot(bt.x, bt.y);
+      if (ab > 0.0) ph = zmul(ph, zmake(bt.x / ab, bt.y / ab));
+      pk[r + 1] = ph;
+    }
+  }
+  __syncthreads();
+  // modified Gram-Schmidt over the b vectors (block-cooperative)
+  for (int i = 0; i < b; ++i) {
+    double* yi = y + (size_t)i * n;
+    for (int jj = 0; jj <= i; ++jj) {
+      const double* yj = y + (size_t)jj * n;
+      double s = 0.0;
+      for (int r = tid; r < n; r += blockDim.x) s = fma(yj[r], yi[r], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if ((tid & 31) == 0) red[tid >> 5] = s;
+      __syncthreads();
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+      __syncthreads();
+      if (jj < i) {
+        for (int r = tid; r < n; r += blockDim.x) yi[r] = fma(-tot, yj[r], yi[r]);
+      } else {
+        const double sc = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+        for (int r = tid; r < n; r += blockDim.x) yi[r] *= sc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------ back-transformation
+// X = Q D y with Q = H_0 H_1 ... H_{n-2}: one warp per column, reflectors
+// applied from the last to the first, in FP32 (the reflectors are FP32).
+__global__ void backtransform_kernel(const zf* __restrict__ A32, const double* __restrict__ tau,
+                                     const zd* __restrict__ phase, const double* __restrict__ Y,
+                                     int n, int b, zf* __restrict__ X32, zd* __restrict__ X64) {
+  const int k = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.y * (blockDim.x >> 5) + warp;
+  if (i >= b) return;
+  const zf* a = A32 + (size_t)k * n * n;
+  const double* tk = tau + (size_t)k * n;
+  const zd* pk = phase + (size_t)k * n;
+  const double* y = Y + ((size_t)k * b + i) * n;
+  zf* x = X32 + ((size_t)k * b + i) * n;
+  for (int r = lane; r < n; r += 32) {
+    const zd v = zscale(pk[r], y[r]);
+    x[r] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncwarp();
+  for (int j = n - 2; j >= 0; --j) {
+    const float t = (float)tk[j];
+    if (t == 0.0f) continue;
+    // s = v^dagger x over rows j+1..n-1 (v[j+1] = 1)
+    float sr = 0.f, si = 0.f;
+    for (int r = j + 1 + lane; r < n; r += 32) {
+      const zf v = r == j + 1 ? make_float2(1.f, 0.f) : a[r + (size_t)j * n];
+      const zf xv = x[r];
+      sr = fmaf(v.x, xv.x, fmaf(v.y, xv.y, sr));
+      si = fmaf(v.x, xv.y, fmaf(-v.y, xv.x, si));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    const zf ts = make_float2(t * sr, t * si);
+    for (int r = j + 1 + lane; r < n; r += 32) {
+      const zf v = r == j + 1 ? make_float2(1.f, 0.f) : a[r + (size_t)j * n];
+      x[r] = zsub(x[r], zmul(v, ts));
+    }
+    __syncwarp();
+  }
+  zd* xo = X64 + (size_t)k * n * b + (size_t)i * n;
+  for (int r = lane; r < n; r += 32) xo[r] = zmake(x[r].x, x[r].y);
+}
+
+// ------------------------------------------------------------ small eigenproblem
+// H w = theta G w for b x b Hermitian H and HPD G (b <= 32, even): Cholesky
+// of G, standard form, cyclic parallel Jacobi with the round-robin pairing.
+constexpr int BMAX = 32;
+
+__global__ void small_eig_kernel(const zd* __restrict__ Gg, const zd* __restrict__ Hg, int b,
+                                 double* __restrict__ theta, zd* __restrict__ Wg,
+                                 int* __restrict__ stat) {
+  __shared__ zd G[BMAX][BMAX + 1], A[BMAX][BMAX + 1], V[BMAX][BMAX + 1];
+  __shared__ double cs_[BMAX / 2], sn_[BMAX / 2];
+  __shared__ zd ph_[BMAX / 2];
+  __shared__ int pp_[BMAX / 2], qq_[BMAX / 2];
+  __shared__ double offn, totn;
+  __shared__ int fail;
+  const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const zd* gk = Gg + (size_t)k * b * b;
+  const zd* hk = Hg + (size_t)k * b * b;
+  for (int e = tid; e < b * b; e += nt) {
+    const int r = e % b, c = e / b;
+    G[r][c] = gk[e];
+    A[r][c] = hk[e];
+  }
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  // Cholesky G = L L^dagger (lower, in place), column by column
+  for (int c = 0; c < b; ++c) {
+    if (tid == 0) {
+      double p = G[c][c].x;
+      for (int t = 0; t < c; ++t) p -= G[c][t].x * G[c][t].x + G[c][t].y * G[c][t].y;
+      if (!(p > 0.0)) {
+        fail = 1;
+        p = 1.0;
+      }
+      G[c][c] = zmake(sqrt(p), 0.0);
+    }
+    __syncthreads();
+    for (int r = c + 1 + tid; r < b; r += nt) {
+      zd s = G[r][c];
+      for (int t = 0; t < c; ++t) s = zfnmac(G[r][t], G[c][t], s);
+      G[r][c] = zscale(s, 1.0 / G[c][c].x);
+    }
+    __syncthreads();
+  }
+  // A <- L^-1 A L^-dagger: forward substitution on columns, then on rows
+  for (int c = tid; c < b; c += nt)
+    for (int r = 0; r < b; ++r) {
+      zd s = A[r][c];
+      for (int t = 0; t < r; ++t) s = zsub(s, zmul(G[r][t], A[t][c]));
+      A[r][c] = zscale(s, 1.0 / G[r][r].x);
+    }
+  __syncthreads();
+  for (int r = tid; r < b; r += nt)
+    for (int c = 0; c < b; ++c) {
+      zd s = A[r][c];
+      for (int t = 0; t < c; ++t) s = zsub(s, zmul(A[r][t], zconj(G[c][t])));
+      A[r][c] = zscale(s, 1.0 / G[c][c].x);
+    }
+  __syncthreads();
+  for (int e = tid; e < b * b; e += nt) {
+    const int r = e % b, c = e / b;
+    V[r][c] = zmake(r == c ? 1.0 : 0.0, 0.0);
+    if (r == c) A[r][c].y = 0.0;
+  }
+  __syncthreads();
+  const int np = b / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) {
+      double o = 0.0, t = 0.0;
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) {
+          const double m2 = A[r][c].x * A[r][c].x + A[r][c].y * A[r][c].y;
+          t += m2;
+          if (r != c) o += m2;
+        }
+      offn = o;
+      totn = t;
+    }
+    __syncthreads();
+    if (offn <= 1e-30 * totn) break;
+    for (int rd = 0; rd < b - 1; ++rd) {
+      if (tid < np) {
+        int p, q;
+        if (tid == 0) {
+          p = rd % (b - 1);
+          q = b - 1;
+        } else {
+          p = (rd + tid) % (b - 1);
+          q = (rd - tid + (b - 1)) % (b - 1);
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        const zd c = A[p][q];
+        const double ca = hypot(c.x, c.y);
+        double cs = 1.0, sn = 0.0;
+        zd ph = zmake(1.0, 0.0);
+        if (ca > 0.0) {
+          ph = zmake(c.x / ca, c.y / ca);
+          const double zeta = (A[q][q].x - A[p][p].x) / (2.0 * ca);
+          const double t = zeta >= 0.0 ? 1.0 / (zeta + sqrt(1.0 + zeta * zeta))
+                                       : -1.0 / (-zeta + sqrt(1.0 + zeta * zeta));
+          cs = 1.0 / sqrt(1.0 + t * t);
+          sn = t * cs;
+        }
+        pp_[tid] = p;
+        qq_[tid] = q;
+        cs_[tid] = cs;
+        sn_[tid] = sn;
+        ph_[tid] = ph;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J with J = [[cs, sn], [-sn conj(ph), cs conj(ph)]]
+      for (int e = tid; e < np * b; e += nt) {
+        const int u = e / b, r = e % b, p = pp_[u], q = qq_[u];
+        const double cs = cs_[u], sn = sn_[u];
+        const zd cph = zconj(ph_[u]);
+        const zd ap = A[r][p], aq = zmul(A[r][q], cph);
+        A[r][p] = zsub(zscale(ap, cs), zscale(aq, sn));
+        A[r][q] = zadd(zscale(ap, sn), zscale(aq, cs));
+        const zd vp = V[r][p], vq = zmul(V[r][q], cph);
+        V[r][p] = zsub(zscale(vp, cs), zscale(vq, sn));
+        V[r][q] = zadd(zscale(vp, sn), zscale(vq, cs));
+      }
+      __syncthreads();
+      // rows: A <- J^dagger A
+      for (int e = tid; e < np * b; e += nt) {
+        const int u = e / b, c = e % b, p = pp_[u], q = qq_[u];
+        const double cs = cs_[u], sn = sn_[u];
+        const zd ap = A[p][c], aq = zmul(A[q][c], ph_[u]);
+        A[p][c] = zsub(zscale(ap, cs), zscale(aq, sn));
+        A[q][c] = zadd(zscale(ap, sn), zscale(aq, cs));
+      }
+      __syncthreads();
+    }
+  }
+  // sort ascending (selection, one thread), W = L^-dagger V
+  __shared__ int ord[BMAX];
+  __shared__ double ev[BMAX];
+  if (tid == 0) {
+    for (int r = 0; r < b; ++r) {
+      ev[r] = A[r][r].x;
+      ord[r] = r;
+    }
+    for (int r = 0; r < b; ++r)
+      for (int s = r + 1; s < b; ++s)
+        if (ev[ord[s]] < ev[ord[r]]) {
+          const int t = ord[r];
+          ord[r] = ord[s];
+          ord[s] = t;
+        }
+  }
+  __syncthreads();
+  for (int c = tid; c < b; c += nt) {
+    const int oc = ord[c];
+    theta[(size_t)k * b + c] = ev[oc];
+    // back substitution L^dagger w = v
+    for (int r = b - 1; r >= 0; --r) {
+      zd s = V[r][oc];
+      for (int t = r + 1; t < b; ++t) s = zsub(s, zmul(zconj(G[t][r]), Wg[(size_t)k * b * b + t + (size_t)c * b]));
+      Wg[(size_t)k * b * b + r + (size_t)c * b] = zscale(s, 1.0 / G[r][r].x);
+    }
+  }
+  if (tid == 0 && fail) stat[k] = BS_ENOTPD;
+}
+
+// ------------------------------------------------------------ residuals and output
+// r_i = C X w_i - theta_i X w_i; bound_i = ||r_i||^2 / (lambda_{b+1}(T) - theta_i).
+__global__ void residual_kernel(const zd* __restrict__ CX, const zd* __restrict__ X,
+                                const zd* __restrict__ W, const double* __restrict__ theta,
+                                const double* __restrict__ lamT, int lstride, int n, int b,
+                                int nbands, double tol, double floor2, double* __restrict__ omega,
+                                int* __restrict__ stat) {
+  __shared__ int bad;
+  const int k = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const zd* cx = CX + (size_t)k * n * b;
+  const zd* x = X + (size_t)k * n * b;
+  const zd* w = W + (size_t)k * b * b;
+  const double gapref = lamT[(size_t)k * lstride + b];
+  for (int i = warp; i < nbands; i += nw) {
+    const double th = theta[(size_t)k * b + i];
+    double s2 = 0.0;
+    for (int r = lane; r < n; r += 32) {
+      zd acc = zmake(0.0, 0.0);
+      for (int l = 0; l < b; ++l) {
+        const zd wl = w[l + (size_t)i * b];
+        acc = zfma(zsub(cx[r + (size_t)l * n], zscale(x[r + (size_t)l * n], th)), wl, acc);
+      }
+      s2 = fma(acc.x, acc.x, fma(acc.y, acc.y, s2));
+    }
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) {
+      const double gap = fmax(gapref - th, 1e-300);
+      const double bound = s2 / gap;
+      if (!(bound <= tol * 2.0 * fmax(th, floor2)) || !isfinite(th)) atomicOr(&bad, 1);
+      omega[(size_t)k * nbands + i] = sqrt(fmax(th, 0.0));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && stat[k] == 0 && bad) stat[k] = BS_ENOCONV;
+}
+
+__global__ void zero_int_kernel(int* p, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 0;
+}
+
+}  // namespace
+
+// Block size of the refinement: nbands plus up to 8 guard vectors, even
+// (round-robin Jacobi), at most BMAX and at most n - 1 (T's eigenvalue
+// b + 1 serves as the gap reference).  Callers ensure nbands + 2 <= n.
+int bs_mixed_guard(int nbands, int n) {
+  int b = (nbands + 8 + 3) / 4 * 4;
+  if (b > BMAX) b = BMAX;
+  if (b > n - 1) b = n - 1;
+  if (b & 1) --b;
+  if (b < nbands) b = nbands + (nbands & 1);
+  return b;
+}
+
+int bs_launch_builder_mixed(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,
+                            double q2x, double q2y, zd* C64, zf* C32, cudaStream_t s) {
+  const size_t nn = (size_t)n * n;
+  builder_mixed_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Cm, n, Q, nk, q1x, q1y, q2x,
+                                                                    q2y, C64, C32);
+  BS_CHECK_LAUNCH("builder_mixed_kernel");
+  return BS_OK;
+}
+
+int bs_launch_mixed_refine(const MixedWs& w, int n, int kb, int nbands, int b, double tol,
+                           double floor2, double* omega, int* stat, cudaStream_t s) {
+  zero_int_kernel<<<(kb + 255) / 256, 256, 0, s>>>(stat, kb);
+  BS_CHECK_LAUNCH("zero_int_kernel");
+  tri_eigvec_kernel<<<kb, 64, 0, s>>>(w.de, w.beta, w.lamT, n, b, b + 1, w.scratch, w.Y, w.phase);
+  BS_CHECK_LAUNCH("tri_eigvec_kernel");
+  backtransform_kernel<<<dim3(kb, (b + 7) / 8), 256, 0, s>>>(w.C32, w.tau, w.phase, w.Y, n, b,
+                                                              w.X32, w.X64);
+  BS_CHECK_LAUNCH("backtransform_kernel");
+  const zd one = zmake(1.0, 0.0);
+  const long nn = (long)n * n, nb = (long)n * b, bb = (long)b * b;
+  TRY_LAUNCH(bs_launch_zgemm(false, false, n, b, n, one, w.C64, n, nn, w.X64, n, nb, nullptr, 0,
+                             w.CX, n, nb, kb, 0, s));
+  TRY_LAUNCH(bs_launch_zgemm(true, false, b, b, n, one, w.X64, n, nb, w.X64, n, nb, nullptr, 0,
+                             w.G, b, bb, kb, 0, s));
+  TRY_LAUNCH(bs_launch_zgemm(true, false, b, b, n, one, w.X64, n, nb, w.CX, n, nb, nullptr, 0,
+                             w.H, b, bb, kb, 0, s));
+  small_eig_kernel<<<kb, 128, 0, s>>>(w.G, w.H, b, w.theta, w.W, stat);
+  BS_CHECK_LAUNCH("small_eig_kernel");
+  residual_kernel<<<kb, 256, 0, s>>>(w.CX, w.X64, w.W, w.theta, w.lamT, b + 1, n, b, nbands, tol,
+                                     floor2, omega, stat);
+  BS_CHECK_LAUNCH("residual_kernel");
+  return BS_OK;
+}

@@ -1,6 +1,7 @@
-// Batched FP64 Householder reduction of Hermitian matrices to real
-// symmetric tridiagonal form (the first stage of the eigensolve of
-// Eq. (eigenvalueproblem) once the pencil is reduced to standard form).
+// Batched Householder reduction of Hermitian matrices to tridiagonal form
+// (the first stage of the eigensolve of Eq. (eigenvalueproblem) once the
+// pencil is reduced to standard form), in FP64 (the plain path) or FP32
+// (the reduction of the mixed path, refined afterwards in FP64).
 //
 // Step j (j = 0 .. n-2) with reflector H_j = I - tau v v^dagger (tau real,
 // v[j+1] = 1) needs p = tau B v on the trailing block B = A[j+1:, j+1:],
@@ -10,8 +11,9 @@
 // lower triangle (each element is read and written once per step), and
 // the last tile of each matrix to finish (an arrival counter, no waiting)
 // reduces the tile partials, forms w, applies the update to column j+1
-// and builds the next reflector.  The arithmetic is FP64 and FMA bound on
-// GB300, so the tile loop is written for FP64 issue, not for bandwidth.
+// and builds the next reflector.  In FP64 the loop is bound by the FP64
+// pipe of GB300, so it is written for FP64 issue: 16 FMAs per element and
+// one shared-memory reduction of the row and column partials per tile.
 #include "bs_internal.h"
 
 namespace {
@@ -40,57 +42,76 @@ __device__ double block_sum(double v, double* sh) {
   return sh[NT / 32];
 }
 
-__device__ __forceinline__ zd ldg_cg(const zd* p) { return __ldcg(p); }
+template <typename C>
+__device__ __forceinline__ C ldg_cg(const C* p) { return __ldcg(p); }
 
-// Reflector of column c below the diagonal: x = A[c+1:n, c].  Writes v
-// (v[c+1] = 1), tau and the tridiagonal off-diagonal |beta| = ||x||.
-__device__ void householder(const zd* a, int n, int c, zd* v, double* tau_out, double* e_out,
-                            double* sh) {
+// Reflector of column c below the diagonal, x = A[c+1:n, c]: H x = beta e1
+// with beta = -(x0/|x0|) ||x||, tau = (|x0| + ||x||)/||x||, v = x / (x0 - beta).
+// The scalars are formed in FP64 for both precisions.  Writes v to the
+// vector buffer and to A[c+2:n, c], tau_j, beta_j and |beta_j|.
+template <typename R>
+__device__ void householder(typename Cplx<R>::T* a, int n, int c, typename Cplx<R>::T* v,
+                            double* tau_out, zd* beta_out, double* e_out, double* sh) {
+  typedef typename Cplx<R>::T C;
   const int tid = threadIdx.x, r0 = c + 1;
   double s = 0.0;
   for (int r = r0 + 1 + tid; r < n; r += NT) {
-    zd x = ldg_cg(a + r + (size_t)c * n);
-    s = fma(x.x, x.x, fma(x.y, x.y, s));
+    const C x = ldg_cg(a + r + (size_t)c * n);
+    s = fma((double)x.x, (double)x.x, fma((double)x.y, (double)x.y, s));
   }
   s = block_sum(s, sh);
-  const zd alpha = ldg_cg(a + r0 + (size_t)c * n);
+  const C al = ldg_cg(a + r0 + (size_t)c * n);
+  const zd alpha = zmake(al.x, al.y);
   const double aa = hypot(alpha.x, alpha.y);
   const double nu = sqrt(fma(aa, aa, s));
   double tau = 0.0;
-  zd scale = zmake(0.0, 0.0);
+  zd scale = zmake(0.0, 0.0), beta = zmake(0.0, 0.0);
   if (nu > 0.0) {
-    const zd beta = aa > 0.0 ? zscale(alpha, -nu / aa) : zmake(-nu, 0.0);
+    beta = aa > 0.0 ? zscale(alpha, -nu / aa) : zmake(-nu, 0.0);
     tau = (aa + nu) / nu;
     const zd den = zsub(alpha, beta);
     const double d2 = den.x * den.x + den.y * den.y;
     scale = zmake(den.x / d2, -den.y / d2);
   }
-  for (int r = r0 + 1 + tid; r < n; r += NT) v[r] = zmul(ldg_cg(a + r + (size_t)c * n), scale);
+  for (int r = r0 + 1 + tid; r < n; r += NT) {
+    C* ap = a + r + (size_t)c * n;
+    const C x = ldg_cg(ap);
+    const zd y = zmul(zmake(x.x, x.y), scale);
+    const C vr = Cplx<R>::make((R)y.x, (R)y.y);
+    v[r] = vr;
+    *ap = vr;
+  }
   if (tid == 0) {
-    v[r0] = zmake(1.0, 0.0);
+    v[r0] = Cplx<R>::make((R)1, (R)0);
     *tau_out = tau;
+    *beta_out = beta;
     *e_out = nu;
   }
 }
 
-__global__ void __launch_bounds__(NT) tridiag_init_kernel(const zd* __restrict__ A, int n,
-                                                          zd* __restrict__ vec,
+template <typename R>
+__global__ void __launch_bounds__(NT) tridiag_init_kernel(typename Cplx<R>::T* __restrict__ A,
+                                                          int n,
+                                                          typename Cplx<R>::T* __restrict__ vec,
                                                           double* __restrict__ de,
                                                           double* __restrict__ tau,
+                                                          zd* __restrict__ beta,
                                                           unsigned* __restrict__ count) {
+  typedef typename Cplx<R>::T C;
   __shared__ double sh[NT / 32 + 1];
   const int b = blockIdx.x;
-  const zd* a = A + (size_t)b * n * n;
-  zd* vb = vec + (size_t)b * 3 * n;
-  for (int r = threadIdx.x; r < 3 * n; r += NT) vb[r] = zmake(0.0, 0.0);
+  C* a = A + (size_t)b * n * n;
+  C* vb = vec + (size_t)b * 3 * n;
+  for (int r = threadIdx.x; r < 3 * n; r += NT) vb[r] = Cplx<R>::make((R)0, (R)0);
   __syncthreads();
   double* d = de + (size_t)b * 2 * n;
   if (threadIdx.x == 0) {
     d[0] = a[0].x;
     count[b] = 0u;
-    tau[b] = 0.0;
+    tau[(size_t)b * n] = 0.0;
+    beta[(size_t)b * n] = zmake(0.0, 0.0);
   }
-  if (n > 1) householder(a, n, 0, vb, tau + b, d + n, sh);
+  if (n > 1) householder<R>(a, n, 0, vb, tau + (size_t)b * n, beta + (size_t)b * n, d + n, sh);
 }
 
 __device__ __forceinline__ void tri_index(int l, int& bi, int& bk) {
@@ -101,72 +122,95 @@ __device__ __forceinline__ void tri_index(int l, int& bi, int& bk) {
   bk = l - r * (r + 1) / 2;
 }
 
-__global__ void __launch_bounds__(NT, 2) tridiag_step_kernel(zd* __restrict__ A, int n, int j,
-                                                             zd* __restrict__ vec,
-                                                             zd* __restrict__ part,
+template <typename R>
+__global__ void __launch_bounds__(NT, 2) tridiag_step_kernel(typename Cplx<R>::T* __restrict__ A,
+                                                             int n, int j,
+                                                             typename Cplx<R>::T* __restrict__ vec,
+                                                             typename Cplx<R>::T* __restrict__ part,
                                                              double* __restrict__ de,
                                                              double* __restrict__ tau,
+                                                             zd* __restrict__ beta,
                                                              unsigned* __restrict__ count,
                                                              int ntl) {
+  typedef typename Cplx<R>::T C;
   // Thread (tx, ty) owns rows R*TS + tx + 16v and columns S*TS + ty + 16u,
   // u, v = 0..3: its 16 elements give 4 row and 4 column partials of p,
   // reduced once per tile through shared memory.
-  __shared__ zd vpS[TS], wpS[TS], vcS[TS];
-  __shared__ zd rowred[TS / 4][TS];   // [ty][row]
-  __shared__ zd colred[TS / 4][TS];   // [tx][col]
+  __shared__ C vpS[TS], wpS[TS], vcS[TS];
+  __shared__ C rowred[TS / 4][TS];   // [ty][row]
+  __shared__ C colred[TS / 4][TS];   // [tx][col]
   __shared__ double sh[NT / 32 + 1];
   __shared__ int is_last;
 
   const int b = blockIdx.y, tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int nt = (n + TS - 1) / TS, t0 = (j + 1) / TS, r0 = j + 1;
-  zd* a = A + (size_t)b * n * n;
-  zd* vb = vec + (size_t)b * 3 * n;
-  zd* vcur = vb + (size_t)(j & 1) * n;
-  zd* vprev = vb + (size_t)((j + 1) & 1) * n;
-  zd* w = vb + 2 * (size_t)n;
-  zd* pt = part + (size_t)b * nt * n;
+  const C zero = Cplx<R>::make((R)0, (R)0);
+  C* a = A + (size_t)b * n * n;
+  C* vb = vec + (size_t)b * 3 * n;
+  C* vcur = vb + (size_t)(j & 1) * n;
+  C* vprev = vb + (size_t)((j + 1) & 1) * n;
+  C* w = vb + 2 * (size_t)n;
+  C* pt = part + (size_t)b * nt * n;
 
   int bi, bk;
   tri_index(blockIdx.x, bi, bk);
-  const int R = t0 + bi, S = t0 + bk;
-  const int rbase = R * TS, sbase = S * TS;
+  const int Rt = t0 + bi, St = t0 + bk;
+  const int rbase = Rt * TS, sbase = St * TS;
 
   if (tid < TS) {
     const int s = sbase + tid;
     const bool ok = s < n && s >= r0;
-    vpS[tid] = ok ? vprev[s] : zmake(0.0, 0.0);
-    wpS[tid] = ok ? w[s] : zmake(0.0, 0.0);
-    vcS[tid] = ok ? vcur[s] : zmake(0.0, 0.0);
+    vpS[tid] = ok ? vprev[s] : zero;
+    wpS[tid] = ok ? w[s] : zero;
+    vcS[tid] = ok ? vcur[s] : zero;
   }
-  zd vpr[4], wpr[4], vcr[4], racc[4];
+  C vpr[4], wpr[4], vcr[4], racc[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const int r = rbase + tx + 16 * v;
     const bool ok = r < n && r >= r0;
-    vpr[v] = ok ? vprev[r] : zmake(0.0, 0.0);
-    wpr[v] = ok ? w[r] : zmake(0.0, 0.0);
-    vcr[v] = ok ? vcur[r] : zmake(0.0, 0.0);
-    racc[v] = zmake(0.0, 0.0);
+    vpr[v] = ok ? vprev[r] : zero;
+    wpr[v] = ok ? w[r] : zero;
+    vcr[v] = ok ? vcur[r] : zero;
+    racc[v] = zero;
   }
   __syncthreads();
 
+  // FP32: all 16 loads first (the stores below could alias them as far as
+  // the compiler knows, which would serialise one load latency per element
+  // in a loop that is otherwise light).  FP64: interleaved, the FP64 pipe
+  // hides the latency and the registers are needed for the accumulators.
+  constexpr bool kHoist = sizeof(R) == 4;
+  C xs[4][4];
+  if constexpr (kHoist) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = sbase + ty + 16 * u;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int r = rbase + tx + 16 * v;
+        xs[u][v] = (s >= r0 && r < n && r >= s) ? a[r + (size_t)s * n] : zero;
+      }
+    }
+  }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int sl = ty + 16 * u, s = sbase + sl;
-    const zd vps = vpS[sl], wps = wpS[sl], vcs = vcS[sl];
-    zd cacc = zmake(0.0, 0.0);
+    const C vps = vpS[sl], wps = wpS[sl], vcs = vcS[sl];
+    C cacc = zero;
     const bool sok = s >= r0;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int r = rbase + tx + 16 * v;
       if (sok && r < n && r >= s) {
-        zd* ap = a + r + (size_t)s * n;
-        zd x = *ap;
+        C x;
+        if constexpr (kHoist) x = xs[u][v];
+        else x = a[r + (size_t)s * n];
         x = zfnmac(vpr[v], wps, x);
         x = zfnmac(wpr[v], vps, x);
-        if (r == s) x.y = 0.0;
-        *ap = x;
+        if (r == s) x.y = (R)0;
+        a[r + (size_t)s * n] = x;
         racc[v] = zfma(x, vcs, racc[v]);
         if (r != s) cacc = zfma(zconj(x), vcr[v], cacc);
       }
@@ -179,22 +223,23 @@ __global__ void __launch_bounds__(NT, 2) tridiag_step_kernel(zd* __restrict__ A,
   if (tid < 2 * TS) {
     const bool isrow = tid < TS;
     const int l = isrow ? tid : tid - TS;
-    zd acc = zmake(0.0, 0.0);
+    C acc = zero;
 #pragma unroll
     for (int q = 0; q < TS / 4; ++q) acc = zadd(acc, isrow ? rowred[q][l] : colred[q][l]);
-    if (R == S) {
+    if (Rt == St) {
       // diagonal tile: row and column partials of the same index meet here
       if (isrow) rowred[0][l] = acc;
       else colred[0][l] = acc;
     } else if (isrow) {
-      if (rbase + l < n) pt[(size_t)S * n + rbase + l] = acc;
+      if (rbase + l < n) pt[(size_t)St * n + rbase + l] = acc;
     } else {
-      pt[(size_t)R * n + sbase + l] = acc;
+      pt[(size_t)Rt * n + sbase + l] = acc;
     }
   }
-  if (R == S) {
+  if (Rt == St) {
     __syncthreads();
-    if (tid < TS && rbase + tid < n) pt[(size_t)R * n + rbase + tid] = zadd(rowred[0][tid], colred[0][tid]);
+    if (tid < TS && rbase + tid < n)
+      pt[(size_t)Rt * n + rbase + tid] = zadd(rowred[0][tid], colred[0][tid]);
   }
   __threadfence();
   __syncthreads();
@@ -204,38 +249,40 @@ __global__ void __launch_bounds__(NT, 2) tridiag_step_kernel(zd* __restrict__ A,
   __threadfence();
 
   // ---- epilogue: one CTA per matrix
-  const double tj = tau[b];
+  const R tj = (R)tau[(size_t)b * n + j];
   double kp = 0.0;
   for (int rr = r0 + tid; rr < n; rr += NT) {
-    zd p = zmake(0.0, 0.0);
+    C p = zero;
     for (int t = t0; t < nt; ++t) p = zadd(p, ldg_cg(pt + (size_t)t * n + rr));
     p = zscale(p, tj);
     w[rr] = p;
-    const zd v = vcur[rr];
-    kp = fma(v.x, p.x, fma(v.y, p.y, kp));
+    const C v = vcur[rr];
+    kp = fma((double)v.x, (double)p.x, fma((double)v.y, (double)p.y, kp));
   }
-  const double K = 0.5 * tj * block_sum(kp, sh);
+  const R K = (R)(0.5 * (double)tj * block_sum(kp, sh));
   for (int rr = r0 + tid; rr < n; rr += NT) {
-    const zd v = vcur[rr];
+    const C v = vcur[rr];
     w[rr] = zsub(w[rr], zscale(v, K));
   }
   __syncthreads();
-  const zd wj = w[r0], vj = vcur[r0];
+  const C wj = w[r0], vj = vcur[r0];
   for (int rr = r0 + tid; rr < n; rr += NT) {
-    zd* ap = a + rr + (size_t)r0 * n;
-    zd x = ldg_cg(ap);
+    C* ap = a + rr + (size_t)r0 * n;
+    C x = ldg_cg(ap);
     x = zfnmac(vcur[rr], wj, x);
     x = zfnmac(w[rr], vj, x);
-    if (rr == r0) x.y = 0.0;
+    if (rr == r0) x.y = (R)0;
     *ap = x;
   }
   __syncthreads();
   double* d = de + (size_t)b * 2 * n;
   if (tid == 0) {
-    d[r0] = a[r0 + (size_t)r0 * n].x;
+    d[r0] = (double)a[r0 + (size_t)r0 * n].x;
     count[b] = 0u;
   }
-  if (r0 + 1 < n) householder(a, n, r0, vprev, tau + b, d + n + r0, sh);
+  if (r0 + 1 < n)
+    householder<R>(a, n, r0, vprev, tau + (size_t)b * n + r0, beta + (size_t)b * n + r0,
+                   d + n + r0, sh);
 }
 
 }  // namespace
@@ -243,16 +290,24 @@ __global__ void __launch_bounds__(NT, 2) tridiag_step_kernel(zd* __restrict__ A,
 size_t bs_tridiag_vec_elems(int n) { return 3 * (size_t)n; }
 size_t bs_tridiag_part_elems(int n) { return (size_t)((n + TS - 1) / TS) * n; }
 
-int bs_launch_tridiag(zd* A, int n, int batch, zd* vec, zd* part, double* de, double* tau,
+template <typename R>
+int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
+                      typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
                       unsigned* count, cudaStream_t s) {
-  tridiag_init_kernel<<<batch, NT, 0, s>>>(A, n, vec, de, tau, count);
+  tridiag_init_kernel<R><<<batch, NT, 0, s>>>(A, n, vec, de, tau, beta, count);
   BS_CHECK_LAUNCH("tridiag_init_kernel");
   const int nt = (n + TS - 1) / TS;
   for (int j = 0; j + 1 < n; ++j) {
     const int m = nt - (j + 1) / TS;
     const int ntl = m * (m + 1) / 2;
-    tridiag_step_kernel<<<dim3(ntl, batch), NT, 0, s>>>(A, n, j, vec, part, de, tau, count, ntl);
+    tridiag_step_kernel<R><<<dim3(ntl, batch), NT, 0, s>>>(A, n, j, vec, part, de, tau, beta,
+                                                           count, ntl);
     BS_CHECK_LAUNCH("tridiag_step_kernel");
   }
   return BS_OK;
 }
+
+template int bs_launch_tridiag<double>(zd*, int, int, zd*, zd*, double*, double*, zd*, unsigned*,
+                                       cudaStream_t);
+template int bs_launch_tridiag<float>(zf*, int, int, zf*, zf*, double*, double*, zd*, unsigned*,
+                                      cudaStream_t);
