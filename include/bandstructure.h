@@ -166,6 +166,24 @@ int bs_reduced_matrix(bs_cell* cell, const double* Q, double* out, void* stream)
 int bs_tridiag_eigenvalues(const double* d, const double* e, int n, int batch, int nbands,
                            double* lam_out, void* stream);
 
+/*
+ * bs_gemm_bf16 - the tensor-core contraction primitive on its own:
+ * D[z][n][m] = sum_k A[z][m][k] B[z][n][k] for z < batch, with BF16
+ * operands (raw 16-bit patterns) and FP32 results accumulated in tensor
+ * memory.  The library uses it on "digit planes" (small-integer BF16
+ * values) for which every product and every partial sum is exact, to
+ * evaluate the form-factor sums (Eqs. (eo), (ep)) and the Rayleigh-Ritz
+ * products of the mixed path at FP64 accuracy.
+ *   A : batch x M x K, row-major (K contiguous); host or device.
+ *   B : batch x N x K, row-major; host or device.
+ *   D : batch x N x M, n-major (D[z][n][m] at (z N + n) M + m); host or device.
+ * Requires 8 <= K <= 4096 with K % 8 == 0 and 16-byte aligned device
+ * operands.  Synchronises `stream`.  BS_ECUDA if a pipeline wait reached
+ * its iteration limit (the kernel then returns without results).
+ */
+int bs_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K, int batch,
+                 void* stream);
+
 /* bs_cell_dims - N (plane waves) and n = 2N (eigen dimension). */
 int bs_cell_dims(const bs_cell* cell, int* N, int* n);
 

@@ -58,6 +58,7 @@ def _load():
         "bs_phase_times": [vp, dp],
         "bs_launch_count": [ctypes.POINTER(ctypes.c_longlong)],
         "bs_tridiag_eigenvalues": [dp, dp, i32, i32, i32, dp, vp],
+        "bs_gemm_bf16": [dp, dp, dp, i32, i32, i32, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -73,7 +74,8 @@ _lib = _load()
 #: every symbol the C header declares (checked by the tests)
 EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_factors",
             "bs_reduced_matrix", "bs_cell_dims", "bs_sync", "bs_destroy_cell", "bs_last_error",
-            "bs_set_profiling", "bs_phase_times", "bs_launch_count", "bs_tridiag_eigenvalues"]
+            "bs_set_profiling", "bs_phase_times", "bs_launch_count", "bs_tridiag_eigenvalues",
+            "bs_gemm_bf16"]
 
 
 def bs_last_error() -> str:
@@ -95,7 +97,8 @@ def _ptr(x, dtype):
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
         import torch
-        tdt = {np.float64: torch.float64, np.uint16: torch.uint16, np.int32: torch.int32}[dtype]
+        tdt = {np.float64: torch.float64, np.uint16: torch.uint16, np.int32: torch.int32,
+               np.float32: torch.float32}[dtype]
         if x.dtype != tdt or not x.is_contiguous():
             raise TypeError(f"expected a contiguous {tdt} tensor")
         return x.data_ptr()
@@ -160,6 +163,15 @@ def bs_tridiag_eigenvalues(d, e, nbands: int, lam_out, stream=None):
     _check(_lib.bs_tridiag_eigenvalues(_ptr(d, np.float64), _ptr(e, np.float64), n, batch,
                                        int(nbands), _ptr(lam_out, np.float64), _stream(stream)))
     return lam_out
+
+
+def bs_gemm_bf16(A, B, D, stream=None):
+    """A: (batch, M, K) uint16 BF16 bits, B: (batch, N, K), D: (batch, N, M) float32."""
+    batch, M, K = (int(x) for x in A.shape)
+    N = int(B.shape[1])
+    _check(_lib.bs_gemm_bf16(_ptr(A, np.uint16), _ptr(B, np.uint16), _ptr(D, np.float32), M, N, K,
+                             batch, _stream(stream)))
+    return D
 
 
 def bs_cell_dims(cell):

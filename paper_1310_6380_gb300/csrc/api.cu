@@ -111,8 +111,12 @@ static int copy_in(void* ddst, const void* src, size_t bytes, cudaStream_t s) {
 
 static void free_workspace(bs_cell* c) {
   void* mixed[] = {c->d_C32, c->d_vec32, c->d_part32, c->d_lamT, c->d_scr, c->d_mY, c->d_mphase,
-                   c->d_X32, c->d_X64, c->d_CX, c->d_mG, c->d_H, c->d_W, c->d_theta, c->d_beta};
+                   c->d_X32, c->d_X64, c->d_CX, c->d_mG, c->d_H, c->d_W, c->d_theta, c->d_beta,
+                   c->d_cxA, c->d_cxB, c->d_cxD, c->d_cxeA, c->d_cxeB};
   for (void* p : mixed) cudaFree(p);
+  c->d_cxA = c->d_cxB = nullptr;
+  c->d_cxD = nullptr;
+  c->d_cxeA = c->d_cxeB = nullptr;
   c->d_C32 = c->d_vec32 = c->d_part32 = c->d_X32 = nullptr;
   c->d_lamT = c->d_scr = c->d_mY = c->d_theta = nullptr;
   c->d_mphase = c->d_X64 = c->d_CX = c->d_mG = c->d_H = c->d_W = c->d_beta = nullptr;
@@ -168,6 +172,13 @@ static int ensure_workspace(bs_cell* c, int kb, int nb) {
     TRY(dalloc(&c->d_H, (size_t)kb * b * b, "H"));
     TRY(dalloc(&c->d_W, (size_t)kb * b * b, "W"));
     TRY(dalloc(&c->d_theta, (size_t)kb * b, "theta"));
+    size_t ca = 0, cb = 0, cd = 0;
+    bs_cx_tc_elems(n, b, kb, &ca, &cb, &cd);
+    TRY(dalloc(&c->d_cxA, ca, "C digit planes"));
+    TRY(dalloc(&c->d_cxB, cb, "X digit planes"));
+    TRY(dalloc(&c->d_cxD, cd, "C X digit-pair products"));
+    TRY(dalloc(&c->d_cxeA, (size_t)kb * n, "C exponents"));
+    TRY(dalloc(&c->d_cxeB, (size_t)kb * b, "X exponents"));
     c->bcap = b;
   }
   c->kcap = kb;
@@ -262,6 +273,13 @@ extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
   if (!r) r = dalloc(&c->d_Pp, 12 * NN, "P");
   if (!r) r = dalloc(&c->d_Cm, 6 * nn, "Cm");
   if (!r) r = dalloc(&c->d_info, 4, "info");
+  size_t sa = 0, sb = 0, sd = 0;
+  bs_fields_tc_elems(P, c->D, &sa, &sb, &sd);
+  if (!r) r = dalloc(&c->d_sliceA, sa, "field digit planes");
+  if (!r) r = dalloc(&c->d_sliceB, sb, "exponential digit planes");
+  if (!r) r = dalloc(&c->d_sliceD, sd, "digit-pair products");
+  if (!r) r = dalloc(&c->d_expA, 3 * (size_t)P, "field exponents");
+  if (!r) r = dalloc(&c->d_expB, 2 * (size_t)c->D, "table exponents");
   if (r) {
     bs_destroy_cell(c);
     return r;
@@ -304,6 +322,11 @@ extern "C" int bs_destroy_cell(bs_cell* c) {
   cudaFree(c->d_Pp);
   cudaFree(c->d_Cm);
   cudaFree(c->d_info);
+  cudaFree(c->d_sliceA);
+  cudaFree(c->d_sliceB);
+  cudaFree(c->d_sliceD);
+  cudaFree(c->d_expA);
+  cudaFree(c->d_expB);
   delete c;
   return BS_OK;
 }
@@ -326,7 +349,7 @@ extern "C" int bs_assemble(bs_cell* c, void* stream) {
   }
   cudaStream_t s = (cudaStream_t)stream;
   const size_t NN = (size_t)c->N * c->N;
-  CK(cudaMemsetAsync(c->d_info, 0, sizeof(int), s), "bs_assemble");
+  CK(cudaMemsetAsync(c->d_info, 0, 2 * sizeof(int), s), "bs_assemble");
   for (int i = 0; i < PH_COUNT; ++i) c->prof_ready[i] = false;
   bs_phase_begin(c, PH_ASM, s);
   TRY(bs_launch_assembly(c, s));                                   // a1 + a2
@@ -344,12 +367,16 @@ extern "C" int bs_assemble(bs_cell* c, void* stream) {
 }
 
 static int check_info(bs_cell* c, cudaStream_t s) {
-  int info = 0;
-  CK(cudaMemcpyAsync(&info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, s), "info");
+  int info[2] = {0, 0};
+  CK(cudaMemcpyAsync(info, c->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "info");
   CK(cudaStreamSynchronize(s), "sync");
-  if (info) {
+  if (info[0]) {
     bs_set_error("Cholesky of a Gram matrix failed (not positive definite)");
     return BS_ENOTPD;
+  }
+  if (info[1]) {
+    bs_set_error("a tensor-core pipeline wait reached its limit");
+    return BS_ECUDA;
   }
   return BS_OK;
 }
@@ -395,6 +422,8 @@ static int solve_chunk_mixed(bs_cell* c, int kb, int nbands, cudaStream_t s) {
   w.lamT = c->d_lamT; w.scratch = c->d_scr; w.Y = c->d_mY; w.phase = c->d_mphase;
   w.X32 = c->d_X32; w.X64 = c->d_X64; w.CX = c->d_CX; w.G = c->d_mG; w.H = c->d_H; w.W = c->d_W;
   w.theta = c->d_theta;
+  w.cxA = c->d_cxA; w.cxB = c->d_cxB; w.cxD = c->d_cxD; w.cxeA = c->d_cxeA; w.cxeB = c->d_cxeB;
+  w.err = c->d_info + 1;
   TRY(bs_launch_mixed_refine(w, n, kb, nbands, b, c->tol, c->floor2, c->d_w, c->d_stat, s));
   bs_phase_end(c, PH_REFINE, s);
   return BS_OK;
@@ -430,9 +459,10 @@ extern "C" int bs_solve_k(bs_cell* c, const double* Q, int nk, int nbands, doubl
     bs_set_error("bs_solve_k: nbands=%d outside [1, %d]", nbands, c->n);
     return BS_EINVAL;
   }
-  if (c->precision == BS_PREC_MIXED && (nbands > BS_MIXED_MAX_BANDS || nbands + 2 > c->n)) {
-    bs_set_error("bs_solve_k: the mixed path needs nbands <= %d and nbands + 2 <= n (%d)",
-                 BS_MIXED_MAX_BANDS, c->n);
+  if (c->precision == BS_PREC_MIXED &&
+      (nbands > BS_MIXED_MAX_BANDS || nbands + 2 > c->n || c->n > 2048)) {
+    bs_set_error("bs_solve_k: the mixed path needs nbands <= %d, nbands + 2 <= n and n <= 2048 "
+                 "(n = %d)", BS_MIXED_MAX_BANDS, c->n);
     return BS_EINVAL;
   }
   if (nk == 0) return BS_OK;
@@ -553,6 +583,56 @@ extern "C" int bs_phase_times(bs_cell* c, double ms[8]) {
 }
 
 // ------------------------------------------------------------------ diagnostics
+extern "C" int bs_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
+                            int batch, void* stream) {
+  if (!A || !B || !D || M < 1 || N < 1 || K < 8 || K % 8 || K > 4096 || batch < 1 ||
+      batch > 65535) {
+    bs_set_error("bs_gemm_bf16: need non-NULL arrays, M, N >= 1, 8 <= K <= 4096, K %% 8 == 0, "
+                 "1 <= batch <= 65535");
+    return BS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t na = (size_t)batch * M * K, nb = (size_t)batch * N * K, nd = (size_t)batch * M * N;
+  uint16_t *dA = nullptr, *dB = nullptr;
+  float* dD = nullptr;
+  int* err = nullptr;
+  const bool ad = is_device_ptr(A), bd = is_device_ptr(B), dd = is_device_ptr(D);
+  int r = BS_OK;
+  if (!ad) r = dalloc(&dA, na, "A");
+  if (!r && !bd) r = dalloc(&dB, nb, "B");
+  if (!r && !dd) r = dalloc(&dD, nd, "D");
+  if (!r) r = dalloc(&err, 1, "err");
+  cudaError_t ce = cudaSuccess;
+  if (!r) ce = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (!r && ce == cudaSuccess && !ad) ce = cudaMemcpyAsync(dA, A, na * 2, cudaMemcpyHostToDevice, s);
+  if (!r && ce == cudaSuccess && !bd) ce = cudaMemcpyAsync(dB, B, nb * 2, cudaMemcpyHostToDevice, s);
+  if (!r && ce != cudaSuccess) r = bs_cuda_status(ce, "bs_gemm_bf16 copy");
+  if (!r)
+    r = bs_launch_slice_gemm(ad ? A : dA, bd ? B : dB, dd ? D : dD, M, N, K, batch, (long)M * K,
+                             (long)N * K, M, (long)M * N, err, s);
+  int herr = 0;
+  if (!r && !dd) {
+    ce = cudaMemcpyAsync(D, dD, nd * 4, cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) r = bs_cuda_status(ce, "bs_gemm_bf16 copy out");
+  }
+  if (!r) {
+    ce = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) r = bs_cuda_status(ce, "bs_gemm_bf16 sync");
+    else if (herr) {
+      bs_set_error("bs_gemm_bf16: a tensor-core pipeline wait reached its limit");
+      r = BS_ECUDA;
+    }
+  } else {
+    cudaStreamSynchronize(s);
+  }
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dD);
+  cudaFree(err);
+  return r;
+}
+
 extern "C" int bs_tridiag_eigenvalues(const double* d, const double* e, int n, int batch,
                                       int nbands, double* lam_out, void* stream) {
   if (!d || (!e && n > 1) || !lam_out || n < 1 || batch < 1 || nbands < 1 || nbands > n ||

@@ -40,26 +40,8 @@ __global__ void exp_table_kernel(int P, int M, int D, zd* __restrict__ E) {
   E[i] = zmake(c, -s);
 }
 
-// Stage 1: Y[f][p][d] = sum_q g_f[p][q] E[d][q]
-__global__ void stage1_kernel(const uint16_t* __restrict__ phase, const double* __restrict__ tab,
-                              int nphase, int P, int D, const zd* __restrict__ E,
-                              zd* __restrict__ Y) {
-  extern __shared__ double g[];
-  int p = blockIdx.x, f = blockIdx.y;
-  for (int q = threadIdx.x; q < P; q += blockDim.x)
-    g[q] = tab[f * nphase + phase[(size_t)p * P + q]];
-  __syncthreads();
-  for (int d = threadIdx.x; d < D; d += blockDim.x) {
-    const zd* e = E + (size_t)d * P;
-    double ar = 0.0, ai = 0.0;
-    for (int q = 0; q < P; ++q) {
-      zd v = e[q];
-      ar = fma(g[q], v.x, ar);
-      ai = fma(g[q], v.y, ai);
-    }
-    Y[((size_t)f * P + p) * D + d] = zmake(ar, ai);
-  }
-}
+// Stage 1 (Y[f][p][d] = sum_q g_f[p][q] E[d][q]) runs as an exact-slice
+// tensor-core contraction, see slices.cu.
 
 // Stage 2: ghat[f][da][db] = w * sum_p E[da][p] Y[f][p][db]
 __global__ void stage2_kernel(int P, int D, double w, const zd* __restrict__ E,
@@ -99,9 +81,8 @@ int bs_launch_assembly(bs_cell* c, cudaStream_t s) {
   BS_CHECK_LAUNCH("table_kernel");
   exp_table_kernel<<<(D * P + 255) / 256, 256, 0, s>>>(P, c->M, D, c->d_E);
   BS_CHECK_LAUNCH("exp_table_kernel");
-  stage1_kernel<<<dim3(P, 3), 64, P * sizeof(double), s>>>(c->d_phase, c->d_table, c->nphase, P,
-                                                           D, c->d_E, c->d_Y);
-  BS_CHECK_LAUNCH("stage1_kernel");
+  // first stage (the bulk: 3 P^2 D complex-by-real products) on the tensor cores
+  TRY_LAUNCH(bs_launch_fields_tc(c, s));
   stage2_kernel<<<dim3(D, 3), 64, 0, s>>>(P, D, c->V / ((double)P * P), c->d_E, c->d_Y,
                                           c->d_ghat);
   BS_CHECK_LAUNCH("stage2_kernel");

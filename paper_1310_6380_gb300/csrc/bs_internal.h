@@ -107,7 +107,13 @@ struct bs_cell {
   zd* d_F;             // 6 x N x N: F_X^a = L_R^-1 diag(G_a) L_X^-dagger
   zd* d_Pp;            // 12 x N x N: F_X^a F_X^b^dagger, a <= b
   zd* d_Cm;            // 6 x n x n monomial matrices of C(k)
-  int* d_info;         // [0] Cholesky failure flags
+  int* d_info;         // [0] Cholesky failure, [1] tensor-core pipeline timeout
+  // exact-slice assembly operands
+  uint16_t* d_sliceA;  // 3 S P x Kp digit planes of the fields
+  uint16_t* d_sliceB;  // S 2D x Kp digit planes of the exponential table
+  float* d_sliceD;     // (S 2D) x (3 S P) digit-pair products
+  int* d_expA;         // 3 P row exponents
+  int* d_expB;         // 2D row exponents
 
   // per-k workspace (grown on demand)
   int kcap;            // matrices the workspace holds
@@ -132,6 +138,11 @@ struct bs_cell {
   zd* d_H;
   zd* d_W;
   double* d_theta;
+  uint16_t* d_cxA;     // Rayleigh-Ritz product digit planes of C(k)
+  uint16_t* d_cxB;     // ... of X
+  float* d_cxD;        // digit-pair products
+  int* d_cxeA;
+  int* d_cxeB;
   int bcap;            // guard-extended block size the mixed workspace holds
   double tol;          // relative omega tolerance the mixed path certifies
   double floor2;       // omega_floor^2 of the cell
@@ -183,6 +194,18 @@ int bs_launch_zgemm(bool conjA, bool conjB, int m, int nn, int k, zd alpha,
                     int tri, cudaStream_t s);
 int bs_launch_monomials(bs_cell* c, cudaStream_t s);
 
+// tc_gemm.cu / slices.cu: exact-slice contractions on tcgen05
+#define BS_SLICES_ASM 7   // digit planes per operand in the assembly (~2^-48)
+#define BS_SLICES_RR 6    // digit planes per operand in C X (~2^-41)
+// D[z][n][m] = sum_k A[z][m][k] B[z][n][k]; BF16 operands, K % 8 == 0, K <= 4096
+int bs_launch_slice_gemm(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
+                         int batch, long sA, long sB, long ldd, long sD, int* err, cudaStream_t s);
+int bs_launch_fields_tc(bs_cell* c, cudaStream_t s);
+size_t bs_fields_tc_elems(int P, int D, size_t* nA, size_t* nB, size_t* nD);
+int bs_launch_cx_tc(const zd* C, const zd* X, int n, int b, int kb, uint16_t* sA, uint16_t* sB,
+                    float* sD, int* eA, int* eB, zd* Y, int* err, cudaStream_t s);
+void bs_cx_tc_elems(int n, int b, int kb, size_t* nA, size_t* nB, size_t* nD);
+
 // builder.cu
 int bs_launch_builder(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,
                       double q2x, double q2y, zd* C, cudaStream_t s);
@@ -216,6 +239,12 @@ struct MixedWs {
   zd* H;          // kb x b x b
   zd* W;          // kb x b x b Ritz coefficients
   double* theta;  // kb x b Ritz values
+  uint16_t* cxA;  // C X digit planes and products (tensor cores)
+  uint16_t* cxB;
+  float* cxD;
+  int* cxeA;
+  int* cxeB;
+  int* err;       // tensor-core pipeline timeout flag
 };
 #define BS_MIXED_MAX_BANDS 24
 int bs_mixed_guard(int nbands, int n);

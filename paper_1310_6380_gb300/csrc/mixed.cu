@@ -473,9 +473,10 @@ int bs_launch_mixed_refine(const MixedWs& w, int n, int kb, int nbands, int b, d
                                                               w.X32, w.X64);
   BS_CHECK_LAUNCH("backtransform_kernel");
   const zd one = zmake(1.0, 0.0);
-  const long nn = (long)n * n, nb = (long)n * b, bb = (long)b * b;
-  TRY_LAUNCH(bs_launch_zgemm(false, false, n, b, n, one, w.C64, n, nn, w.X64, n, nb, nullptr, 0,
-                             w.CX, n, nb, kb, 0, s));
+  const long nb = (long)n * b, bb = (long)b * b;
+  // C X with FP64-level accuracy on the tensor cores (exact digit-plane contraction)
+  TRY_LAUNCH(bs_launch_cx_tc(w.C64, w.X64, n, b, kb, w.cxA, w.cxB, w.cxD, w.cxeA, w.cxeB, w.CX,
+                             w.err, s));
   TRY_LAUNCH(bs_launch_zgemm(true, false, b, b, n, one, w.X64, n, nb, w.X64, n, nb, nullptr, 0,
                              w.G, b, bb, kb, 0, s));
   TRY_LAUNCH(bs_launch_zgemm(true, false, b, b, n, one, w.X64, n, nb, w.CX, n, nb, nullptr, 0,

@@ -1,0 +1,247 @@
+// Digit-plane packing and FP64 recombination around the tcgen05 exact-slice
+// contraction (tc_gemm.cu), for the two contractions that use it:
+//
+//  * assembly, first separable stage of the form factors:
+//      Y_f[p][d] = sum_q g_f[p][q] E[d][q],  E[d][q] = exp(-i pi dd (2q+1)/P),
+//    A rows (f, s, p) = digits of g_f (per-row scale), B rows (t, d, re|im)
+//    = digits of E; K = P.
+//  * mixed path, Rayleigh-Ritz product Y = C X (C Hermitian n x n, X n x b):
+//      Re Y = [Cr | Ci] [Xr; -Xi],  Im Y = [Cr | Ci] [Xi; Xr],
+//    A rows (s, r) = digits of row r of [Cr | Ci] (row r of C is the
+//    conjugate of column r, so it is read contiguously), B rows
+//    (t, i, part) = digits of the two stacked columns; K = 2n.
+//
+// Digits: u = x 2^-e in (-1, 1) (e from frexp of the row maximum), then
+// t_0 = rint(64 u), r_0 = 64 u - t_0, t_s = rint(128 r_{s-1}), ...: every
+// |t_s| <= 64 and x = 2^e sum_s t_s 2^(-6 - 7s) + O(2^(e - 7 - 7S)).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "bs_internal.h"
+
+namespace {
+
+__device__ __forceinline__ uint16_t bf16_bits(double t) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn((float)t));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// block-wide max of |x| over a row; blockDim.x == 128
+__device__ double row_max(double v, double* sh) {
+  v = warp_max(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const double m = fmax(fmax(sh[0], sh[1]), fmax(sh[2], sh[3]));
+  __syncthreads();
+  return m;
+}
+
+__device__ __forceinline__ int row_exp(double m) {
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  return e;
+}
+
+__device__ __forceinline__ void put_digits(double x, int e, int S, uint16_t* out, size_t plane) {
+  double r = ldexp(x, -e) * 64.0;
+  for (int s = 0; s < S; ++s) {
+    const double t = rint(r);
+    out[(size_t)s * plane] = bf16_bits(t);
+    r = (r - t) * 128.0;
+  }
+}
+
+// ---- assembly operands
+// A rows (f, s, p): grid (P, 3), block 128
+__global__ void pack_fields_kernel(const uint16_t* __restrict__ phase,
+                                   const double* __restrict__ tab, int nphase, int P, int S,
+                                   int Kp, uint16_t* __restrict__ A, int* __restrict__ eA) {
+  __shared__ double sh[4];
+  const int p = blockIdx.x, f = blockIdx.y;
+  double m = 0.0;
+  for (int q = threadIdx.x; q < P; q += 128)
+    m = fmax(m, fabs(tab[f * nphase + phase[(size_t)p * P + q]]));
+  const int e = row_exp(row_max(m, sh));
+  const size_t plane = (size_t)P * Kp;
+  uint16_t* base = A + ((size_t)f * S * P + p) * Kp;
+  for (int q = threadIdx.x; q < Kp; q += 128) {
+    const double g = q < P ? tab[f * nphase + phase[(size_t)p * P + q]] : 0.0;
+    put_digits(g, e, S, base + q, plane);
+  }
+  if (threadIdx.x == 0) eA[f * P + p] = e;
+}
+
+// B rows (t, d, c): grid (2D), block 128; E from the exponential table
+__global__ void pack_exp_kernel(const zd* __restrict__ E, int P, int D, int S, int Kp,
+                                uint16_t* __restrict__ B, int* __restrict__ eB) {
+  __shared__ double sh[4];
+  const int row = blockIdx.x, d = row >> 1, c = row & 1;
+  double m = 0.0;
+  for (int q = threadIdx.x; q < P; q += 128) {
+    const zd v = E[(size_t)d * P + q];
+    m = fmax(m, fabs(c ? v.y : v.x));
+  }
+  const int e = row_exp(row_max(m, sh));
+  const size_t plane = (size_t)2 * D * Kp;
+  uint16_t* base = B + (size_t)row * Kp;
+  for (int q = threadIdx.x; q < Kp; q += 128) {
+    double x = 0.0;
+    if (q < P) {
+      const zd v = E[(size_t)d * P + q];
+      x = c ? v.y : v.x;
+    }
+    put_digits(x, e, S, base + q, plane);
+  }
+  if (threadIdx.x == 0) eB[row] = e;
+}
+
+// Y[f][p][d] = sum_{s,t} 2^(eA+eB-12-7(s+t)) Dm[(t,d,c)][(f,s,p)]
+__global__ void recombine_fields_kernel(const float* __restrict__ Dm, const int* __restrict__ eA,
+                                        const int* __restrict__ eB, int P, int D, int S,
+                                        zd* __restrict__ Y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)3 * P * D) return;
+  const int d = (int)(i % D), p = (int)((i / D) % P), f = (int)(i / ((size_t)P * D));
+  const size_t M = (size_t)3 * S * P;
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const size_t m = ((size_t)f * S + s) * P + p;
+    for (int t = 0; t < S; ++t) {
+      const double w = ldexp(1.0, -12 - 7 * (s + t));
+      const size_t nr = ((size_t)t * D + d) * 2;
+      re = fma(w, (double)Dm[nr * M + m], re);
+      im = fma(w, (double)Dm[(nr + 1) * M + m], im);
+    }
+  }
+  const int ea = eA[f * P + p];
+  Y[i] = zmake(ldexp(re, ea + eB[2 * d]), ldexp(im, ea + eB[2 * d + 1]));
+}
+
+// ---- Rayleigh-Ritz product operands
+// A rows (s, r) of [Cr | Ci] for each k: grid (n, kb), block 128
+__global__ void pack_cmat_kernel(const zd* __restrict__ C, int n, int S, int Kp,
+                                 uint16_t* __restrict__ A, int* __restrict__ eA) {
+  __shared__ double sh[4];
+  const int r = blockIdx.x, k = blockIdx.y;
+  const zd* col = C + (size_t)k * n * n + (size_t)r * n;   // column r = conj(row r)
+  double m = 0.0;
+  for (int c = threadIdx.x; c < n; c += 128) {
+    const zd v = col[c];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  const int e = row_exp(row_max(m, sh));
+  const size_t plane = (size_t)n * Kp;
+  uint16_t* base = A + (size_t)k * S * plane + (size_t)r * Kp;
+  for (int c = threadIdx.x; c < Kp; c += 128) {
+    double x = 0.0;
+    if (c < n) x = col[c].x;                   // Re C[r][c] = Re C[c][r]
+    else if (c < 2 * n) x = -col[c - n].y;     // Im C[r][c] = -Im C[c][r]
+    put_digits(x, e, S, base + c, plane);
+  }
+  if (threadIdx.x == 0) eA[(size_t)k * n + r] = e;
+}
+
+// B rows (t, i, part): part 0 = [Xr; -Xi], part 1 = [Xi; Xr]; grid (b, kb), block 128
+__global__ void pack_xmat_kernel(const zd* __restrict__ X, int n, int b, int S, int Kp,
+                                 uint16_t* __restrict__ B, int* __restrict__ eB) {
+  __shared__ double sh[4];
+  const int i = blockIdx.x, k = blockIdx.y;
+  const zd* x = X + (size_t)k * n * b + (size_t)i * n;
+  double m = 0.0;
+  for (int r = threadIdx.x; r < n; r += 128) m = fmax(m, fmax(fabs(x[r].x), fabs(x[r].y)));
+  const int e = row_exp(row_max(m, sh));
+  const size_t plane = (size_t)2 * b * Kp;
+  uint16_t* base0 = B + (size_t)k * S * plane + (size_t)(2 * i) * Kp;
+  uint16_t* base1 = base0 + Kp;
+  for (int c = threadIdx.x; c < Kp; c += 128) {
+    double v0 = 0.0, v1 = 0.0;
+    if (c < n) {
+      v0 = x[c].x;
+      v1 = x[c].y;
+    } else if (c < 2 * n) {
+      v0 = -x[c - n].y;
+      v1 = x[c - n].x;
+    }
+    put_digits(v0, e, S, base0 + c, plane);
+    put_digits(v1, e, S, base1 + c, plane);
+  }
+  if (threadIdx.x == 0) eB[(size_t)k * b + i] = e;
+}
+
+// Y[k][r + i n] = sum_{s,t} 2^(eA+eB-12-7(s+t)) (Dm[(t,i,0)][(s,r)] + i Dm[(t,i,1)][(s,r)])
+__global__ void recombine_cx_kernel(const float* __restrict__ Dm, const int* __restrict__ eA,
+                                    const int* __restrict__ eB, int n, int b, int S,
+                                    zd* __restrict__ Y) {
+  const int k = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * b) return;
+  const int r = idx % n, i = idx / n;
+  const size_t M = (size_t)S * n, Nn = (size_t)S * 2 * b;
+  const float* dk = Dm + (size_t)k * M * Nn;
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const size_t m = (size_t)s * n + r;
+    for (int t = 0; t < S; ++t) {
+      const double w = ldexp(1.0, -12 - 7 * (s + t));
+      const size_t nr = ((size_t)t * b + i) * 2;
+      re = fma(w, (double)dk[nr * M + m], re);
+      im = fma(w, (double)dk[(nr + 1) * M + m], im);
+    }
+  }
+  const int ex = eA[(size_t)k * n + r] + eB[(size_t)k * b + i];
+  Y[(size_t)k * n * b + idx] = zmake(ldexp(re, ex), ldexp(im, ex));
+}
+
+}  // namespace
+
+int bs_launch_fields_tc(bs_cell* c, cudaStream_t s) {
+  const int P = c->P, D = c->D, S = BS_SLICES_ASM, Kp = (P + 7) / 8 * 8;
+  pack_fields_kernel<<<dim3(P, 3), 128, 0, s>>>(c->d_phase, c->d_table, c->nphase, P, S, Kp,
+                                                c->d_sliceA, c->d_expA);
+  BS_CHECK_LAUNCH("pack_fields_kernel");
+  pack_exp_kernel<<<2 * D, 128, 0, s>>>(c->d_E, P, D, S, Kp, c->d_sliceB, c->d_expB);
+  BS_CHECK_LAUNCH("pack_exp_kernel");
+  const int M = 3 * S * P, N = 2 * S * D;
+  TRY_LAUNCH(bs_launch_slice_gemm(c->d_sliceA, c->d_sliceB, c->d_sliceD, M, N, Kp, 1,
+                                  (long)M * Kp, (long)N * Kp, M, (long)M * N, c->d_info + 1, s));
+  const size_t tot = (size_t)3 * P * D;
+  recombine_fields_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      c->d_sliceD, c->d_expA, c->d_expB, P, D, S, c->d_Y);
+  BS_CHECK_LAUNCH("recombine_fields_kernel");
+  return BS_OK;
+}
+
+size_t bs_fields_tc_elems(int P, int D, size_t* nA, size_t* nB, size_t* nD) {
+  const int S = BS_SLICES_ASM, Kp = (P + 7) / 8 * 8;
+  *nA = (size_t)3 * S * P * Kp;
+  *nB = (size_t)2 * S * D * Kp;
+  *nD = (size_t)3 * S * P * 2 * S * D;
+  return *nA + *nB;
+}
+
+int bs_launch_cx_tc(const zd* C, const zd* X, int n, int b, int kb, uint16_t* sA, uint16_t* sB,
+                    float* sD, int* eA, int* eB, zd* Y, int* err, cudaStream_t s) {
+  const int S = BS_SLICES_RR, Kp = (2 * n + 7) / 8 * 8;
+  pack_cmat_kernel<<<dim3(n, kb), 128, 0, s>>>(C, n, S, Kp, sA, eA);
+  BS_CHECK_LAUNCH("pack_cmat_kernel");
+  pack_xmat_kernel<<<dim3(b, kb), 128, 0, s>>>(X, n, b, S, Kp, sB, eB);
+  BS_CHECK_LAUNCH("pack_xmat_kernel");
+  const int M = S * n, N = 2 * S * b;
+  TRY_LAUNCH(bs_launch_slice_gemm(sA, sB, sD, M, N, Kp, kb, (long)M * Kp, (long)N * Kp, M,
+                                  (long)M * N, err, s));
+  recombine_cx_kernel<<<dim3((n * b + 255) / 256, kb), 256, 0, s>>>(sD, eA, eB, n, b, S, Y);
+  BS_CHECK_LAUNCH("recombine_cx_kernel");
+  return BS_OK;
+}
+
+void bs_cx_tc_elems(int n, int b, int kb, size_t* nA, size_t* nB, size_t* nD) {
+  const int S = BS_SLICES_RR, Kp = (2 * n + 7) / 8 * 8;
+  *nA = (size_t)kb * S * n * Kp;
+  *nB = (size_t)kb * S * 2 * b * Kp;
+  *nD = (size_t)kb * S * n * 2 * S * b;
+}

@@ -1,0 +1,255 @@
+// Exact-slice contractions on the tcgen05 tensor cores.
+//
+// D[z][n][m] = sum_k A[z][m][k] B[z][n][k] for BF16 A (M x K) and B (N x K),
+// both K-contiguous, with FP32 accumulation in tensor memory and FP32 D
+// stored n-major (column-major M x N).  One CTA computes a 128 x 128 tile:
+// a TMA producer thread streams 128 x 64 tiles of A and B through a
+// 4-stage shared-memory ring (128-byte swizzle, mbarrier completion), one
+// thread issues tcgen05.mma (kind::f16, M=128, N=128, K=16) into a TMEM
+// accumulator, and all four warps drain TMEM with tcgen05.ld.
+//
+// The library feeds it "digit planes": an FP64 operand x with per-row
+// scale 2^e is written as sum_s t_s 2^(e - 6 - 7s) with integer digits
+// |t_s| <= 64 (balanced rounding, radix 2^7).  Every product of two digits
+// is an integer of magnitude <= 2^12 and every sum over K <= 4096 terms
+// stays below 2^24, so the FP32 accumulation is exact, and the FP64
+// recombination of the digit-pair products reproduces the FP64 contraction
+// to about 2^-47 of |A||B| (six digits) on the BF16 tensor pipe.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "bs_internal.h"
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int TILE_A = BM * BK * 2, TILE_B = BN * BK * 2;   // bytes per stage
+constexpr int SMEM_BYTES = STAGES * (TILE_A + TILE_B) + 1024;
+constexpr long WAIT_LIMIT = 1L << 20;   // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: sets *err and returns false when the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;              // leading-dimension offset (unused when swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride-dimension offset
+  d |= (uint64_t)1 << 46;              // descriptor version of tcgen05
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__global__ void __launch_bounds__(128, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                      const __grid_constant__ CUtensorMap tmB, float* __restrict__ D, int M,
+                      int N, int K, long ldd, long strideD, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ uint32_t tmem_base;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * TILE_A;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, z = blockIdx.z;
+  const int nk = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, err)) break;
+      mbar_expect_tx(&full[s], TILE_A + TILE_B);
+      tma_load_3d(sA + s * TILE_A, &tmA, kb * BK, m0, z, &full[s]);
+      tma_load_3d(sB + s * TILE_B, &tmB, kb * BK, n0, z, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + s * TILE_A), b0 = smem_u32(sB + s * TILE_B);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t ad = sdesc(a0 + kk * 32), bd = sdesc(b0 + kk * 32);
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&empty[s]))
+          : "memory");
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&done))
+        : "memory");
+  }
+  __syncwarp();
+  // tcgen05.ld is warp-collective: every lane of a warp takes the same branch
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&done, 0u, err));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int m = m0 + warp * 32 + lane;
+    float* dz = D + (size_t)z * strideD;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < N) dz[(size_t)n * ldd + m] = __uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+int make_map(CUtensorMap* tm, const uint16_t* base, int K, int rows, int batch, long bstride,
+             int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    bs_set_error("cuTensorMapEncodeTiled is unavailable");
+    return BS_ECUDA;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)bstride * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    bs_set_error("cuTensorMapEncodeTiled failed (%d): K=%d rows=%d batch=%d", (int)r, K, rows,
+                 batch);
+    return BS_ECUDA;
+  }
+  return BS_OK;
+}
+
+}  // namespace
+
+int bs_launch_slice_gemm(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
+                         int batch, long sA, long sB, long ldd, long sD, int* err,
+                         cudaStream_t s) {
+  if (K % 8 != 0 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || sA % 8 || sB % 8 || K > 4096 ||
+      M < 1 || N < 1 || batch < 1 || batch > 65535) {
+    bs_set_error("slice GEMM: need K %% 8 == 0, K <= 4096, 16-byte aligned operands");
+    return BS_EINVAL;
+  }
+  CUtensorMap ta, tb;
+  int r = make_map(&ta, A, K, M, batch, sA, BM);
+  if (!r) r = make_map(&tb, B, K, N, batch, sB, BN);
+  if (r) return r;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return bs_cuda_status(e, "slice GEMM smem");
+    attr = true;
+  }
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, batch);
+  slice_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ta, tb, D, M, N, K, ldd, sD, err);
+  BS_CHECK_LAUNCH("slice_gemm_kernel");
+  return BS_OK;
+}

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "bandstructure.h")).read()
-    return sorted(set(re.findall(r"\b(bs_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(bs_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_symbols_exported():
