@@ -74,7 +74,7 @@ typedef struct bs_cell bs_cell;
  *             strain, Sec. IV); need mu > 0, lam + mu > 0, rho > 0.
  *   M       : plane-wave truncation, alpha, beta in [-M, M]
  *             (Eq. (approximation2d)); N = (2M+1)^2 waves, eigen dimension
- *             n = 2N; requires 2M+1 <= P.
+ *             n = 2N; requires 2M+1 <= P and M <= 15.
  *   precision : BS_PREC_FP64 or BS_PREC_MIXED.
  */
 typedef struct bs_cell_desc {

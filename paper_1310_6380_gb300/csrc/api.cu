@@ -203,9 +203,9 @@ extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
   }
   *out = nullptr;
   const int P = d->P, M = d->M, np = d->nphase;
-  if (P < 1 || P > 4096 || M < 0 || M > 16 || 2 * M + 1 > P || np < 1 || np > 65536 ||
+  if (P < 1 || P > 4096 || M < 0 || M > 15 || 2 * M + 1 > P || np < 1 || np > 65536 ||
       !d->phase || !d->lam || !d->mu || !d->rho) {
-    bs_set_error("bs_create_cell: need 1 <= P <= 4096, 0 <= M <= 16, 2M+1 <= P, 1 <= nphase "
+    bs_set_error("bs_create_cell: need 1 <= P <= 4096, 0 <= M <= 15, 2M+1 <= P, 1 <= nphase "
                  "<= 65536 and non-NULL arrays (P=%d M=%d nphase=%d)", P, M, np);
     return BS_EINVAL;
   }
@@ -280,6 +280,14 @@ extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
   if (!r) r = dalloc(&c->d_sliceD, sd, "digit-pair products");
   if (!r) r = dalloc(&c->d_expA, 3 * (size_t)P, "field exponents");
   if (!r) r = dalloc(&c->d_expB, 2 * (size_t)c->D, "table exponents");
+  size_t ma = 0, mb = 0, md = 0;
+  bs_zgemm_tc_elems(c->N, 2, &ma, &mb, &md);
+  if (!r) r = dalloc(&c->d_mA, ma, "monomial digit planes A");
+  if (!r) r = dalloc(&c->d_mB, mb, "monomial digit planes B");
+  if (!r) r = dalloc(&c->d_mD, md, "monomial digit-pair products");
+  if (!r) r = dalloc(&c->d_meA, 2 * (size_t)c->N, "monomial exponents A");
+  if (!r) r = dalloc(&c->d_meB, 2 * (size_t)c->N, "monomial exponents B");
+  if (!r) r = dalloc(&c->d_LinvR2, 2 * NN, "L_R^-1 pair");
   if (r) {
     bs_destroy_cell(c);
     return r;
@@ -327,6 +335,12 @@ extern "C" int bs_destroy_cell(bs_cell* c) {
   cudaFree(c->d_sliceD);
   cudaFree(c->d_expA);
   cudaFree(c->d_expB);
+  cudaFree(c->d_mA);
+  cudaFree(c->d_mB);
+  cudaFree(c->d_mD);
+  cudaFree(c->d_meA);
+  cudaFree(c->d_meB);
+  cudaFree(c->d_LinvR2);
   delete c;
   return BS_OK;
 }

@@ -114,6 +114,13 @@ struct bs_cell {
   float* d_sliceD;     // (S 2D) x (3 S P) digit-pair products
   int* d_expA;         // 3 P row exponents
   int* d_expB;         // 2D row exponents
+  // exact-slice workspace of the k-monomial products (batch of 2)
+  uint16_t* d_mA;
+  uint16_t* d_mB;
+  float* d_mD;
+  int* d_meA;
+  int* d_meB;
+  zd* d_LinvR2;        // L_R^-1 twice (the A operand of the batched F products)
 
   // per-k workspace (grown on demand)
   int kcap;            // matrices the workspace holds
@@ -205,6 +212,11 @@ size_t bs_fields_tc_elems(int P, int D, size_t* nA, size_t* nB, size_t* nD);
 int bs_launch_cx_tc(const zd* C, const zd* X, int n, int b, int kb, uint16_t* sA, uint16_t* sB,
                     float* sD, int* eA, int* eB, zd* Y, int* err, cudaStream_t s);
 void bs_cx_tc_elems(int n, int b, int kb, size_t* nA, size_t* nB, size_t* nD);
+// C[z] = A[z] diag(sc) B[z]^dagger for complex N x N column-major matrices (2N <= 4096)
+void bs_zgemm_tc_elems(int N, int batch, size_t* nA, size_t* nB, size_t* nD);
+int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long sB, zd* C, long sC,
+                       int N, int batch, uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB,
+                       int* err, cudaStream_t s);
 
 // builder.cu
 int bs_launch_builder(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,

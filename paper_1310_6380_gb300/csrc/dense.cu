@@ -91,8 +91,11 @@ __global__ void chol_panel_kernel(zd* __restrict__ A, int n, long stride, int j0
   }
 }
 
+// (bi, bk) with bi >= bk of the l-th lower-triangular tile, row-major;
+// FP32 square root (FP64 square root is a long sequence on GB300), then
+// exact integer correction
 __device__ __forceinline__ void tri_index(int l, int& bi, int& bk) {
-  int r = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+  int r = (int)((sqrtf(8.0f * (float)l + 1.0f) - 1.0f) * 0.5f);
   while ((r + 1) * (r + 2) / 2 <= l) ++r;
   while (r * (r + 1) / 2 > l) --r;
   bi = r;
@@ -375,22 +378,27 @@ int bs_launch_zgemm(bool conjA, bool conjB, int m, int nn, int k, zd alpha, cons
 int bs_launch_monomials(bs_cell* c, cudaStream_t s) {
   const int N = c->N;
   const size_t NN = (size_t)N * N;
-  const zd one = zmake(1.0, 0.0);
   const zd* LinvR = c->d_Linv + 2 * NN;
-  // F_X^a = L_R^-1 diag(s_a) L_X^-dagger for X in {kappa, mu} (batched), a = 0, 1, 2
+  int* err = c->d_info + 1;
+  // F_X^a = L_R^-1 diag(s_a) L_X^-dagger for X in {kappa, mu} (batch of 2), a = 0, 1, 2,
+  // as exact-slice tensor-core contractions (FP64 accuracy)
+  cudaError_t e = cudaMemcpyAsync(c->d_LinvR2, LinvR, NN * sizeof(zd), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_LinvR2 + NN, LinvR, NN * sizeof(zd), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return bs_cuda_status(e, "monomials copy");
   for (int a = 0; a < 3; ++a) {
     const double* sc = a == 0 ? nullptr : c->d_G + (size_t)(a - 1) * N;
-    int r = bs_launch_zgemm(false, true, N, N, N, one, LinvR, N, 0, c->d_Linv, N, (long)NN, sc, 0,
-                            c->d_F + (size_t)a * NN, N, (long)(3 * NN), 2, 3, s);
-    if (r) return r;
+    TRY_LAUNCH(bs_launch_zgemm_tc(c->d_LinvR2, (long)NN, sc, c->d_Linv, (long)NN,
+                                  c->d_F + (size_t)a * NN, (long)(3 * NN), N, 2, c->d_mA, c->d_mB,
+                                  c->d_mD, c->d_meA, c->d_meB, err, s));
   }
   // P_X^{ab} = F_X^a F_X^b^dagger, a <= b
   const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
   for (int t = 0; t < 6; ++t) {
-    int r = bs_launch_zgemm(false, true, N, N, N, one, c->d_F + (size_t)pa[t] * NN, N, (long)(3 * NN),
-                            c->d_F + (size_t)pb[t] * NN, N, (long)(3 * NN), nullptr, 0,
-                            c->d_Pp + (size_t)t * NN, N, (long)(6 * NN), 2, 0, s);
-    if (r) return r;
+    TRY_LAUNCH(bs_launch_zgemm_tc(c->d_F + (size_t)pa[t] * NN, (long)(3 * NN), nullptr,
+                                  c->d_F + (size_t)pb[t] * NN, (long)(3 * NN),
+                                  c->d_Pp + (size_t)t * NN, (long)(6 * NN), N, 2, c->d_mA, c->d_mB,
+                                  c->d_mD, c->d_meA, c->d_meB, err, s));
   }
   const size_t tot = (size_t)c->n * c->n;
   monomial_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->d_Pp, N, c->V * c->V, c->d_Cm);

@@ -66,6 +66,20 @@ __global__ void builder_mixed_kernel(const zd* __restrict__ Cm, int n,
 }
 
 // ------------------------------------------------------------ tridiagonal eigenvectors
+// 1/q: FP32 seed refined by two Newton-Raphson steps r <- r + r (1 - q r)
+// (FP64 division is a long sequence on GB300); exact division outside the
+// FP32 normal range.
+__device__ __forceinline__ double rcp64(double q) {
+  const double aq = fabs(q);
+  if (aq > 1e-36 && aq < 1e36) {
+    double r = (double)__frcp_rn((float)q);
+    r = fma(r, fma(-q, r, 1.0), r);
+    r = fma(r, fma(-q, r, 1.0), r);
+    return r;
+  }
+  return 1.0 / q;
+}
+
 __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
   unsigned h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
   h ^= h >> 15;
@@ -108,18 +122,19 @@ __global__ void tri_eigvec_kernel(const double* __restrict__ de, const zd* __res
       const double dn = d[r + 1] - sigma, en = r + 2 < n ? e[r + 1] : 0.0;
       if (fabs(al) >= fabs(g)) {
         const double a0 = fabs(al) < tiny ? (al < 0 ? -tiny : tiny) : al;
-        const double mlt = g / a0;
-        u0[r] = a0; u1[r] = bt; u2[r] = 0.0; ml[r] = mlt; pv[r] = 0.0;
+        const double ia = rcp64(a0);
+        const double mlt = g * ia;
+        u0[r] = ia; u1[r] = bt; u2[r] = 0.0; ml[r] = mlt; pv[r] = 0.0;
         al = dn - mlt * bt;
         bt = en;
       } else {
-        const double mlt = al / g;
-        u0[r] = g; u1[r] = dn; u2[r] = en; ml[r] = mlt; pv[r] = 1.0;
+        const double mlt = al * rcp64(g);
+        u0[r] = rcp64(g); u1[r] = dn; u2[r] = en; ml[r] = mlt; pv[r] = 1.0;
         al = bt - mlt * dn;
         bt = -mlt * en;
       }
     }
-    u0[n - 1] = fabs(al) < tiny ? (al < 0 ? -tiny : tiny) : al;
+    u0[n - 1] = rcp64(fabs(al) < tiny ? (al < 0 ? -tiny : tiny) : al);   // u0 holds 1/pivot
     double* yi = y + (size_t)i * n;
     for (int r = 0; r < n; ++r) yi[r] = hash_unit(r, i + 977u * k);
     for (int it = 0; it < 2; ++it) {
@@ -140,7 +155,7 @@ __global__ void tri_eigvec_kernel(const double* __restrict__ de, const zd* __res
         double s = yi[r];
         if (r + 1 < n) s -= u1[r] * yi[r + 1];
         if (r + 2 < n) s -= u2[r] * yi[r + 2];
-        yi[r] = s / u0[r];
+        yi[r] = s * u0[r];
         amax = fmax(amax, fabs(yi[r]));
       }
       const double sc = amax > 0.0 ? 1.0 / amax : 1.0;
@@ -287,27 +302,52 @@ __global__ void small_eig_kernel(const zd* __restrict__ Gg, const zd* __restrict
       A[r][c] = zscale(s, 1.0 / G[c][c].x);
     }
   __syncthreads();
+  // Hermitian part: H = X^dagger (C X) is Hermitian only to the accuracy of
+  // the C X product, and one-sided rotations cannot remove an anti-Hermitian
+  // residue, so the sweeps would never meet the stopping test
+  for (int e = tid; e < b * b; e += nt) {
+    const int r = e % b, c = e / b;
+    if (r < c) {
+      const zd h = zscale(zadd(A[r][c], zconj(A[c][r])), 0.5);
+      A[r][c] = h;
+      A[c][r] = zconj(h);
+    }
+  }
+  __syncthreads();
   for (int e = tid; e < b * b; e += nt) {
     const int r = e % b, c = e / b;
     V[r][c] = zmake(r == c ? 1.0 : 0.0, 0.0);
     if (r == c) A[r][c].y = 0.0;
   }
   __syncthreads();
+  __shared__ double red[4][2];
   const int np = b / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) {
-      double o = 0.0, t = 0.0;
-      for (int r = 0; r < b; ++r)
-        for (int c = 0; c < b; ++c) {
-          const double m2 = A[r][c].x * A[r][c].x + A[r][c].y * A[r][c].y;
-          t += m2;
-          if (r != c) o += m2;
-        }
-      offn = o;
-      totn = t;
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double o = 0.0, t = 0.0;
+    for (int e = tid; e < b * b; e += nt) {
+      const int r = e % b, c = e / b;
+      const double m2 = A[r][c].x * A[r][c].x + A[r][c].y * A[r][c].y;
+      t += m2;
+      if (r != c) o += m2;
+    }
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      o += __shfl_xor_sync(0xffffffffu, o, sh);
+      t += __shfl_xor_sync(0xffffffffu, t, sh);
+    }
+    if ((tid & 31) == 0) {
+      red[tid >> 5][0] = o;
+      red[tid >> 5][1] = t;
     }
     __syncthreads();
-    if (offn <= 1e-30 * totn) break;
+    if (tid == 0) {
+      offn = red[0][0] + red[1][0] + red[2][0] + red[3][0];
+      totn = red[0][1] + red[1][1] + red[2][1] + red[3][1];
+    }
+    __syncthreads();
+    // off-diagonal Frobenius norm below 1e-12 of the whole: the Ritz values
+    // then carry errors of order (1e-12 ||H||)^2 / gap, far below FP64 noise
+    if (offn <= 1e-24 * totn) break;
+
     for (int rd = 0; rd < b - 1; ++rd) {
       if (tid < np) {
         int p, q;

@@ -24,6 +24,9 @@ namespace {
 __device__ __forceinline__ uint16_t bf16_bits(double t) {
   return __bfloat16_as_ushort(__float2bfloat16_rn((float)t));
 }
+__device__ __forceinline__ uint16_t bf16_bits(long long t) {   // exact for |t| <= 256
+  return __bfloat16_as_ushort(__int2bfloat16_rn((int)t));
+}
 
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
@@ -47,12 +50,29 @@ __device__ __forceinline__ int row_exp(double m) {
   return e;
 }
 
+// Digits by integer arithmetic on the FP64 bit pattern (FP64 arithmetic is
+// slow on GB300): X = round(x 2^(48-e)) as a signed 64-bit integer
+// (|X| <= 2^48), then t_0 = floor((X + 2^41) / 2^42), remainder r, and
+// t_s = floor((r + 2^(41-7s)) / 2^(42-7s)) for s >= 1, each in [-64, 64].
 __device__ __forceinline__ void put_digits(double x, int e, int S, uint16_t* out, size_t plane) {
-  double r = ldexp(x, -e) * 64.0;
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long X = 0;
+  if (E != 0) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = 1075 - E - 48 + e;   // X = m 2^-sh
+    if (sh <= 0) X = m << (-sh);        // not reached: |x| <= 2^e keeps sh >= 4
+    else if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
+    if (bits < 0) X = -X;
+  }
+  long long r = X;
   for (int s = 0; s < S; ++s) {
-    const double t = rint(r);
+    const int sh = 42 - 7 * s;
+    long long t;
+    if (sh > 0) t = (r + (1LL << (sh - 1))) >> sh;
+    else t = r;
+    r -= t << (sh > 0 ? sh : 0);
     out[(size_t)s * plane] = bf16_bits(t);
-    r = (r - t) * 128.0;
   }
 }
 
@@ -244,4 +264,98 @@ void bs_cx_tc_elems(int n, int b, int kb, size_t* nA, size_t* nB, size_t* nD) {
   *nA = (size_t)kb * S * n * Kp;
   *nB = (size_t)kb * S * 2 * b * Kp;
   *nD = (size_t)kb * S * n * 2 * S * b;
+}
+
+// ---- complex N x N products C = A diag(sc) B^dagger (column-major, FP64)
+//   Re C = [Ar sc | Ai sc] [Br | Bi]^T,  Im C = [Ar sc | Ai sc] [-Bi | Br]^T
+// A rows (s, r), B rows (t, c, part); K = 2N.  One thread per row.
+namespace {
+
+__global__ void pack_zrows_kernel(const zd* __restrict__ A, long sA, const double* __restrict__ sc,
+                                  int N, int S, int Kp, int parts, uint16_t* __restrict__ out,
+                                  int* __restrict__ ex) {
+  // one CTA (128 threads) per row: the digit planes are written along K
+  __shared__ double sh[4];
+  const int r = blockIdx.x, z = blockIdx.y;
+  const zd* a = A + (size_t)z * sA;
+  double m = 0.0;
+  for (int k = threadIdx.x; k < N; k += 128) {
+    zd v = a[r + (size_t)k * N];
+    if (sc) v = zscale(v, sc[k]);
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  const int e = row_exp(row_max(m, sh));
+  const size_t rows = (size_t)parts * N, plane = rows * Kp;
+  uint16_t* base = out + (size_t)z * S * plane + (size_t)r * parts * Kp;
+  for (int k = threadIdx.x; k < Kp; k += 128) {
+    double v0 = 0.0, v1 = 0.0;
+    if (k < 2 * N) {
+      const int kk = k < N ? k : k - N;
+      zd v = a[r + (size_t)kk * N];
+      if (sc) v = zscale(v, sc[kk]);
+      if (k < N) {          // part 0: [re | im], part 1: [-im | re]
+        v0 = v.x;
+        v1 = -v.y;
+      } else {
+        v0 = v.y;
+        v1 = v.x;
+      }
+    }
+    put_digits(v0, e, S, base + k, plane);
+    if (parts == 2) put_digits(v1, e, S, base + Kp + k, plane);
+  }
+  if (threadIdx.x == 0) ex[(size_t)z * N + r] = e;
+}
+
+__global__ void recombine_z_kernel(const float* __restrict__ Dm, const int* __restrict__ eA,
+                                   const int* __restrict__ eB, int N, int S,
+                                   zd* __restrict__ C, long sC) {
+  const int z = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * N) return;
+  const int r = idx % N, c = idx / N;
+  const size_t M = (size_t)S * N, Nn = (size_t)S * 2 * N;
+  const float* dz = Dm + (size_t)z * M * Nn;
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const size_t m = (size_t)s * N + r;
+    for (int t = 0; t < S; ++t) {
+      const double w = ldexp(1.0, -12 - 7 * (s + t));
+      const size_t nr = ((size_t)t * N + c) * 2;
+      re = fma(w, (double)dz[nr * M + m], re);
+      im = fma(w, (double)dz[(nr + 1) * M + m], im);
+    }
+  }
+  const int ex = eA[(size_t)z * N + r] + eB[(size_t)z * N + c];
+  C[(size_t)z * sC + idx] = zmake(ldexp(re, ex), ldexp(im, ex));
+}
+
+}  // namespace
+
+void bs_zgemm_tc_elems(int N, int batch, size_t* nA, size_t* nB, size_t* nD) {
+  const int S = BS_SLICES_ASM, Kp = (2 * N + 7) / 8 * 8;
+  *nA = (size_t)batch * S * N * Kp;
+  *nB = (size_t)batch * S * 2 * N * Kp;
+  *nD = (size_t)batch * S * N * 2 * S * N;
+}
+
+int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long sB, zd* C, long sC,
+                       int N, int batch, uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB,
+                       int* err, cudaStream_t s) {
+  const int S = BS_SLICES_ASM, Kp = (2 * N + 7) / 8 * 8;
+  if (2 * N > 4096) {
+    bs_set_error("complex product: 2N = %d exceeds the exact-slice limit 4096", 2 * N);
+    return BS_EINVAL;
+  }
+  const dim3 g(N, batch);
+  pack_zrows_kernel<<<g, 128, 0, s>>>(A, sA, sc, N, S, Kp, 1, wA, eA);
+  BS_CHECK_LAUNCH("pack_zrows_kernel A");
+  pack_zrows_kernel<<<g, 128, 0, s>>>(B, sB, nullptr, N, S, Kp, 2, wB, eB);
+  BS_CHECK_LAUNCH("pack_zrows_kernel B");
+  const int M = S * N, Nn = 2 * S * N;
+  TRY_LAUNCH(bs_launch_slice_gemm(wA, wB, wD, M, Nn, Kp, batch, (long)M * Kp, (long)Nn * Kp, M,
+                                  (long)M * Nn, err, s));
+  recombine_z_kernel<<<dim3((N * N + 255) / 256, batch), 256, 0, s>>>(wD, eA, eB, N, S, C, sC);
+  BS_CHECK_LAUNCH("recombine_z_kernel");
+  return BS_OK;
 }

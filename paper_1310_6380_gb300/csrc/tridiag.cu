@@ -14,6 +14,8 @@
 // and builds the next reflector.  In FP64 the loop is bound by the FP64
 // pipe of GB300, so it is written for FP64 issue: 16 FMAs per element and
 // one shared-memory reduction of the row and column partials per tile.
+#include <algorithm>
+
 #include "bs_internal.h"
 
 namespace {
@@ -114,16 +116,20 @@ __global__ void __launch_bounds__(NT) tridiag_init_kernel(typename Cplx<R>::T* _
   if (n > 1) householder<R>(a, n, 0, vb, tau + (size_t)b * n, beta + (size_t)b * n, d + n, sh);
 }
 
+// (bi, bk) with bi >= bk of the l-th lower-triangular tile, row-major;
+// FP32 square root (FP64 square root is a long sequence on GB300), then
+// exact integer correction
 __device__ __forceinline__ void tri_index(int l, int& bi, int& bk) {
-  int r = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+  int r = (int)((sqrtf(8.0f * (float)l + 1.0f) - 1.0f) * 0.5f);
   while ((r + 1) * (r + 2) / 2 <= l) ++r;
   while (r * (r + 1) / 2 > l) --r;
   bi = r;
   bk = l - r * (r + 1) / 2;
 }
 
+// FP32: 3 CTAs per SM (memory latency needs warps); FP64: 2 (its pipe is the limit)
 template <typename R>
-__global__ void __launch_bounds__(NT, 2) tridiag_step_kernel(typename Cplx<R>::T* __restrict__ A,
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) tridiag_step_kernel(typename Cplx<R>::T* __restrict__ A,
                                                              int n, int j,
                                                              typename Cplx<R>::T* __restrict__ vec,
                                                              typename Cplx<R>::T* __restrict__ part,
@@ -294,15 +300,29 @@ template <typename R>
 int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
                       typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
                       unsigned* count, cudaStream_t s) {
-  tridiag_init_kernel<R><<<batch, NT, 0, s>>>(A, n, vec, de, tau, beta, count);
-  BS_CHECK_LAUNCH("tridiag_init_kernel");
+  typedef typename Cplx<R>::T C;
+  // The whole batch runs in every step launch.  (Reducing it in L2-sized
+  // groups one after another was measured slower for FP32: the per-step
+  // launch and epilogue latency then repeats once per group.)
+  const int group = batch;
   const int nt = (n + TS - 1) / TS;
-  for (int j = 0; j + 1 < n; ++j) {
-    const int m = nt - (j + 1) / TS;
-    const int ntl = m * (m + 1) / 2;
-    tridiag_step_kernel<R><<<dim3(ntl, batch), NT, 0, s>>>(A, n, j, vec, part, de, tau, beta,
-                                                           count, ntl);
-    BS_CHECK_LAUNCH("tridiag_step_kernel");
+  for (int g0 = 0; g0 < batch; g0 += group) {
+    const int gb = std::min(group, batch - g0);
+    C* Ag = A + (size_t)g0 * n * n;
+    C* vg = vec + (size_t)g0 * bs_tridiag_vec_elems(n);
+    C* pg = part + (size_t)g0 * bs_tridiag_part_elems(n);
+    double* dg = de + (size_t)g0 * 2 * n;
+    double* tg = tau + (size_t)g0 * n;
+    zd* bg = beta + (size_t)g0 * n;
+    unsigned* cg = count + g0;
+    tridiag_init_kernel<R><<<gb, NT, 0, s>>>(Ag, n, vg, dg, tg, bg, cg);
+    BS_CHECK_LAUNCH("tridiag_init_kernel");
+    for (int j = 0; j + 1 < n; ++j) {
+      const int m = nt - (j + 1) / TS;
+      const int ntl = m * (m + 1) / 2;
+      tridiag_step_kernel<R><<<dim3(ntl, gb), NT, 0, s>>>(Ag, n, j, vg, pg, dg, tg, bg, cg, ntl);
+      BS_CHECK_LAUNCH("tridiag_step_kernel");
+    }
   }
   return BS_OK;
 }
