@@ -184,6 +184,26 @@ int bs_tridiag_eigenvalues(const double* d, const double* e, int n, int batch, i
 int bs_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K, int batch,
                  void* stream);
 
+/*
+ * bs_tridiag_eigenvalues_static - bs_tridiag_eigenvalues without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc/cudaFree, such as code whose
+ * device memory is owned by another allocator that reserved it up front,
+ * or pipelined code that cannot let cudaFree wait for the whole device.
+ *   d, e, lam_out : DEVICE pointers with the layout of
+ *                   bs_tridiag_eigenvalues (host pointers: BS_EINVAL).
+ *   Limit: batch * 2n <= 1048576 (the scratch is a fixed 8 MiB array in the
+ *   library's device image, held by every GPU that loads the library until
+ *   the process exits); larger batches return BS_EINVAL - split them.
+ * The first call on a device looks up the array's device address with the
+ * runtime (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents, so calls that overlap on the GPU (different streams, or
+ * different host threads) race: serialise them.  Asynchronous on `stream`.
+ */
+int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int batch, int nbands,
+                                  double* lam_out, void* stream);
+
 /* bs_cell_dims - N (plane waves) and n = 2N (eigen dimension). */
 int bs_cell_dims(const bs_cell* cell, int* N, int* n);
 

@@ -59,6 +59,7 @@ def _load():
         "bs_launch_count": [ctypes.POINTER(ctypes.c_longlong)],
         "bs_tridiag_eigenvalues": [dp, dp, i32, i32, i32, dp, vp],
         "bs_gemm_bf16": [dp, dp, dp, i32, i32, i32, i32, vp],
+        "bs_tridiag_eigenvalues_static": [dp, dp, i32, i32, i32, dp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -75,7 +76,7 @@ _lib = _load()
 EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_factors",
             "bs_reduced_matrix", "bs_cell_dims", "bs_sync", "bs_destroy_cell", "bs_last_error",
             "bs_set_profiling", "bs_phase_times", "bs_launch_count", "bs_tridiag_eigenvalues",
-            "bs_gemm_bf16"]
+            "bs_gemm_bf16", "bs_tridiag_eigenvalues_static"]
 
 
 def bs_last_error() -> str:
@@ -162,6 +163,15 @@ def bs_tridiag_eigenvalues(d, e, nbands: int, lam_out, stream=None):
     batch, n = int(d.shape[0]), int(d.shape[1])
     _check(_lib.bs_tridiag_eigenvalues(_ptr(d, np.float64), _ptr(e, np.float64), n, batch,
                                        int(nbands), _ptr(lam_out, np.float64), _stream(stream)))
+    return lam_out
+
+
+def bs_tridiag_eigenvalues_static(d, e, nbands: int, lam_out, stream=None):
+    """As bs_tridiag_eigenvalues, on device tensors only, with no device allocation."""
+    batch, n = int(d.shape[0]), int(d.shape[1])
+    _check(_lib.bs_tridiag_eigenvalues_static(_ptr(d, np.float64), _ptr(e, np.float64), n, batch,
+                                              int(nbands), _ptr(lam_out, np.float64),
+                                              _stream(stream)))
     return lam_out
 
 
