@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="c1", choices=["c0", "c1"])
+    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=6)
@@ -52,22 +52,25 @@ def parse_args():
 
 
 def workload(name):
+    """(cell config, JSON config, precision) of a named workload."""
     from paper_1310_6380_gb300 import cells
-    cfg = cells.config1() if name == "c1" else cells.config0()
-    cell = cfg["cell"]
+    cfg = cells.config0() if name == "c0" else cells.config1()
     N = (2 * cfg["M"] + 1) ** 2
     desc = {
         "c1": "256x256 periodic Voronoi, 1132 phases (seed 1310), square a=1",
+        "c2": "256x256 periodic Voronoi, 1132 phases (seed 1310), square a=1",
         "c0": "32x32 circle r=0.3a, two phases, square a=1",
     }[name]
+    path = ("mixed path (FP32 reduction + FP64 Rayleigh-Ritz, tolerance 1e-6)" if name == "c2"
+            else "FP64 path")
     config = {
         "workload": f"{name}: {desc}, M={cfg['M']} ({N} plane waves, n={2 * N}), "
-                    f"{len(cfg['Q'])} k on G-X-M-G, lowest {cfg['nbands']} branches, FP64 path",
+                    f"{len(cfg['Q'])} k on G-X-M-G, lowest {cfg['nbands']} branches, {path}",
         "cells": 1, "k_points": len(cfg["Q"]), "plane_waves": N, "n": 2 * N,
-        "nbands": cfg["nbands"], "precision": "fp64",
+        "nbands": cfg["nbands"], "precision": "mixed" if name == "c2" else "fp64",
         "l2": "flushed between timed steps (256 MiB write, untimed)",
     }
-    return cfg, config
+    return cfg, config, (1 if name == "c2" else 0)
 
 
 # ---------------------------------------------------------------- clocks
@@ -179,7 +182,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cfg, config = workload(args.config)
+    cfg, config, _ = workload(args.config)
     cores = len(os.sched_getaffinity(0))
     times, vals = [], []
     for i in range(args.warmup + args.steps):
@@ -202,6 +205,73 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def measure_mixed(bs, torch, args, cell, M, nb, nk, Qd, stream, flush, barrier, dev, ms_fp64,
+                  omega_fp64, world):
+    """Config 2: the config-1 cell on the mixed path, timed like the main line."""
+    hm = bs.bs_create_cell(cell.h1, cell.h2, dev(cell.phase.astype(np.uint16)), dev(cell.lam),
+                           dev(cell.mu), dev(cell.rho), M, bs.BS_PREC_MIXED)
+    bs.bs_set_profiling(hm, True)
+    wm = torch.empty((nk, nb), dtype=torch.float64, device="cuda")
+    stm = torch.empty(nk, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        bs.bs_assemble(hm, stream)
+        bs.bs_solve_k(hm, Qd, nb, wm, stm, stream)
+    barrier()
+    times, phs = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bs.bs_assemble(hm, stream)
+        bs.bs_solve_k(hm, Qd, nb, wm, stm, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        phs.append(bs.bs_phase_times(hm))
+    bs.bs_destroy_cell(hm)
+    mms = statistics.mean(times)
+    om = wm.cpu().numpy()
+    return {"config": "c2: the c1 cell, FP32 Householder reduction + FP64 Rayleigh-Ritz "
+                      "(tensor-core exact-slice products), tolerance 1e-6",
+            "value": world * nk / (mms / 1e3), "unit": "k-solves/s", "ms_per_step": mms,
+            "speedup_vs_fp64_path": ms_fp64 / mms,
+            "status_nonzero": int(np.count_nonzero(stm.cpu().numpy())),
+            "phases_ms": {k: round(statistics.mean(p[k] for p in phs), 3)
+                          for k in phs[0] if k != "reserved"},
+            "max_rel_err_vs_fp64_path": float(rel_err(om, omega_fp64, cell).max()),
+            "_omega": om}
+
+
+def measure_tensor(bs, torch, stream, nk, n):
+    """Tensor-core utilisation of the exact-slice contraction on the shape of the
+    mixed path's Rayleigh-Ritz products (nk x [6n x 336 x 2n])."""
+    rng = np.random.default_rng(0)
+    zb, Mg, Ng, Kg = nk, 6 * n, 2 * 6 * 28, (2 * n + 7) // 8 * 8
+    bits = lambda a: torch.from_numpy(
+        (np.asarray(a, np.float32).view(np.uint32) >> 16).astype(np.uint16)).cuda()
+    Ag = bits(rng.integers(-64, 65, (zb, Mg, Kg)))
+    Bg = bits(rng.integers(-64, 65, (zb, Ng, Kg)))
+    Dg = torch.empty((zb, Ng, Mg), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        bs.bs_gemm_bf16(Ag, Bg, Dg, stream)
+    tcs = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bs.bs_gemm_bf16(Ag, Bg, Dg, stream)
+        e1.record(stream)
+        e1.synchronize()
+        tcs.append(e0.elapsed_time(e1))
+    tc_ms = min(tcs)
+    tflops = 2.0 * zb * Mg * Ng * Kg / (tc_ms / 1e3) / 1e12
+    return {"kernel": "slice_gemm_kernel (tcgen05.mma kind::f16, TMA, TMEM)",
+            "shape": f"{zb} x [{Mg} x {Ng} x {Kg}] BF16 -> FP32", "ms": tc_ms,
+            "achieved_tflops": tflops, "peak_tflops": 1940.2,
+            "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)", "frac": tflops / 1940.2}
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -215,14 +285,14 @@ def run_ours(args):
 
     from paper_1310_6380_gb300 import binding as bs
 
-    cfg, config = workload(args.config)
+    cfg, config, prec = workload(args.config)
     cell, M, nb = cfg["cell"], cfg["M"], cfg["nbands"]
     Q = np.ascontiguousarray(cfg["Q"])
     nk = len(Q)
     n = 2 * (2 * M + 1) ** 2
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     h = bs.bs_create_cell(cell.h1, cell.h2, dev(cell.phase.astype(np.uint16)), dev(cell.lam),
-                          dev(cell.mu), dev(cell.rho), M)
+                          dev(cell.mu), dev(cell.rho), M, prec)
     bs.bs_set_profiling(h, True)
     stream = torch.cuda.current_stream()
     Qd = dev(Q)
@@ -276,14 +346,23 @@ def run_ours(args):
 
     # dominant kernel: the Householder tridiagonalisation
     ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-    trid_flops = nk * 16.0 / 3.0 * n ** 3
-    achieved = trid_flops / (ph["tridiag"] / 1e3) / 1e12
-    traffic = traffic_record("tridiag_step_kernel")
-    roofline = {"bound": "alu", "kernel": "tridiag_step_kernel (all launches of one step)",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
-                "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}"}
+    if prec == 0:
+        trid_flops = nk * 16.0 / 3.0 * n ** 3
+        achieved = trid_flops / (ph["tridiag"] / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "tridiag_step_kernel<double> (all launches of one step)",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": traffic_record("tridiag_step_kernel") if args.config == "c1" else None,
+                    "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                    "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}"}
+    else:
+        tri_bytes = nk * sum(m * (m + 1) // 2 for m in range(1, n)) * 16.0
+        achieved = tri_bytes / (ph["tridiag"] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "tridiag_step_kernel<float> (all launches of one step)",
+                    "achieved": achieved, "peak": 6771.1, "unit": "GB/s", "frac": achieved / 6771.1,
+                    "traffic": None, "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+                    "algorithmic": "read + write (8 B each) of every trailing lower triangle, "
+                                   f"{nk} matrices, n={n}"}
 
     # end to end through the public API with host (pinned) buffers
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -293,7 +372,7 @@ def run_ours(args):
     hs = torch.empty(nk, dtype=torch.int32).pin_memory()
 
     def e2e_step():
-        c = bs.bs_create_cell(cell.h1, cell.h2, hp, hl, hm, hr, M)
+        c = bs.bs_create_cell(cell.h1, cell.h2, hp, hl, hm, hr, M, prec)
         try:
             bs.bs_assemble(c, stream)
             bs.bs_solve_k(c, hQ, nb, hw, hs, stream)
@@ -318,21 +397,38 @@ def run_ours(args):
            "d2h_bytes_per_step": d2h,
            "api": "bs_create_cell + bs_assemble + bs_solve_k + bs_destroy_cell, pinned host buffers"}
 
+    # on config 1, also measure config 2 (the same cell on the mixed path) and the
+    # tensor-core utilisation of the exact-slice contraction
+    mixed = tensor = None
+    if args.config == "c1":
+        mixed = measure_mixed(bs, torch, args, cell, M, nb, nk, Qd, stream, flush, barrier, dev,
+                              ms, omega, world)
+        tensor = measure_tensor(bs, torch, stream, nk, n)
+
     out = {
         "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config, "e2e": e2e, "gpu_launches": launches,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == 0 else "f32 reduction, bf16 exact-slice tensor products, f64 refinement",
+        "data": "synthetic", "config": config, "e2e": e2e, "gpu_launches": launches,
         "gpu_launches_per_step": launches // max(1, args.steps), "roofline": roofline,
-        "phases_ms": {k: round(v, 3) for k, v in ph.items()},
+        "phases_ms": {k: round(v, 3) for k, v in ph.items() if k != "reserved" and v > 0},
         "wall_s_timed_region": t_wall, "clocks": clocks,
     }
+    omega_mixed = None
+    if mixed is not None:
+        omega_mixed = mixed.pop("_omega")
+        out["mixed_path"] = mixed
+        out["tensor_core"] = tensor
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, idx, ws, desc, _ = cpu_oracle_sample(cfg, args.cpu_sample_k)
         out["cpu_baseline"] = {"value": v, "unit": "k-solves/s",
                                "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                                "sample": desc}
         out["max_rel_err_vs_oracle"] = float(rel_err(omega[idx], ws, cell).max())
+        if omega_mixed is not None:
+            out["mixed_path"]["max_rel_err_vs_oracle"] = float(
+                rel_err(omega_mixed[idx], ws, cell).max())
         out["oracle_sampled_k"] = idx.tolist()
     bs.bs_destroy_cell(h)
     if rank == 0:
