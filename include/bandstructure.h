@@ -204,6 +204,39 @@ int bs_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, i
 int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int batch, int nbands,
                                   double* lam_out, void* stream);
 
+/*
+ * A batch of independent cells solved together on the mixed path (the
+ * regime of many-cell band-structure optimisation the paper's conclusions
+ * point to).  Cells may differ in lattice, materials, number of phases and
+ * truncation M, but share the pixel count P and use BS_PREC_MIXED.
+ *
+ * bs_batch_create - copy `ncells` descriptions (host or device arrays; the
+ *   caller keeps ownership) into device storage and size the workspace for
+ *   `nk` wavevectors per cell and `nbands` branches (nbands <= 24,
+ *   nbands + 2 <= n <= 2048 for every cell).  Errors: BS_EINVAL (with the
+ *   failing cell's index in the message), BS_ENOMEM, BS_ECUDA.  Synchronous.
+ * bs_batch_solve - Q: ncells * nk * 2 fractional wavevectors (cell-major),
+ *   omega_out: ncells * nk * nbands (cell-major, ascending per k),
+ *   status_out: ncells * nk (0, or BS_ENOCONV where the Rayleigh-Ritz
+ *   residual bound misses 1e-6) or NULL; host or device pointers.  The first
+ *   call times both tile edges of the reduction per truncation group and
+ *   keeps the faster (autotuning).  Synchronises `stream` when an output is
+ *   a host pointer.
+ * bs_batch_set_graph - on != 0: the next bs_batch_solve records the whole
+ *   solve in a CUDA graph, later calls replay it (the Q and output pointers
+ *   of the recording call must be reused); on == 0 drops the graph.
+ * bs_batch_tiles - the tile edge chosen for each truncation group and the
+ *   group's eigen dimension n.
+ * bs_batch_destroy - free everything (NULL is a no-op).
+ */
+typedef struct bs_batch bs_batch;
+int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, int nbands, bs_batch** out);
+int bs_batch_solve(bs_batch* batch, const double* Q, double* omega_out, int* status_out,
+                   void* stream);
+int bs_batch_set_graph(bs_batch* batch, int on);
+int bs_batch_tiles(const bs_batch* batch, int* tiles, int* ns, int ngroups_max, int* ngroups);
+int bs_batch_destroy(bs_batch* batch);
+
 /* bs_cell_dims - N (plane waves) and n = 2N (eigen dimension). */
 int bs_cell_dims(const bs_cell* cell, int* N, int* n);
 

@@ -60,6 +60,11 @@ def _load():
         "bs_tridiag_eigenvalues": [dp, dp, i32, i32, i32, dp, vp],
         "bs_gemm_bf16": [dp, dp, dp, i32, i32, i32, i32, vp],
         "bs_tridiag_eigenvalues_static": [dp, dp, i32, i32, i32, dp, vp],
+        "bs_batch_create": [ctypes.POINTER(bs_cell_desc), i32, i32, i32, ctypes.POINTER(vp)],
+        "bs_batch_solve": [vp, dp, dp, dp, vp],
+        "bs_batch_set_graph": [vp, i32],
+        "bs_batch_tiles": [vp, dp, dp, i32, ctypes.POINTER(i32)],
+        "bs_batch_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -76,7 +81,8 @@ _lib = _load()
 EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_factors",
             "bs_reduced_matrix", "bs_cell_dims", "bs_sync", "bs_destroy_cell", "bs_last_error",
             "bs_set_profiling", "bs_phase_times", "bs_launch_count", "bs_tridiag_eigenvalues",
-            "bs_gemm_bf16", "bs_tridiag_eigenvalues_static"]
+            "bs_gemm_bf16", "bs_tridiag_eigenvalues_static", "bs_batch_create", "bs_batch_solve",
+            "bs_batch_set_graph", "bs_batch_tiles", "bs_batch_destroy"]
 
 
 def bs_last_error() -> str:
@@ -164,6 +170,49 @@ def bs_tridiag_eigenvalues(d, e, nbands: int, lam_out, stream=None):
     _check(_lib.bs_tridiag_eigenvalues(_ptr(d, np.float64), _ptr(e, np.float64), n, batch,
                                        int(nbands), _ptr(lam_out, np.float64), _stream(stream)))
     return lam_out
+
+
+def _desc(cell_args):
+    h1, h2, phase, lam, mu, rho, M, precision = cell_args
+    d = bs_cell_desc()
+    d.h1[0], d.h1[1] = float(h1[0]), float(h1[1])
+    d.h2[0], d.h2[1] = float(h2[0]), float(h2[1])
+    d.P, d.M, d.precision = int(phase.shape[0]), int(M), int(precision)
+    d.nphase = int(lam.shape[0])
+    d.phase = _ptr(phase, np.uint16)
+    d.lam, d.mu, d.rho = _ptr(lam, np.float64), _ptr(mu, np.float64), _ptr(rho, np.float64)
+    return d
+
+
+def bs_batch_create(cells, nk: int, nbands: int):
+    """cells: list of (h1, h2, phase, lam, mu, rho, M, precision) tuples (arrays
+    must stay alive during the call)."""
+    arr = (bs_cell_desc * len(cells))(*[_desc(c) for c in cells])
+    out = ctypes.c_void_p()
+    _check(_lib.bs_batch_create(arr, len(cells), int(nk), int(nbands), ctypes.byref(out)))
+    return out
+
+
+def bs_batch_solve(batch, Q, omega_out, status_out=None, stream=None):
+    _check(_lib.bs_batch_solve(batch, _ptr(Q, np.float64), _ptr(omega_out, np.float64),
+                               _ptr(status_out, np.int32), _stream(stream)))
+    return omega_out
+
+
+def bs_batch_set_graph(batch, on: bool):
+    _check(_lib.bs_batch_set_graph(batch, int(bool(on))))
+
+
+def bs_batch_tiles(batch):
+    tiles = np.zeros(16, np.int32)
+    ns = np.zeros(16, np.int32)
+    ng = ctypes.c_int()
+    _check(_lib.bs_batch_tiles(batch, tiles.ctypes.data, ns.ctypes.data, 16, ctypes.byref(ng)))
+    return dict(zip(ns[:ng.value].tolist(), tiles[:ng.value].tolist()))
+
+
+def bs_batch_destroy(batch):
+    _check(_lib.bs_batch_destroy(batch))
 
 
 def bs_tridiag_eigenvalues_static(d, e, nbands: int, lam_out, stream=None):

@@ -1,0 +1,596 @@
+// A batch of independent unit cells with uneven truncations, solved
+// together on the mixed path (the "thousands of cells" regime the paper
+// points to for band-structure optimisation).
+//
+// Cells are grouped by their truncation M (all cells of a group share the
+// eigen dimension n).  Each cell is assembled in turn on one worker cell per
+// group (its inputs stay resident for the whole batch; only the worker's
+// k-independent state is rebuilt per cell) and its C(k) for all of its
+// wavevectors is written into the group's chunk buffers.  Every chunk of
+// cells is then reduced and refined as ONE batch of (cell, k) matrices:
+// the FP32 Householder reduction, the eigenvalue shifts, inverse iteration,
+// the FP64 Rayleigh-Ritz with tensor-core products and the residual bounds.
+// The whole sequence can be captured in a CUDA graph on the first solve and
+// replayed afterwards.  The reduction's tile edge (32 or 64) is chosen per
+// group by timing both on the group's first chunk.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "bs_internal.h"
+
+namespace {
+
+#define CK(call, where)                                        \
+  do {                                                         \
+    cudaError_t e__ = (call);                                  \
+    if (e__ != cudaSuccess) return bs_cuda_status(e__, where); \
+  } while (0)
+
+template <typename T>
+int balloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return BS_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    bs_set_error("cudaMalloc(%s, %zu bytes) failed: %s", what, count * sizeof(T),
+                 cudaGetErrorString(e));
+    return BS_ENOMEM;
+  }
+  return BS_OK;
+}
+
+bool dev_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// rows [k][0..w) of src go to dst rows idx[k]: per-cell outputs back in caller order
+__global__ void scatter_rows_kernel(const double* __restrict__ src, const int* __restrict__ idx,
+                                    int rows, int w, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * w) return;
+  dst[(size_t)idx[i / w] * w + i % w] = src[i];
+}
+__global__ void scatter_int_kernel(const int* __restrict__ src, const int* __restrict__ idx,
+                                   int rows, int w, int* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * w) return;
+  dst[(size_t)idx[i / w] * w + i % w] = src[i];
+}
+
+}  // namespace
+
+constexpr int kWorkers = 8;   // cells assembled concurrently per truncation group
+
+struct BatchGroup {
+  int M, N, n, b;
+  std::vector<int> cells;     // caller indices
+  bs_cell* workers[kWorkers]; // each assembles one cell at a time, on its own stream
+  cudaStream_t wstream[kWorkers];
+  cudaEvent_t wdone[kWorkers];
+  cudaEvent_t fork;
+  int nworkers;
+  int chunk;                  // cells per reduction batch
+  int tile;                   // tridiagonal tile edge (autotuned)
+  bool tuned;
+  // chunk workspace (chunk * nk matrices)
+  zd* C64;
+  zf* C32;
+  zf* vec32;
+  zf* part32;
+  double* de;
+  double* tau;
+  zd* beta;
+  unsigned* count;
+  double* lamT;
+  double* scr;
+  double* Y;
+  zd* phase;
+  zf* X32;
+  zd* X64;
+  zd* CX;
+  zd* G;
+  zd* H;
+  zd* W;
+  double* theta;
+  uint16_t* cxA;
+  uint16_t* cxB;
+  float* cxD;
+  int* cxeA;
+  int* cxeB;
+  double* w;                  // chunk * nk * nbands
+  int* st;                    // chunk * nk
+  int* d_rowidx;              // cells.size() * nk target rows (cell * nk + k), chunk-major
+  double* d_Gall;             // cells.size() * 2N plane-wave vectors G of each cell
+};
+
+struct bs_batch {
+  int ncells, nk, nbands, P;
+  std::vector<bs_cell_desc> desc;       // geometry kept on the host
+  std::vector<int> nphase;
+  uint16_t* d_phase;                    // ncells * P * P
+  double* d_raw;                        // concatenated (lam, mu, rho) per cell
+  std::vector<size_t> raw_off;
+  double* d_Q;                          // ncells * nk * 2
+  double* d_w;                          // ncells * nk * nbands
+  int* d_st;                            // ncells * nk
+  std::vector<BatchGroup> groups;
+  bool use_graph;
+  cudaGraphExec_t graph;
+  cudaStream_t cap;       // non-blocking stream the graph is recorded and replayed on
+  cudaEvent_t ev_in, ev_out;
+};
+
+static void free_group(BatchGroup& g) {
+  for (int w = 0; w < g.nworkers; ++w) {
+    if (g.workers[w]) bs_destroy_cell(g.workers[w]);
+    if (g.wstream[w]) cudaStreamDestroy(g.wstream[w]);
+    if (g.wdone[w]) cudaEventDestroy(g.wdone[w]);
+  }
+  if (g.fork) cudaEventDestroy(g.fork);
+  void* ps[] = {g.C64, g.C32, g.vec32, g.part32, g.de, g.tau, g.beta, g.count, g.lamT, g.scr, g.Y,
+                g.phase, g.X32, g.X64, g.CX, g.G, g.H, g.W, g.theta, g.cxA, g.cxB, g.cxD, g.cxeA,
+                g.cxeB, g.w, g.st, g.d_rowidx, g.d_Gall};
+  for (void* p : ps) cudaFree(p);
+}
+
+static int alloc_group(BatchGroup& g, int nk, int nbands) {
+  const int n = g.n, b = g.b;
+  const size_t K = (size_t)g.chunk * nk;
+  size_t ca = 0, cb = 0, cd = 0;
+  bs_cx_tc_elems(n, b, (int)K, &ca, &cb, &cd);
+  int r = BS_OK;
+  if (!r) r = balloc(&g.C64, K * n * n, "batch C64");
+  if (!r) r = balloc(&g.C32, K * n * n, "batch C32");
+  if (!r) r = balloc(&g.vec32, K * bs_tridiag_vec_elems(n), "batch vec");
+  if (!r) r = balloc(&g.part32, K * bs_tridiag_part_elems(n), "batch partials");
+  if (!r) r = balloc(&g.de, K * 2 * n, "batch tridiagonal");
+  if (!r) r = balloc(&g.tau, K * n, "batch tau");
+  if (!r) r = balloc(&g.beta, K * n, "batch beta");
+  if (!r) r = balloc(&g.count, K, "batch counters");
+  if (!r) r = balloc(&g.lamT, K * (b + 1), "batch shifts");
+  if (!r) r = balloc(&g.scr, K * b * 5 * n, "batch inverse iteration");
+  if (!r) r = balloc(&g.Y, K * b * n, "batch Y");
+  if (!r) r = balloc(&g.phase, K * n, "batch phases");
+  if (!r) r = balloc(&g.X32, K * b * n, "batch X32");
+  if (!r) r = balloc(&g.X64, K * b * n, "batch X64");
+  if (!r) r = balloc(&g.CX, K * b * n, "batch CX");
+  if (!r) r = balloc(&g.G, K * b * b, "batch G");
+  if (!r) r = balloc(&g.H, K * b * b, "batch H");
+  if (!r) r = balloc(&g.W, K * b * b, "batch W");
+  if (!r) r = balloc(&g.theta, K * b, "batch theta");
+  if (!r) r = balloc(&g.cxA, ca, "batch C digit planes");
+  if (!r) r = balloc(&g.cxB, cb, "batch X digit planes");
+  if (!r) r = balloc(&g.cxD, cd, "batch digit products");
+  if (!r) r = balloc(&g.cxeA, K * n, "batch C exponents");
+  if (!r) r = balloc(&g.cxeB, K * b, "batch X exponents");
+  if (!r) r = balloc(&g.w, K * nbands, "batch omega");
+  if (!r) r = balloc(&g.st, K, "batch status");
+  if (!r) r = balloc(&g.d_rowidx, g.cells.size() * (size_t)nk, "batch row index");
+  if (!r) r = balloc(&g.d_Gall, g.cells.size() * 2 * (size_t)g.N, "batch G vectors");
+  return r;
+}
+
+// point a worker cell at the group's gi-th cell (device-resident inputs)
+static int load_cell(bs_batch* B, BatchGroup& g, bs_cell* c, int gi, cudaStream_t s) {
+  const int ci = g.cells[gi];
+  const bs_cell_desc& d = B->desc[ci];
+  const int np = B->nphase[ci];
+  c->nphase = np;
+  for (int i = 0; i < 2; ++i) {
+    c->h1[i] = d.h1[i];
+    c->h2[i] = d.h2[i];
+  }
+  const double det = d.h1[0] * d.h2[1] - d.h1[1] * d.h2[0];
+  c->V = fabs(det);
+  c->q1[0] = 2.0 * M_PI * d.h2[1] / det;
+  c->q1[1] = -2.0 * M_PI * d.h2[0] / det;
+  c->q2[0] = -2.0 * M_PI * d.h1[1] / det;
+  c->q2[1] = 2.0 * M_PI * d.h1[0] / det;
+  const size_t PP = (size_t)B->P * B->P;
+  CK(cudaMemcpyAsync(c->d_phase, B->d_phase + (size_t)ci * PP, PP * 2, cudaMemcpyDeviceToDevice, s),
+     "batch phase");
+  CK(cudaMemcpyAsync(c->d_table + 3 * np, B->d_raw + B->raw_off[ci], 3 * np * sizeof(double),
+                     cudaMemcpyDeviceToDevice, s),
+     "batch table");
+  CK(cudaMemcpyAsync(c->d_G, g.d_Gall + (size_t)gi * 2 * g.N, 2 * (size_t)g.N * sizeof(double),
+                     cudaMemcpyDeviceToDevice, s),
+     "batch G");
+  return BS_OK;
+}
+
+static double floor2_of(const bs_batch* B, int ci, std::vector<double>& raw) {
+  const bs_cell_desc& d = B->desc[ci];
+  const int np = B->nphase[ci];
+  double ct2 = 1e300;
+  for (int i = 0; i < np; ++i) ct2 = std::min(ct2, raw[B->raw_off[ci] + np + i] / raw[B->raw_off[ci] + 2 * np + i]);
+  const double det = d.h1[0] * d.h2[1] - d.h1[1] * d.h2[0];
+  const double q1x = 2 * M_PI * d.h2[1] / det, q1y = -2 * M_PI * d.h2[0] / det;
+  const double q2x = -2 * M_PI * d.h1[1] / det, q2y = 2 * M_PI * d.h1[0] / det;
+  return ct2 * std::min(q1x * q1x + q1y * q1y, q2x * q2x + q2y * q2y) / 4.0;
+}
+
+// one chunk of a group: assemble its cells, build C(k), reduce + refine as one batch
+static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, cudaStream_t s,
+                     int tile) {
+  const int nk = B->nk, n = g.n, b = g.b;
+  const size_t nn = (size_t)n * n;
+  // fork: the workers start after everything already queued on s
+  CK(cudaEventRecord(g.fork, s), "batch fork");
+  for (int w = 0; w < g.nworkers; ++w) CK(cudaStreamWaitEvent(g.wstream[w], g.fork, 0), "batch fork");
+  for (int i = 0; i < cn; ++i) {
+    const int ci = g.cells[c0 + i], wi = i % g.nworkers;
+    bs_cell* wk = g.workers[wi];
+    cudaStream_t ws = g.wstream[wi];
+    int r = load_cell(B, g, wk, c0 + i, ws);
+    if (!r) r = bs_assemble(wk, ws);
+    if (!r)
+      r = bs_launch_builder_mixed(wk->d_Cm, n, B->d_Q + (size_t)ci * nk * 2, nk, wk->q1[0],
+                                  wk->q1[1], wk->q2[0], wk->q2[1], g.C64 + (size_t)i * nk * nn,
+                                  g.C32 + (size_t)i * nk * nn, ws);
+    if (r) return r;
+  }
+  // join
+  for (int w = 0; w < g.nworkers; ++w) {
+    CK(cudaEventRecord(g.wdone[w], g.wstream[w]), "batch join");
+    CK(cudaStreamWaitEvent(s, g.wdone[w], 0), "batch join");
+  }
+  const int K = cn * nk;
+  TRY_LAUNCH(bs_launch_tridiag<float>(g.C32, n, K, g.vec32, g.part32, g.de, g.tau, g.beta, g.count,
+                                      s, tile));
+  TRY_LAUNCH(bs_launch_bisect(g.de, n, K, b + 1, g.lamT, nullptr, s, false, 1e-9));
+  MixedWs w;
+  w.C64 = g.C64; w.C32 = g.C32; w.de = g.de; w.tau = g.tau; w.beta = g.beta; w.lamT = g.lamT;
+  w.scratch = g.scr; w.Y = g.Y; w.phase = g.phase; w.X32 = g.X32; w.X64 = g.X64; w.CX = g.CX;
+  w.G = g.G; w.H = g.H; w.W = g.W; w.theta = g.theta; w.cxA = g.cxA; w.cxB = g.cxB;
+  w.cxD = g.cxD; w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
+  TRY_LAUNCH(bs_launch_mixed_refine(w, n, K, B->nbands, b, 1e-6, floor2, g.w, g.st, s));
+  // scatter (cell, k) rows into caller order
+  const int* rows = g.d_rowidx + (size_t)c0 * nk;
+  scatter_rows_kernel<<<(K * B->nbands + 255) / 256, 256, 0, s>>>(g.w, rows, K, B->nbands,
+                                                                  B->d_w);
+  BS_CHECK_LAUNCH("scatter_rows_kernel");
+  scatter_int_kernel<<<(K + 255) / 256, 256, 0, s>>>(g.st, rows, K, 1, B->d_st);
+  BS_CHECK_LAUNCH("scatter_int_kernel");
+  return BS_OK;
+}
+
+// the single-cell checks of bs_create_cell, on host copies
+static int validate(const bs_cell_desc& d, int i, const std::vector<double>& lmr,
+                    const std::vector<uint16_t>& ph) {
+  const int np = d.nphase;
+  const double det = d.h1[0] * d.h2[1] - d.h1[1] * d.h2[0];
+  if (d.M < 0 || d.M > 15 || 2 * d.M + 1 > d.P || np < 1 || np > 65536 || !(fabs(det) > 0.0) ||
+      !isfinite(det)) {
+    bs_set_error("bs_batch_create: cell %d: need 0 <= M <= 15, 2M+1 <= P, 1 <= nphase <= 65536 "
+                 "and a lattice basis", i);
+    return BS_EINVAL;
+  }
+  for (int k = 0; k < np; ++k) {
+    const double lam = lmr[k], mu = lmr[np + k], rho = lmr[2 * np + k];
+    if (!isfinite(lam) || !isfinite(mu) || !isfinite(rho) || !(mu > 0.0) || !(lam + mu > 0.0) ||
+        !(rho > 0.0)) {
+      bs_set_error("bs_batch_create: cell %d phase %d has lam=%g mu=%g rho=%g", i, k, lam, mu, rho);
+      return BS_EINVAL;
+    }
+  }
+  for (size_t k = 0; k < ph.size(); ++k)
+    if (ph[k] >= np) {
+      bs_set_error("bs_batch_create: cell %d pixel %zu has phase %u >= nphase %d", i, k, ph[k], np);
+      return BS_EINVAL;
+    }
+  return BS_OK;
+}
+
+extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, int nbands,
+                               bs_batch** out) {
+  if (!descs || !out || ncells < 1 || nk < 1 || nbands < 1 || nbands > BS_MIXED_MAX_BANDS) {
+    bs_set_error("bs_batch_create: need descs, ncells >= 1, nk >= 1, 1 <= nbands <= %d",
+                 BS_MIXED_MAX_BANDS);
+    return BS_EINVAL;
+  }
+  *out = nullptr;
+  const int P = descs[0].P;
+  for (int i = 0; i < ncells; ++i) {
+    const bs_cell_desc& d = descs[i];
+    if (d.P != P || d.precision != BS_PREC_MIXED) {
+      bs_set_error("bs_batch_create: cell %d: all cells need the same P and BS_PREC_MIXED", i);
+      return BS_EINVAL;
+    }
+    const int n = 2 * (2 * d.M + 1) * (2 * d.M + 1);
+    if (nbands + 2 > n || n > 2048) {
+      bs_set_error("bs_batch_create: cell %d: need nbands + 2 <= n <= 2048 (n = %d)", i, n);
+      return BS_EINVAL;
+    }
+  }
+  bs_batch* B = new bs_batch();
+  B->ncells = ncells;
+  B->nk = nk;
+  B->nbands = nbands;
+  B->P = P;
+  B->desc.assign(descs, descs + ncells);
+  B->nphase.resize(ncells);
+  B->raw_off.resize(ncells);
+  size_t rawn = 0;
+  for (int i = 0; i < ncells; ++i) {
+    B->nphase[i] = descs[i].nphase;
+    B->raw_off[i] = rawn;
+    rawn += 3 * (size_t)descs[i].nphase;
+  }
+  int r = BS_OK;
+  const size_t PP = (size_t)P * P;
+  if (!r) r = balloc(&B->d_phase, ncells * PP, "batch phase maps");
+  if (!r) r = balloc(&B->d_raw, rawn, "batch tables");
+  if (!r) r = balloc(&B->d_Q, (size_t)ncells * nk * 2, "batch Q");
+  if (!r) r = balloc(&B->d_w, (size_t)ncells * nk * nbands, "batch omega");
+  if (!r) r = balloc(&B->d_st, (size_t)ncells * nk, "batch status");
+  std::vector<double> raw(rawn);
+  std::map<int, std::vector<int>> byM;
+  std::vector<uint16_t> ph(PP);
+  for (int i = 0; !r && i < ncells; ++i) {
+    const int np = descs[i].nphase;
+    if (np < 1 || !descs[i].phase || !descs[i].lam || !descs[i].mu || !descs[i].rho) {
+      bs_set_error("bs_batch_create: cell %d: NULL array or nphase < 1", i);
+      r = BS_EINVAL;
+      break;
+    }
+    cudaError_t e = cudaMemcpy(ph.data(), descs[i].phase, PP * 2, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(&raw[B->raw_off[i]], descs[i].lam, np * 8, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(&raw[B->raw_off[i] + np], descs[i].mu, np * 8, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(&raw[B->raw_off[i] + 2 * np], descs[i].rho, np * 8, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_phase + i * PP, ph.data(), PP * 2, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      r = bs_cuda_status(e, "bs_batch_create copy");
+      break;
+    }
+    std::vector<double> lmr(raw.begin() + B->raw_off[i], raw.begin() + B->raw_off[i] + 3 * np);
+    r = validate(descs[i], i, lmr, ph);
+    byM[descs[i].M].push_back(i);
+  }
+  if (!r) {
+    cudaError_t e = cudaMemcpy(B->d_raw, raw.data(), rawn * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) r = bs_cuda_status(e, "bs_batch_create tables");
+  }
+  for (auto& kv : byM) {
+    if (r) break;
+    BatchGroup g{};
+    g.cells = kv.second;
+    g.M = kv.first;
+    g.N = (2 * g.M + 1) * (2 * g.M + 1);
+    g.n = 2 * g.N;
+    g.b = bs_mixed_guard(nbands, g.n);
+    int npmax = 1, ci0 = g.cells[0];
+    for (int ci : g.cells) npmax = std::max(npmax, descs[ci].nphase);
+    // worker cell: sized for the group's largest table
+    bs_cell_desc wd = descs[ci0];
+    std::vector<double> ones(npmax, 1.0);
+    std::vector<uint16_t> zero(PP, 0);
+    wd.nphase = npmax;
+    wd.lam = ones.data();
+    wd.mu = ones.data();
+    wd.rho = ones.data();
+    wd.phase = zero.data();
+    g.nworkers = (int)std::min<size_t>(kWorkers, g.cells.size());
+    for (int w = 0; !r && w < g.nworkers; ++w) {
+      r = bs_create_cell(&wd, &g.workers[w]);
+      if (!r) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g.wstream[w], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.wdone[w], cudaEventDisableTiming);
+        if (e != cudaSuccess) r = bs_cuda_status(e, "bs_batch_create worker");
+      }
+    }
+    if (!r) {
+      cudaError_t e = cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
+      if (e != cudaSuccess) r = bs_cuda_status(e, "bs_batch_create fork");
+    }
+    if (r) {
+      B->groups.push_back(g);
+      break;
+    }
+    // chunk: a few GB of workspace per group
+    // bytes per cell: C64 16 n^2, C32 8 n^2, C digit planes 24 n^2, C X
+    // products 288 n b, vectors and inverse-iteration factors ~ 120 n b
+    const double per_cell = (double)nk * g.n * ((16.0 + 8.0 + 24.0) * g.n + 410.0 * g.b);
+    g.chunk = (int)std::max(1.0, std::min((double)g.cells.size(), 12e9 / per_cell));
+    g.tile = 64;
+    g.tuned = false;
+    r = alloc_group(g, nk, nbands);
+    if (!r) {
+      // plane-wave vectors of every cell and the caller row of every (cell, k)
+      std::vector<double> Gall(g.cells.size() * 2 * (size_t)g.N);
+      std::vector<int> rows(g.cells.size() * (size_t)nk);
+      for (size_t i = 0; i < g.cells.size(); ++i) {
+        const bs_cell_desc& d = descs[g.cells[i]];
+        const double det = d.h1[0] * d.h2[1] - d.h1[1] * d.h2[0];
+        const double q1x = 2 * M_PI * d.h2[1] / det, q1y = -2 * M_PI * d.h2[0] / det;
+        const double q2x = -2 * M_PI * d.h1[1] / det, q2y = 2 * M_PI * d.h1[0] / det;
+        for (int a = 0; a < g.N; ++a) {
+          const int al = a / (2 * g.M + 1) - g.M, be = a % (2 * g.M + 1) - g.M;
+          Gall[i * 2 * g.N + a] = al * q1x + be * q2x;
+          Gall[i * 2 * g.N + g.N + a] = al * q1y + be * q2y;
+        }
+        for (int k = 0; k < nk; ++k) rows[i * nk + k] = g.cells[i] * nk + k;
+      }
+      cudaError_t e = cudaMemcpy(g.d_Gall, Gall.data(), Gall.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(g.d_rowidx, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) r = bs_cuda_status(e, "bs_batch_create group tables");
+    }
+    B->groups.push_back(g);
+  }
+  if (r) {
+    bs_batch_destroy(B);
+    return r;
+  }
+  *out = B;
+  return BS_OK;
+}
+
+extern "C" int bs_batch_destroy(bs_batch* B) {
+  if (!B) return BS_OK;
+  for (auto& g : B->groups) free_group(g);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->ev_in) cudaEventDestroy(B->ev_in);
+  if (B->ev_out) cudaEventDestroy(B->ev_out);
+  cudaFree(B->d_phase);
+  cudaFree(B->d_raw);
+  cudaFree(B->d_Q);
+  cudaFree(B->d_w);
+  cudaFree(B->d_st);
+  delete B;
+  return BS_OK;
+}
+
+extern "C" int bs_batch_set_graph(bs_batch* B, int on) {
+  if (!B) {
+    bs_set_error("bs_batch_set_graph: NULL batch");
+    return BS_EINVAL;
+  }
+  B->use_graph = on != 0;
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  return BS_OK;
+}
+
+extern "C" int bs_batch_tiles(const bs_batch* B, int* tiles, int* ns, int ngroups_max,
+                              int* ngroups) {
+  if (!B || !ngroups) {
+    bs_set_error("bs_batch_tiles: NULL argument");
+    return BS_EINVAL;
+  }
+  *ngroups = (int)B->groups.size();
+  for (int i = 0; i < *ngroups && i < ngroups_max; ++i) {
+    if (tiles) tiles[i] = B->groups[i].tile;
+    if (ns) ns[i] = B->groups[i].n;
+  }
+  return BS_OK;
+}
+
+// tile autotuning: time both tile edges on the group's first chunk (once)
+static int tune_group(bs_batch* B, BatchGroup& g, double floor2, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "tune");
+  CK(cudaEventCreate(&e1), "tune");
+  const int cn = std::min(g.chunk, (int)g.cells.size());
+  float best = 1e30f;
+  int best_tile = 64;
+  for (int tile : {64, 32}) {
+    CK(cudaEventRecord(e0, s), "tune");
+    TRY_LAUNCH(run_chunk(B, g, 0, cn, floor2, s, tile));
+    CK(cudaEventRecord(e1, s), "tune");
+    CK(cudaEventSynchronize(e1), "tune");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1), "tune");
+    if (ms < best) {
+      best = ms;
+      best_tile = tile;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g.tile = best_tile;
+  g.tuned = true;
+  return BS_OK;
+}
+
+static int solve_all(bs_batch* B, const std::vector<double>& floors, cudaStream_t s) {
+  for (auto& g : B->groups) {
+    double f2 = 1e300;
+    for (int ci : g.cells) f2 = std::min(f2, floors[ci]);
+    for (int c0 = 0; c0 < (int)g.cells.size(); c0 += g.chunk) {
+      const int cn = std::min(g.chunk, (int)g.cells.size() - c0);
+      TRY_LAUNCH(run_chunk(B, g, c0, cn, f2, s, g.tile));
+    }
+  }
+  return BS_OK;
+}
+
+extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, int* status_out,
+                              void* stream) {
+  if (!B || !Q || !omega_out) {
+    bs_set_error("bs_batch_solve: NULL argument");
+    return BS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nq = (size_t)B->ncells * B->nk;
+  std::vector<double> raw;
+  std::vector<double> floors(B->ncells);
+  {
+    size_t rawn = 0;
+    for (int i = 0; i < B->ncells; ++i) rawn += 3 * (size_t)B->nphase[i];
+    raw.resize(rawn);
+    CK(cudaMemcpy(raw.data(), B->d_raw, rawn * 8, cudaMemcpyDeviceToHost), "bs_batch_solve");
+    for (int i = 0; i < B->ncells; ++i) floors[i] = floor2_of(B, i, raw);
+  }
+  CK(cudaMemcpyAsync(B->d_Q, Q, nq * 2 * sizeof(double), cudaMemcpyDefault, s), "bs_batch_solve Q");
+  for (auto& g : B->groups) {
+    if (g.tuned) continue;
+    double f2 = 1e300;
+    for (int ci : g.cells) f2 = std::min(f2, floors[ci]);
+    TRY_LAUNCH(tune_group(B, g, f2, s));
+  }
+  if (B->use_graph) {
+    // the caller's stream may be the legacy default stream, which cannot be
+    // captured: record and replay on the batch's own stream, ordered after
+    // and before the caller's stream with events
+    if (!B->cap) {
+      CK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "bs_batch_solve stream");
+      CK(cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming), "bs_batch_solve event");
+      CK(cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming), "bs_batch_solve event");
+    }
+    CK(cudaEventRecord(B->ev_in, s), "bs_batch_solve order");
+    CK(cudaStreamWaitEvent(B->cap, B->ev_in, 0), "bs_batch_solve order");
+    if (!B->graph) {
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "bs_batch_solve capture");
+      const int r = solve_all(B, floors, B->cap);
+      cudaError_t ce = cudaStreamEndCapture(B->cap, &graph);
+      if (r) return r;
+      if (ce != cudaSuccess) return bs_cuda_status(ce, "bs_batch_solve end capture");
+      ce = cudaGraphInstantiate(&B->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return bs_cuda_status(ce, "bs_batch_solve instantiate");
+    }
+    CK(cudaGraphLaunch(B->graph, B->cap), "bs_batch_solve graph launch");
+    CK(cudaEventRecord(B->ev_out, B->cap), "bs_batch_solve order");
+    CK(cudaStreamWaitEvent(s, B->ev_out, 0), "bs_batch_solve order");
+  } else {
+    TRY_LAUNCH(solve_all(B, floors, s));
+  }
+  CK(cudaMemcpyAsync(omega_out, B->d_w, nq * B->nbands * sizeof(double), cudaMemcpyDefault, s),
+     "bs_batch_solve omega");
+  if (status_out)
+    CK(cudaMemcpyAsync(status_out, B->d_st, nq * sizeof(int), cudaMemcpyDefault, s),
+       "bs_batch_solve status");
+  if (!dev_ptr(omega_out) || (status_out && !dev_ptr(status_out))) {
+    CK(cudaStreamSynchronize(s), "bs_batch_solve sync");
+    for (auto& g : B->groups)
+      for (int wi = 0; wi < g.nworkers; ++wi) {
+      int info[2] = {0, 0};
+      CK(cudaMemcpy(info, g.workers[wi]->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost), "info");
+      if (info[0]) {
+        bs_set_error("bs_batch_solve: a Gram matrix was not positive definite");
+        return BS_ENOTPD;
+      }
+      if (info[1]) {
+        bs_set_error("bs_batch_solve: a tensor-core pipeline wait reached its limit");
+        return BS_ECUDA;
+      }
+    }
+  }
+  return BS_OK;
+}

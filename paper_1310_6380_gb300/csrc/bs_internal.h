@@ -228,10 +228,11 @@ int bs_launch_builder(const zd* Cm, int n, const double* Q, int nk, double q1x, 
 // (j+1, j) entry of the unitarily reduced (complex) tridiagonal.
 size_t bs_tridiag_vec_elems(int n);
 size_t bs_tridiag_part_elems(int n);
+// tile: 64 (default) or 32 (tile edge of the fused update + matrix-vector step)
 template <typename R>
 int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
                       typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
-                      unsigned* count, cudaStream_t s);
+                      unsigned* count, cudaStream_t s, int tile = 64);
 
 // mixed.cu: FP32 reduction + FP64 Rayleigh-Ritz refinement
 struct MixedWs {

@@ -20,8 +20,9 @@
 
 namespace {
 
-constexpr int TS = 64;    // tile edge
-constexpr int NT = 256;   // threads per CTA (8 warps)
+constexpr int TSMAX = 64;  // largest tile edge (the default)
+constexpr int TSMIN = 32;  // smallest tile edge (sizes the partial-sum buffer)
+constexpr int NT = 256;    // threads per CTA (8 warps), a 16 x 16 thread grid
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -127,8 +128,9 @@ __device__ __forceinline__ void tri_index(int l, int& bi, int& bk) {
   bk = l - r * (r + 1) / 2;
 }
 
-// FP32: 3 CTAs per SM (memory latency needs warps); FP64: 2 (its pipe is the limit)
-template <typename R>
+// FP32: 3 CTAs per SM (memory latency needs warps); FP64: 2 (its pipe is the limit).
+// TS = 64 (4 x 4 elements per thread) or 32 (2 x 2): the tile edge is tuned per n.
+template <typename R, int TS>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) tridiag_step_kernel(typename Cplx<R>::T* __restrict__ A,
                                                              int n, int j,
                                                              typename Cplx<R>::T* __restrict__ vec,
@@ -140,17 +142,18 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) tridiag_step_kerne
                                                              int ntl) {
   typedef typename Cplx<R>::T C;
   // Thread (tx, ty) owns rows R*TS + tx + 16v and columns S*TS + ty + 16u,
-  // u, v = 0..3: its 16 elements give 4 row and 4 column partials of p,
+  // u, v < EPT: its EPT^2 elements give EPT row and EPT column partials of p,
   // reduced once per tile through shared memory.
+  constexpr int EPT = TS / 16;
   __shared__ C vpS[TS], wpS[TS], vcS[TS];
-  __shared__ C rowred[TS / 4][TS];   // [ty][row]
-  __shared__ C colred[TS / 4][TS];   // [tx][col]
+  __shared__ C rowred[16][TS];   // [ty][row]
+  __shared__ C colred[16][TS];   // [tx][col]
   __shared__ double sh[NT / 32 + 1];
   __shared__ int is_last;
 
   const int b = blockIdx.y, tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int nt = (n + TS - 1) / TS, t0 = (j + 1) / TS, r0 = j + 1;
+  const int nt = (n + TS - 1) / TS, t0 = (j + 1) / TS, r0 = j + 1;   // TS: template
   const C zero = Cplx<R>::make((R)0, (R)0);
   C* a = A + (size_t)b * n * n;
   C* vb = vec + (size_t)b * 3 * n;
@@ -171,9 +174,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) tridiag_step_kerne
     wpS[tid] = ok ? w[s] : zero;
     vcS[tid] = ok ? vcur[s] : zero;
   }
-  C vpr[4], wpr[4], vcr[4], racc[4];
+  C vpr[EPT], wpr[EPT], vcr[EPT], racc[EPT];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < EPT; ++v) {
     const int r = rbase + tx + 16 * v;
     const bool ok = r < n && r >= r0;
     vpr[v] = ok ? vprev[r] : zero;
@@ -188,26 +191,26 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) tridiag_step_kerne
   // in a loop that is otherwise light).  FP64: interleaved, the FP64 pipe
   // hides the latency and the registers are needed for the accumulators.
   constexpr bool kHoist = sizeof(R) == 4;
-  C xs[4][4];
+  C xs[EPT][EPT];
   if constexpr (kHoist) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < EPT; ++u) {
       const int s = sbase + ty + 16 * u;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
+      for (int v = 0; v < EPT; ++v) {
         const int r = rbase + tx + 16 * v;
         xs[u][v] = (s >= r0 && r < n && r >= s) ? a[r + (size_t)s * n] : zero;
       }
     }
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < EPT; ++u) {
     const int sl = ty + 16 * u, s = sbase + sl;
     const C vps = vpS[sl], wps = wpS[sl], vcs = vcS[sl];
     C cacc = zero;
     const bool sok = s >= r0;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < EPT; ++v) {
       const int r = rbase + tx + 16 * v;
       if (sok && r < n && r >= s) {
         C x;
@@ -224,14 +227,14 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) tridiag_step_kerne
     colred[tx][sl] = cacc;
   }
 #pragma unroll
-  for (int v = 0; v < 4; ++v) rowred[ty][tx + 16 * v] = racc[v];
+  for (int v = 0; v < EPT; ++v) rowred[ty][tx + 16 * v] = racc[v];
   __syncthreads();
   if (tid < 2 * TS) {
     const bool isrow = tid < TS;
     const int l = isrow ? tid : tid - TS;
     C acc = zero;
 #pragma unroll
-    for (int q = 0; q < TS / 4; ++q) acc = zadd(acc, isrow ? rowred[q][l] : colred[q][l]);
+    for (int q = 0; q < 16; ++q) acc = zadd(acc, isrow ? rowred[q][l] : colred[q][l]);
     if (Rt == St) {
       // diagonal tile: row and column partials of the same index meet here
       if (isrow) rowred[0][l] = acc;
@@ -294,40 +297,38 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) tridiag_step_kerne
 }  // namespace
 
 size_t bs_tridiag_vec_elems(int n) { return 3 * (size_t)n; }
-size_t bs_tridiag_part_elems(int n) { return (size_t)((n + TS - 1) / TS) * n; }
+size_t bs_tridiag_part_elems(int n) { return (size_t)((n + TSMIN - 1) / TSMIN) * n; }
 
-template <typename R>
-int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
-                      typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
-                      unsigned* count, cudaStream_t s) {
-  typedef typename Cplx<R>::T C;
-  // The whole batch runs in every step launch.  (Reducing it in L2-sized
-  // groups one after another was measured slower for FP32: the per-step
-  // launch and epilogue latency then repeats once per group.)
-  const int group = batch;
+template <typename R, int TS>
+static int launch_steps(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
+                        typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
+                        unsigned* count, cudaStream_t s) {
+  tridiag_init_kernel<R><<<batch, NT, 0, s>>>(A, n, vec, de, tau, beta, count);
+  BS_CHECK_LAUNCH("tridiag_init_kernel");
   const int nt = (n + TS - 1) / TS;
-  for (int g0 = 0; g0 < batch; g0 += group) {
-    const int gb = std::min(group, batch - g0);
-    C* Ag = A + (size_t)g0 * n * n;
-    C* vg = vec + (size_t)g0 * bs_tridiag_vec_elems(n);
-    C* pg = part + (size_t)g0 * bs_tridiag_part_elems(n);
-    double* dg = de + (size_t)g0 * 2 * n;
-    double* tg = tau + (size_t)g0 * n;
-    zd* bg = beta + (size_t)g0 * n;
-    unsigned* cg = count + g0;
-    tridiag_init_kernel<R><<<gb, NT, 0, s>>>(Ag, n, vg, dg, tg, bg, cg);
-    BS_CHECK_LAUNCH("tridiag_init_kernel");
-    for (int j = 0; j + 1 < n; ++j) {
-      const int m = nt - (j + 1) / TS;
-      const int ntl = m * (m + 1) / 2;
-      tridiag_step_kernel<R><<<dim3(ntl, gb), NT, 0, s>>>(Ag, n, j, vg, pg, dg, tg, bg, cg, ntl);
-      BS_CHECK_LAUNCH("tridiag_step_kernel");
-    }
+  for (int j = 0; j + 1 < n; ++j) {
+    const int m = nt - (j + 1) / TS;
+    const int ntl = m * (m + 1) / 2;
+    tridiag_step_kernel<R, TS><<<dim3(ntl, batch), NT, 0, s>>>(A, n, j, vec, part, de, tau, beta,
+                                                               count, ntl);
+    BS_CHECK_LAUNCH("tridiag_step_kernel");
   }
   return BS_OK;
 }
 
+template <typename R>
+int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
+                      typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
+                      unsigned* count, cudaStream_t s, int tile) {
+  // The whole batch runs in every step launch.  (Reducing it in L2-sized
+  // groups one after another was measured slower for FP32: the per-step
+  // launch and epilogue latency then repeats once per group.)
+  if (tile == 32)
+    return launch_steps<R, 32>(A, n, batch, vec, part, de, tau, beta, count, s);
+  return launch_steps<R, 64>(A, n, batch, vec, part, de, tau, beta, count, s);
+}
+
 template int bs_launch_tridiag<double>(zd*, int, int, zd*, zd*, double*, double*, zd*, unsigned*,
-                                       cudaStream_t);
+                                       cudaStream_t, int);
 template int bs_launch_tridiag<float>(zf*, int, int, zf*, zf*, double*, double*, zd*, unsigned*,
-                                      cudaStream_t);
+                                      cudaStream_t, int);
