@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2"])
+    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3"])
+    ap.add_argument("--cells", type=int, default=4096, help="cells of the config-3 batch")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=6)
@@ -182,6 +183,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.config == "c3":
+        return run_reference_batch(args)
     cfg, config, _ = workload(args.config)
     cores = len(os.sched_getaffinity(0))
     times, vals = [], []
@@ -270,6 +273,178 @@ def measure_tensor(bs, torch, stream, nk, n):
             "shape": f"{zb} x [{Mg} x {Ng} x {Kg}] BF16 -> FP32", "ms": tc_ms,
             "achieved_tflops": tflops, "peak_tflops": 1940.2,
             "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)", "frac": tflops / 1940.2}
+
+
+def run_batch(args):
+    """Config 3: a ragged batch of cells on the mixed path (bs_batch_*)."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1310_6380_gb300 import binding as bs
+    from paper_1310_6380_gb300 import cells
+
+    ncell, nk, nb = args.cells, 30, 10
+    cfgs = [cells.config3_cell(i) for i in range(ncell)]
+    cargs = [(c["cell"].h1, c["cell"].h2, np.ascontiguousarray(c["cell"].phase, np.uint16),
+              c["cell"].lam, c["cell"].mu, c["cell"].rho, c["M"], bs.BS_PREC_MIXED) for c in cfgs]
+    Ms = [c["M"] for c in cfgs]
+    ns = np.array([2 * (2 * m + 1) ** 2 for m in Ms])
+    Qd = torch.tensor(np.stack([c["Q"] for c in cfgs]), device="cuda")
+    b = bs.bs_batch_create(cargs, nk, nb)
+    w = torch.empty((ncell, nk, nb), dtype=torch.float64, device="cuda")
+    st = torch.empty((ncell, nk), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(graph):
+        bs.bs_batch_set_graph(b, graph)
+        bs.bs_batch_set_profiling(b, not graph)
+        for _ in range(args.warmup):
+            bs.bs_batch_solve(b, Qd, w, st, stream)
+        barrier()
+        times, phs = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bs.bs_batch_solve(b, Qd, w, st, stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            if not graph:
+                phs.append(bs.bs_batch_phase_times(b))
+        barrier()
+        return statistics.mean(times), phs
+
+    launches0 = bs.bs_launch_count()
+    sampler = ClockSampler(device_bus_id(torch))
+    sampler.start()
+    ms_plain, phs = timed(False)
+    clocks = sampler.stop()
+    launches = (bs.bs_launch_count() - launches0) // max(1, args.steps + args.warmup)
+    ms_graph, _ = timed(True)
+    ms = min(ms_plain, ms_graph)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    omega = w.cpu().numpy()
+    status = st.cpu().numpy()
+    ph = {k: statistics.mean(p[k] for p in phs) for k in phs[0]}
+    bs.bs_batch_destroy(b)
+
+    # end to end through the public API with pinned host buffers: create the
+    # batch from host arrays (includes the copies to the device), solve with
+    # host wavevectors and outputs (includes the first call's tile tuning), destroy
+    hQ = torch.from_numpy(np.stack([c["Q"] for c in cfgs])).pin_memory()
+    hw = torch.empty((ncell, nk, nb), dtype=torch.float64).pin_memory()
+    hs = torch.empty((ncell, nk), dtype=torch.int32).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b2 = bs.bs_batch_create(cargs, nk, nb)
+        bs.bs_batch_solve(b2, hQ, hw, hs, stream)
+        bs.bs_batch_destroy(b2)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = sum(a[2].nbytes + 3 * a[3].nbytes for a in cargs) + hQ.numel() * 8
+    e2e = {"value": world * ncell * nk / e2e_s, "unit": "k-solves/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": hw.numel() * 8 + hs.numel() * 4,
+           "api": "bs_batch_create (host arrays) + bs_batch_solve (host Q, outputs; first call "
+                  "includes tile autotuning) + bs_batch_destroy"}
+    # dominant kernel: the FP32 Householder reduction (HBM/latency bound)
+    tri_bytes = sum(nk * sum(m * (m + 1) // 2 for m in range(1, int(n))) * 16.0 for n in ns)
+    achieved = tri_bytes / (ph["reduction"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "tridiag_step_kernel<float> (all launches of one step)",
+                "achieved": achieved, "peak": 6771.1, "unit": "GB/s", "frac": achieved / 6771.1,
+                "traffic": None, "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+                "algorithmic": "read + write (8 B each) of every trailing lower triangle of "
+                               f"{ncell * nk} matrices (n = 242..578)"}
+    value = world * ncell * nk / (ms / 1e3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 reduction, bf16 exact-slice tensor products, f64 refinement",
+        "data": "synthetic",
+        "config": {"workload": f"c3: {ncell} cells (seeds 6380+i), 64x64 pixels, square/hex, "
+                               "ellipse/Voronoi maps with 2-16 phases, M = 5..8 (n = 242..578), "
+                               "30 k per cell on its IBZ path, lowest 10 branches, mixed path",
+                   "cells": ncell, "k_points": ncell * nk,
+                   "cells_per_M": {int(m): Ms.count(m) for m in sorted(set(Ms))},
+                   "l2": "flushed between timed steps (256 MiB write, untimed)"},
+        "ms_per_step_plain": ms_plain, "ms_per_step_graph": ms_graph,
+        "tiles": bs.bs_batch_tiles(b), "phases_ms": {k: round(v, 1) for k, v in ph.items()},
+        "status_nonzero": int(np.count_nonzero(status)), "gpu_launches_per_step": launches,
+        "gpu_launches": launches * args.steps, "e2e": e2e, "roofline": roofline, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import mixed_variational as mv
+        samp = list(range(0, ncell, max(1, ncell // 8)))[:8]
+        t0 = time.perf_counter()
+        errs = []
+        for i in samp:
+            c = cfgs[i]
+            oc = mv.OracleCell(c["cell"], c["M"])
+            ref = np.array([oc.omega(q, nb) for q in c["Q"]])
+            errs.append(rel_err(omega[i], ref, c["cell"]).max())
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(samp) * nk / secs, "unit": "k-solves/s",
+                               "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                               "sample": f"{len(samp)} of the {ncell} cells, all 30 k each "
+                                         f"({secs:.1f} s); value = their k-solves / time"}
+        out["max_rel_err_vs_oracle"] = float(max(errs))
+        out["oracle_sampled_cells"] = samp
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference_batch(args):
+    """The oracle on the host cores for config 3: each step solves 2 of the
+    batch's cells (all 30 k), value = k-solves / time."""
+    from oracle import mixed_variational as mv
+    from paper_1310_6380_gb300 import cells
+    times, vals = [], []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        nsolve = 0
+        for ci in (2 * i, 2 * i + 1):
+            c = cells.config3_cell(ci)
+            oc = mv.OracleCell(c["cell"], c["M"])
+            for q in c["Q"]:
+                oc.omega(q, 10)
+                nsolve += 1
+        secs = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(secs)
+            vals.append(nsolve / secs)
+    value = statistics.mean(vals)
+    cores = len(os.sched_getaffinity(0))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "k-solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"c3: {args.cells} cells, 64x64, M = 5..8, 30 k, 10 branches"},
+        "cpu_baseline": {"value": value, "unit": "k-solves/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step: 2 cells of the batch, all 30 k each"},
+        "e2e": {"value": value, "unit": "k-solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
 
 
 def run_ours(args):
@@ -441,6 +616,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "c3":
+        run_batch(args)
     else:
         run_ours(args)
 

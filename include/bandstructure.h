@@ -227,6 +227,12 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   of the recording call must be reused); on == 0 drops the graph.
  * bs_batch_tiles - the tile edge chosen for each truncation group and the
  *   group's eigen dimension n.
+ * bs_batch_set_profiling / bs_batch_phase_times - with profiling on, a
+ *   solve that does not replay a graph records CUDA events around each
+ *   chunk's phases; phase_times returns milliseconds summed over chunks:
+ *   ms[0] assembly (all cells' k-independent set-up and C(k) build),
+ *   ms[1] FP32 Householder reduction, ms[2] eigenvalue shifts, ms[3] FP64
+ *   refinement.
  * bs_batch_destroy - free everything (NULL is a no-op).
  */
 typedef struct bs_batch bs_batch;
@@ -235,6 +241,8 @@ int bs_batch_solve(bs_batch* batch, const double* Q, double* omega_out, int* sta
                    void* stream);
 int bs_batch_set_graph(bs_batch* batch, int on);
 int bs_batch_tiles(const bs_batch* batch, int* tiles, int* ns, int ngroups_max, int* ngroups);
+int bs_batch_set_profiling(bs_batch* batch, int on);
+int bs_batch_phase_times(bs_batch* batch, double ms[4]);
 int bs_batch_destroy(bs_batch* batch);
 
 /* bs_cell_dims - N (plane waves) and n = 2N (eigen dimension). */

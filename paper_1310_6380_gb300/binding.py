@@ -65,6 +65,8 @@ def _load():
         "bs_batch_set_graph": [vp, i32],
         "bs_batch_tiles": [vp, dp, dp, i32, ctypes.POINTER(i32)],
         "bs_batch_destroy": [vp],
+        "bs_batch_set_profiling": [vp, i32],
+        "bs_batch_phase_times": [vp, dp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -82,7 +84,8 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_reduced_matrix", "bs_cell_dims", "bs_sync", "bs_destroy_cell", "bs_last_error",
             "bs_set_profiling", "bs_phase_times", "bs_launch_count", "bs_tridiag_eigenvalues",
             "bs_gemm_bf16", "bs_tridiag_eigenvalues_static", "bs_batch_create", "bs_batch_solve",
-            "bs_batch_set_graph", "bs_batch_tiles", "bs_batch_destroy"]
+            "bs_batch_set_graph", "bs_batch_tiles", "bs_batch_destroy", "bs_batch_set_profiling",
+            "bs_batch_phase_times"]
 
 
 def bs_last_error() -> str:
@@ -209,6 +212,16 @@ def bs_batch_tiles(batch):
     ng = ctypes.c_int()
     _check(_lib.bs_batch_tiles(batch, tiles.ctypes.data, ns.ctypes.data, 16, ctypes.byref(ng)))
     return dict(zip(ns[:ng.value].tolist(), tiles[:ng.value].tolist()))
+
+
+def bs_batch_set_profiling(batch, on: bool):
+    _check(_lib.bs_batch_set_profiling(batch, int(bool(on))))
+
+
+def bs_batch_phase_times(batch) -> dict:
+    ms = np.zeros(4)
+    _check(_lib.bs_batch_phase_times(batch, ms.ctypes.data))
+    return dict(zip(("assembly", "reduction", "shifts", "refinement"), ms.tolist()))
 
 
 def bs_batch_destroy(batch):

@@ -130,7 +130,24 @@ struct bs_batch {
   cudaGraphExec_t graph;
   cudaStream_t cap;       // non-blocking stream the graph is recorded and replayed on
   cudaEvent_t ev_in, ev_out;
+  // profiling: event pairs per chunk and phase (assembly, reduction, shifts, refinement)
+  bool prof;
+  std::vector<cudaEvent_t> pev;
+  size_t pev_used;
 };
+
+static void prof_mark(bs_batch* B, cudaStream_t s) {
+  if (!B->prof) return;
+  if (B->pev_used == B->pev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    B->pev.push_back(e);
+  }
+  cudaEventRecord(B->pev[B->pev_used++], s);
+}
 
 static void free_group(BatchGroup& g) {
   for (int w = 0; w < g.nworkers; ++w) {
@@ -226,6 +243,7 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
                      int tile) {
   const int nk = B->nk, n = g.n, b = g.b;
   const size_t nn = (size_t)n * n;
+  prof_mark(B, s);   // assembly begins
   // fork: the workers start after everything already queued on s
   CK(cudaEventRecord(g.fork, s), "batch fork");
   for (int w = 0; w < g.nworkers; ++w) CK(cudaStreamWaitEvent(g.wstream[w], g.fork, 0), "batch fork");
@@ -247,15 +265,19 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
     CK(cudaStreamWaitEvent(s, g.wdone[w], 0), "batch join");
   }
   const int K = cn * nk;
+  prof_mark(B, s);   // assembly ends, reduction begins
   TRY_LAUNCH(bs_launch_tridiag<float>(g.C32, n, K, g.vec32, g.part32, g.de, g.tau, g.beta, g.count,
                                       s, tile));
+  prof_mark(B, s);
   TRY_LAUNCH(bs_launch_bisect(g.de, n, K, b + 1, g.lamT, nullptr, s, false, 1e-9));
+  prof_mark(B, s);
   MixedWs w;
   w.C64 = g.C64; w.C32 = g.C32; w.de = g.de; w.tau = g.tau; w.beta = g.beta; w.lamT = g.lamT;
   w.scratch = g.scr; w.Y = g.Y; w.phase = g.phase; w.X32 = g.X32; w.X64 = g.X64; w.CX = g.CX;
   w.G = g.G; w.H = g.H; w.W = g.W; w.theta = g.theta; w.cxA = g.cxA; w.cxB = g.cxB;
   w.cxD = g.cxD; w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
   TRY_LAUNCH(bs_launch_mixed_refine(w, n, K, B->nbands, b, 1e-6, floor2, g.w, g.st, s));
+  prof_mark(B, s);   // refinement ends
   // scatter (cell, k) rows into caller order
   const int* rows = g.d_rowidx + (size_t)c0 * nk;
   scatter_rows_kernel<<<(K * B->nbands + 255) / 256, 256, 0, s>>>(g.w, rows, K, B->nbands,
@@ -440,6 +462,7 @@ extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, in
 extern "C" int bs_batch_destroy(bs_batch* B) {
   if (!B) return BS_OK;
   for (auto& g : B->groups) free_group(g);
+  for (cudaEvent_t e : B->pev) cudaEventDestroy(e);
   if (B->graph) cudaGraphExecDestroy(B->graph);
   if (B->cap) cudaStreamDestroy(B->cap);
   if (B->ev_in) cudaEventDestroy(B->ev_in);
@@ -507,6 +530,36 @@ static int tune_group(bs_batch* B, BatchGroup& g, double floor2, cudaStream_t s)
   return BS_OK;
 }
 
+extern "C" int bs_batch_set_profiling(bs_batch* B, int on) {
+  if (!B) {
+    bs_set_error("bs_batch_set_profiling: NULL batch");
+    return BS_EINVAL;
+  }
+  B->prof = on != 0;
+  B->pev_used = 0;
+  return BS_OK;
+}
+
+// ms[0] assembly, ms[1] reduction, ms[2] shifts, ms[3] refinement (sums over chunks of the
+// last non-graph solve)
+extern "C" int bs_batch_phase_times(bs_batch* B, double ms[4]) {
+  if (!B || !ms) {
+    bs_set_error("bs_batch_phase_times: NULL argument");
+    return BS_EINVAL;
+  }
+  for (int i = 0; i < 4; ++i) ms[i] = 0.0;
+  if (!B->prof) return BS_OK;
+  for (size_t c = 0; c + 5 <= B->pev_used; c += 5) {   // 5 marks per chunk
+    CK(cudaEventSynchronize(B->pev[c + 4]), "bs_batch_phase_times");
+    for (int i = 0; i < 4; ++i) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, B->pev[c + i], B->pev[c + i + 1]), "bs_batch_phase_times");
+      ms[i] += t;
+    }
+  }
+  return BS_OK;
+}
+
 static int solve_all(bs_batch* B, const std::vector<double>& floors, cudaStream_t s) {
   for (auto& g : B->groups) {
     double f2 = 1e300;
@@ -537,6 +590,8 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
     for (int i = 0; i < B->ncells; ++i) floors[i] = floor2_of(B, i, raw);
   }
   CK(cudaMemcpyAsync(B->d_Q, Q, nq * 2 * sizeof(double), cudaMemcpyDefault, s), "bs_batch_solve Q");
+  const bool prof = B->prof;
+  B->prof = false;   // not while tuning or recording a graph
   for (auto& g : B->groups) {
     if (g.tuned) continue;
     double f2 = 1e300;
@@ -569,8 +624,11 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
     CK(cudaEventRecord(B->ev_out, B->cap), "bs_batch_solve order");
     CK(cudaStreamWaitEvent(s, B->ev_out, 0), "bs_batch_solve order");
   } else {
+    B->prof = prof;
+    B->pev_used = 0;
     TRY_LAUNCH(solve_all(B, floors, s));
   }
+  B->prof = prof;
   CK(cudaMemcpyAsync(omega_out, B->d_w, nq * B->nbands * sizeof(double), cudaMemcpyDefault, s),
      "bs_batch_solve omega");
   if (status_out)
