@@ -134,6 +134,46 @@ int bs_bands(bs_cell* cell, int path, int nk, int nbands,
              double* Q_out, double* omega_out, void* stream);
 
 /*
+ * bs_solve_k_lobpcg - the lowest `nbands` angular frequencies of the same
+ * eigenproblem (Eq. (eigenvalueproblem)) by block LOBPCG instead of a dense
+ * reduction.  The paper solves the dense problem; this iterative path is an
+ * addition whose cost depends on the starting block, so a good guess of the
+ * eigen-subspace (the previous wavevector's vectors, or a learned
+ * prediction) saves iterations.
+ *   Iterations run in FP32 on C(k) (block of 16 vectors, fewer when n is
+ *   small; diagonal preconditioner; soft locking; at most BS_LOB_MAXIT;
+ *   the wanted columns stop once their FP32 residual meets the bound below
+ *   with a margin); an FP64 Rayleigh-Ritz projection then gives the
+ *   frequencies, certified by the same residual bound as the mixed path
+ *   (|theta - lambda| <= ||r||^2 / gap <= 2 tol max(theta, omega_floor^2)).
+ *   Wavevectors the bound does not certify are solved again by the dense
+ *   FP64 path (the fallback); their status is that solve's.
+ *   Q, omega_out, status_out : as bs_solve_k (host or device).
+ *   X0       : optional starting vectors, nk x nvec x n complex64
+ *              (interleaved re, im) of plane-wave displacement coefficients
+ *              u (index I*N + a, component I in {x, y}, wave a in the order
+ *              of bs_cell_desc's M), host or device; NULL for the cold
+ *              start (unit vectors at the smallest diagonal entries of
+ *              C(k), with 1e-3 deterministic noise).  Columns beyond nvec
+ *              come from the cold start.  0 <= nvec <= b.
+ *   iters_out : nk ints, FP32 iterations taken (-1: the starting block
+ *              could not be made full rank), or NULL; host or device.
+ *   fallback_out : nk ints, 1 where the dense fallback was used, or NULL.
+ *   vec_out  : optional nk x nbands x n complex64 eigenvectors u (Ritz
+ *              vectors of the FP64 projection, u^dagger Omega u = 1), NaN
+ *              for wavevectors that fell back; host or device.
+ * Requires a BS_PREC_MIXED cell, 1 <= nbands <= BS_LOB_MAX_BANDS,
+ * nbands + 5 <= n and n <= 2048 (BS_EINVAL otherwise).  Synchronises
+ * `stream`.  Returns BS_ENOCONV when status_out is NULL and a fallback
+ * solve failed.
+ */
+#define BS_LOB_MAX_BANDS 12
+#define BS_LOB_MAXIT 80
+int bs_solve_k_lobpcg(bs_cell* cell, const double* Q, int nk, int nbands,
+                      const float* X0, int nvec, double* omega_out, int* status_out,
+                      int* iters_out, int* fallback_out, float* vec_out, void* stream);
+
+/*
  * bs_form_factors - copy the assembled form factors to `out`
  * (host or device): 3 fields (1/(lam+mu), 1/mu, rho) x D x D complex
  * (interleaved re, im), D = 4M+1, index [f][da+2M][db+2M].

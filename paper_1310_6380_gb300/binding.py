@@ -67,6 +67,7 @@ def _load():
         "bs_batch_destroy": [vp],
         "bs_batch_set_profiling": [vp, i32],
         "bs_batch_phase_times": [vp, dp],
+        "bs_solve_k_lobpcg": [vp, dp, i32, i32, dp, i32, dp, dp, dp, dp, dp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -85,7 +86,8 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_set_profiling", "bs_phase_times", "bs_launch_count", "bs_tridiag_eigenvalues",
             "bs_gemm_bf16", "bs_tridiag_eigenvalues_static", "bs_batch_create", "bs_batch_solve",
             "bs_batch_set_graph", "bs_batch_tiles", "bs_batch_destroy", "bs_batch_set_profiling",
-            "bs_batch_phase_times"]
+            "bs_batch_phase_times", "bs_solve_k_lobpcg"]
+BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
 
 
 def bs_last_error() -> str:
@@ -108,7 +110,7 @@ def _ptr(x, dtype):
     if hasattr(x, "data_ptr"):
         import torch
         tdt = {np.float64: torch.float64, np.uint16: torch.uint16, np.int32: torch.int32,
-               np.float32: torch.float32}[dtype]
+               np.float32: torch.float32, np.complex64: torch.complex64}[dtype]
         if x.dtype != tdt or not x.is_contiguous():
             raise TypeError(f"expected a contiguous {tdt} tensor")
         return x.data_ptr()
@@ -147,6 +149,19 @@ def bs_solve_k(cell, Q, nbands: int, omega_out, status_out=None, stream=None):
     _check(_lib.bs_solve_k(cell, _ptr(Q, np.float64), nk, int(nbands),
                            _ptr(omega_out, np.float64), _ptr(status_out, np.int32),
                            _stream(stream)))
+    return omega_out
+
+
+def bs_solve_k_lobpcg(cell, Q, nbands: int, omega_out, X0=None, status_out=None, iters_out=None,
+                      fallback_out=None, vec_out=None, stream=None):
+    """X0: (nk, nvec, n) complex64 starting vectors (displacement coefficients) or None;
+    vec_out: (nk, nbands, n) complex64 or None."""
+    nk = int(Q.shape[0])
+    nvec = 0 if X0 is None else int(X0.shape[1])
+    _check(_lib.bs_solve_k_lobpcg(cell, _ptr(Q, np.float64), nk, int(nbands), _ptr(X0, np.complex64),
+                                  nvec, _ptr(omega_out, np.float64), _ptr(status_out, np.int32),
+                                  _ptr(iters_out, np.int32), _ptr(fallback_out, np.int32),
+                                  _ptr(vec_out, np.complex64), _stream(stream)))
     return omega_out
 
 

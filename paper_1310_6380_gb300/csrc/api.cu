@@ -139,6 +139,41 @@ static void free_workspace(bs_cell* c) {
   c->wcap = 0;
 }
 
+static void free_lob_workspace(bs_cell* c) {
+  void* p[] = {c->d_lS, c->d_lCS, c->d_lA, c->d_lpart, c->d_lZ, c->d_lY, c->d_lst, c->d_lX0,
+               c->d_lndone, c->d_liters, c->d_lvec};
+  for (void* q : p) cudaFree(q);
+  c->d_lS = c->d_lCS = c->d_lA = c->d_lpart = c->d_lZ = c->d_lY = c->d_lX0 = nullptr;
+  c->d_lst = nullptr;
+  c->d_lndone = c->d_liters = nullptr;
+  c->d_lvec = nullptr;
+  c->lcap = 0;
+  c->lbcap = 0;
+}
+
+// LOBPCG workspace for `kb` wavevectors and block size `b`
+static int ensure_lob_workspace(bs_cell* c, int kb, int b) {
+  if (kb <= c->lcap && b <= c->lbcap) return BS_OK;
+  kb = std::max(kb, c->lcap);
+  b = std::max(b, c->lbcap);
+  free_lob_workspace(c);
+  const size_t n = c->n, coef = (size_t)BS_LOB_MAX_BLOCK * 3 * BS_LOB_MAX_BLOCK;
+  TRY(dalloc(&c->d_lS, 2 * (size_t)kb * 3 * b * n, "LOBPCG basis"));
+  TRY(dalloc(&c->d_lCS, 2 * (size_t)kb * 3 * b * n, "LOBPCG C basis"));
+  TRY(dalloc(&c->d_lA, (size_t)kb * bs_lob_small_elems(), "LOBPCG Gram"));
+  TRY(dalloc(&c->d_lpart, (size_t)kb * bs_lob_part_elems(c->n), "LOBPCG partial Gram"));
+  TRY(dalloc(&c->d_lZ, (size_t)kb * coef, "LOBPCG Ritz coefficients"));
+  TRY(dalloc(&c->d_lY, (size_t)kb * coef, "LOBPCG P coefficients"));
+  TRY(dalloc(&c->d_lst, (size_t)kb, "LOBPCG state"));
+  TRY(dalloc(&c->d_lX0, (size_t)kb * b * n, "LOBPCG starting block"));
+  TRY(dalloc(&c->d_lndone, 1, "LOBPCG counter"));
+  TRY(dalloc(&c->d_liters, (size_t)kb, "LOBPCG iterations"));
+  TRY(dalloc(&c->d_lvec, (size_t)kb * b * n, "LOBPCG vectors"));
+  c->lcap = kb;
+  c->lbcap = b;
+  return BS_OK;
+}
+
 // per-k workspace for `kb` matrices and `nb` bands
 static int ensure_workspace(bs_cell* c, int kb, int nb) {
   if (kb <= c->kcap && nb <= c->wcap) return BS_OK;
@@ -318,6 +353,7 @@ extern "C" int bs_destroy_cell(bs_cell* c) {
   if (!c) return BS_OK;
   bs_set_profiling(c, 0);
   free_workspace(c);
+  free_lob_workspace(c);
   cudaFree(c->d_phase);
   cudaFree(c->d_table);
   cudaFree(c->d_E);
@@ -508,6 +544,203 @@ extern "C" int bs_solve_k(bs_cell* c, const double* Q, int nk, int nbands, doubl
           return BS_ENOCONV;
         }
   }
+  return BS_OK;
+}
+
+// ------------------------------------------------------------------ LOBPCG
+// One chunk of kb wavevectors (in c->d_Q): FP32 LOBPCG from the starting
+// block, FP64 Rayleigh-Ritz tail; omega / status in c->d_w / c->d_stat,
+// iterations in c->d_liters, vectors (optional) in c->d_lvec.
+static int solve_chunk_lobpcg(bs_cell* c, int kb, int nbands, int b, const float* X0, bool x0_dev,
+                              int nvec, bool want_vec, cudaStream_t s) {
+  const int n = c->n, N = c->N;
+  bs_phase_begin(c, PH_BUILD, s);
+  TRY(bs_launch_builder_mixed(c->d_Cm, n, c->d_Q, kb, c->q1[0], c->q1[1], c->q2[0], c->q2[1],
+                              c->d_C, c->d_C32, s, true));
+  if (nvec > 0) {
+    // starting vectors in displacement coefficients -> reduced basis y = L_R^dagger u
+    CK(cudaMemcpyAsync(c->d_lvec, X0, (size_t)kb * nvec * n * sizeof(float2),
+                       x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+       "LOBPCG starting vectors");
+    TRY(bs_launch_lob_to_reduced(c->d_lvec, c->d_T + 2 * (size_t)N * N, N, kb, nvec, c->d_lX0, s));
+  }
+  bs_phase_end(c, PH_BUILD, s);
+  bs_phase_begin(c, PH_TRID, s);
+  LobWs w;
+  w.C32 = c->d_C32;
+  w.S = c->d_lS;
+  w.CS = c->d_lCS;
+  w.Axp = c->d_lA;
+  w.part = c->d_lpart;
+  w.Z = c->d_lZ;
+  w.Y = c->d_lY;
+  w.st = c->d_lst;
+  w.X0 = nvec > 0 ? c->d_lX0 : nullptr;
+  w.nvec = nvec;
+  w.ndone = c->d_lndone;
+  const float tol32 = (float)std::max(sqrt(c->tol), 3e-4);
+  TRY(bs_launch_lobpcg(w, n, kb, b, nbands, BS_LOB_MAXIT, tol32, (float)c->tol, (float)c->floor2,
+                       4, s));
+  TRY(bs_launch_lob_export(w, n, kb, b, c->d_X64, c->d_liters, s));
+  bs_phase_end(c, PH_TRID, s);
+  bs_phase_begin(c, PH_REFINE, s);
+  MixedWs m;
+  memset(&m, 0, sizeof(m));
+  m.C64 = c->d_C;
+  m.X64 = c->d_X64;
+  m.CX = c->d_CX;
+  m.G = c->d_mG;
+  m.H = c->d_H;
+  m.W = c->d_W;
+  m.theta = c->d_theta;
+  m.lamT = nullptr;
+  m.cxA = c->d_cxA;
+  m.cxB = c->d_cxB;
+  m.cxD = c->d_cxD;
+  m.cxeA = c->d_cxeA;
+  m.cxeB = c->d_cxeB;
+  m.err = c->d_info + 1;
+  CK(cudaMemsetAsync(c->d_stat, 0, kb * sizeof(int), s), "status");
+  TRY(bs_launch_rr_tail(m, n, kb, nbands, b, c->tol, c->floor2, c->d_w, c->d_stat, s));
+  if (want_vec)
+    TRY(bs_launch_lob_vectors(c->d_X64, c->d_W, c->d_Linv + 2 * (size_t)N * N, N, b, nbands, kb,
+                              c->d_lvec, s));
+  bs_phase_end(c, PH_REFINE, s);
+  return BS_OK;
+}
+
+// dense FP64 solve of the wavevectors Qf (host, nf x 2): omega (host, nf x nbands)
+static int solve_dense_fp64(bs_cell* c, const std::vector<double>& Qf, int nbands,
+                            std::vector<double>& om, std::vector<int>& st, cudaStream_t s) {
+  const int nf = (int)Qf.size() / 2;
+  om.assign((size_t)nf * nbands, 0.0);
+  st.assign(nf, 0);
+  const int cap = c->kcap;
+  for (int k0 = 0; k0 < nf; k0 += cap) {
+    const int kb = std::min(cap, nf - k0);
+    CK(cudaMemcpyAsync(c->d_Q, Qf.data() + 2 * (size_t)k0, 2 * kb * sizeof(double),
+                       cudaMemcpyHostToDevice, s), "fallback Q");
+    TRY(bs_launch_builder(c->d_Cm, c->n, c->d_Q, kb, c->q1[0], c->q1[1], c->q2[0], c->q2[1],
+                          c->d_C, s));
+    TRY(bs_launch_tridiag<double>(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
+                                  c->d_beta, c->d_count, s));
+    TRY(bs_launch_bisect(c->d_de, c->n, kb, nbands, c->d_w, c->d_stat, s));
+    CK(cudaMemcpyAsync(om.data() + (size_t)k0 * nbands, c->d_w, (size_t)kb * nbands * 8,
+                       cudaMemcpyDeviceToHost, s), "fallback omega");
+    CK(cudaMemcpyAsync(st.data() + k0, c->d_stat, kb * sizeof(int), cudaMemcpyDeviceToHost, s),
+       "fallback status");
+    CK(cudaStreamSynchronize(s), "fallback sync");
+  }
+  return BS_OK;
+}
+
+extern "C" int bs_solve_k_lobpcg(bs_cell* c, const double* Q, int nk, int nbands,
+                                 const float* X0, int nvec, double* omega_out, int* status_out,
+                                 int* iters_out, int* fallback_out, float* vec_out,
+                                 void* stream) {
+  if (!c || !Q || !omega_out || nk < 0) {
+    bs_set_error("bs_solve_k_lobpcg: NULL argument or nk < 0");
+    return BS_EINVAL;
+  }
+  if (!c->assembled) {
+    bs_set_error("bs_solve_k_lobpcg: call bs_assemble first");
+    return BS_ESTATE;
+  }
+  if (c->precision != BS_PREC_MIXED) {
+    bs_set_error("bs_solve_k_lobpcg: the cell must be created with BS_PREC_MIXED");
+    return BS_EINVAL;
+  }
+  if (nbands < 1 || nbands > BS_LOB_MAX_BANDS || nbands + 5 > c->n || c->n > 2048) {
+    bs_set_error("bs_solve_k_lobpcg: need 1 <= nbands <= %d, nbands + 5 <= n and n <= 2048 "
+                 "(nbands = %d, n = %d)", BS_LOB_MAX_BANDS, nbands, c->n);
+    return BS_EINVAL;
+  }
+  const int b = bs_lob_block(nbands, c->n);
+  if (nvec < 0 || nvec > b || (nvec > 0 && !X0)) {
+    bs_set_error("bs_solve_k_lobpcg: nvec = %d outside [0, %d] or X0 NULL", nvec, b);
+    return BS_EINVAL;
+  }
+  if (nk == 0) return BS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = c->n;
+  const bool q_dev = is_device_ptr(Q), w_dev = is_device_ptr(omega_out);
+  const bool st_dev = status_out && is_device_ptr(status_out);
+  const bool it_dev = iters_out && is_device_ptr(iters_out);
+  const bool fb_dev = fallback_out && is_device_ptr(fallback_out);
+  const bool v_dev = vec_out && is_device_ptr(vec_out);
+  const bool x0_dev = X0 && is_device_ptr(X0);
+  const int cap = std::min(k_batch_cap(c), 1024);
+  TRY(ensure_workspace(c, std::min(nk, cap), nbands));
+  TRY(ensure_lob_workspace(c, std::min(nk, cap), b));
+  std::vector<double> Qh(2 * (size_t)nk);
+  TRY(fetch_to_host(Qh.data(), Q, Qh.size() * sizeof(double)));
+  std::vector<int> fb(nk, 0);
+  for (int k0 = 0; k0 < nk; k0 += cap) {
+    const int kb = std::min(cap, nk - k0);
+    CK(cudaMemcpyAsync(c->d_Q, Qh.data() + 2 * (size_t)k0, 2 * kb * sizeof(double),
+                       cudaMemcpyHostToDevice, s), "bs_solve_k_lobpcg Q");
+    TRY(solve_chunk_lobpcg(c, kb, nbands, b, X0 ? X0 + (size_t)k0 * nvec * n * 2 : nullptr, x0_dev,
+                           nvec, vec_out != nullptr, s));
+    CK(cudaMemcpyAsync(omega_out + (size_t)k0 * nbands, c->d_w, (size_t)kb * nbands * sizeof(double),
+                       w_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+       "bs_solve_k_lobpcg omega");
+    if (iters_out)
+      CK(cudaMemcpyAsync(iters_out + k0, c->d_liters, kb * sizeof(int),
+                         it_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+         "bs_solve_k_lobpcg iterations");
+    if (vec_out)
+      CK(cudaMemcpyAsync(vec_out + (size_t)k0 * nbands * n * 2, c->d_lvec,
+                         (size_t)kb * nbands * n * sizeof(float2),
+                         v_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+         "bs_solve_k_lobpcg vectors");
+    std::vector<int> sth(kb);
+    CK(cudaMemcpyAsync(sth.data(), c->d_stat, kb * sizeof(int), cudaMemcpyDeviceToHost, s),
+       "bs_solve_k_lobpcg status");
+    TRY(check_info(c, s));
+    for (int k = 0; k < kb; ++k) fb[k0 + k] = sth[k] != 0;
+  }
+  // dense FP64 fallback for the wavevectors the residual bound did not certify
+  std::vector<double> Qf;
+  std::vector<int> idx;
+  for (int k = 0; k < nk; ++k)
+    if (fb[k]) {
+      idx.push_back(k);
+      Qf.push_back(Qh[2 * (size_t)k]);
+      Qf.push_back(Qh[2 * (size_t)k + 1]);
+    }
+  std::vector<int> stk(nk, 0);
+  if (!idx.empty()) {
+    bs_phase_begin(c, PH_BISECT, s);
+    std::vector<double> om;
+    std::vector<int> st;
+    TRY(solve_dense_fp64(c, Qf, nbands, om, st, s));
+    bs_phase_end(c, PH_BISECT, s);
+    const std::vector<float> nanv((size_t)nbands * n * 2, NAN);
+    for (size_t t = 0; t < idx.size(); ++t) {
+      const int k = idx[t];
+      stk[k] = st[t];
+      CK(cudaMemcpyAsync(omega_out + (size_t)k * nbands, om.data() + t * nbands, nbands * 8,
+                         w_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s),
+         "fallback scatter");
+      if (vec_out)
+        CK(cudaMemcpyAsync(vec_out + (size_t)k * nbands * n * 2, nanv.data(), nanv.size() * 4,
+                           v_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s),
+           "fallback vectors");
+    }
+    CK(cudaStreamSynchronize(s), "fallback sync");
+  }
+  if (status_out)
+    CK(cudaMemcpyAsync(status_out, stk.data(), nk * sizeof(int),
+                       st_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s), "status out");
+  if (fallback_out)
+    CK(cudaMemcpyAsync(fallback_out, fb.data(), nk * sizeof(int),
+                       fb_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s), "fallback out");
+  CK(cudaStreamSynchronize(s), "bs_solve_k_lobpcg sync");
+  for (int k = 0; k < nk; ++k)
+    if (stk[k] && !status_out) {
+      bs_set_error("bs_solve_k_lobpcg: wavevector %d did not converge", k);
+      return BS_ENOCONV;
+    }
   return BS_OK;
 }
 

@@ -85,6 +85,8 @@ enum { PH_ASM = 0, PH_GRAM = 1, PH_MONO = 2, PH_BUILD = 3, PH_TRID = 4, PH_BISEC
        PH_REFINE = 6, PH_COUNT = 8 };
 
 // ------------------------------------------------------------------ cell
+struct LobState;
+
 struct bs_cell {
   // geometry and truncation
   int P, M, N, n, D, nphase, precision;
@@ -158,6 +160,20 @@ struct bs_cell {
   double* d_w;         // kcap x nbands_cap output
   int* d_stat;         // kcap
   int wcap;            // capacity of d_w per k
+  // LOBPCG workspace (grown on demand)
+  int lcap;            // k the LOBPCG workspace holds
+  int lbcap;           // block size it was sized for
+  zf* d_lS;
+  zf* d_lCS;
+  zf* d_lA;
+  zf* d_lpart;
+  zf* d_lZ;
+  zf* d_lY;
+  LobState* d_lst;
+  zf* d_lX0;
+  int* d_lndone;
+  int* d_liters;
+  float2* d_lvec;
 
   // profiling: events around each phase of the last call
   bool prof;
@@ -261,10 +277,60 @@ struct MixedWs {
 };
 #define BS_MIXED_MAX_BANDS 24
 int bs_mixed_guard(int nbands, int n);
+// full32: write the whole FP32 matrix (the LOBPCG path), else its lower triangle
 int bs_launch_builder_mixed(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,
-                            double q2x, double q2y, zd* C64, zf* C32, cudaStream_t s);
+                            double q2x, double q2y, zd* C64, zf* C32, cudaStream_t s,
+                            bool full32 = false);
 int bs_launch_mixed_refine(const MixedWs& w, int n, int kb, int nbands, int b, double tol,
                            double floor2, double* omega, int* stat, cudaStream_t s);
+
+// lobpcg.cu: block LOBPCG (FP32) with soft locking, batched over k
+#define BS_LOB_MAX_BLOCK 16
+struct LobState {
+  int done;        // 1: no further iterations (converged, limit or breakdown)
+  int it;          // updates taken
+  int nx, np, nw;  // columns of X, P and W in the current basis
+  int cur;         // which of the two basis buffers is current
+  int npn;         // P columns of the next update
+  int nact;        // unconverged columns of X
+  unsigned amask;  // bit c: column c of X is unconverged
+  int seedfail;    // the starting block could not be made full rank
+  float dshift;    // preconditioner shift (1e-3 of the mean diagonal of C)
+  float rmax;      // largest relative FP32 residual of the wanted columns
+  float theta[BS_LOB_MAX_BLOCK];
+};
+struct LobWs {
+  const zf* C32;   // kb x n x n full Hermitian FP32 C(k), column-major
+  zf* S;           // 2 x kb x 3b x n basis blocks X | P | W (column-major)
+  zf* CS;          // 2 x kb x 3b x n C times the basis blocks
+  zf* Axp;         // kb x (3B)^2 Gram block of [X P] (B = BS_LOB_MAX_BLOCK)
+  zf* part;        // kb x bs_lob_part_elems(n) partial S^dagger C W per row block
+  zf* Z;           // kb x B x 3B Ritz coefficients
+  zf* Y;           // kb x B x 3B coefficients of the P directions
+  LobState* st;    // kb
+  const zf* X0;    // kb x nvec x n starting vectors (reduced basis) or nullptr
+  int nvec;
+  int* ndone;      // finished-k counter
+};
+size_t bs_lob_part_elems(int n);
+size_t bs_lob_small_elems();
+int bs_lob_block(int nbands, int n);
+// seed + iterations (check_every > 0: stop early once every k has finished,
+// reading the counter every check_every iterations; 0: fixed count)
+// tol: relative FP32 residual of every column; tolb: the residual bound the
+// FP64 stage certifies (wanted columns only)
+int bs_launch_lobpcg(const LobWs& w, int n, int kb, int b, int nb, int maxit, float tol,
+                     float tolb, float floor2, int check_every, cudaStream_t s);
+int bs_launch_lob_export(const LobWs& w, int n, int kb, int b, zd* X64, int* iters, cudaStream_t s);
+int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int kb, int nvec, float2* y,
+                             cudaStream_t s);
+int bs_launch_lob_vectors(const zd* X64, const zd* Wc, const zd* LinvR, int N, int b, int nbands,
+                          int kb, float2* out, cudaStream_t s);
+// mixed.cu: the FP64 Rayleigh-Ritz tail on a given FP64 block X64 (CX, G, H,
+// small eigenproblem, residual bound); gap reference lambda_{b+1} of T
+// (lamT) or, when lamT is null, the largest Ritz value of the block
+int bs_launch_rr_tail(const MixedWs& w, int n, int kb, int nbands, int b, double tol,
+                      double floor2, double* omega, int* stat, cudaStream_t s);
 
 // bisect.cu
 // lowest nbands eigenvalues of batch tridiagonals packed as [b][d(n) | e(n-1), pad];

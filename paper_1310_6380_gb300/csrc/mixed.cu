@@ -22,17 +22,18 @@
 namespace {
 
 // ------------------------------------------------------------ builder
-// C64 full (FP64) and C32 lower triangle (FP32) from the full monomials.
+// C64 full (FP64) and C32 (FP32; lower triangle, or all of it) from the
+// full monomials.
 __global__ void builder_mixed_kernel(const zd* __restrict__ Cm, int n,
                                      const double* __restrict__ Q, int nk, double q1x, double q1y,
                                      double q2x, double q2y, zd* __restrict__ C64,
-                                     zf* __restrict__ C32) {
+                                     zf* __restrict__ C32, bool full32) {
   constexpr int KB = 32;
   __shared__ double coef[KB][6];
   const size_t nn = (size_t)n * n;
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = e < nn;
-  const bool lower = live && (int)(e % n) >= (int)(e / n);
+  const bool lower = live && (full32 || (int)(e % n) >= (int)(e / n));
   zd m[6];
   if (live) {
 #pragma unroll
@@ -451,7 +452,9 @@ __global__ void residual_kernel(const zd* __restrict__ CX, const zd* __restrict_
   const zd* cx = CX + (size_t)k * n * b;
   const zd* x = X + (size_t)k * n * b;
   const zd* w = W + (size_t)k * b * b;
-  const double gapref = lamT[(size_t)k * lstride + b];
+  // lambda_{b+1} of T, or (no T: the LOBPCG block) the largest Ritz value,
+  // which lies at or below lambda_{b+1} once the block has converged
+  const double gapref = lamT ? lamT[(size_t)k * lstride + b] : theta[(size_t)k * b + b - 1];
   for (int i = warp; i < nbands; i += nw) {
     const double th = theta[(size_t)k * b + i];
     double s2 = 0.0;
@@ -495,10 +498,11 @@ int bs_mixed_guard(int nbands, int n) {
 }
 
 int bs_launch_builder_mixed(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,
-                            double q2x, double q2y, zd* C64, zf* C32, cudaStream_t s) {
+                            double q2x, double q2y, zd* C64, zf* C32, cudaStream_t s,
+                            bool full32) {
   const size_t nn = (size_t)n * n;
   builder_mixed_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Cm, n, Q, nk, q1x, q1y, q2x,
-                                                                    q2y, C64, C32);
+                                                                    q2y, C64, C32, full32);
   BS_CHECK_LAUNCH("builder_mixed_kernel");
   return BS_OK;
 }
@@ -512,6 +516,11 @@ int bs_launch_mixed_refine(const MixedWs& w, int n, int kb, int nbands, int b, d
   backtransform_kernel<<<dim3(kb, (b + 7) / 8), 256, 0, s>>>(w.C32, w.tau, w.phase, w.Y, n, b,
                                                               w.X32, w.X64);
   BS_CHECK_LAUNCH("backtransform_kernel");
+  return bs_launch_rr_tail(w, n, kb, nbands, b, tol, floor2, omega, stat, s);
+}
+
+int bs_launch_rr_tail(const MixedWs& w, int n, int kb, int nbands, int b, double tol,
+                      double floor2, double* omega, int* stat, cudaStream_t s) {
   const zd one = zmake(1.0, 0.0);
   const long nb = (long)n * b, bb = (long)b * b;
   // C X with FP64-level accuracy on the tensor cores (exact digit-plane contraction)
