@@ -257,11 +257,11 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   failing cell's index in the message), BS_ENOMEM, BS_ECUDA.  Synchronous.
  * bs_batch_solve - Q: ncells * nk * 2 fractional wavevectors (cell-major),
  *   omega_out: ncells * nk * nbands (cell-major, ascending per k),
- *   status_out: ncells * nk (0, or BS_ENOCONV where the Rayleigh-Ritz
- *   residual bound misses 1e-6) or NULL; host or device pointers.  The first
- *   call times both tile edges of the reduction per truncation group and
- *   keeps the faster (autotuning).  Synchronises `stream` when an output is
- *   a host pointer.
+ *   status_out: ncells * nk (0, or the failure status of the dense
+ *   fallback below, which re-solves every entry the residual bound did not
+ *   certify) or
+ *   NULL; host or device pointers.  The first call times both tile edges of
+ *   the reduction per truncation group and keeps the faster (autotuning).
  * bs_batch_set_graph - on != 0: the next bs_batch_solve records the whole
  *   solve in a CUDA graph, later calls replay it (the Q and output pointers
  *   of the recording call must be reused); on == 0 drops the graph.
@@ -274,6 +274,30 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   ms[1] FP32 Householder reduction, ms[2] eigenvalue shifts, ms[3] FP64
  *   refinement.
  * bs_batch_destroy - free everything (NULL is a no-op).
+ * bs_batch_set_solver - BS_SOLVER_DENSE (default: the FP32 Householder
+ *   reduction above) or BS_SOLVER_LOBPCG (the block LOBPCG of
+ *   bs_solve_k_lobpcg, its FP64 Rayleigh-Ritz tail and residual bound;
+ *   needs nbands <= BS_LOB_MAX_BANDS and nbands + 5 <= n).  Drops a
+ *   recorded graph when the solver changes.
+ * bs_batch_set_start - LOBPCG starting vectors: U holds ncells * nk * nvec
+ *   vectors (cell-major, then k, then vector) of 2 (2Mp+1)^2 complex64
+ *   displacement coefficients each, of the plane waves |alpha|, |beta| <= Mp
+ *   only (component-major, waves ordered as for a cell of truncation Mp);
+ *   the other coefficients are zero.  Copied at the call (host or device
+ *   U); NULL returns to the cold start.  Needs Mp <= every cell's M and
+ *   1 <= nvec <= the LOBPCG block size.
+ * bs_batch_stats - per (cell, k) of the last solve: LOBPCG iterations
+ *   (0 on the dense solver) and 1 where the dense FP64 fallback ran.
+ * bs_batch_set_vectors - Mp >= 0 (at most every cell's M): later solves
+ *   also keep the eigenvectors of the nbands branches as the displacement
+ *   coefficients u of the waves |alpha|, |beta| <= Mp (u^dagger Omega u = 1
+ *   for the full vector); Mp < 0 stops.  Drops a recorded graph.
+ * bs_batch_vectors - copy them out: ncells * nk * nbands * 2 (2Mp+1)^2
+ *   complex64 (cell-major, then k, band, component, wave), NaN for entries
+ *   of the dense fallback; host or device U_out.
+ * Every bs_batch_solve ends with that fallback: the (cell, k) entries whose
+ * residual bound failed are solved again by the dense FP64 path (the cell
+ * is assembled again), so the call always synchronises `stream`.
  */
 typedef struct bs_batch bs_batch;
 int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, int nbands, bs_batch** out);
@@ -284,6 +308,58 @@ int bs_batch_tiles(const bs_batch* batch, int* tiles, int* ns, int ngroups_max, 
 int bs_batch_set_profiling(bs_batch* batch, int on);
 int bs_batch_phase_times(bs_batch* batch, double ms[4]);
 int bs_batch_destroy(bs_batch* batch);
+#define BS_SOLVER_DENSE  0
+#define BS_SOLVER_LOBPCG 1
+int bs_batch_set_solver(bs_batch* batch, int solver);
+int bs_batch_set_start(bs_batch* batch, const float* U, int Mp, int nvec);
+int bs_batch_stats(const bs_batch* batch, int* iters_out, int* fallback_out);
+int bs_batch_set_vectors(bs_batch* batch, int Mp);
+int bs_batch_vectors(const bs_batch* batch, float* U_out);
+
+/*
+ * Learned warm start for bs_solve_k_lobpcg / BS_SOLVER_LOBPCG (not in the
+ * paper): a small convolutional network that maps a 64 x 64 cell (its
+ * per-pixel lam, mu, rho) and a wavevector to nvec starting vectors, given
+ * as the displacement coefficients of the plane waves |alpha|, |beta| <= Mp
+ * (the layout of bs_batch_set_start).  Architecture (FP32): three input
+ * channels log(lam + 2 mu), log mu, log rho (standardised); four 3x3
+ * convolutions with circular padding (3->16->32->32->32 channels), each
+ * followed by ReLU and 2x2 mean pooling (64 -> 4 pixels per side, 512
+ * features per cell); per (cell, k) the features and 7 wavevector features
+ * (Q1, Q2, cos/sin 2 pi Q1, cos/sin 2 pi Q2, hexagonal flag) pass three dense
+ * layers 519 -> 512 -> 512 -> nvec * 2 (2Mp+1)^2 complex (ReLU between).
+ * Training minimises, per sample, the part of the true eigenvectors' low-order
+ * coefficients V (nb vectors) outside the predicted span U:
+ *   loss = (||V||^2 - tr(B^H (U^H U + 1e-4 I)^-1 B)) / ||V||^2, B = U^H V,
+ * averaged over the batch, with Adam (beta 0.9, 0.999, eps 1e-8).
+ *   bs_cnn_create - nvec <= 16, Mp <= 3; capacity max_cells per call and
+ *     max_samples = cells * kper per call.
+ *   bs_cnn_num_params / set_params / get_params - the flat FP32 parameter
+ *     vector (conv weights [co][ci][3][3] and biases layer by layer, then the
+ *     dense weights [out][in] and biases); set_params resets Adam; get_params
+ *     also returns the gradients of the last train step (grad may be NULL).
+ *   bs_cnn_forward - cells c < ncells: phase maps (ncells x 64 x 64 uint16),
+ *     their (lam | mu | rho) tables at table + toff[c] with nph[c] phases,
+ *     hex[c] != 0 for hexagonal lattices; Q: ncells * kper fractional
+ *     wavevectors (kper per cell, cell-major); U_out: ncells * kper * nvec *
+ *     2 (2Mp+1)^2 complex64.  Any pointer may be host or device.  Synchronous.
+ *   bs_cnn_train_step - the same inputs plus targets V (ncells * kper * nb *
+ *     2 (2Mp+1)^2 complex64, nb <= 16); one forward, backward and (lr > 0)
+ *     Adam step; per-sample losses to loss_out (or NULL).  With lr = 0 only
+ *     the gradients are computed.  Synchronous.
+ */
+typedef struct bs_cnn bs_cnn;
+int bs_cnn_create(int nvec, int Mp, int max_cells, int max_samples, bs_cnn** out);
+int bs_cnn_destroy(bs_cnn* net);
+int bs_cnn_num_params(const bs_cnn* net, long long* n);
+int bs_cnn_set_params(bs_cnn* net, const float* params);
+int bs_cnn_get_params(const bs_cnn* net, float* params, float* grad);
+int bs_cnn_forward(bs_cnn* net, const uint16_t* phase, const double* table, const long* toff,
+                   const int* nph, const int* hex, int ncells, const double* Q, int kper,
+                   float* U_out, void* stream);
+int bs_cnn_train_step(bs_cnn* net, const uint16_t* phase, const double* table, const long* toff,
+                      const int* nph, const int* hex, int ncells, const double* Q, int kper,
+                      const float* V, int nb, float lr, float* loss_out, void* stream);
 
 /* bs_cell_dims - N (plane waves) and n = 2N (eigen dimension). */
 int bs_cell_dims(const bs_cell* cell, int* N, int* n);

@@ -68,6 +68,19 @@ def _load():
         "bs_batch_set_profiling": [vp, i32],
         "bs_batch_phase_times": [vp, dp],
         "bs_solve_k_lobpcg": [vp, dp, i32, i32, dp, i32, dp, dp, dp, dp, dp, vp],
+        "bs_batch_set_solver": [vp, i32],
+        "bs_batch_set_start": [vp, dp, i32, i32],
+        "bs_batch_stats": [vp, dp, dp],
+        "bs_batch_set_vectors": [vp, i32],
+        "bs_batch_vectors": [vp, dp],
+        "bs_cnn_create": [i32, i32, i32, i32, ctypes.POINTER(vp)],
+        "bs_cnn_destroy": [vp],
+        "bs_cnn_num_params": [vp, ctypes.POINTER(ctypes.c_longlong)],
+        "bs_cnn_set_params": [vp, dp],
+        "bs_cnn_get_params": [vp, dp, dp],
+        "bs_cnn_forward": [vp, dp, dp, dp, dp, dp, i32, dp, i32, dp, vp],
+        "bs_cnn_train_step": [vp, dp, dp, dp, dp, dp, i32, dp, i32, dp, i32, ctypes.c_float, dp,
+                              vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -86,7 +99,11 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_set_profiling", "bs_phase_times", "bs_launch_count", "bs_tridiag_eigenvalues",
             "bs_gemm_bf16", "bs_tridiag_eigenvalues_static", "bs_batch_create", "bs_batch_solve",
             "bs_batch_set_graph", "bs_batch_tiles", "bs_batch_destroy", "bs_batch_set_profiling",
-            "bs_batch_phase_times", "bs_solve_k_lobpcg"]
+            "bs_batch_phase_times", "bs_solve_k_lobpcg", "bs_batch_set_solver",
+            "bs_batch_set_start", "bs_batch_stats", "bs_batch_set_vectors", "bs_batch_vectors",
+            "bs_cnn_create", "bs_cnn_destroy", "bs_cnn_num_params", "bs_cnn_set_params",
+            "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step"]
+BS_SOLVER_DENSE, BS_SOLVER_LOBPCG = 0, 1
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
 
 
@@ -110,7 +127,8 @@ def _ptr(x, dtype):
     if hasattr(x, "data_ptr"):
         import torch
         tdt = {np.float64: torch.float64, np.uint16: torch.uint16, np.int32: torch.int32,
-               np.float32: torch.float32, np.complex64: torch.complex64}[dtype]
+               np.float32: torch.float32, np.complex64: torch.complex64,
+               np.int64: torch.int64}[dtype]
         if x.dtype != tdt or not x.is_contiguous():
             raise TypeError(f"expected a contiguous {tdt} tensor")
         return x.data_ptr()
@@ -243,6 +261,38 @@ def bs_batch_destroy(batch):
     _check(_lib.bs_batch_destroy(batch))
 
 
+def bs_batch_set_solver(batch, solver: int):
+    _check(_lib.bs_batch_set_solver(batch, int(solver)))
+
+
+def bs_batch_set_start(batch, U, Mp: int = 0):
+    """U: (ncells, nk, nvec, 2 (2Mp+1)^2) complex64 low-order displacement
+    coefficients (numpy or CUDA tensor), or None for the cold start."""
+    if U is None:
+        _check(_lib.bs_batch_set_start(batch, None, 0, 0))
+        return
+    nvec = int(U.shape[2])
+    _check(_lib.bs_batch_set_start(batch, _ptr(U, np.complex64), int(Mp), nvec))
+
+
+def bs_batch_set_vectors(batch, Mp: int):
+    _check(_lib.bs_batch_set_vectors(batch, int(Mp)))
+
+
+def bs_batch_vectors(batch, U_out):
+    """U_out: (ncells, nk, nbands, 2 (2Mp+1)^2) complex64 (numpy or CUDA tensor)."""
+    _check(_lib.bs_batch_vectors(batch, _ptr(U_out, np.complex64)))
+    return U_out
+
+
+def bs_batch_stats(batch, nq: int):
+    """(iterations, fallback flags) per (cell, k) of the last solve."""
+    it = np.zeros(nq, np.int32)
+    fb = np.zeros(nq, np.int32)
+    _check(_lib.bs_batch_stats(batch, it.ctypes.data, fb.ctypes.data))
+    return it, fb
+
+
 def bs_tridiag_eigenvalues_static(d, e, nbands: int, lam_out, stream=None):
     """As bs_tridiag_eigenvalues, on device tensors only, with no device allocation."""
     batch, n = int(d.shape[0]), int(d.shape[1])
@@ -292,3 +342,52 @@ def bs_launch_count() -> int:
 
 def bs_destroy_cell(cell):
     _check(_lib.bs_destroy_cell(cell))
+
+
+# ------------------------------------------------------------------ warm-start network
+def bs_cnn_create(nvec: int, Mp: int, max_cells: int, max_samples: int):
+    out = ctypes.c_void_p()
+    _check(_lib.bs_cnn_create(int(nvec), int(Mp), int(max_cells), int(max_samples),
+                              ctypes.byref(out)))
+    return out
+
+
+def bs_cnn_destroy(net):
+    _check(_lib.bs_cnn_destroy(net))
+
+
+def bs_cnn_num_params(net) -> int:
+    n = ctypes.c_longlong()
+    _check(_lib.bs_cnn_num_params(net, ctypes.byref(n)))
+    return n.value
+
+
+def bs_cnn_set_params(net, params):
+    _check(_lib.bs_cnn_set_params(net, _ptr(params, np.float32)))
+
+
+def bs_cnn_get_params(net, params=None, grad=None):
+    _check(_lib.bs_cnn_get_params(net, _ptr(params, np.float32), _ptr(grad, np.float32)))
+    return params, grad
+
+
+def bs_cnn_forward(net, phase, table, toff, nph, hexflag, Q, kper: int, U_out, stream=None):
+    """phase (C, 64, 64) uint16, table float64, toff int64 (C), nph int32 (C),
+    hexflag int32 (C), Q (C*kper, 2) float64, U_out (C*kper, nvec*L*2) float32."""
+    _check(_lib.bs_cnn_forward(net, _ptr(phase, np.uint16), _ptr(table, np.float64),
+                               _ptr(toff, np.int64), _ptr(nph, np.int32), _ptr(hexflag, np.int32),
+                               int(phase.shape[0]), _ptr(Q, np.float64), int(kper),
+                               _ptr(U_out, np.float32), _stream(stream)))
+    return U_out
+
+
+def bs_cnn_train_step(net, phase, table, toff, nph, hexflag, Q, kper: int, V, lr: float,
+                      loss_out=None, stream=None):
+    """V: (C*kper, nb, L) complex64 targets; lr = 0: gradients only."""
+    nb = int(V.shape[1])
+    _check(_lib.bs_cnn_train_step(net, _ptr(phase, np.uint16), _ptr(table, np.float64),
+                                  _ptr(toff, np.int64), _ptr(nph, np.int32),
+                                  _ptr(hexflag, np.int32), int(phase.shape[0]),
+                                  _ptr(Q, np.float64), int(kper), _ptr(V, np.complex64), nb,
+                                  float(lr), _ptr(loss_out, np.float32), _stream(stream)))
+    return loss_out

@@ -228,20 +228,36 @@ def config1():
     return dict(cell=cell, M=10, Q=ibz_path("square", 90), nbands=18)
 
 
-def config3_cell(i: int, P: int = 64):
-    """Cell i of the ragged batch: seed 6380+i; square or hexagonal lattice
-    with probability 1/2; half ellipse maps, half Voronoi; 2..16 phases;
-    truncation M uniform in {5..8}; 30 k on its lattice's path; 10 bands."""
-    rng = np.random.default_rng(6380 + i)
+def c3_style_cell(seed: int, P: int = 64, tag: str = "c3"):
+    """A cell of the ragged-batch style from one seed: square or hexagonal
+    lattice with probability 1/2; half ellipse maps, half Voronoi; 2..16
+    phases; truncation M uniform in {5..8}; 30 k on its lattice's path;
+    10 bands."""
+    rng = np.random.default_rng(seed)
     lattice = "square" if rng.random() < 0.5 else "hex"
     nphase = int(rng.integers(2, 17))
     M = int(rng.integers(5, 9))
     sub = int(rng.integers(0, 2**31 - 1))
     if rng.random() < 0.5:
-        cell = ellipse_cell(P, nphase - 1, sub, lattice, name=f"c3_{i}_ellipses")
+        cell = ellipse_cell(P, nphase - 1, sub, lattice, name=f"{tag}_{seed}_ellipses")
     else:
-        cell = voronoi_cell(P, nphase, sub, lattice, name=f"c3_{i}_voronoi")
+        cell = voronoi_cell(P, nphase, sub, lattice, name=f"{tag}_{seed}_voronoi")
     return dict(cell=cell, M=M, Q=ibz_path(lattice, 30, cell.h1, cell.h2), nbands=10)
+
+
+def config3_cell(i: int, P: int = 64):
+    """Cell i of the 4096-cell ragged batch: seed 6380+i."""
+    return c3_style_cell(6380 + i, P, tag=f"c3_{i}")
+
+
+def config4_train_cell(i: int):
+    """Training cell i of the learned warm start: seed 10^6 + i."""
+    return c3_style_cell(1_000_000 + i, tag="c4train")
+
+
+def config4_eval_cell(i: int):
+    """Held-out evaluation cell i of the learned warm start: seed 2 10^6 + i."""
+    return c3_style_cell(2_000_000 + i, tag="c4eval")
 
 
 CONFIGS = {"c0": config0, "c1": config1}

@@ -562,7 +562,8 @@ static int solve_chunk_lobpcg(bs_cell* c, int kb, int nbands, int b, const float
     CK(cudaMemcpyAsync(c->d_lvec, X0, (size_t)kb * nvec * n * sizeof(float2),
                        x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
        "LOBPCG starting vectors");
-    TRY(bs_launch_lob_to_reduced(c->d_lvec, c->d_T + 2 * (size_t)N * N, N, kb, nvec, c->d_lX0, s));
+    TRY(bs_launch_lob_to_reduced(c->d_lvec, c->d_T + 2 * (size_t)N * N, N, c->M, -1, kb, nvec,
+                                 c->d_lX0, s));
   }
   bs_phase_end(c, PH_BUILD, s);
   bs_phase_begin(c, PH_TRID, s);
@@ -603,31 +604,31 @@ static int solve_chunk_lobpcg(bs_cell* c, int kb, int nbands, int b, const float
   CK(cudaMemsetAsync(c->d_stat, 0, kb * sizeof(int), s), "status");
   TRY(bs_launch_rr_tail(m, n, kb, nbands, b, c->tol, c->floor2, c->d_w, c->d_stat, s));
   if (want_vec)
-    TRY(bs_launch_lob_vectors(c->d_X64, c->d_W, c->d_Linv + 2 * (size_t)N * N, N, b, nbands, kb,
-                              c->d_lvec, s));
+    TRY(bs_launch_lob_vectors(c->d_X64, c->d_W, c->d_Linv + 2 * (size_t)N * N, 0, kb, N, c->M, -1,
+                              b, nbands, kb, nullptr, c->d_lvec, s));
   bs_phase_end(c, PH_REFINE, s);
   return BS_OK;
 }
 
-// dense FP64 solve of the wavevectors Qf (host, nf x 2): omega (host, nf x nbands)
-static int solve_dense_fp64(bs_cell* c, const std::vector<double>& Qf, int nbands,
-                            std::vector<double>& om, std::vector<int>& st, cudaStream_t s) {
-  const int nf = (int)Qf.size() / 2;
-  om.assign((size_t)nf * nbands, 0.0);
-  st.assign(nf, 0);
+// dense FP64 solve of the wavevectors Q (host, nf x 2) on an assembled cell:
+// omega (host, nf x nbands) and status (host, nf)
+int bs_cell_dense_fp64(bs_cell* c, const double* Q, int nf, int nbands, double* om, int* st,
+                       cudaStream_t s) {
+  if (nf <= 0) return BS_OK;
+  TRY(ensure_workspace(c, std::min(nf, std::min(k_batch_cap(c), 256)), nbands));
   const int cap = c->kcap;
   for (int k0 = 0; k0 < nf; k0 += cap) {
     const int kb = std::min(cap, nf - k0);
-    CK(cudaMemcpyAsync(c->d_Q, Qf.data() + 2 * (size_t)k0, 2 * kb * sizeof(double),
+    CK(cudaMemcpyAsync(c->d_Q, Q + 2 * (size_t)k0, 2 * kb * sizeof(double),
                        cudaMemcpyHostToDevice, s), "fallback Q");
     TRY(bs_launch_builder(c->d_Cm, c->n, c->d_Q, kb, c->q1[0], c->q1[1], c->q2[0], c->q2[1],
                           c->d_C, s));
     TRY(bs_launch_tridiag<double>(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
                                   c->d_beta, c->d_count, s));
     TRY(bs_launch_bisect(c->d_de, c->n, kb, nbands, c->d_w, c->d_stat, s));
-    CK(cudaMemcpyAsync(om.data() + (size_t)k0 * nbands, c->d_w, (size_t)kb * nbands * 8,
+    CK(cudaMemcpyAsync(om + (size_t)k0 * nbands, c->d_w, (size_t)kb * nbands * 8,
                        cudaMemcpyDeviceToHost, s), "fallback omega");
-    CK(cudaMemcpyAsync(st.data() + k0, c->d_stat, kb * sizeof(int), cudaMemcpyDeviceToHost, s),
+    CK(cudaMemcpyAsync(st + k0, c->d_stat, kb * sizeof(int), cudaMemcpyDeviceToHost, s),
        "fallback status");
     CK(cudaStreamSynchronize(s), "fallback sync");
   }
@@ -711,9 +712,9 @@ extern "C" int bs_solve_k_lobpcg(bs_cell* c, const double* Q, int nk, int nbands
   std::vector<int> stk(nk, 0);
   if (!idx.empty()) {
     bs_phase_begin(c, PH_BISECT, s);
-    std::vector<double> om;
-    std::vector<int> st;
-    TRY(solve_dense_fp64(c, Qf, nbands, om, st, s));
+    std::vector<double> om(idx.size() * nbands);
+    std::vector<int> st(idx.size());
+    TRY(bs_cell_dense_fp64(c, Qf.data(), (int)idx.size(), nbands, om.data(), st.data(), s));
     bs_phase_end(c, PH_BISECT, s);
     const std::vector<float> nanv((size_t)nbands * n * 2, NAN);
     for (size_t t = 0; t < idx.size(); ++t) {

@@ -113,6 +113,19 @@ struct BatchGroup {
   int* st;                    // chunk * nk
   int* d_rowidx;              // cells.size() * nk target rows (cell * nk + k), chunk-major
   double* d_Gall;             // cells.size() * 2N plane-wave vectors G of each cell
+  // LOBPCG workspace (chunk * nk problems), allocated when the solver is chosen
+  int lb;                     // LOBPCG block size (0: not allocated)
+  zf* lS;
+  zf* lCS;
+  zf* lA;
+  zf* lpart;
+  zf* lZ;
+  zf* lY;
+  zf* lX0;
+  LobState* lst;
+  int* lndone;
+  int* liters;
+  zd* lLinv;                  // chunk x N x N: L_R^-1 of the chunk's cells (eigenvector output)
 };
 
 struct bs_batch {
@@ -134,6 +147,16 @@ struct bs_batch {
   bool prof;
   std::vector<cudaEvent_t> pev;
   size_t pev_used;
+  // eigen solver and LOBPCG starting vectors
+  int solver;
+  float2* d_U;                          // ncells * nk * nvec * 2 (2Mp+1)^2 coefficients
+  int Mp, nvec;
+  int* d_iters;                         // ncells * nk LOBPCG iterations of the last solve
+  bool capturing;                       // a graph is being recorded
+  int vecMp;                            // eigenvector output: waves |alpha|,|beta| <= vecMp
+  float2* d_vec;                        // ncells * nk * nbands * 2 (2 vecMp + 1)^2, or null
+  std::vector<int> fb;                  // ncells * nk: 1 where the dense fallback ran
+  std::vector<int> cell_group, cell_gi; // group and index within it of every cell
 };
 
 static void prof_mark(bs_batch* B, cudaStream_t s) {
@@ -158,8 +181,28 @@ static void free_group(BatchGroup& g) {
   if (g.fork) cudaEventDestroy(g.fork);
   void* ps[] = {g.C64, g.C32, g.vec32, g.part32, g.de, g.tau, g.beta, g.count, g.lamT, g.scr, g.Y,
                 g.phase, g.X32, g.X64, g.CX, g.G, g.H, g.W, g.theta, g.cxA, g.cxB, g.cxD, g.cxeA,
-                g.cxeB, g.w, g.st, g.d_rowidx, g.d_Gall};
+                g.cxeB, g.w, g.st, g.d_rowidx, g.d_Gall, g.lS, g.lCS, g.lA, g.lpart, g.lZ, g.lY,
+                g.lX0, g.lst, g.lndone, g.liters, g.lLinv};
   for (void* p : ps) cudaFree(p);
+}
+
+static int alloc_lob(BatchGroup& g, int nk, int nbands) {
+  if (g.lb) return BS_OK;
+  const int b = bs_lob_block(nbands, g.n);
+  const size_t K = (size_t)g.chunk * nk, n = g.n, coef = (size_t)BS_LOB_MAX_BLOCK * 3 * BS_LOB_MAX_BLOCK;
+  int r = BS_OK;
+  if (!r) r = balloc(&g.lS, 2 * K * 3 * b * n, "batch LOBPCG basis");
+  if (!r) r = balloc(&g.lCS, 2 * K * 3 * b * n, "batch LOBPCG C basis");
+  if (!r) r = balloc(&g.lA, K * bs_lob_small_elems(), "batch LOBPCG Gram");
+  if (!r) r = balloc(&g.lpart, K * bs_lob_part_elems(g.n), "batch LOBPCG partial Gram");
+  if (!r) r = balloc(&g.lZ, K * coef, "batch LOBPCG Ritz coefficients");
+  if (!r) r = balloc(&g.lY, K * coef, "batch LOBPCG P coefficients");
+  if (!r) r = balloc(&g.lX0, K * b * n, "batch LOBPCG starting block");
+  if (!r) r = balloc(&g.lst, K, "batch LOBPCG state");
+  if (!r) r = balloc(&g.lndone, 1, "batch LOBPCG counter");
+  if (!r) r = balloc(&g.liters, K, "batch LOBPCG iterations");
+  if (!r) g.lb = b;
+  return r;
 }
 
 static int alloc_group(BatchGroup& g, int nk, int nbands) {
@@ -251,12 +294,25 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
     const int ci = g.cells[c0 + i], wi = i % g.nworkers;
     bs_cell* wk = g.workers[wi];
     cudaStream_t ws = g.wstream[wi];
+    const bool lob = B->solver == BS_SOLVER_LOBPCG;
     int r = load_cell(B, g, wk, c0 + i, ws);
     if (!r) r = bs_assemble(wk, ws);
+    if (!r && B->d_vec)
+      r = cudaMemcpyAsync(g.lLinv + (size_t)i * g.N * g.N, wk->d_Linv + 2 * (size_t)g.N * g.N,
+                          (size_t)g.N * g.N * sizeof(zd), cudaMemcpyDeviceToDevice, ws) == cudaSuccess
+              ? BS_OK
+              : bs_cuda_status(cudaGetLastError(), "batch L_R stash");
     if (!r)
       r = bs_launch_builder_mixed(wk->d_Cm, n, B->d_Q + (size_t)ci * nk * 2, nk, wk->q1[0],
                                   wk->q1[1], wk->q2[0], wk->q2[1], g.C64 + (size_t)i * nk * nn,
-                                  g.C32 + (size_t)i * nk * nn, ws);
+                                  g.C32 + (size_t)i * nk * nn, ws, lob);
+    // starting vectors of this cell in the reduced basis (needs its L_R)
+    if (!r && lob && B->d_U) {
+      const size_t nl = 2 * (size_t)(2 * B->Mp + 1) * (2 * B->Mp + 1);
+      r = bs_launch_lob_to_reduced(B->d_U + (size_t)ci * nk * B->nvec * nl,
+                                   wk->d_T + 2 * (size_t)g.N * g.N, g.N, g.M, B->Mp, nk, B->nvec,
+                                   g.lX0 + (size_t)i * nk * B->nvec * n, ws);
+    }
     if (r) return r;
   }
   // join
@@ -265,7 +321,43 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
     CK(cudaStreamWaitEvent(s, g.wdone[w], 0), "batch join");
   }
   const int K = cn * nk;
+  const int* rows = g.d_rowidx + (size_t)c0 * nk;
   prof_mark(B, s);   // assembly ends, reduction begins
+  if (B->solver == BS_SOLVER_LOBPCG) {
+    const int lb = g.lb;
+    LobWs lw;
+    lw.C32 = g.C32;
+    lw.S = g.lS;
+    lw.CS = g.lCS;
+    lw.Axp = g.lA;
+    lw.part = g.lpart;
+    lw.Z = g.lZ;
+    lw.Y = g.lY;
+    lw.st = g.lst;
+    lw.X0 = B->d_U ? g.lX0 : nullptr;
+    lw.nvec = B->d_U ? B->nvec : 0;
+    lw.ndone = g.lndone;
+    // a graph replays a fixed sequence: no early exit there (finished k
+    // return at once from every later launch)
+    TRY_LAUNCH(bs_launch_lobpcg(lw, n, K, lb, B->nbands, BS_LOB_MAXIT, 1e-3f, 1e-6f, (float)floor2,
+                                B->capturing ? 0 : 4, s));
+    TRY_LAUNCH(bs_launch_lob_export(lw, n, K, lb, g.X64, g.liters, s));
+    prof_mark(B, s);
+    prof_mark(B, s);
+    MixedWs w;
+    memset(&w, 0, sizeof(w));
+    w.C64 = g.C64; w.X64 = g.X64; w.CX = g.CX; w.G = g.G; w.H = g.H; w.W = g.W;
+    w.theta = g.theta; w.lamT = nullptr; w.cxA = g.cxA; w.cxB = g.cxB; w.cxD = g.cxD;
+    w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
+    CK(cudaMemsetAsync(g.st, 0, K * sizeof(int), s), "batch status");
+    TRY_LAUNCH(bs_launch_rr_tail(w, n, K, B->nbands, lb, 1e-6, floor2, g.w, g.st, s));
+    if (B->d_vec)
+      TRY_LAUNCH(bs_launch_lob_vectors(g.X64, g.W, g.lLinv, (long)g.N * g.N, nk, g.N, g.M, B->vecMp,
+                                       lb, B->nbands, K, rows, B->d_vec, s));
+    prof_mark(B, s);
+    scatter_int_kernel<<<(K + 255) / 256, 256, 0, s>>>(g.liters, rows, K, 1, B->d_iters);
+    BS_CHECK_LAUNCH("scatter_int_kernel");
+  } else {
   TRY_LAUNCH(bs_launch_tridiag<float>(g.C32, n, K, g.vec32, g.part32, g.de, g.tau, g.beta, g.count,
                                       s, tile));
   prof_mark(B, s);
@@ -277,9 +369,12 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
   w.G = g.G; w.H = g.H; w.W = g.W; w.theta = g.theta; w.cxA = g.cxA; w.cxB = g.cxB;
   w.cxD = g.cxD; w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
   TRY_LAUNCH(bs_launch_mixed_refine(w, n, K, B->nbands, b, 1e-6, floor2, g.w, g.st, s));
+  if (B->d_vec)
+    TRY_LAUNCH(bs_launch_lob_vectors(g.X64, g.W, g.lLinv, (long)g.N * g.N, nk, g.N, g.M, B->vecMp, b,
+                                     B->nbands, K, rows, B->d_vec, s));
   prof_mark(B, s);   // refinement ends
+  }
   // scatter (cell, k) rows into caller order
-  const int* rows = g.d_rowidx + (size_t)c0 * nk;
   scatter_rows_kernel<<<(K * B->nbands + 255) / 256, 256, 0, s>>>(g.w, rows, K, B->nbands,
                                                                   B->d_w);
   BS_CHECK_LAUNCH("scatter_rows_kernel");
@@ -357,6 +452,11 @@ extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, in
   if (!r) r = balloc(&B->d_Q, (size_t)ncells * nk * 2, "batch Q");
   if (!r) r = balloc(&B->d_w, (size_t)ncells * nk * nbands, "batch omega");
   if (!r) r = balloc(&B->d_st, (size_t)ncells * nk, "batch status");
+  if (!r) r = balloc(&B->d_iters, (size_t)ncells * nk, "batch iterations");
+  if (!r && cudaMemset(B->d_iters, 0, (size_t)ncells * nk * sizeof(int)) != cudaSuccess)
+    r = bs_cuda_status(cudaGetLastError(), "bs_batch_create");
+  B->cell_group.assign(ncells, 0);
+  B->cell_gi.assign(ncells, 0);
   std::vector<double> raw(rawn);
   std::map<int, std::vector<int>> byM;
   std::vector<uint16_t> ph(PP);
@@ -420,6 +520,10 @@ extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, in
       B->groups.push_back(g);
       break;
     }
+    for (size_t i = 0; i < g.cells.size(); ++i) {
+      B->cell_group[g.cells[i]] = (int)B->groups.size();
+      B->cell_gi[g.cells[i]] = (int)i;
+    }
     // chunk: a few GB of workspace per group
     // bytes per cell: C64 16 n^2, C32 8 n^2, C digit planes 24 n^2, C X
     // products 288 n b, vectors and inverse-iteration factors ~ 120 n b
@@ -472,7 +576,121 @@ extern "C" int bs_batch_destroy(bs_batch* B) {
   cudaFree(B->d_Q);
   cudaFree(B->d_w);
   cudaFree(B->d_st);
+  cudaFree(B->d_iters);
+  cudaFree(B->d_U);
+  cudaFree(B->d_vec);
   delete B;
+  return BS_OK;
+}
+
+static void drop_graph(bs_batch* B) {
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+}
+
+extern "C" int bs_batch_set_solver(bs_batch* B, int solver) {
+  if (!B || (solver != BS_SOLVER_DENSE && solver != BS_SOLVER_LOBPCG)) {
+    bs_set_error("bs_batch_set_solver: NULL batch or unknown solver");
+    return BS_EINVAL;
+  }
+  if (solver == BS_SOLVER_LOBPCG) {
+    if (B->nbands > BS_LOB_MAX_BANDS) {
+      bs_set_error("bs_batch_set_solver: LOBPCG needs nbands <= %d", BS_LOB_MAX_BANDS);
+      return BS_EINVAL;
+    }
+    for (auto& g : B->groups)
+      if (B->nbands + 5 > g.n) {
+        bs_set_error("bs_batch_set_solver: LOBPCG needs nbands + 5 <= n (n = %d)", g.n);
+        return BS_EINVAL;
+      }
+    for (auto& g : B->groups) TRY_LAUNCH(alloc_lob(g, B->nk, B->nbands));
+  }
+  if (solver != B->solver) drop_graph(B);
+  B->solver = solver;
+  return BS_OK;
+}
+
+extern "C" int bs_batch_set_start(bs_batch* B, const float* U, int Mp, int nvec) {
+  if (!B) {
+    bs_set_error("bs_batch_set_start: NULL batch");
+    return BS_EINVAL;
+  }
+  if (!U) {
+    if (B->d_U) drop_graph(B);
+    cudaFree(B->d_U);
+    B->d_U = nullptr;
+    B->nvec = 0;
+    return BS_OK;
+  }
+  int mmin = 1 << 30;
+  for (auto& g : B->groups) mmin = std::min(mmin, g.M);
+  int bmin = 1 << 30;
+  for (auto& g : B->groups) bmin = std::min(bmin, bs_lob_block(B->nbands, g.n));
+  if (Mp < 0 || Mp > mmin || nvec < 1 || nvec > bmin) {
+    bs_set_error("bs_batch_set_start: need 0 <= Mp <= %d (smallest M) and 1 <= nvec <= %d",
+                 mmin, bmin);
+    return BS_EINVAL;
+  }
+  const size_t count = (size_t)B->ncells * B->nk * nvec * 2 * (2 * Mp + 1) * (2 * Mp + 1);
+  if (!B->d_U || Mp != B->Mp || nvec != B->nvec) {
+    drop_graph(B);
+    cudaFree(B->d_U);
+    B->d_U = nullptr;
+    TRY_LAUNCH(balloc(&B->d_U, count, "batch starting vectors"));
+  }
+  B->Mp = Mp;
+  B->nvec = nvec;
+  CK(cudaMemcpy(B->d_U, U, count * sizeof(float2), cudaMemcpyDefault), "bs_batch_set_start");
+  return BS_OK;
+}
+
+extern "C" int bs_batch_set_vectors(bs_batch* B, int Mp) {
+  if (!B) {
+    bs_set_error("bs_batch_set_vectors: NULL batch");
+    return BS_EINVAL;
+  }
+  drop_graph(B);
+  cudaFree(B->d_vec);
+  B->d_vec = nullptr;
+  if (Mp < 0) return BS_OK;
+  for (auto& g : B->groups)
+    if (Mp > g.M) {
+      bs_set_error("bs_batch_set_vectors: Mp = %d exceeds a cell's M = %d", Mp, g.M);
+      return BS_EINVAL;
+    }
+  for (auto& g : B->groups)
+    if (!g.lLinv) TRY_LAUNCH(balloc(&g.lLinv, (size_t)g.chunk * g.N * g.N, "batch L_R stash"));
+  const size_t len = 2 * (size_t)(2 * Mp + 1) * (2 * Mp + 1);
+  TRY_LAUNCH(balloc(&B->d_vec, (size_t)B->ncells * B->nk * B->nbands * len, "batch vectors"));
+  B->vecMp = Mp;
+  return BS_OK;
+}
+
+extern "C" int bs_batch_vectors(const bs_batch* B, float* U_out) {
+  if (!B || !U_out || !B->d_vec) {
+    bs_set_error("bs_batch_vectors: NULL argument or vectors not enabled");
+    return BS_EINVAL;
+  }
+  const size_t len = 2 * (size_t)(2 * B->vecMp + 1) * (2 * B->vecMp + 1);
+  CK(cudaMemcpy(U_out, B->d_vec, (size_t)B->ncells * B->nk * B->nbands * len * sizeof(float2),
+                cudaMemcpyDefault), "bs_batch_vectors");
+  return BS_OK;
+}
+
+extern "C" int bs_batch_stats(const bs_batch* B, int* iters_out, int* fallback_out) {
+  if (!B) {
+    bs_set_error("bs_batch_stats: NULL batch");
+    return BS_EINVAL;
+  }
+  const size_t nq = (size_t)B->ncells * B->nk;
+  if (iters_out) CK(cudaMemcpy(iters_out, B->d_iters, nq * sizeof(int), cudaMemcpyDefault), "bs_batch_stats");
+  if (fallback_out) {
+    std::vector<int> fb(nq, 0);
+    if (B->fb.size() == nq) fb = B->fb;
+    CK(cudaMemcpy(fallback_out, fb.data(), nq * sizeof(int), cudaMemcpyDefault), "bs_batch_stats");
+  }
   return BS_OK;
 }
 
@@ -560,6 +778,54 @@ extern "C" int bs_batch_phase_times(bs_batch* B, double ms[4]) {
   return BS_OK;
 }
 
+// (cell, k) entries the residual bound did not certify: assemble the cell
+// again on a worker and solve those wavevectors with the dense FP64 path
+static int dense_fallback(bs_batch* B, cudaStream_t s) {
+  const size_t nq = (size_t)B->ncells * B->nk;
+  std::vector<int> st(nq);
+  CK(cudaMemcpyAsync(st.data(), B->d_st, nq * sizeof(int), cudaMemcpyDeviceToHost, s),
+     "bs_batch_solve status");
+  CK(cudaStreamSynchronize(s), "bs_batch_solve sync");
+  B->fb.assign(nq, 0);
+  std::vector<double> Qh;
+  for (int ci = 0; ci < B->ncells; ++ci) {
+    std::vector<int> ks;
+    for (int k = 0; k < B->nk; ++k)
+      if (st[(size_t)ci * B->nk + k]) ks.push_back(k);
+    if (ks.empty()) continue;
+    if (Qh.empty()) {
+      Qh.resize(nq * 2);
+      CK(cudaMemcpy(Qh.data(), B->d_Q, nq * 2 * sizeof(double), cudaMemcpyDeviceToHost),
+         "bs_batch_solve Q");
+    }
+    BatchGroup& g = B->groups[B->cell_group[ci]];
+    bs_cell* wk = g.workers[0];
+    TRY_LAUNCH(load_cell(B, g, wk, B->cell_gi[ci], s));
+    TRY_LAUNCH(bs_assemble(wk, s));
+    std::vector<double> Qf, om(ks.size() * B->nbands);
+    std::vector<int> sf(ks.size());
+    for (int k : ks) {
+      Qf.push_back(Qh[((size_t)ci * B->nk + k) * 2]);
+      Qf.push_back(Qh[((size_t)ci * B->nk + k) * 2 + 1]);
+    }
+    TRY_LAUNCH(bs_cell_dense_fp64(wk, Qf.data(), (int)ks.size(), B->nbands, om.data(), sf.data(), s));
+    for (size_t t = 0; t < ks.size(); ++t) {
+      const size_t row = (size_t)ci * B->nk + ks[t];
+      CK(cudaMemcpy(B->d_w + row * B->nbands, om.data() + t * B->nbands, B->nbands * sizeof(double),
+                    cudaMemcpyHostToDevice), "bs_batch_solve fallback omega");
+      CK(cudaMemcpy(B->d_st + row, &sf[t], sizeof(int), cudaMemcpyHostToDevice),
+         "bs_batch_solve fallback status");
+      if (B->d_vec) {
+        const size_t len = 2 * (size_t)(2 * B->vecMp + 1) * (2 * B->vecMp + 1) * B->nbands;
+        CK(cudaMemset(B->d_vec + row * len, 0xff, len * sizeof(float2)),
+           "bs_batch_solve fallback vectors");   // NaN: no vectors for fallback entries
+      }
+      B->fb[row] = 1;
+    }
+  }
+  return BS_OK;
+}
+
 static int solve_all(bs_batch* B, const std::vector<double>& floors, cudaStream_t s) {
   for (auto& g : B->groups) {
     double f2 = 1e300;
@@ -593,7 +859,7 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
   const bool prof = B->prof;
   B->prof = false;   // not while tuning or recording a graph
   for (auto& g : B->groups) {
-    if (g.tuned) continue;
+    if (g.tuned || B->solver == BS_SOLVER_LOBPCG) continue;
     double f2 = 1e300;
     for (int ci : g.cells) f2 = std::min(f2, floors[ci]);
     TRY_LAUNCH(tune_group(B, g, f2, s));
@@ -612,7 +878,9 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
     if (!B->graph) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "bs_batch_solve capture");
+      B->capturing = true;
       const int r = solve_all(B, floors, B->cap);
+      B->capturing = false;
       cudaError_t ce = cudaStreamEndCapture(B->cap, &graph);
       if (r) return r;
       if (ce != cudaSuccess) return bs_cuda_status(ce, "bs_batch_solve end capture");
@@ -629,6 +897,7 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
     TRY_LAUNCH(solve_all(B, floors, s));
   }
   B->prof = prof;
+  TRY_LAUNCH(dense_fallback(B, s));
   CK(cudaMemcpyAsync(omega_out, B->d_w, nq * B->nbands * sizeof(double), cudaMemcpyDefault, s),
      "bs_batch_solve omega");
   if (status_out)

@@ -322,10 +322,19 @@ int bs_lob_block(int nbands, int n);
 int bs_launch_lobpcg(const LobWs& w, int n, int kb, int b, int nb, int maxit, float tol,
                      float tolb, float floor2, int check_every, cudaStream_t s);
 int bs_launch_lob_export(const LobWs& w, int n, int kb, int b, zd* X64, int* iters, cudaStream_t s);
-int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int kb, int nvec, float2* y,
-                             cudaStream_t s);
-int bs_launch_lob_vectors(const zd* X64, const zd* Wc, const zd* LinvR, int N, int b, int nbands,
-                          int kb, float2* out, cudaStream_t s);
+// Mp < 0: u holds all n coefficients per vector; Mp >= 0: only the waves
+// |alpha|, |beta| <= Mp, 2 (2Mp+1)^2 per vector
+int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int M, int Mp, int kb, int nvec,
+                             float2* y, cudaStream_t s);
+// dense FP64 solve of nf host wavevectors on an assembled cell (host outputs)
+int bs_cell_dense_fp64(bs_cell* c, const double* Q, int nf, int nbands, double* om, int* st,
+                       cudaStream_t s);
+// u = (I_2 (x) L_R^-dagger) X w_j (problem k: L_R^-1 at LinvR + (k / kper) lstride);
+// rows (or identity) place problem k's nbands vectors; Mp >= 0 keeps only the
+// low-order waves
+int bs_launch_lob_vectors(const zd* X64, const zd* Wc, const zd* LinvR, long lstride, int kper,
+                          int N, int M, int Mp, int b, int nbands, int kb, const int* rows,
+                          float2* out, cudaStream_t s);
 // mixed.cu: the FP64 Rayleigh-Ritz tail on a given FP64 block X64 (CX, G, H,
 // small eigenproblem, residual bound); gap reference lambda_{b+1} of T
 // (lamT) or, when lamT is null, the largest Ritz value of the block

@@ -1114,12 +1114,30 @@ __global__ void lob_export_kernel(LobWs w, int n, int kb, int b, zd* X64, int* i
 }
 
 // y = (I_2 (x) L_R^dagger) u for starting vectors given in plane-wave
-// displacement coefficients: u [k][v][n] (complex64) -> y [k][v][n]
-__global__ void lob_to_reduced_kernel(const float2* u, const zd* LR, int N, int nvec, float2* y) {
+// displacement coefficients: u [k][v][n] (complex64) -> y [k][v][n].  With
+// Mp >= 0 the input holds only the waves |alpha|, |beta| <= Mp
+// (2 (2Mp+1)^2 coefficients per vector, same ordering rules); the others are 0.
+__global__ void lob_to_reduced_kernel(const float2* u, const zd* LR, int N, int M, int Mp,
+                                      float2* y) {
   extern __shared__ double2 ush[];
   const int kv = blockIdx.x, n = 2 * N;
-  const float2* uk = u + (size_t)kv * n;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) ush[r] = zmake(uk[r].x, uk[r].y);
+  if (Mp < 0) {
+    const float2* uk = u + (size_t)kv * n;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) ush[r] = zmake(uk[r].x, uk[r].y);
+  } else {
+    const int wl = 2 * Mp + 1, Nl = wl * wl;
+    const float2* uk = u + (size_t)kv * 2 * Nl;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const int I = r / N, a = r % N;
+      const int al = a / (2 * M + 1) - M, be = a % (2 * M + 1) - M;
+      zd v = zmake(0.0, 0.0);
+      if (al >= -Mp && al <= Mp && be >= -Mp && be <= Mp) {
+        const float2 f = uk[I * Nl + (al + Mp) * wl + (be + Mp)];
+        v = zmake(f.x, f.y);
+      }
+      ush[r] = v;
+    }
+  }
   __syncthreads();
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     const int I = r / N, i = r % N;
@@ -1128,29 +1146,42 @@ __global__ void lob_to_reduced_kernel(const float2* u, const zd* LR, int N, int 
     for (int t = i; t < N; ++t) acc = zfmac(ush[I * N + t], col[t], acc);
     y[(size_t)kv * n + r] = make_float2((float)acc.x, (float)acc.y);
   }
-  (void)nvec;
 }
 
 // Ritz vectors of the tail mapped back to displacement coefficients:
-// u = (I_2 (x) L_R^-dagger) X w_j for j < nbands, as complex64 [k][j][n]
-__global__ void lob_vectors_kernel(const zd* X64, const zd* Wc, const zd* LinvR, int N, int b,
-                                   int nbands, float2* out) {
+// u = (I_2 (x) L_R^-dagger) X w_j for j < nbands.  Problem k uses
+// L_R^-1 at LinvR + (k / kper) * lstride (one factor per cell).  Output row
+// rows[k] (or k) of [row][j][len]: all n coefficients (Mp < 0) or only the
+// waves |alpha|, |beta| <= Mp (len = 2 (2Mp+1)^2).
+__global__ void lob_vectors_kernel(const zd* X64, const zd* Wc, const zd* LinvR, long lstride,
+                                   int kper, int N, int M, int Mp, int b, int nbands,
+                                   const int* rows, float2* out) {
   extern __shared__ double2 ysh[];
   const int k = blockIdx.y, j = blockIdx.x, n = 2 * N;
   const zd* x = X64 + (size_t)k * n * b;
   const zd* wj = Wc + (size_t)k * b * b + (size_t)j * b;
+  const zd* Li = LinvR + (size_t)(k / kper) * lstride;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     zd acc = zmake(0.0, 0.0);
     for (int l = 0; l < b; ++l) acc = zfma(x[r + (size_t)l * n], wj[l], acc);
     ysh[r] = acc;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+  const int wl = 2 * Mp + 1;
+  const int len = Mp < 0 ? n : 2 * wl * wl;
+  const size_t row = rows ? (size_t)rows[k] : (size_t)k;
+  for (int o = threadIdx.x; o < len; o += blockDim.x) {
+    int r = o;
+    if (Mp >= 0) {
+      const int I = o / (wl * wl), a = o % (wl * wl);
+      const int al = a / wl - Mp, be = a % wl - Mp;
+      r = I * N + (al + M) * (2 * M + 1) + (be + M);
+    }
     const int I = r / N, i = r % N;
     zd acc = zmake(0.0, 0.0);
-    const zd* col = LinvR + (size_t)i * N;   // column i of L_R^-1, rows t >= i
+    const zd* col = Li + (size_t)i * N;   // column i of L_R^-1, rows t >= i
     for (int t = i; t < N; ++t) acc = zfmac(ysh[I * N + t], col[t], acc);
-    out[((size_t)k * nbands + j) * n + r] = make_float2((float)acc.x, (float)acc.y);
+    out[(row * nbands + j) * len + o] = make_float2((float)acc.x, (float)acc.y);
   }
 }
 
@@ -1215,22 +1246,28 @@ int bs_launch_lob_export(const LobWs& w, int n, int kb, int b, zd* X64, int* ite
   return BS_OK;
 }
 
-int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int kb, int nvec, float2* y,
-                             cudaStream_t s) {
+int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int M, int Mp, int kb, int nvec,
+                             float2* y, cudaStream_t s) {
+  if (Mp > M) {
+    bs_set_error("starting vectors with Mp = %d > M = %d", Mp, M);
+    return BS_EINVAL;
+  }
   const size_t sh = (size_t)2 * N * sizeof(double2);
   if (sh > 48 * 1024)
     cudaFuncSetAttribute(lob_to_reduced_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-  lob_to_reduced_kernel<<<kb * nvec, 256, sh, s>>>(u, LR, N, nvec, y);
+  lob_to_reduced_kernel<<<kb * nvec, 256, sh, s>>>(u, LR, N, M, Mp, y);
   BS_CHECK_LAUNCH("lob_to_reduced_kernel");
   return BS_OK;
 }
 
-int bs_launch_lob_vectors(const zd* X64, const zd* Wc, const zd* LinvR, int N, int b, int nbands,
-                          int kb, float2* out, cudaStream_t s) {
+int bs_launch_lob_vectors(const zd* X64, const zd* Wc, const zd* LinvR, long lstride, int kper,
+                          int N, int M, int Mp, int b, int nbands, int kb, const int* rows,
+                          float2* out, cudaStream_t s) {
   const size_t sh = (size_t)2 * N * sizeof(double2);
   if (sh > 48 * 1024)
     cudaFuncSetAttribute(lob_vectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-  lob_vectors_kernel<<<dim3(nbands, kb), 256, sh, s>>>(X64, Wc, LinvR, N, b, nbands, out);
+  lob_vectors_kernel<<<dim3(nbands, kb), 256, sh, s>>>(X64, Wc, LinvR, lstride, kper, N, M, Mp, b,
+                                                       nbands, rows, out);
   BS_CHECK_LAUNCH("lob_vectors_kernel");
   return BS_OK;
 }

@@ -1,0 +1,123 @@
+"""The ragged batch on the LOBPCG solver: against the dense-solver batch and
+the oracle, graph record/replay, warm starts given as low-order plane-wave
+coefficients, and the per-(cell, k) statistics."""
+import numpy as np
+import pytest
+
+from oracle import mixed_variational as mv
+from paper_1310_6380_gb300 import cells, warmstart
+
+from _helpers import omega_floor, omega_rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1310_6380_gb300 import binding as bs  # noqa: E402
+
+TOL = 1e-6
+NK, NB = 5, 10
+
+
+def _args(cell, M):
+    return (cell.h1, cell.h2, np.ascontiguousarray(cell.phase, np.uint16), cell.lam.copy(),
+            cell.mu.copy(), cell.rho.copy(), M, bs.BS_PREC_MIXED)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    cfgs = [cells.config3_cell(i) for i in range(12)]
+    Qs = np.ascontiguousarray(np.stack([c["Q"][::6][:NK] for c in cfgs]))
+    b = bs.bs_batch_create([_args(c["cell"], c["M"]) for c in cfgs], NK, NB)
+    wd = np.empty((len(cfgs), NK, NB))
+    std = np.empty((len(cfgs), NK), np.int32)
+    bs.bs_batch_solve(b, Qs, wd, std)
+    bs.bs_batch_set_solver(b, bs.BS_SOLVER_LOBPCG)
+    w = np.empty_like(wd)
+    st = np.empty_like(std)
+    bs.bs_batch_solve(b, Qs, w, st)
+    it, fb = bs.bs_batch_stats(b, len(cfgs) * NK)
+    yield cfgs, Qs, w, st, it, fb, wd, std, b
+    bs.bs_batch_destroy(b)
+
+
+def test_lobpcg_batch_matches_dense_batch_and_oracle(batch):
+    cfgs, Qs, w, st, it, fb, wd, std, _ = batch
+    assert not st.any() and not std.any()
+    for i, c in enumerate(cfgs):
+        assert omega_rel_err(w[i], wd[i], omega_floor(c["cell"])).max() <= 2 * TOL, i
+    for i in (1, 6, 10):
+        c = cfgs[i]
+        oc = mv.OracleCell(c["cell"], c["M"])
+        ref = np.array([oc.omega(q, NB) for q in Qs[i]])
+        assert omega_rel_err(w[i], ref, omega_floor(c["cell"])).max() <= TOL, i
+    assert (it >= 1).all() and (it <= bs.BS_LOB_MAXIT).all()
+    assert fb.sum() <= 2, fb
+
+
+def test_lobpcg_batch_graph_replay(batch):
+    cfgs, Qs, w, _, it, _, _, _, b = batch
+    Qd = torch.tensor(Qs, device="cuda")
+    wd = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    bs.bs_batch_set_graph(b, True)
+    try:
+        for _ in range(2):
+            wd.zero_()
+            bs.bs_batch_solve(b, Qd, wd, None, s)
+            s.synchronize()
+            got = wd.cpu().numpy()
+            # the replay runs the iteration limit with finished k idling, so
+            # every k stops at the same iterate as the plain solve
+            assert np.array_equal(got, w)
+    finally:
+        bs.bs_batch_set_graph(b, False)
+
+
+def test_lobpcg_batch_warm_start(batch):
+    """Start vectors = each k's own eigenvectors cut to |alpha|, |beta| <= 3:
+    same bands, fewer iterations than the cold start."""
+    cfgs, Qs, w, _, it_cold, _, _, _, b = batch
+    Mp = 3
+    U = []
+    for i, c in enumerate(cfgs):
+        h = bs.bs_create_cell(*_args(c["cell"], c["M"]))
+        try:
+            bs.bs_assemble(h)
+            N, n = bs.bs_cell_dims(h)
+            om = np.empty((NK, NB))
+            vec = np.empty((NK, NB, n), np.complex64)
+            bs.bs_solve_k_lobpcg(h, Qs[i], NB, om, vec_out=vec)
+        finally:
+            bs.bs_destroy_cell(h)
+        U.append(warmstart.truncate(vec, c["M"], Mp))
+    U = np.ascontiguousarray(np.stack(U))            # (cells, k, nvec, 2 (2Mp+1)^2)
+    assert np.isfinite(U).all()
+    bs.bs_batch_set_start(b, U, Mp)
+    try:
+        w2 = np.empty_like(w)
+        st2 = np.empty(w.shape[:2], np.int32)
+        bs.bs_batch_solve(b, Qs, w2, st2)
+        it_warm, fb = bs.bs_batch_stats(b, len(cfgs) * NK)
+    finally:
+        bs.bs_batch_set_start(b, None)
+    for i, c in enumerate(cfgs):
+        assert omega_rel_err(w2[i], w[i], omega_floor(c["cell"])).max() <= 2 * TOL, i
+    assert not st2.any()
+    # the cut vectors miss the high-order waves, which the iterations must
+    # still resolve: a modest but definite saving
+    assert it_warm.mean() < 0.9 * it_cold.mean(), (it_warm.mean(), it_cold.mean())
+
+
+def test_lobpcg_batch_start_validation(batch):
+    cfgs, _, _, _, _, _, _, _, b = batch
+    mmin = min(c["M"] for c in cfgs)
+    U = np.zeros((len(cfgs), NK, 4, 2 * (2 * (mmin + 1) + 1) ** 2), np.complex64)
+    with pytest.raises(bs.BSError) as ei:
+        bs.bs_batch_set_start(b, U, mmin + 1)
+    assert ei.value.code == bs.BS_EINVAL
+    U = np.zeros((len(cfgs), NK, 17, 2 * 9), np.complex64)
+    with pytest.raises(bs.BSError) as ei:
+        bs.bs_batch_set_start(b, U, 1)
+    assert ei.value.code == bs.BS_EINVAL
