@@ -44,8 +44,12 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3"])
-    ap.add_argument("--cells", type=int, default=4096, help="cells of the config-3 batch")
+    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--cells", type=int, default=None,
+                    help="cells of the config-3 batch (4096) or config-4 evaluation set (1024)")
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1310_6380_gb300", "data",
+                                                       "warmstart.npz"),
+                    help="trained warm-start network (config 4)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=6)
@@ -183,7 +187,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.config == "c3":
+    if args.config in ("c3", "c4"):
         return run_reference_batch(args)
     cfg, config, _ = workload(args.config)
     cores = len(os.sched_getaffinity(0))
@@ -415,16 +419,18 @@ def run_batch(args):
 
 
 def run_reference_batch(args):
-    """The oracle on the host cores for config 3: each step solves 2 of the
-    batch's cells (all 30 k), value = k-solves / time."""
+    """The oracle on the host cores for configs 3 and 4: each step solves 2 of
+    the batch's cells (all 30 k), value = k-solves / time."""
     from oracle import mixed_variational as mv
     from paper_1310_6380_gb300 import cells
+    gen = cells.config3_cell if args.config == "c3" else cells.config4_eval_cell
+    ncell = args.cells or (4096 if args.config == "c3" else 1024)
     times, vals = [], []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         nsolve = 0
         for ci in (2 * i, 2 * i + 1):
-            c = cells.config3_cell(ci)
+            c = gen(ci)
             oc = mv.OracleCell(c["cell"], c["M"])
             for q in c["Q"]:
                 oc.omega(q, 10)
@@ -440,7 +446,7 @@ def run_reference_batch(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"c3: {args.cells} cells, 64x64, M = 5..8, 30 k, 10 branches"},
+        "config": {"workload": f"{args.config}: {ncell} cells, 64x64, M = 5..8, 30 k, 10 branches"},
         "cpu_baseline": {"value": value, "unit": "k-solves/s", "cores": cores, "kind": "oracle",
                          "sample": "each step: 2 cells of the batch, all 30 k each"},
         "e2e": {"value": value, "unit": "k-solves/s", "h2d_bytes_per_step": 0,
@@ -612,12 +618,222 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_c4(args):
+    """Config 4: the learned warm start.  Held-out cells (seeds 2e6 + i), 30 k
+    each, 10 branches, batch LOBPCG from (a) the cold start and (b) the trained
+    network's 12-vector starting subspaces; one step = network inference for
+    every (cell, k) + the batch solve (assembly, LOBPCG, FP64 Rayleigh-Ritz,
+    count certificate, dense fallback).  The plain FP64 dense GPU path is timed
+    on a sample of the same cells for comparison."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1310_6380_gb300 import binding as bs
+    from paper_1310_6380_gb300 import cells
+    from paper_1310_6380_gb300 import warmstart as ws
+
+    if not os.path.exists(args.weights):
+        raise SystemExit(f"no trained network at {args.weights}: run "
+                         "python -m paper_1310_6380_gb300.train_warmstart --out <file>")
+    saved = np.load(args.weights)
+    meta = json.loads(str(saved["meta"]))
+    ncell, nk, nb, Mp, nvec = args.cells or 1024, 30, 10, meta["Mp"], meta["nvec"]
+    cfgs = [cells.config4_eval_cell(i) for i in range(ncell)]
+    cl = [c["cell"] for c in cfgs]
+    Ms = [c["M"] for c in cfgs]
+    Qh = np.ascontiguousarray(np.stack([c["Q"] for c in cfgs]))
+    cargs = [(c.h1, c.h2, np.ascontiguousarray(c.phase, np.uint16), c.lam, c.mu, c.rho, M,
+              bs.BS_PREC_MIXED) for c, M in zip(cl, Ms)]
+    net = ws.WarmStartNet(nvec, Mp, max_cells=256, max_samples=256 * nk)
+    net.set_params(saved["params"])
+    pack = ws.CellPack(cl)
+    b = bs.bs_batch_create(cargs, nk, nb)
+    bs.bs_batch_set_solver(b, bs.BS_SOLVER_LOBPCG)
+    Qd = torch.tensor(Qh, device="cuda")
+    w = torch.empty((ncell, nk, nb), dtype=torch.float64, device="cuda")
+    st = torch.empty((ncell, nk), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(warm):
+        if warm:
+            U = net.predict(pack, Qh)
+            bs.bs_batch_set_start(b, U, Mp)
+        else:
+            bs.bs_batch_set_start(b, None)
+        bs.bs_batch_solve(b, Qd, w, st, stream)
+
+    def timed(warm):
+        for _ in range(args.warmup):
+            step(warm)
+        barrier()
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(warm)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        barrier()
+        it, fb = bs.bs_batch_stats(b, ncell * nk)
+        return statistics.mean(times), it, fb, w.cpu().numpy(), st.cpu().numpy()
+
+    ms_cold, it_cold, fb_cold, om_cold, st_cold = timed(False)
+    launches0 = bs.bs_launch_count()
+    sampler = ClockSampler(device_bus_id(torch))
+    sampler.start()
+    ms_warm, it_warm, fb_warm, om_warm, st_warm = timed(True)
+    clocks = sampler.stop()
+    launches = (bs.bs_launch_count() - launches0) // max(1, args.steps + args.warmup)
+    bs.bs_batch_set_profiling(b, True)
+    step(True)
+    torch.cuda.synchronize()
+    ph = bs.bs_batch_phase_times(b)
+    bs.bs_batch_set_profiling(b, False)
+    ms = ms_warm
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ncell * nk / (ms / 1e3)
+
+    # the plain FP64 dense GPU path (bs_solve_k, FP64 cell) on a sample of the cells
+    samp = list(range(0, ncell, max(1, ncell // 32)))[:32]
+    fp64_ms = 0.0
+    for i in samp:
+        c, M = cl[i], Ms[i]
+        h = bs.bs_create_cell(c.h1, c.h2, np.ascontiguousarray(c.phase, np.uint16), c.lam.copy(),
+                              c.mu.copy(), c.rho.copy(), M, bs.BS_PREC_FP64)
+        wq = torch.empty((nk, nb), dtype=torch.float64, device="cuda")
+        bs.bs_assemble(h, stream)
+        bs.bs_solve_k(h, Qd[i], nb, wq, None, stream)      # warm-up (workspace)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bs.bs_assemble(h, stream)
+        bs.bs_solve_k(h, Qd[i], nb, wq, None, stream)
+        e1.record(stream)
+        e1.synchronize()
+        fp64_ms += e0.elapsed_time(e1)
+        bs.bs_destroy_cell(h)
+    fp64_rate = len(samp) * nk / (fp64_ms / 1e3)
+
+    # end to end through the public API, host buffers: network inference on
+    # host inputs, batch creation from host arrays, solve with host Q/outputs
+    hw = torch.empty((ncell, nk, nb), dtype=torch.float64).pin_memory()
+    hs = torch.empty((ncell, nk), dtype=torch.int32).pin_memory()
+    hQ = torch.from_numpy(Qh).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b2 = bs.bs_batch_create(cargs, nk, nb)
+        bs.bs_batch_set_solver(b2, bs.BS_SOLVER_LOBPCG)
+        bs.bs_batch_set_start(b2, net.predict(pack, Qh), Mp)
+        bs.bs_batch_solve(b2, hQ, hw, hs, stream)
+        bs.bs_batch_destroy(b2)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = (sum(a[2].nbytes + 3 * a[3].nbytes for a in cargs) + Qh.nbytes + pack.phase.nbytes
+           + pack.table.nbytes + ncell * nk * nvec * 2 * (2 * Mp + 1) ** 2 * 8)
+    e2e = {"value": world * ncell * nk / e2e_s, "unit": "k-solves/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": hw.numel() * 8 + hs.numel() * 4
+           + ncell * nk * nvec * 2 * (2 * Mp + 1) ** 2 * 8,
+           "api": "bs_cnn_forward (host inputs, starting vectors to host) + bs_batch_create + "
+                  "bs_batch_set_solver/set_start + bs_batch_solve (host Q, outputs) + "
+                  "bs_batch_destroy"}
+    ns = np.array([2 * (2 * m + 1) ** 2 for m in Ms], float)
+    # dominant phase: the LOBPCG iterations; algorithmic FP32 flops of the
+    # C W products at the full block width (an upper bound on the active width)
+    b_lob = 16
+    cw_flops = float(np.sum(it_warm.reshape(ncell, nk) * (8.0 * ns[:, None] ** 2 * b_lob)))
+    achieved = cw_flops / (ph["reduction"] / 1e3) / 1e12
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    roofline = {"bound": "alu", "kernel": "LOBPCG iterations (lob_cw_kernel + lob_eig_kernel + "
+                                          "lob_update_kernel, one step)",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": "nominal FP32 CUDA-core rate: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                "algorithmic": "8 n^2 b flops (C W, b = 16) per LOBPCG iteration per (cell, k)"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 network and LOBPCG, bf16 exact-slice tensor products, f64 Rayleigh-Ritz",
+        "data": "synthetic",
+        "config": {"workload": f"c4: learned warm start, {ncell} held-out cells (seeds 2e6+i, "
+                               "64x64, square/hex, ellipse/Voronoi, 2-16 phases, M = 5..8), 30 k "
+                               "each, lowest 10 branches, batch LOBPCG from the network's "
+                               f"{nvec}-vector subspaces (|alpha|,|beta| <= {Mp})",
+                   "cells": ncell, "k_points": ncell * nk,
+                   "network": {k: meta[k] for k in ("cells", "kper", "epochs", "M_train", "Mp",
+                                                   "nvec", "seeds")},
+                   "l2": "flushed between timed steps (256 MiB write, untimed)"},
+        "cold_start": {"value": world * ncell * nk / (ms_cold / 1e3), "ms_per_step": ms_cold,
+                       "iterations_mean": float(it_cold.mean()),
+                       "fallbacks": int(fb_cold.sum())},
+        "warm_start": {"iterations_mean": float(it_warm.mean()), "fallbacks": int(fb_warm.sum()),
+                       "iteration_ratio_vs_cold": float(it_warm.mean() / it_cold.mean()),
+                       "speedup_vs_cold": ms_cold / ms_warm},
+        "fp64_dense_gpu": {"value": fp64_rate, "unit": "k-solves/s",
+                           "sample": f"{len(samp)} cells x {nk} k, bs_assemble + bs_solve_k on "
+                                     "FP64 cells, one cell per call",
+                           "speedup_of_value": value / fp64_rate},
+        "status_nonzero": int(np.count_nonzero(st_warm)),
+        "phases_ms": {k: round(v, 1) for k, v in ph.items()},
+        "gpu_launches_per_step": launches, "gpu_launches": launches * args.steps,
+        "e2e": e2e, "roofline": roofline, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import mixed_variational as mv
+        osamp = list(range(0, ncell, max(1, ncell // 6)))[:6]
+        t0 = time.perf_counter()
+        errs = []
+        for i in osamp:
+            oc = mv.OracleCell(cl[i], Ms[i])
+            ref = np.array([oc.omega(q, nb) for q in Qh[i]])
+            errs.append(max(rel_err(om_warm[i], ref, cl[i]).max(),
+                            rel_err(om_cold[i], ref, cl[i]).max()))
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(osamp) * nk / secs, "unit": "k-solves/s",
+                               "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                               "sample": f"{len(osamp)} of the {ncell} cells, all 30 k each "
+                                         f"({secs:.1f} s); value = their k-solves / time"}
+        out["max_rel_err_vs_oracle"] = float(max(errs))
+        out["oracle_sampled_cells"] = osamp
+    bs.bs_batch_destroy(b)
+    net.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "c3":
+        args.cells = args.cells or 4096
         run_batch(args)
+    elif args.config == "c4":
+        run_c4(args)
     else:
         run_ours(args)
 

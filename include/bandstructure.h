@@ -287,7 +287,10 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   U); NULL returns to the cold start.  Needs Mp <= every cell's M and
  *   1 <= nvec <= the LOBPCG block size.
  * bs_batch_stats - per (cell, k) of the last solve: LOBPCG iterations
- *   (0 on the dense solver) and 1 where the dense FP64 fallback ran.
+ *   (0 on the dense solver) and the fallback taken: 0 none, 1 the dense FP64
+ *   solve, 2 the dense mixed path (LOBPCG entries whose residual bound or
+ *   eigenvalue count failed are re-solved there within their chunk when the
+ *   solve is not replayed from a graph; what still fails takes the FP64 one).
  * bs_batch_set_vectors - Mp >= 0 (at most every cell's M): later solves
  *   also keep the eigenvectors of the nbands branches as the displacement
  *   coefficients u of the waves |alpha|, |beta| <= Mp (u^dagger Omega u = 1

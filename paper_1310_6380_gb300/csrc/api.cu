@@ -141,12 +141,14 @@ static void free_workspace(bs_cell* c) {
 
 static void free_lob_workspace(bs_cell* c) {
   void* p[] = {c->d_lS, c->d_lCS, c->d_lA, c->d_lpart, c->d_lZ, c->d_lY, c->d_lst, c->d_lX0,
-               c->d_lndone, c->d_liters, c->d_lvec};
+               c->d_lndone, c->d_liters, c->d_lvec, c->d_lsig, c->d_lsc, c->d_liw};
   for (void* q : p) cudaFree(q);
   c->d_lS = c->d_lCS = c->d_lA = c->d_lpart = c->d_lZ = c->d_lY = c->d_lX0 = nullptr;
   c->d_lst = nullptr;
   c->d_lndone = c->d_liters = nullptr;
   c->d_lvec = nullptr;
+  c->d_lsig = c->d_lsc = nullptr;
+  c->d_liw = nullptr;
   c->lcap = 0;
   c->lbcap = 0;
 }
@@ -169,6 +171,9 @@ static int ensure_lob_workspace(bs_cell* c, int kb, int b) {
   TRY(dalloc(&c->d_lndone, 1, "LOBPCG counter"));
   TRY(dalloc(&c->d_liters, (size_t)kb, "LOBPCG iterations"));
   TRY(dalloc(&c->d_lvec, (size_t)kb * b * n, "LOBPCG vectors"));
+  TRY(dalloc(&c->d_lsig, (size_t)kb, "inertia shifts"));
+  TRY(dalloc(&c->d_lsc, (size_t)kb * n, "inertia scales"));
+  TRY(dalloc(&c->d_liw, 3 * (size_t)kb, "inertia counters"));
   c->lcap = kb;
   c->lbcap = b;
   return BS_OK;
@@ -603,6 +608,9 @@ static int solve_chunk_lobpcg(bs_cell* c, int kb, int nbands, int b, const float
   m.err = c->d_info + 1;
   CK(cudaMemsetAsync(c->d_stat, 0, kb * sizeof(int), s), "status");
   TRY(bs_launch_rr_tail(m, n, kb, nbands, b, c->tol, c->floor2, c->d_w, c->d_stat, s));
+  // no eigenvalue skipped below the wanted ones (C32 is free after the iterations)
+  TRY(bs_launch_inertia_check(c->d_C32, n, kb, c->d_theta, b, nbands, c->floor2, c->d_lsig,
+                              c->d_lsc, c->d_liw, c->d_stat, nullptr, s));
   if (want_vec)
     TRY(bs_launch_lob_vectors(c->d_X64, c->d_W, c->d_Linv + 2 * (size_t)N * N, 0, kb, N, c->M, -1,
                               b, nbands, kb, nullptr, c->d_lvec, s));

@@ -126,6 +126,12 @@ struct BatchGroup {
   int* lndone;
   int* liters;
   zd* lLinv;                  // chunk x N x N: L_R^-1 of the chunk's cells (eigenvector output)
+  float* lsig;                // inertia check scratch
+  float* lsc;
+  int* liw;
+  double* fbw;                // dense-mixed rescue of uncertified LOBPCG entries
+  int* fbst;
+  int* fbrow;
 };
 
 struct bs_batch {
@@ -182,9 +188,13 @@ static void free_group(BatchGroup& g) {
   void* ps[] = {g.C64, g.C32, g.vec32, g.part32, g.de, g.tau, g.beta, g.count, g.lamT, g.scr, g.Y,
                 g.phase, g.X32, g.X64, g.CX, g.G, g.H, g.W, g.theta, g.cxA, g.cxB, g.cxD, g.cxeA,
                 g.cxeB, g.w, g.st, g.d_rowidx, g.d_Gall, g.lS, g.lCS, g.lA, g.lpart, g.lZ, g.lY,
-                g.lX0, g.lst, g.lndone, g.liters, g.lLinv};
+                g.lX0, g.lst, g.lndone, g.liters, g.lLinv, g.lsig, g.lsc, g.liw, g.fbw,
+                g.fbst, g.fbrow};
   for (void* p : ps) cudaFree(p);
 }
+
+static int mixed_rescue(bs_batch* B, BatchGroup& g, int c0, const std::vector<int>& f,
+                        double floor2, cudaStream_t s);
 
 static int alloc_lob(BatchGroup& g, int nk, int nbands) {
   if (g.lb) return BS_OK;
@@ -201,6 +211,12 @@ static int alloc_lob(BatchGroup& g, int nk, int nbands) {
   if (!r) r = balloc(&g.lst, K, "batch LOBPCG state");
   if (!r) r = balloc(&g.lndone, 1, "batch LOBPCG counter");
   if (!r) r = balloc(&g.liters, K, "batch LOBPCG iterations");
+  if (!r) r = balloc(&g.lsig, K, "batch inertia shifts");
+  if (!r) r = balloc(&g.lsc, K * n, "batch inertia scales");
+  if (!r) r = balloc(&g.liw, 3 * K, "batch inertia counters");
+  if (!r) r = balloc(&g.fbw, K * nbands, "batch rescue omega");
+  if (!r) r = balloc(&g.fbst, K, "batch rescue status");
+  if (!r) r = balloc(&g.fbrow, K, "batch rescue rows");
   if (!r) g.lb = b;
   return r;
 }
@@ -351,12 +367,32 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
     w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
     CK(cudaMemsetAsync(g.st, 0, K * sizeof(int), s), "batch status");
     TRY_LAUNCH(bs_launch_rr_tail(w, n, K, B->nbands, lb, 1e-6, floor2, g.w, g.st, s));
+    TRY_LAUNCH(bs_launch_inertia_check(g.C32, n, K, g.theta, lb, B->nbands, floor2, g.lsig, g.lsc,
+                                       g.liw, g.st, nullptr, s));
     if (B->d_vec)
       TRY_LAUNCH(bs_launch_lob_vectors(g.X64, g.W, g.lLinv, (long)g.N * g.N, nk, g.N, g.M, B->vecMp,
                                        lb, B->nbands, K, rows, B->d_vec, s));
     prof_mark(B, s);
     scatter_int_kernel<<<(K + 255) / 256, 256, 0, s>>>(g.liters, rows, K, 1, B->d_iters);
     BS_CHECK_LAUNCH("scatter_int_kernel");
+    scatter_rows_kernel<<<(K * B->nbands + 255) / 256, 256, 0, s>>>(g.w, rows, K, B->nbands,
+                                                                    B->d_w);
+    BS_CHECK_LAUNCH("scatter_rows_kernel");
+    scatter_int_kernel<<<(K + 255) / 256, 256, 0, s>>>(g.st, rows, K, 1, B->d_st);
+    BS_CHECK_LAUNCH("scatter_int_kernel");
+    // outside a graph: the uncertified entries of this chunk go through the
+    // dense mixed path at once (their FP64 C(k) are still here)
+    if (!B->capturing) {
+      std::vector<int> sth(K);
+      CK(cudaMemcpyAsync(sth.data(), g.st, K * sizeof(int), cudaMemcpyDeviceToHost, s),
+         "batch rescue status");
+      CK(cudaStreamSynchronize(s), "batch rescue sync");
+      std::vector<int> f;
+      for (int k = 0; k < K; ++k)
+        if (sth[k]) f.push_back(k);
+      if (!f.empty()) TRY_LAUNCH(mixed_rescue(B, g, c0, f, floor2, s));
+    }
+    return BS_OK;
   } else {
   TRY_LAUNCH(bs_launch_tridiag<float>(g.C32, n, K, g.vec32, g.part32, g.de, g.tau, g.beta, g.count,
                                       s, tile));
@@ -778,6 +814,47 @@ extern "C" int bs_batch_phase_times(bs_batch* B, double ms[4]) {
   return BS_OK;
 }
 
+// Dense mixed path on the entries f (chunk indices) of the chunk starting at
+// cell c0 whose LOBPCG solve was not certified: their FP64 C(k) are moved to
+// the front of the chunk buffer (ascending, so no source is overwritten
+// before it is read), reduced in FP32 and refined; results go to their rows.
+static int mixed_rescue(bs_batch* B, BatchGroup& g, int c0, const std::vector<int>& f,
+                        double floor2, cudaStream_t s) {
+  const int nk = B->nk, n = g.n, nf = (int)f.size();
+  const size_t nn = (size_t)n * n;
+  std::vector<int> rows(nf);
+  for (int i = 0; i < nf; ++i) {
+    if (f[i] != i)
+      CK(cudaMemcpyAsync(g.C64 + (size_t)i * nn, g.C64 + (size_t)f[i] * nn, nn * sizeof(zd),
+                         cudaMemcpyDeviceToDevice, s), "batch rescue copy");
+    rows[i] = g.cells[c0 + f[i] / nk] * nk + f[i] % nk;
+    B->fb[rows[i]] = 2;
+    if (B->d_vec) {   // no vectors for rescued entries (NaN)
+      const size_t len = 2 * (size_t)(2 * B->vecMp + 1) * (2 * B->vecMp + 1) * B->nbands;
+      CK(cudaMemsetAsync(B->d_vec + (size_t)rows[i] * len, 0xff, len * sizeof(float2), s),
+         "batch rescue vectors");
+    }
+  }
+  CK(cudaMemcpyAsync(g.fbrow, rows.data(), nf * sizeof(int), cudaMemcpyHostToDevice, s),
+     "batch rescue rows");
+  TRY_LAUNCH(bs_launch_c64_to_c32(g.C64, g.C32, n, nf, s));
+  TRY_LAUNCH(bs_launch_tridiag<float>(g.C32, n, nf, g.vec32, g.part32, g.de, g.tau, g.beta,
+                                      g.count, s, g.tile));
+  TRY_LAUNCH(bs_launch_bisect(g.de, n, nf, g.b + 1, g.lamT, nullptr, s, false, 1e-9));
+  MixedWs w;
+  w.C64 = g.C64; w.C32 = g.C32; w.de = g.de; w.tau = g.tau; w.beta = g.beta; w.lamT = g.lamT;
+  w.scratch = g.scr; w.Y = g.Y; w.phase = g.phase; w.X32 = g.X32; w.X64 = g.X64; w.CX = g.CX;
+  w.G = g.G; w.H = g.H; w.W = g.W; w.theta = g.theta; w.cxA = g.cxA; w.cxB = g.cxB;
+  w.cxD = g.cxD; w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
+  TRY_LAUNCH(bs_launch_mixed_refine(w, n, nf, B->nbands, g.b, 1e-6, floor2, g.fbw, g.fbst, s));
+  scatter_rows_kernel<<<(nf * B->nbands + 255) / 256, 256, 0, s>>>(g.fbw, g.fbrow, nf,
+                                                                   B->nbands, B->d_w);
+  BS_CHECK_LAUNCH("scatter_rows_kernel");
+  scatter_int_kernel<<<(nf + 255) / 256, 256, 0, s>>>(g.fbst, g.fbrow, nf, 1, B->d_st);
+  BS_CHECK_LAUNCH("scatter_int_kernel");
+  return BS_OK;
+}
+
 // (cell, k) entries the residual bound did not certify: assemble the cell
 // again on a worker and solve those wavevectors with the dense FP64 path
 static int dense_fallback(bs_batch* B, cudaStream_t s) {
@@ -786,7 +863,7 @@ static int dense_fallback(bs_batch* B, cudaStream_t s) {
   CK(cudaMemcpyAsync(st.data(), B->d_st, nq * sizeof(int), cudaMemcpyDeviceToHost, s),
      "bs_batch_solve status");
   CK(cudaStreamSynchronize(s), "bs_batch_solve sync");
-  B->fb.assign(nq, 0);
+  if (B->fb.size() != nq) B->fb.assign(nq, 0);
   std::vector<double> Qh;
   for (int ci = 0; ci < B->ncells; ++ci) {
     std::vector<int> ks;
@@ -856,6 +933,7 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
     for (int i = 0; i < B->ncells; ++i) floors[i] = floor2_of(B, i, raw);
   }
   CK(cudaMemcpyAsync(B->d_Q, Q, nq * 2 * sizeof(double), cudaMemcpyDefault, s), "bs_batch_solve Q");
+  B->fb.assign(nq, 0);
   const bool prof = B->prof;
   B->prof = false;   // not while tuning or recording a graph
   for (auto& g : B->groups) {

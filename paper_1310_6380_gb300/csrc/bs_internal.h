@@ -174,6 +174,9 @@ struct bs_cell {
   int* d_lndone;
   int* d_liters;
   float2* d_lvec;
+  float* d_lsig;       // inertia check: shifts, row scales, counters
+  float* d_lsc;
+  int* d_liw;
 
   // profiling: events around each phase of the last call
   bool prof;
@@ -283,6 +286,8 @@ int bs_launch_builder_mixed(const zd* Cm, int n, const double* Q, int nk, double
                             bool full32 = false);
 int bs_launch_mixed_refine(const MixedWs& w, int n, int kb, int nbands, int b, double tol,
                            double floor2, double* omega, int* stat, cudaStream_t s);
+// C32 lower triangle (FP32) from the full FP64 C of kb matrices
+int bs_launch_c64_to_c32(const zd* C64, zf* C32, int n, int kb, cudaStream_t s);
 
 // lobpcg.cu: block LOBPCG (FP32) with soft locking, batched over k
 #define BS_LOB_MAX_BLOCK 16
@@ -326,6 +331,13 @@ int bs_launch_lob_export(const LobWs& w, int n, int kb, int b, zd* X64, int* ite
 // |alpha|, |beta| <= Mp, 2 (2Mp+1)^2 per vector
 int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int M, int Mp, int kb, int nvec,
                              float2* y, cudaStream_t s);
+// inertia.cu: eigenvalue-count certificate (FP32 LDL^dagger of the scaled
+// C - sigma I, sigma in a gap above the wanted Ritz values); A (lower part of
+// C(k), overwritten), sigma (kb), sc (kb x n) floats and iwork (3 kb ints)
+// scratch; stat[k] = BS_ENOCONV where the count fails; verdict optional
+int bs_launch_inertia_check(zf* A, int n, int kb, const double* theta, int b, int nb,
+                            double floor2, float* sigma, float* sc, int* iwork, int* stat,
+                            int* verdict, cudaStream_t s);
 // dense FP64 solve of nf host wavevectors on an assembled cell (host outputs)
 int bs_cell_dense_fp64(bs_cell* c, const double* Q, int nf, int nbands, double* om, int* st,
                        cudaStream_t s);

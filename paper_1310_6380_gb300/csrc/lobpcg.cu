@@ -690,25 +690,51 @@ __global__ void __launch_bounds__(32) lob_eig_kernel(LobWs w, int n, int kb, int
   const float tnorm = fmaxf(fabsf(gl), fabsf(gu));
   const float pivmin = FLT_MIN * fmaxf(1.f, emax2);
   const float tinyp = FLT_EPSILON * fmaxf(tnorm, FLT_MIN);
-  // Sturm bisection: lane c finds eigenvalue c (ascending)
-  if (lane < q) {
-    float lo = gl - FLT_EPSILON * tnorm, hi = gu + FLT_EPSILON * tnorm;
-    for (int it = 0; it < 64; ++it) {
-      if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
-      const float mid = 0.5f * (lo + hi);
+  // Sturm multisection: lanes c and c + 16 find eigenvalue c (ascending),
+  // each step the pair counts at the two interior third points.  The wanted
+  // eigenvalues lie in [0, theta_top] of the previous block (the basis
+  // contains that block, so the Ritz values can only decrease, and A is
+  // positive semidefinite); that bracket is used when one count confirms it.
+  {
+    auto sturm = [&](float x) {
       int cnt = 0;
-      float qv = s.d[0] - mid;
+      float qv = s.d[0] - x;
       if (fabsf(qv) < pivmin) qv = -pivmin;
       cnt += qv < 0.f;
       for (int i = 1; i < m; ++i) {
-        qv = s.d[i] - mid - s.e2[i - 1] / qv;
+        qv = s.d[i] - x - __fdividef(s.e2[i - 1], qv);
         if (fabsf(qv) < pivmin) qv = -pivmin;
         cnt += qv < 0.f;
       }
-      if (cnt > lane) hi = mid;
-      else lo = mid;
+      return cnt;
+    };
+    const int c = lane & (LB - 1), h = lane / LB;
+    float lo = gl - FLT_EPSILON * tnorm, hi = gu + FLT_EPSILON * tnorm;
+    if (nx > 0) {
+      const float top = stp->theta[q - 1];
+      const float hb = top + 1e-3f * fabsf(top) + 16.f * FLT_EPSILON * tnorm;
+      if (hb < hi && sturm(hb) >= q) {
+        hi = hb;
+        lo = fmaxf(lo, -16.f * FLT_EPSILON * tnorm);
+      }
     }
-    s.th[lane] = 0.5f * (lo + hi);
+    for (int it = 0; it < 48; ++it) {
+      if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
+      const float x1 = lo + (hi - lo) * (1.f / 3.f), x2 = lo + (hi - lo) * (2.f / 3.f);
+      const int mine = sturm(h ? x2 : x1);
+      // the two lanes of a pair run the same number of steps (identical
+      // brackets), so the pair alone synchronises here
+      const int other = __shfl_xor_sync((1u << c) | (1u << (c + LB)), mine, LB);
+      const int c1 = h ? other : mine, c2 = h ? mine : other;
+      if (c1 > c) hi = x1;
+      else if (c2 > c) {
+        lo = x1;
+        hi = x2;
+      } else {
+        lo = x2;
+      }
+    }
+    if (h == 0 && c < q) s.th[c] = 0.5f * (lo + hi);
   }
   __syncwarp();
   // inverse iteration on T - theta I (tridiagonal LU with partial pivoting);

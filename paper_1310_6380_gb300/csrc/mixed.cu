@@ -478,6 +478,16 @@ __global__ void residual_kernel(const zd* __restrict__ CX, const zd* __restrict_
   if (threadIdx.x == 0 && stat[k] == 0 && bad) stat[k] = BS_ENOCONV;
 }
 
+// C32 (lower triangle, FP32) from the full FP64 C, batch of kb
+__global__ void c64_to_c32_kernel(const zd* __restrict__ C64, zf* __restrict__ C32, int n, int kb) {
+  const size_t nn = (size_t)n * n;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn * kb) return;
+  const size_t l = e % nn;
+  if ((int)(l % n) < (int)(l / n)) return;
+  C32[e] = make_float2((float)C64[e].x, (float)C64[e].y);
+}
+
 __global__ void zero_int_kernel(int* p, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = 0;
@@ -504,6 +514,13 @@ int bs_launch_builder_mixed(const zd* Cm, int n, const double* Q, int nk, double
   builder_mixed_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Cm, n, Q, nk, q1x, q1y, q2x,
                                                                     q2y, C64, C32, full32);
   BS_CHECK_LAUNCH("builder_mixed_kernel");
+  return BS_OK;
+}
+
+int bs_launch_c64_to_c32(const zd* C64, zf* C32, int n, int kb, cudaStream_t s) {
+  const size_t tot = (size_t)n * n * kb;
+  c64_to_c32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C64, C32, n, kb);
+  BS_CHECK_LAUNCH("c64_to_c32_kernel");
   return BS_OK;
 }
 

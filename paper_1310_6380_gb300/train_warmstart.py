@@ -8,8 +8,8 @@ targets: the network predicts only the waves |alpha|, |beta| <= 3, whose
 coefficients the larger truncations of the evaluation cells change little.
 Each cell contributes `kper` wavevectors drawn uniformly from its 30-point
 IBZ path.  The targets are the low-order coefficients of the lowest 10
-eigenvectors from the batch solver (bs_batch_set_vectors); entries that fell
-back to the dense solve carry no vectors and are left out.  Training is
+eigenvectors from the batch solver (dense mixed path, bs_batch_set_vectors);
+entries that fell back to the FP64 solve carry no vectors and are left out.  Training is
 Adam on minibatches of cells with every kernel in the library (bs_cnn_*).
 """
 from __future__ import annotations
@@ -56,12 +56,11 @@ def make_targets(cell_list, paths, kper, seed, chunk, log):
         sl = slice(c0, min(C, c0 + chunk))
         t0 = time.time()
         w, st, it, fb, vec = ws.solve_batch(cell_list[sl], [M_TRAIN] * (sl.stop - sl.start),
-                                            np.ascontiguousarray(Q[sl]), NB, bs.BS_SOLVER_LOBPCG,
+                                            np.ascontiguousarray(Q[sl]), NB, bs.BS_SOLVER_DENSE,
                                             Mp=MP, vectors=True)
         V[sl] = vec
         keep[sl] = (fb == 0) & np.isfinite(vec).all(axis=(2, 3))
-        log(f"targets {sl.stop}/{C}: {time.time() - t0:.1f} s, mean LOBPCG iterations "
-            f"{it.mean():.1f}, fallbacks {int(fb.sum())}")
+        log(f"targets {sl.stop}/{C}: {time.time() - t0:.1f} s, fallbacks {int(fb.sum())}")
     return Q, V, keep
 
 
