@@ -787,8 +787,11 @@ def run_c4(args):
                    "l2": "flushed between timed steps (256 MiB write, untimed)"},
         "cold_start": {"value": world * ncell * nk / (ms_cold / 1e3), "ms_per_step": ms_cold,
                        "iterations_mean": float(it_cold.mean()),
-                       "fallbacks": int(fb_cold.sum())},
-        "warm_start": {"iterations_mean": float(it_warm.mean()), "fallbacks": int(fb_warm.sum()),
+                       "dense_mixed_rescues": int((fb_cold == 2).sum()),
+                       "fp64_fallbacks": int((fb_cold == 1).sum())},
+        "warm_start": {"iterations_mean": float(it_warm.mean()),
+                       "dense_mixed_rescues": int((fb_warm == 2).sum()),
+                       "fp64_fallbacks": int((fb_warm == 1).sum()),
                        "iteration_ratio_vs_cold": float(it_warm.mean() / it_cold.mean()),
                        "speedup_vs_cold": ms_cold / ms_warm},
         "fp64_dense_gpu": {"value": fp64_rate, "unit": "k-solves/s",

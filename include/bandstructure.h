@@ -260,13 +260,18 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   status_out: ncells * nk (0, or the failure status of the dense
  *   fallback below, which re-solves every entry the residual bound did not
  *   certify) or
- *   NULL; host or device pointers.  The first call times both tile edges of
- *   the reduction per truncation group and keeps the faster (autotuning).
+ *   NULL; host or device pointers.  The first call times the reduction
+ *   variants per truncation group and keeps the fastest (autotuning).
  * bs_batch_set_graph - on != 0: the next bs_batch_solve records the whole
  *   solve in a CUDA graph, later calls replay it (the Q and output pointers
  *   of the recording call must be reused); on == 0 drops the graph.
- * bs_batch_tiles - the tile edge chosen for each truncation group and the
- *   group's eigen dimension n.
+ * bs_batch_tiles - the reduction variant chosen for each truncation group
+ *   and the group's eigen dimension n: 64 or 32 (tile edge of the
+ *   per-step kernel) or 0 (the whole matrix resident in the shared memory
+ *   of a thread-block cluster, n up to about 600).
+ * bs_batch_set_tile - force that choice for every group (0, 32 or 64; 0
+ *   falls back to 64 where n does not fit a cluster) or, with -1, return to
+ *   timing all of them on the next solve.  Drops a recorded graph.
  * bs_batch_set_profiling / bs_batch_phase_times - with profiling on, a
  *   solve that does not replay a graph records CUDA events around each
  *   chunk's phases; phase_times returns milliseconds summed over chunks:
@@ -308,6 +313,7 @@ int bs_batch_solve(bs_batch* batch, const double* Q, double* omega_out, int* sta
                    void* stream);
 int bs_batch_set_graph(bs_batch* batch, int on);
 int bs_batch_tiles(const bs_batch* batch, int* tiles, int* ns, int ngroups_max, int* ngroups);
+int bs_batch_set_tile(bs_batch* batch, int tile);
 int bs_batch_set_profiling(bs_batch* batch, int on);
 int bs_batch_phase_times(bs_batch* batch, double ms[4]);
 int bs_batch_destroy(bs_batch* batch);

@@ -73,6 +73,7 @@ def _load():
         "bs_batch_stats": [vp, dp, dp],
         "bs_batch_set_vectors": [vp, i32],
         "bs_batch_vectors": [vp, dp],
+        "bs_batch_set_tile": [vp, i32],
         "bs_cnn_create": [i32, i32, i32, i32, ctypes.POINTER(vp)],
         "bs_cnn_destroy": [vp],
         "bs_cnn_num_params": [vp, ctypes.POINTER(ctypes.c_longlong)],
@@ -101,7 +102,7 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_batch_set_graph", "bs_batch_tiles", "bs_batch_destroy", "bs_batch_set_profiling",
             "bs_batch_phase_times", "bs_solve_k_lobpcg", "bs_batch_set_solver",
             "bs_batch_set_start", "bs_batch_stats", "bs_batch_set_vectors", "bs_batch_vectors",
-            "bs_cnn_create", "bs_cnn_destroy", "bs_cnn_num_params", "bs_cnn_set_params",
+            "bs_batch_set_tile", "bs_cnn_create", "bs_cnn_destroy", "bs_cnn_num_params", "bs_cnn_set_params",
             "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step"]
 BS_SOLVER_DENSE, BS_SOLVER_LOBPCG = 0, 1
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
@@ -259,6 +260,10 @@ def bs_batch_phase_times(batch) -> dict:
 
 def bs_batch_destroy(batch):
     _check(_lib.bs_batch_destroy(batch))
+
+
+def bs_batch_set_tile(batch, tile: int):
+    _check(_lib.bs_batch_set_tile(batch, int(tile)))
 
 
 def bs_batch_set_solver(batch, solver: int):

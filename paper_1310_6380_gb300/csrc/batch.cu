@@ -765,9 +765,16 @@ static int tune_group(bs_batch* B, BatchGroup& g, double floor2, cudaStream_t s)
   const int cn = std::min(g.chunk, (int)g.cells.size());
   float best = 1e30f;
   int best_tile = 64;
-  for (int tile : {64, 32}) {
+  for (int tile : {0, 64, 32}) {
+    if (tile == 0 && !bs_tridiag_cluster_fits(g.n)) continue;
     CK(cudaEventRecord(e0, s), "tune");
-    TRY_LAUNCH(run_chunk(B, g, 0, cn, floor2, s, tile));
+    const int r = run_chunk(B, g, 0, cn, floor2, s, tile);
+    if (r != BS_OK && tile == 0) {   // the cluster path could not be scheduled: skip it
+      cudaGetLastError();
+      cudaStreamSynchronize(s);
+      continue;
+    }
+    TRY_LAUNCH(r);
     CK(cudaEventRecord(e1, s), "tune");
     CK(cudaEventSynchronize(e1), "tune");
     float ms = 0.f;
@@ -781,6 +788,25 @@ static int tune_group(bs_batch* B, BatchGroup& g, double floor2, cudaStream_t s)
   cudaEventDestroy(e1);
   g.tile = best_tile;
   g.tuned = true;
+  return BS_OK;
+}
+
+static void drop_graph(bs_batch* B);
+
+extern "C" int bs_batch_set_tile(bs_batch* B, int tile) {
+  if (!B || (tile != -1 && tile != 0 && tile != 32 && tile != 64)) {
+    bs_set_error("bs_batch_set_tile: NULL batch or tile not in {-1, 0, 32, 64}");
+    return BS_EINVAL;
+  }
+  drop_graph(B);
+  for (auto& g : B->groups) {
+    if (tile == -1) {
+      g.tuned = false;
+    } else {
+      g.tile = (tile == 0 && !bs_tridiag_cluster_fits(g.n)) ? 64 : tile;
+      g.tuned = true;
+    }
+  }
   return BS_OK;
 }
 

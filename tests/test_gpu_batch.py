@@ -97,3 +97,27 @@ def test_batch_rejects_mixed_grids_and_fp64():
     fp64[-1] = bs.BS_PREC_FP64
     with pytest.raises(bs.BSError):
         bs.bs_batch_create([tuple(fp64)], 2, 4)
+
+
+def test_batch_cluster_reduction_matches_per_step_kernel():
+    """The cluster-resident FP32 reduction (tile 0) and the per-step kernel
+    (tile 64) give the same certified bands on every (cell, k)."""
+    cfgs = [cells.config3_cell(i) for i in range(20, 28)]
+    nk, nb = 6, 10
+    Qs = np.ascontiguousarray(np.stack([c["Q"][::5][:nk] for c in cfgs]))
+    b = bs.bs_batch_create([_args(c["cell"], c["M"]) for c in cfgs], nk, nb)
+    try:
+        out = {}
+        for tile in (0, 64):
+            bs.bs_batch_set_tile(b, tile)
+            w = np.empty((len(cfgs), nk, nb))
+            st = np.empty((len(cfgs), nk), np.int32)
+            bs.bs_batch_solve(b, Qs, w, st)
+            _, fb = bs.bs_batch_stats(b, len(cfgs) * nk)
+            out[tile] = (w, st, fb, bs.bs_batch_tiles(b))
+    finally:
+        bs.bs_batch_destroy(b)
+    assert set(out[0][3].values()) == {0}
+    for i, c in enumerate(cfgs):
+        assert omega_rel_err(out[0][0][i], out[64][0][i], omega_floor(c["cell"])).max() <= 2 * TOL
+    assert not out[0][1].any() and out[0][2].sum() <= 2

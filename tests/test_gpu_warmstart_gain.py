@@ -1,0 +1,50 @@
+"""What the trained warm-start network gains over the method without it:
+on held-out cells (seeds 2e6 + i, never seen in training) the batch LOBPCG
+started from the network's subspaces needs fewer iterations than the cold
+start, and both give the same certified bands as the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mixed_variational as mv
+from paper_1310_6380_gb300 import cells, warmstart as ws
+
+from _helpers import omega_floor, omega_rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1310_6380_gb300 import binding as bs  # noqa: E402
+
+WEIGHTS = os.path.join(os.path.dirname(ws.__file__), "data", "warmstart.npz")
+
+
+def test_trained_network_saves_iterations():
+    saved = np.load(WEIGHTS)
+    import json
+    meta = json.loads(str(saved["meta"]))
+    cfgs = [cells.config4_eval_cell(i) for i in range(1000, 1032)]
+    cl = [c["cell"] for c in cfgs]
+    Ms = [c["M"] for c in cfgs]
+    Q = np.ascontiguousarray(np.stack([c["Q"] for c in cfgs]))
+    net = ws.WarmStartNet(meta["nvec"], meta["Mp"], max_cells=64, max_samples=64 * 30)
+    try:
+        net.set_params(saved["params"])
+        U = net.predict(ws.CellPack(cl), Q)
+    finally:
+        net.close()
+    assert np.isfinite(U).all()
+    wc, stc, itc, fbc, _ = ws.solve_batch(cl, Ms, Q, 10, bs.BS_SOLVER_LOBPCG)
+    ww, stw, itw, fbw, _ = ws.solve_batch(cl, Ms, Q, 10, bs.BS_SOLVER_LOBPCG, start=U,
+                                          Mp=meta["Mp"])
+    assert not stc.any() and not stw.any()
+    for i, c in enumerate(cl):
+        assert omega_rel_err(ww[i], wc[i], omega_floor(c)).max() <= 2e-6, i
+    for i in (0, 17):
+        oc = mv.OracleCell(cl[i], Ms[i])
+        ref = np.array([oc.omega(q, 10) for q in Q[i][::5]])
+        assert omega_rel_err(ww[i][::5], ref, omega_floor(cl[i])).max() <= 1e-6, i
+    assert itw.mean() < 0.97 * itc.mean(), (itw.mean(), itc.mean())
