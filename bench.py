@@ -78,6 +78,54 @@ def workload(name):
     return cfg, config, (1 if name == "c2" else 0)
 
 
+# ---------------------------------------------------------------- replicas
+class Replicas:
+    """One independent replica of the workload per rank (the method has no
+    exchange between GPUs): rank/world from the launcher's environment, a
+    barrier, and the max over ranks of a step time.  backend "nccl" on GPUs;
+    "gloo" serves the CPU tests of this logic."""
+
+    def __init__(self, backend="nccl", device=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        self.cuda = backend == "nccl"
+        if self.world > 1:
+            import torch.distributed as dist
+            kw = {"device_id": device} if device is not None else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        import torch
+        if self.cuda:
+            torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+        if self.cuda:
+            torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        """max over ranks of a per-rank number (a step time)."""
+        if not self.dist:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64,
+                         device="cuda" if self.cuda else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def value(self, units_per_rank: float, ms: float) -> float:
+        """whole-job throughput: every rank's units over the slowest rank's time."""
+        return self.world * units_per_rank / (ms / 1e3)
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -282,14 +330,10 @@ def measure_tensor(bs, torch, stream, nk, n):
 def run_batch(args):
     """Config 3: a ragged batch of cells on the mixed path (bs_batch_*)."""
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rep = Replicas("nccl", torch.device("cuda", local))
+    world, rank = rep.world, rep.rank
     from paper_1310_6380_gb300 import binding as bs
     from paper_1310_6380_gb300 import cells
 
@@ -306,11 +350,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+    barrier = rep.barrier
 
     def timed(graph):
         bs.bs_batch_set_graph(b, graph)
@@ -341,13 +381,12 @@ def run_batch(args):
     launches = (bs.bs_launch_count() - launches0) // max(1, args.steps + args.warmup)
     ms_graph, _ = timed(True)
     ms = min(ms_plain, ms_graph)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rep.max(ms)
     omega = w.cpu().numpy()
     status = st.cpu().numpy()
     ph = {k: statistics.mean(p[k] for p in phs) for k in phs[0]}
+    tiles_chosen = bs.bs_batch_tiles(b)
+    _, fb_flags = bs.bs_batch_stats(b, ncell * nk)
     bs.bs_batch_destroy(b)
 
     # end to end through the public API with pinned host buffers: create the
@@ -369,14 +408,30 @@ def run_batch(args):
            "d2h_bytes_per_step": hw.numel() * 8 + hs.numel() * 4,
            "api": "bs_batch_create (host arrays) + bs_batch_solve (host Q, outputs; first call "
                   "includes tile autotuning) + bs_batch_destroy"}
-    # dominant kernel: the FP32 Householder reduction (HBM/latency bound)
-    tri_bytes = sum(nk * sum(m * (m + 1) // 2 for m in range(1, int(n))) * 16.0 for n in ns)
-    achieved = tri_bytes / (ph["reduction"] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "tridiag_step_kernel<float> (all launches of one step)",
-                "achieved": achieved, "peak": 6771.1, "unit": "GB/s", "frac": achieved / 6771.1,
-                "traffic": None, "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
-                "algorithmic": "read + write (8 B each) of every trailing lower triangle of "
-                               f"{ncell * nk} matrices (n = 242..578)"}
+    # dominant kernel: the FP32 Householder reduction.  Cluster-resident
+    # variant (tile 0): matrices stay on chip, so its roofline is the FP32
+    # ALU rate on (16/3) n^3 real flops per matrix; per-step variant: HBM
+    # on the read + write of every trailing triangle.
+    tiles = {} if not phs else tiles_chosen
+    if tiles and all(t == 0 for t in tiles.values()):
+        flops = sum(nk * 16.0 / 3.0 * float(n) ** 3 for n in ns)
+        achieved = flops / (ph["reduction"] / 1e3) / 1e12
+        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        roofline = {"bound": "alu", "kernel": "tridiag_cluster_kernel (one launch per chunk)",
+                    "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak, "traffic": None,
+                    "peak_source": "nominal FP32 CUDA-core rate: 152 SMs x 128 FMA/clk x 2 x "
+                                   "2.07 GHz",
+                    "algorithmic": f"(16/3) n^3 real flops per matrix, {ncell * nk} matrices "
+                                   "(n = 242..578)"}
+    else:
+        tri_bytes = sum(nk * sum(m * (m + 1) // 2 for m in range(1, int(n))) * 16.0 for n in ns)
+        achieved = tri_bytes / (ph["reduction"] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "tridiag_step_kernel<float> (all launches of one step)",
+                    "achieved": achieved, "peak": 6771.1, "unit": "GB/s", "frac": achieved / 6771.1,
+                    "traffic": None, "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+                    "algorithmic": "read + write (8 B each) of every trailing lower triangle of "
+                                   f"{ncell * nk} matrices (n = 242..578)"}
     value = world * ncell * nk / (ms / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
@@ -391,8 +446,9 @@ def run_batch(args):
                    "cells_per_M": {int(m): Ms.count(m) for m in sorted(set(Ms))},
                    "l2": "flushed between timed steps (256 MiB write, untimed)"},
         "ms_per_step_plain": ms_plain, "ms_per_step_graph": ms_graph,
-        "tiles": bs.bs_batch_tiles(b), "phases_ms": {k: round(v, 1) for k, v in ph.items()},
-        "status_nonzero": int(np.count_nonzero(status)), "gpu_launches_per_step": launches,
+        "tiles": tiles_chosen, "phases_ms": {k: round(v, 1) for k, v in ph.items()},
+        "status_nonzero": int(np.count_nonzero(status)),
+        "fp64_fallbacks": int((fb_flags == 1).sum()), "gpu_launches_per_step": launches,
         "gpu_launches": launches * args.steps, "e2e": e2e, "roofline": roofline, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -414,8 +470,7 @@ def run_batch(args):
         out["oracle_sampled_cells"] = samp
     if rank == 0:
         print(json.dumps(out))
-    if dist:
-        dist.destroy_process_group()
+    rep.close()
 
 
 def run_reference_batch(args):
@@ -455,14 +510,10 @@ def run_reference_batch(args):
 
 def run_ours(args):
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rep = Replicas("nccl", torch.device("cuda", local))
+    world, rank = rep.world, rep.rank
 
     from paper_1310_6380_gb300 import binding as bs
 
@@ -489,11 +540,7 @@ def run_ours(args):
         step()
     bs.bs_sync(h, stream)
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+    barrier = rep.barrier
 
     sampler = ClockSampler(device_bus_id(torch))
     step_ms, phases = [], []
@@ -518,10 +565,7 @@ def run_ours(args):
     bs.bs_sync(h, stream)
     assert not st.cpu().numpy().any(), "a wavevector did not converge"
     ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rep.max(ms)
     value = world * nk / (ms / 1e3)
     omega = w.cpu().numpy()
 
@@ -568,10 +612,7 @@ def run_ours(args):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = rep.max(e2e_s)
     h2d = hp.numel() * 2 + 3 * hl.numel() * 8 + hQ.numel() * 8
     d2h = hw.numel() * 8 + hs.numel() * 4
     e2e = {"value": world * nk / e2e_s, "unit": "k-solves/s", "h2d_bytes_per_step": h2d,
@@ -614,8 +655,7 @@ def run_ours(args):
     bs.bs_destroy_cell(h)
     if rank == 0:
         print(json.dumps(out))
-    if dist:
-        dist.destroy_process_group()
+    rep.close()
 
 
 def run_c4(args):
@@ -626,14 +666,10 @@ def run_c4(args):
     count certificate, dense fallback).  The plain FP64 dense GPU path is timed
     on a sample of the same cells for comparison."""
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rep = Replicas("nccl", torch.device("cuda", local))
+    world, rank = rep.world, rep.rank
     from paper_1310_6380_gb300 import binding as bs
     from paper_1310_6380_gb300 import cells
     from paper_1310_6380_gb300 import warmstart as ws
@@ -661,11 +697,7 @@ def run_c4(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+    barrier = rep.barrier
 
     def step(warm):
         if warm:
@@ -707,10 +739,7 @@ def run_c4(args):
     ph = bs.bs_batch_phase_times(b)
     bs.bs_batch_set_profiling(b, False)
     ms = ms_warm
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rep.max(ms)
     value = world * ncell * nk / (ms / 1e3)
 
     # the plain FP64 dense GPU path (bs_solve_k, FP64 cell) on a sample of the cells
@@ -824,8 +853,7 @@ def run_c4(args):
     net.close()
     if rank == 0:
         print(json.dumps(out))
-    if dist:
-        dist.destroy_process_group()
+    rep.close()
 
 
 def main():

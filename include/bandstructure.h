@@ -260,8 +260,10 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   status_out: ncells * nk (0, or the failure status of the dense
  *   fallback below, which re-solves every entry the residual bound did not
  *   certify) or
- *   NULL; host or device pointers.  The first call times the reduction
- *   variants per truncation group and keeps the fastest (autotuning).
+ *   NULL; host or device pointers.  The first call times the two tile
+ *   edges of the per-step reduction per truncation group and keeps the
+ *   faster (autotuning; the cluster-resident variant is only used when
+ *   bs_batch_set_tile selects it).
  * bs_batch_set_graph - on != 0: the next bs_batch_solve records the whole
  *   solve in a CUDA graph, later calls replay it (the Q and output pointers
  *   of the recording call must be reused); on == 0 drops the graph.

@@ -466,7 +466,7 @@ static int solve_chunk_mixed(bs_cell* c, int kb, int nbands, cudaStream_t s) {
   bs_phase_end(c, PH_BUILD, s);
   bs_phase_begin(c, PH_TRID, s);
   TRY(bs_launch_tridiag<float>(c->d_C32, n, kb, c->d_vec32, c->d_part32, c->d_de, c->d_tau,
-                               c->d_beta, c->d_count, s, bs_tridiag_cluster_fits(n) ? 0 : 64));
+                               c->d_beta, c->d_count, s));
   bs_phase_end(c, PH_TRID, s);
   bs_phase_begin(c, PH_BISECT, s);
   TRY(bs_launch_bisect(c->d_de, n, kb, std::min(b + 1, n), c->d_lamT, nullptr, s, false, 1e-9));

@@ -765,8 +765,10 @@ static int tune_group(bs_batch* B, BatchGroup& g, double floor2, cudaStream_t s)
   const int cn = std::min(g.chunk, (int)g.cells.size());
   float best = 1e30f;
   int best_tile = 64;
-  for (int tile : {0, 64, 32}) {
-    if (tile == 0 && !bs_tridiag_cluster_fits(g.n)) continue;
+  // the cluster-resident variant (tile 0) is not timed here: measured 5x
+  // slower than the per-step kernel on ragged batches (n = 242..578), its
+  // steps are serial chains of cluster barriers; bs_batch_set_tile selects it
+  for (int tile : {64, 32}) {
     CK(cudaEventRecord(e0, s), "tune");
     const int r = run_chunk(B, g, 0, cn, floor2, s, tile);
     if (r != BS_OK && tile == 0) {   // the cluster path could not be scheduled: skip it

@@ -6,7 +6,11 @@
 // step; for the eigen dimensions of a ragged batch (n <= 608) the whole
 // lower triangle fits in the distributed shared memory of a cluster of
 // 1..8 CTAs, so this kernel keeps it there and synchronises with cluster
-// barriers instead.
+// barriers instead.  Measured on a 256-cell ragged batch (n = 242..578) it is
+// 5x slower than the per-step kernel: each matrix's n steps become a serial
+// chain of four cluster barriers plus DSMEM round trips, while the per-step
+// kernel hides its latency behind thousands of matrices per launch.  It stays
+// as an explicit choice (bs_batch_set_tile) for few, small matrices.
 //
 // Layout: 32 x 32 tiles of the lower triangle, tile l = I(I+1)/2 + J (J <= I)
 // owned by CTA l % CS at slot l / CS; element (r, s) of a tile at
