@@ -71,7 +71,7 @@ __global__ void scatter_int_kernel(const int* __restrict__ src, const int* __res
 
 }  // namespace
 
-constexpr int kWorkers = 8;   // cells assembled concurrently per truncation group
+constexpr int kWorkers = 16;  // cells assembled concurrently per truncation group
 
 struct BatchGroup {
   int M, N, n, b;
@@ -520,6 +520,22 @@ extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, in
     cudaError_t e = cudaMemcpy(B->d_raw, raw.data(), rawn * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) r = bs_cuda_status(e, "bs_batch_create tables");
   }
+  // chunk budget: 60 % of the device memory free now, shared by the groups in
+  // proportion to the workspace each would need to hold all of its cells
+  // bytes per cell: C64 16 n^2, C32 8 n^2, C digit planes 24 n^2, C X
+  // products 288 n b, vectors and inverse-iteration factors ~ 120 n b
+  auto per_cell_bytes = [&](int M) {
+    const double n = 2.0 * (2 * M + 1) * (2 * M + 1);
+    return (double)nk * n * ((16.0 + 8.0 + 24.0) * n + 410.0 * bs_mixed_guard(nbands, (int)n));
+  };
+  double need = 0.0;
+  for (auto& kv : byM) need += kv.second.size() * per_cell_bytes(kv.first);
+  double budget = 12e9 * byM.size();
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = 0.6 * (double)fr;
+    else cudaGetLastError();
+  }
   for (auto& kv : byM) {
     if (r) break;
     BatchGroup g{};
@@ -560,11 +576,9 @@ extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, in
       B->cell_group[g.cells[i]] = (int)B->groups.size();
       B->cell_gi[g.cells[i]] = (int)i;
     }
-    // chunk: a few GB of workspace per group
-    // bytes per cell: C64 16 n^2, C32 8 n^2, C digit planes 24 n^2, C X
-    // products 288 n b, vectors and inverse-iteration factors ~ 120 n b
-    const double per_cell = (double)nk * g.n * ((16.0 + 8.0 + 24.0) * g.n + 410.0 * g.b);
-    g.chunk = (int)std::max(1.0, std::min((double)g.cells.size(), 12e9 / per_cell));
+    const double per_cell = per_cell_bytes(g.M);
+    const double share = budget * (g.cells.size() * per_cell) / std::max(need, 1.0);
+    g.chunk = (int)std::max(1.0, std::min((double)g.cells.size(), share / per_cell));
     g.tile = 64;
     g.tuned = false;
     r = alloc_group(g, nk, nbands);

@@ -957,7 +957,7 @@ __global__ void __launch_bounds__(32) lob_eig_kernel(LobWs w, int n, int kb, int
 }
 
 // ------------------------------------------------------------ update, residuals, next W
-__global__ void __launch_bounds__(UT) lob_update_kernel(LobWs w, int n, int kb, int b, int nb,
+__global__ void __launch_bounds__(UT, 2) lob_update_kernel(LobWs w, int n, int kb, int b, int nb,
                                                         int maxit, float tol, float tolb,
                                                         float floor2) {
   extern __shared__ float4 dyn_u[];
