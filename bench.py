@@ -52,6 +52,8 @@ def parse_args():
                     help="trained warm-start network (config 4)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="config 3: time the plain solve only (no CUDA graph record/replay)")
     ap.add_argument("--cpu-sample-k", type=int, default=6)
     return ap.parse_args()
 
@@ -379,8 +381,8 @@ def run_batch(args):
     ms_plain, phs = timed(False)
     clocks = sampler.stop()
     launches = (bs.bs_launch_count() - launches0) // max(1, args.steps + args.warmup)
-    ms_graph, _ = timed(True)
-    ms = min(ms_plain, ms_graph)
+    ms_graph = None if args.no_graph else timed(True)[0]
+    ms = ms_plain if ms_graph is None else min(ms_plain, ms_graph)
     ms = rep.max(ms)
     omega = w.cpu().numpy()
     status = st.cpu().numpy()

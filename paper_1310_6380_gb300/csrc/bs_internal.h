@@ -308,6 +308,8 @@ struct LobState {
   int seedfail;    // the starting block could not be made full rank
   float dshift;    // preconditioner shift (1e-3 of the mean diagonal of C)
   float rmax;      // largest relative FP32 residual of the wanted columns
+  float rbest;     // smallest rmax so far, and the iteration it was reached
+  int itbest;
   float theta[BS_LOB_MAX_BLOCK];
 };
 struct LobWs {

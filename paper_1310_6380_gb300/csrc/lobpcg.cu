@@ -418,6 +418,8 @@ __global__ void __launch_bounds__(UT) lob_seed_kernel(LobWs w, int n, int kb, in
     st.amask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
     st.dshift = dshift;
     st.rmax = 0.f;
+    st.rbest = FLT_MAX;
+    st.itbest = 0;
     st.seedfail = nk < b ? 1 : 0;
     for (int j = 0; j < LB; ++j) st.theta[j] = 0.f;
     w.st[k] = st;
@@ -1078,7 +1080,13 @@ __global__ void __launch_bounds__(UT, 2) lob_update_kernel(LobWs w, int n, int k
     st.rmax = rmax;
     st.nact = na;
     st.amask = mask;
-    const bool stop = wanted || st.it >= maxit || na == 0;
+    // stagnation (the FP32 rounding floor): no 10 % gain in 12 iterations
+    if (rmax < 0.9f * st.rbest) {
+      st.rbest = rmax;
+      st.itbest = st.it;
+    }
+    const bool stuck = st.it - st.itbest >= 12;
+    const bool stop = wanted || st.it >= maxit || na == 0 || stuck;
     flag = stop ? 1 : 0;
     if (stop) st.done = 1;
   }
