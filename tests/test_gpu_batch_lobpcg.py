@@ -58,7 +58,7 @@ def test_lobpcg_batch_matches_dense_batch_and_oracle(batch):
 
 
 def test_lobpcg_batch_graph_replay(batch):
-    cfgs, Qs, w, _, it, _, _, _, b = batch
+    cfgs, Qs, w, _, it, fb, _, _, b = batch
     Qd = torch.tensor(Qs, device="cuda")
     wd = torch.empty(w.shape, dtype=torch.float64, device="cuda")
     s = torch.cuda.current_stream()
@@ -69,9 +69,16 @@ def test_lobpcg_batch_graph_replay(batch):
             bs.bs_batch_solve(b, Qd, wd, None, s)
             s.synchronize()
             got = wd.cpu().numpy()
+            _, fbg = bs.bs_batch_stats(b, len(cfgs) * NK)
             # the replay runs the iteration limit with finished k idling, so
-            # every k stops at the same iterate as the plain solve
-            assert np.array_equal(got, w)
+            # every certified k stops at the same iterate as the plain solve;
+            # uncertified ones take the FP64 fallback in a replay (no host
+            # decision inside a graph) and the dense mixed rescue otherwise
+            same = ((fb == 0) & (fbg == 0)).reshape(w.shape[:2])
+            assert same.any()
+            assert np.array_equal(got[same], w[same])
+            for i, c in enumerate(cfgs):
+                assert omega_rel_err(got[i], w[i], omega_floor(c["cell"])).max() <= 2 * TOL, i
     finally:
         bs.bs_batch_set_graph(b, False)
 
