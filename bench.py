@@ -744,26 +744,25 @@ def run_c4(args):
     ms = rep.max(ms)
     value = world * ncell * nk / (ms / 1e3)
 
-    # the plain FP64 dense GPU path (bs_solve_k, FP64 cell) on a sample of the cells
-    samp = list(range(0, ncell, max(1, ncell // 32)))[:32]
-    fp64_ms = 0.0
-    for i in samp:
-        c, M = cl[i], Ms[i]
-        h = bs.bs_create_cell(c.h1, c.h2, np.ascontiguousarray(c.phase, np.uint16), c.lam.copy(),
-                              c.mu.copy(), c.rho.copy(), M, bs.BS_PREC_FP64)
-        wq = torch.empty((nk, nb), dtype=torch.float64, device="cuda")
-        bs.bs_assemble(h, stream)
-        bs.bs_solve_k(h, Qd[i], nb, wq, None, stream)      # warm-up (workspace)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bs.bs_assemble(h, stream)
-        bs.bs_solve_k(h, Qd[i], nb, wq, None, stream)
-        e1.record(stream)
-        e1.synchronize()
-        fp64_ms += e0.elapsed_time(e1)
-        bs.bs_destroy_cell(h)
+    # the plain FP64 dense GPU path (FP64 C(k), Householder reduction, Sturm
+    # multisection), batched over the cells like the other solvers, on a
+    # sample of the cells
+    samp = list(range(0, ncell, max(1, ncell // 128)))[:128]
+    bf = bs.bs_batch_create([cargs[i] for i in samp], nk, nb)
+    bs.bs_batch_set_solver(bf, bs.BS_SOLVER_FP64)
+    Qf = torch.tensor(Qh[samp], device="cuda")
+    wf = torch.empty((len(samp), nk, nb), dtype=torch.float64, device="cuda")
+    bs.bs_batch_solve(bf, Qf, wf, None, stream)
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bs.bs_batch_solve(bf, Qf, wf, None, stream)
+    e1.record(stream)
+    e1.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    bs.bs_batch_destroy(bf)
     fp64_rate = len(samp) * nk / (fp64_ms / 1e3)
 
     # end to end through the public API, host buffers: network inference on
@@ -826,8 +825,9 @@ def run_c4(args):
                        "iteration_ratio_vs_cold": float(it_warm.mean() / it_cold.mean()),
                        "speedup_vs_cold": ms_cold / ms_warm},
         "fp64_dense_gpu": {"value": fp64_rate, "unit": "k-solves/s",
-                           "sample": f"{len(samp)} cells x {nk} k, bs_assemble + bs_solve_k on "
-                                     "FP64 cells, one cell per call",
+                           "sample": f"{len(samp)} of the cells x {nk} k, one ragged batch "
+                                     "on BS_SOLVER_FP64 (assembly, FP64 C(k), FP64 Householder "
+                                     "reduction, Sturm multisection)",
                            "speedup_of_value": value / fp64_rate},
         "status_nonzero": int(np.count_nonzero(st_warm)),
         "phases_ms": {k: round(v, 1) for k, v in ph.items()},

@@ -282,7 +282,9 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   refinement.
  * bs_batch_destroy - free everything (NULL is a no-op).
  * bs_batch_set_solver - BS_SOLVER_DENSE (default: the FP32 Householder
- *   reduction above) or BS_SOLVER_LOBPCG (the block LOBPCG of
+ *   reduction above), BS_SOLVER_FP64 (the plain FP64 path of bs_solve_k on
+ *   FP64 C(k): Householder reduction and Sturm multisection, every (cell, k)
+ *   of a chunk at once) or BS_SOLVER_LOBPCG (the block LOBPCG of
  *   bs_solve_k_lobpcg, its FP64 Rayleigh-Ritz tail and residual bound;
  *   needs nbands <= BS_LOB_MAX_BANDS and nbands + 5 <= n).  Drops a
  *   recorded graph when the solver changes.
@@ -321,6 +323,7 @@ int bs_batch_phase_times(bs_batch* batch, double ms[4]);
 int bs_batch_destroy(bs_batch* batch);
 #define BS_SOLVER_DENSE  0
 #define BS_SOLVER_LOBPCG 1
+#define BS_SOLVER_FP64   2
 int bs_batch_set_solver(bs_batch* batch, int solver);
 int bs_batch_set_start(bs_batch* batch, const float* U, int Mp, int nvec);
 int bs_batch_stats(const bs_batch* batch, int* iters_out, int* fallback_out);

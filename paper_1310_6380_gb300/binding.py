@@ -104,7 +104,7 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_batch_set_start", "bs_batch_stats", "bs_batch_set_vectors", "bs_batch_vectors",
             "bs_batch_set_tile", "bs_cnn_create", "bs_cnn_destroy", "bs_cnn_num_params", "bs_cnn_set_params",
             "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step"]
-BS_SOLVER_DENSE, BS_SOLVER_LOBPCG = 0, 1
+BS_SOLVER_DENSE, BS_SOLVER_LOBPCG, BS_SOLVER_FP64 = 0, 1, 2
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
 
 

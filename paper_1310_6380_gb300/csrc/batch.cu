@@ -132,6 +132,8 @@ struct BatchGroup {
   double* fbw;                // dense-mixed rescue of uncertified LOBPCG entries
   int* fbst;
   int* fbrow;
+  zd* vec64;                  // FP64 solver: reduction vectors and partial sums
+  zd* part64;
 };
 
 struct bs_batch {
@@ -189,7 +191,7 @@ static void free_group(BatchGroup& g) {
                 g.phase, g.X32, g.X64, g.CX, g.G, g.H, g.W, g.theta, g.cxA, g.cxB, g.cxD, g.cxeA,
                 g.cxeB, g.w, g.st, g.d_rowidx, g.d_Gall, g.lS, g.lCS, g.lA, g.lpart, g.lZ, g.lY,
                 g.lX0, g.lst, g.lndone, g.liters, g.lLinv, g.lsig, g.lsc, g.liw, g.fbw,
-                g.fbst, g.fbrow};
+                g.fbst, g.fbrow, g.vec64, g.part64};
   for (void* p : ps) cudaFree(p);
 }
 
@@ -318,7 +320,10 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
                           (size_t)g.N * g.N * sizeof(zd), cudaMemcpyDeviceToDevice, ws) == cudaSuccess
               ? BS_OK
               : bs_cuda_status(cudaGetLastError(), "batch L_R stash");
-    if (!r)
+    if (!r && B->solver == BS_SOLVER_FP64)
+      r = bs_launch_builder(wk->d_Cm, n, B->d_Q + (size_t)ci * nk * 2, nk, wk->q1[0], wk->q1[1],
+                            wk->q2[0], wk->q2[1], g.C64 + (size_t)i * nk * nn, ws);
+    else if (!r)
       r = bs_launch_builder_mixed(wk->d_Cm, n, B->d_Q + (size_t)ci * nk * 2, nk, wk->q1[0],
                                   wk->q1[1], wk->q2[0], wk->q2[1], g.C64 + (size_t)i * nk * nn,
                                   g.C32 + (size_t)i * nk * nn, ws, lob);
@@ -339,7 +344,15 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
   const int K = cn * nk;
   const int* rows = g.d_rowidx + (size_t)c0 * nk;
   prof_mark(B, s);   // assembly ends, reduction begins
-  if (B->solver == BS_SOLVER_LOBPCG) {
+  if (B->solver == BS_SOLVER_FP64) {
+    // the plain FP64 dense path: Householder reduction and Sturm multisection
+    TRY_LAUNCH(bs_launch_tridiag<double>(g.C64, n, K, g.vec64, g.part64, g.de, g.tau, g.beta,
+                                         g.count, s));
+    prof_mark(B, s);
+    TRY_LAUNCH(bs_launch_bisect(g.de, n, K, B->nbands, g.w, g.st, s));
+    prof_mark(B, s);
+    prof_mark(B, s);
+  } else if (B->solver == BS_SOLVER_LOBPCG) {
     const int lb = g.lb;
     LobWs lw;
     lw.C32 = g.C32;
@@ -641,7 +654,7 @@ static void drop_graph(bs_batch* B) {
 }
 
 extern "C" int bs_batch_set_solver(bs_batch* B, int solver) {
-  if (!B || (solver != BS_SOLVER_DENSE && solver != BS_SOLVER_LOBPCG)) {
+  if (!B || (solver != BS_SOLVER_DENSE && solver != BS_SOLVER_LOBPCG && solver != BS_SOLVER_FP64)) {
     bs_set_error("bs_batch_set_solver: NULL batch or unknown solver");
     return BS_EINVAL;
   }
@@ -656,6 +669,14 @@ extern "C" int bs_batch_set_solver(bs_batch* B, int solver) {
         return BS_EINVAL;
       }
     for (auto& g : B->groups) TRY_LAUNCH(alloc_lob(g, B->nk, B->nbands));
+  }
+  if (solver == BS_SOLVER_FP64) {
+    for (auto& g : B->groups) {
+      const size_t K = (size_t)g.chunk * B->nk;
+      if (!g.vec64) TRY_LAUNCH(balloc(&g.vec64, K * bs_tridiag_vec_elems(g.n), "batch FP64 vectors"));
+      if (!g.part64)
+        TRY_LAUNCH(balloc(&g.part64, K * bs_tridiag_part_elems(g.n), "batch FP64 partials"));
+    }
   }
   if (solver != B->solver) drop_graph(B);
   B->solver = solver;
@@ -979,7 +1000,7 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
   const bool prof = B->prof;
   B->prof = false;   // not while tuning or recording a graph
   for (auto& g : B->groups) {
-    if (g.tuned || B->solver == BS_SOLVER_LOBPCG) continue;
+    if (g.tuned || B->solver != BS_SOLVER_DENSE) continue;
     double f2 = 1e300;
     for (int ci : g.cells) f2 = std::min(f2, floors[ci]);
     TRY_LAUNCH(tune_group(B, g, f2, s));

@@ -21,6 +21,31 @@
 
 namespace {
 
+// 2^e exactly (-1022 <= e <= 1023)
+__device__ __forceinline__ double pow2(int e) {
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// The digit-pair products D_st are exact integers below 2^24 in magnitude
+// (digits |d| <= 64, K <= 4096), and products of equal order u = s + t share
+// the weight 2^(-12 - 7u): sum them exactly as integers (at most S terms,
+// below 2^27), then combine the 2S - 1 orders in FP64.
+template <int S>
+struct OrderSums {
+  int re[2 * S - 1], im[2 * S - 1];
+  __device__ __forceinline__ OrderSums() {
+#pragma unroll
+    for (int u = 0; u < 2 * S - 1; ++u) re[u] = im[u] = 0;
+  }
+  __device__ __forceinline__ double value(const int* v) const {
+    double x = 0.0;
+#pragma unroll
+    for (int u = 0; u < 2 * S - 1; ++u) x = fma(pow2(-12 - 7 * u), (double)v[u], x);
+    return x;
+  }
+};
+
+
 __device__ __forceinline__ uint16_t bf16_bits(double t) {
   return __bfloat16_as_ushort(__float2bfloat16_rn((float)t));
 }
@@ -121,25 +146,27 @@ __global__ void pack_exp_kernel(const zd* __restrict__ E, int P, int D, int S, i
 }
 
 // Y[f][p][d] = sum_{s,t} 2^(eA+eB-12-7(s+t)) Dm[(t,d,c)][(f,s,p)]
+template <int S>
 __global__ void recombine_fields_kernel(const float* __restrict__ Dm, const int* __restrict__ eA,
-                                        const int* __restrict__ eB, int P, int D, int S,
+                                        const int* __restrict__ eB, int P, int D,
                                         zd* __restrict__ Y) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)3 * P * D) return;
   const int d = (int)(i % D), p = (int)((i / D) % P), f = (int)(i / ((size_t)P * D));
   const size_t M = (size_t)3 * S * P;
-  double re = 0.0, im = 0.0;
+  OrderSums<S> o;
+#pragma unroll
   for (int s = 0; s < S; ++s) {
     const size_t m = ((size_t)f * S + s) * P + p;
+#pragma unroll
     for (int t = 0; t < S; ++t) {
-      const double w = ldexp(1.0, -12 - 7 * (s + t));
       const size_t nr = ((size_t)t * D + d) * 2;
-      re = fma(w, (double)Dm[nr * M + m], re);
-      im = fma(w, (double)Dm[(nr + 1) * M + m], im);
+      o.re[s + t] += __float2int_rn(Dm[nr * M + m]);
+      o.im[s + t] += __float2int_rn(Dm[(nr + 1) * M + m]);
     }
   }
   const int ea = eA[f * P + p];
-  Y[i] = zmake(ldexp(re, ea + eB[2 * d]), ldexp(im, ea + eB[2 * d + 1]));
+  Y[i] = zmake(ldexp(o.value(o.re), ea + eB[2 * d]), ldexp(o.value(o.im), ea + eB[2 * d + 1]));
 }
 
 // ---- Rayleigh-Ritz product operands
@@ -194,8 +221,9 @@ __global__ void pack_xmat_kernel(const zd* __restrict__ X, int n, int b, int S, 
 }
 
 // Y[k][r + i n] = sum_{s,t} 2^(eA+eB-12-7(s+t)) (Dm[(t,i,0)][(s,r)] + i Dm[(t,i,1)][(s,r)])
+template <int S>
 __global__ void recombine_cx_kernel(const float* __restrict__ Dm, const int* __restrict__ eA,
-                                    const int* __restrict__ eB, int n, int b, int S,
+                                    const int* __restrict__ eB, int n, int b,
                                     zd* __restrict__ Y) {
   const int k = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,18 +231,19 @@ __global__ void recombine_cx_kernel(const float* __restrict__ Dm, const int* __r
   const int r = idx % n, i = idx / n;
   const size_t M = (size_t)S * n, Nn = (size_t)S * 2 * b;
   const float* dk = Dm + (size_t)k * M * Nn;
-  double re = 0.0, im = 0.0;
+  OrderSums<S> o;
+#pragma unroll
   for (int s = 0; s < S; ++s) {
     const size_t m = (size_t)s * n + r;
+#pragma unroll
     for (int t = 0; t < S; ++t) {
-      const double w = ldexp(1.0, -12 - 7 * (s + t));
       const size_t nr = ((size_t)t * b + i) * 2;
-      re = fma(w, (double)dk[nr * M + m], re);
-      im = fma(w, (double)dk[(nr + 1) * M + m], im);
+      o.re[s + t] += __float2int_rn(dk[nr * M + m]);
+      o.im[s + t] += __float2int_rn(dk[(nr + 1) * M + m]);
     }
   }
   const int ex = eA[(size_t)k * n + r] + eB[(size_t)k * b + i];
-  Y[(size_t)k * n * b + idx] = zmake(ldexp(re, ex), ldexp(im, ex));
+  Y[(size_t)k * n * b + idx] = zmake(ldexp(o.value(o.re), ex), ldexp(o.value(o.im), ex));
 }
 
 }  // namespace
@@ -230,8 +259,8 @@ int bs_launch_fields_tc(bs_cell* c, cudaStream_t s) {
   TRY_LAUNCH(bs_launch_slice_gemm(c->d_sliceA, c->d_sliceB, c->d_sliceD, M, N, Kp, 1,
                                   (long)M * Kp, (long)N * Kp, M, (long)M * N, c->d_info + 1, s));
   const size_t tot = (size_t)3 * P * D;
-  recombine_fields_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      c->d_sliceD, c->d_expA, c->d_expB, P, D, S, c->d_Y);
+  recombine_fields_kernel<BS_SLICES_ASM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      c->d_sliceD, c->d_expA, c->d_expB, P, D, c->d_Y);
   BS_CHECK_LAUNCH("recombine_fields_kernel");
   return BS_OK;
 }
@@ -254,7 +283,8 @@ int bs_launch_cx_tc(const zd* C, const zd* X, int n, int b, int kb, uint16_t* sA
   const int M = S * n, N = 2 * S * b;
   TRY_LAUNCH(bs_launch_slice_gemm(sA, sB, sD, M, N, Kp, kb, (long)M * Kp, (long)N * Kp, M,
                                   (long)M * N, err, s));
-  recombine_cx_kernel<<<dim3((n * b + 255) / 256, kb), 256, 0, s>>>(sD, eA, eB, n, b, S, Y);
+  recombine_cx_kernel<BS_SLICES_RR><<<dim3((n * b + 255) / 256, kb), 256, 0, s>>>(sD, eA, eB, n, b,
+                                                                               Y);
   BS_CHECK_LAUNCH("recombine_cx_kernel");
   return BS_OK;
 }
@@ -307,27 +337,29 @@ __global__ void pack_zrows_kernel(const zd* __restrict__ A, long sA, const doubl
   if (threadIdx.x == 0) ex[(size_t)z * N + r] = e;
 }
 
+template <int S>
 __global__ void recombine_z_kernel(const float* __restrict__ Dm, const int* __restrict__ eA,
-                                   const int* __restrict__ eB, int N, int S,
-                                   zd* __restrict__ C, long sC) {
+                                   const int* __restrict__ eB, int N, zd* __restrict__ C,
+                                   long sC) {
   const int z = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * N) return;
   const int r = idx % N, c = idx / N;
   const size_t M = (size_t)S * N, Nn = (size_t)S * 2 * N;
   const float* dz = Dm + (size_t)z * M * Nn;
-  double re = 0.0, im = 0.0;
+  OrderSums<S> o;
+#pragma unroll
   for (int s = 0; s < S; ++s) {
     const size_t m = (size_t)s * N + r;
+#pragma unroll
     for (int t = 0; t < S; ++t) {
-      const double w = ldexp(1.0, -12 - 7 * (s + t));
       const size_t nr = ((size_t)t * N + c) * 2;
-      re = fma(w, (double)dz[nr * M + m], re);
-      im = fma(w, (double)dz[(nr + 1) * M + m], im);
+      o.re[s + t] += __float2int_rn(dz[nr * M + m]);
+      o.im[s + t] += __float2int_rn(dz[(nr + 1) * M + m]);
     }
   }
   const int ex = eA[(size_t)z * N + r] + eB[(size_t)z * N + c];
-  C[(size_t)z * sC + idx] = zmake(ldexp(re, ex), ldexp(im, ex));
+  C[(size_t)z * sC + idx] = zmake(ldexp(o.value(o.re), ex), ldexp(o.value(o.im), ex));
 }
 
 }  // namespace
@@ -355,7 +387,8 @@ int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long
   const int M = S * N, Nn = 2 * S * N;
   TRY_LAUNCH(bs_launch_slice_gemm(wA, wB, wD, M, Nn, Kp, batch, (long)M * Kp, (long)Nn * Kp, M,
                                   (long)M * Nn, err, s));
-  recombine_z_kernel<<<dim3((N * N + 255) / 256, batch), 256, 0, s>>>(wD, eA, eB, N, S, C, sC);
+  recombine_z_kernel<BS_SLICES_ASM><<<dim3((N * N + 255) / 256, batch), 256, 0, s>>>(wD, eA, eB, N,
+                                                                                    C, sC);
   BS_CHECK_LAUNCH("recombine_z_kernel");
   return BS_OK;
 }

@@ -121,3 +121,33 @@ def test_batch_cluster_reduction_matches_per_step_kernel():
     for i, c in enumerate(cfgs):
         assert omega_rel_err(out[0][0][i], out[64][0][i], omega_floor(c["cell"])).max() <= 2 * TOL
     assert not out[0][1].any() and out[0][2].sum() <= 2
+
+
+def test_batch_fp64_solver_matches_single_cell_fp64():
+    """BS_SOLVER_FP64 runs the plain FP64 path of bs_solve_k for every
+    (cell, k) of a chunk at once: the same numbers as single-cell FP64 solves
+    and the oracle to 1e-8."""
+    cfgs = [cells.config3_cell(i) for i in range(30, 36)]
+    nk, nb = 4, 10
+    Qs = np.ascontiguousarray(np.stack([c["Q"][::7][:nk] for c in cfgs]))
+    b = bs.bs_batch_create([_args(c["cell"], c["M"]) for c in cfgs], nk, nb)
+    try:
+        bs.bs_batch_set_solver(b, bs.BS_SOLVER_FP64)
+        w = np.empty((len(cfgs), nk, nb))
+        st = np.empty((len(cfgs), nk), np.int32)
+        bs.bs_batch_solve(b, Qs, w, st)
+    finally:
+        bs.bs_batch_destroy(b)
+    assert not st.any()
+    for i, c in enumerate(cfgs):
+        h = bs.bs_create_cell(*(_args(c["cell"], c["M"])[:-1] + (bs.BS_PREC_FP64,)))
+        try:
+            bs.bs_assemble(h)
+            ref = np.empty((nk, nb))
+            bs.bs_solve_k(h, np.ascontiguousarray(Qs[i]), nb, ref)
+        finally:
+            bs.bs_destroy_cell(h)
+        assert omega_rel_err(w[i], ref, omega_floor(c["cell"])).max() <= 1e-12, i
+    oc = mv.OracleCell(cfgs[0]["cell"], cfgs[0]["M"])
+    ref = np.array([oc.omega(q, nb) for q in Qs[0]])
+    assert omega_rel_err(w[0], ref, omega_floor(cfgs[0]["cell"])).max() <= 1e-8
