@@ -32,7 +32,7 @@ namespace {
 constexpr int LB = BS_LOB_MAX_BLOCK;   // largest block size b
 constexpr int LM = 3 * LB;             // largest Rayleigh-Ritz dimension
 constexpr int UT = 256;                // threads of the per-k kernels
-constexpr int RC = 32;                 // rows per staging step of the tall Gram products
+constexpr int RC = 64;                 // rows per staging step of the tall Gram products
 constexpr int PPT = (LM * LM + UT - 1) / UT;
 constexpr int CWT = 128;               // rows of C W per CTA
 constexpr int CWJ = 64;                // columns of C per staged chunk of W
@@ -721,7 +721,8 @@ __global__ void __launch_bounds__(32) lob_eig_kernel(LobWs w, int n, int kb, int
       }
     }
     for (int it = 0; it < 48; ++it) {
-      if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
+      // 1e-6 relative: the FP64 Rayleigh-Ritz stage recomputes the values
+      if (hi - lo <= 1e-6f * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
       const float x1 = lo + (hi - lo) * (1.f / 3.f), x2 = lo + (hi - lo) * (2.f / 3.f);
       const int mine = sturm(h ? x2 : x1);
       // the two lanes of a pair run the same number of steps (identical
@@ -770,7 +771,7 @@ __global__ void __launch_bounds__(32) lob_eig_kernel(LobWs w, int n, int kb, int
     lu_set(s, 0, m - 1, lane, fabsf(cd) < tinyp ? (cd < 0.f ? -tinyp : tinyp) : cd);
     for (int i = 0; i < m; ++i) s.U[i * LB + lane] = hash_unit(i, 7919u + lane);
   }
-  for (int pass = 0; pass < 3; ++pass) {
+  for (int pass = 0; pass < 2; ++pass) {
     if (lane < q) {
       float* u = s.U + lane;
       for (int i = 0; i < m - 1; ++i) {
