@@ -80,6 +80,15 @@ struct BatchGroup {
   cudaStream_t wstream[kWorkers];
   cudaEvent_t wdone[kWorkers];
   cudaEvent_t fork;
+  // double buffering: chunk c is assembled into buffer set c & 1 while the
+  // main stream reduces chunk c - 1 from the other set
+  zd* C64b[2];
+  zf* C32b[2];
+  zf* lX0b[2];
+  zd* lLinvb[2];
+  cudaEvent_t adone[2][kWorkers];   // worker w finished assembling into set p
+  cudaEvent_t rdone[2];             // the reduction that read set p is done
+  bool used[2];
   int nworkers;
   int chunk;                  // cells per reduction batch
   int tile;                   // tridiagonal tile edge (autotuned)
@@ -187,10 +196,19 @@ static void free_group(BatchGroup& g) {
     if (g.wdone[w]) cudaEventDestroy(g.wdone[w]);
   }
   if (g.fork) cudaEventDestroy(g.fork);
-  void* ps[] = {g.C64, g.C32, g.vec32, g.part32, g.de, g.tau, g.beta, g.count, g.lamT, g.scr, g.Y,
+  for (int p = 0; p < 2; ++p) {
+    for (int w = 0; w < kWorkers; ++w)
+      if (g.adone[p][w]) cudaEventDestroy(g.adone[p][w]);
+    if (g.rdone[p]) cudaEventDestroy(g.rdone[p]);
+    cudaFree(g.C64b[p]);
+    cudaFree(g.C32b[p]);
+    cudaFree(g.lX0b[p]);
+    cudaFree(g.lLinvb[p]);
+  }
+  void* ps[] = {g.vec32, g.part32, g.de, g.tau, g.beta, g.count, g.lamT, g.scr, g.Y,
                 g.phase, g.X32, g.X64, g.CX, g.G, g.H, g.W, g.theta, g.cxA, g.cxB, g.cxD, g.cxeA,
                 g.cxeB, g.w, g.st, g.d_rowidx, g.d_Gall, g.lS, g.lCS, g.lA, g.lpart, g.lZ, g.lY,
-                g.lX0, g.lst, g.lndone, g.liters, g.lLinv, g.lsig, g.lsc, g.liw, g.fbw,
+                g.lst, g.lndone, g.liters, g.lsig, g.lsc, g.liw, g.fbw,
                 g.fbst, g.fbrow, g.vec64, g.part64};
   for (void* p : ps) cudaFree(p);
 }
@@ -209,7 +227,9 @@ static int alloc_lob(BatchGroup& g, int nk, int nbands) {
   if (!r) r = balloc(&g.lpart, K * bs_lob_part_elems(g.n), "batch LOBPCG partial Gram");
   if (!r) r = balloc(&g.lZ, K * coef, "batch LOBPCG Ritz coefficients");
   if (!r) r = balloc(&g.lY, K * coef, "batch LOBPCG P coefficients");
-  if (!r) r = balloc(&g.lX0, K * b * n, "batch LOBPCG starting block");
+  for (int p = 0; p < 2; ++p)
+    if (!r) r = balloc(&g.lX0b[p], K * b * n, "batch LOBPCG starting block");
+  g.lX0 = g.lX0b[0];
   if (!r) r = balloc(&g.lst, K, "batch LOBPCG state");
   if (!r) r = balloc(&g.lndone, 1, "batch LOBPCG counter");
   if (!r) r = balloc(&g.liters, K, "batch LOBPCG iterations");
@@ -229,8 +249,12 @@ static int alloc_group(BatchGroup& g, int nk, int nbands) {
   size_t ca = 0, cb = 0, cd = 0;
   bs_cx_tc_elems(n, b, (int)K, &ca, &cb, &cd);
   int r = BS_OK;
-  if (!r) r = balloc(&g.C64, K * n * n, "batch C64");
-  if (!r) r = balloc(&g.C32, K * n * n, "batch C32");
+  for (int p = 0; p < 2; ++p) {
+    if (!r) r = balloc(&g.C64b[p], K * n * n, "batch C64");
+    if (!r) r = balloc(&g.C32b[p], K * n * n, "batch C32");
+  }
+  g.C64 = g.C64b[0];
+  g.C32 = g.C32b[0];
   if (!r) r = balloc(&g.vec32, K * bs_tridiag_vec_elems(n), "batch vec");
   if (!r) r = balloc(&g.part32, K * bs_tridiag_part_elems(n), "batch partials");
   if (!r) r = balloc(&g.de, K * 2 * n, "batch tridiagonal");
@@ -300,14 +324,30 @@ static double floor2_of(const bs_batch* B, int ci, std::vector<double>& raw) {
 }
 
 // one chunk of a group: assemble its cells, build C(k), reduce + refine as one batch
-static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, cudaStream_t s,
-                     int tile) {
-  const int nk = B->nk, n = g.n, b = g.b;
-  const size_t nn = (size_t)n * n;
-  prof_mark(B, s);   // assembly begins
-  // fork: the workers start after everything already queued on s
+static void use_buffers(BatchGroup& g, int p) {
+  g.C64 = g.C64b[p];
+  g.C32 = g.C32b[p];
+  if (g.lX0b[p]) g.lX0 = g.lX0b[p];
+  if (g.lLinvb[p]) g.lLinv = g.lLinvb[p];
+}
+
+// the workers start after everything already queued on s
+static int fork_workers(BatchGroup& g, cudaStream_t s) {
   CK(cudaEventRecord(g.fork, s), "batch fork");
   for (int w = 0; w < g.nworkers; ++w) CK(cudaStreamWaitEvent(g.wstream[w], g.fork, 0), "batch fork");
+  g.used[0] = g.used[1] = false;
+  return BS_OK;
+}
+
+// enqueue the assembly and C(k) build of chunk (c0, cn) into buffer set p on
+// the worker streams (after the reduction that last read set p)
+static int assemble_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, int p) {
+  const int nk = B->nk, n = g.n;
+  const size_t nn = (size_t)n * n;
+  use_buffers(g, p);
+  if (g.used[p])
+    for (int w = 0; w < g.nworkers; ++w)
+      CK(cudaStreamWaitEvent(g.wstream[w], g.rdone[p], 0), "batch buffer reuse");
   for (int i = 0; i < cn; ++i) {
     const int ci = g.cells[c0 + i], wi = i % g.nworkers;
     bs_cell* wk = g.workers[wi];
@@ -336,11 +376,41 @@ static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, 
     }
     if (r) return r;
   }
-  // join
-  for (int w = 0; w < g.nworkers; ++w) {
-    CK(cudaEventRecord(g.wdone[w], g.wstream[w]), "batch join");
-    CK(cudaStreamWaitEvent(s, g.wdone[w], 0), "batch join");
-  }
+  for (int w = 0; w < g.nworkers; ++w)
+    CK(cudaEventRecord(g.adone[p][w], g.wstream[w]), "batch join");
+  return BS_OK;
+}
+
+static int reduce_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, int p, double floor2,
+                        cudaStream_t s, int tile);
+static int reduce_chunk_body(bs_batch* B, BatchGroup& g, int c0, int cn, int p, double floor2,
+                             cudaStream_t s, int tile);
+
+// one chunk start to finish (tile autotuning)
+static int run_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, double floor2, cudaStream_t s,
+                     int tile) {
+  TRY_LAUNCH(fork_workers(g, s));
+  TRY_LAUNCH(assemble_chunk(B, g, c0, cn, 0));
+  return reduce_chunk(B, g, c0, cn, 0, floor2, s, tile);
+}
+
+// reduce and refine chunk (c0, cn) from buffer set p on the main stream; marks
+// set p free for reuse once done
+static int reduce_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, int p, double floor2,
+                        cudaStream_t s, int tile) {
+  const int r = reduce_chunk_body(B, g, c0, cn, p, floor2, s, tile);
+  if (r) return r;
+  CK(cudaEventRecord(g.rdone[p], s), "batch buffer done");
+  g.used[p] = true;
+  return BS_OK;
+}
+
+static int reduce_chunk_body(bs_batch* B, BatchGroup& g, int c0, int cn, int p, double floor2,
+                             cudaStream_t s, int tile) {
+  const int nk = B->nk, n = g.n, b = g.b;
+  use_buffers(g, p);
+  prof_mark(B, s);   // exposed assembly begins (the main stream waits for the workers)
+  for (int w = 0; w < g.nworkers; ++w) CK(cudaStreamWaitEvent(s, g.adone[p][w], 0), "batch join");
   const int K = cn * nk;
   const int* rows = g.d_rowidx + (size_t)c0 * nk;
   prof_mark(B, s);   // assembly ends, reduction begins
@@ -539,7 +609,7 @@ extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, in
   // products 288 n b, vectors and inverse-iteration factors ~ 120 n b
   auto per_cell_bytes = [&](int M) {
     const double n = 2.0 * (2 * M + 1) * (2 * M + 1);
-    return (double)nk * n * ((16.0 + 8.0 + 24.0) * n + 410.0 * bs_mixed_guard(nbands, (int)n));
+    return (double)nk * n * ((2 * (16.0 + 8.0) + 24.0) * n + 410.0 * bs_mixed_guard(nbands, (int)n));
   };
   double need = 0.0;
   for (auto& kv : byM) need += kv.second.size() * per_cell_bytes(kv.first);
@@ -579,7 +649,12 @@ extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, in
     }
     if (!r) {
       cudaError_t e = cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
-      if (e != cudaSuccess) r = bs_cuda_status(e, "bs_batch_create fork");
+      for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+        e = cudaEventCreateWithFlags(&g.rdone[p], cudaEventDisableTiming);
+        for (int w = 0; w < g.nworkers && e == cudaSuccess; ++w)
+          e = cudaEventCreateWithFlags(&g.adone[p][w], cudaEventDisableTiming);
+      }
+      if (e != cudaSuccess) r = bs_cuda_status(e, "bs_batch_create events");
     }
     if (r) {
       B->groups.push_back(g);
@@ -732,7 +807,10 @@ extern "C" int bs_batch_set_vectors(bs_batch* B, int Mp) {
       return BS_EINVAL;
     }
   for (auto& g : B->groups)
-    if (!g.lLinv) TRY_LAUNCH(balloc(&g.lLinv, (size_t)g.chunk * g.N * g.N, "batch L_R stash"));
+    for (int q = 0; q < 2; ++q)
+      if (!g.lLinvb[q])
+        TRY_LAUNCH(balloc(&g.lLinvb[q], (size_t)g.chunk * g.N * g.N, "batch L_R stash"));
+  for (auto& g : B->groups) g.lLinv = g.lLinvb[0];
   const size_t len = 2 * (size_t)(2 * Mp + 1) * (2 * Mp + 1);
   TRY_LAUNCH(balloc(&B->d_vec, (size_t)B->ncells * B->nk * B->nbands * len, "batch vectors"));
   B->vecMp = Mp;
@@ -970,9 +1048,18 @@ static int solve_all(bs_batch* B, const std::vector<double>& floors, cudaStream_
   for (auto& g : B->groups) {
     double f2 = 1e300;
     for (int ci : g.cells) f2 = std::min(f2, floors[ci]);
-    for (int c0 = 0; c0 < (int)g.cells.size(); c0 += g.chunk) {
-      const int cn = std::min(g.chunk, (int)g.cells.size() - c0);
-      TRY_LAUNCH(run_chunk(B, g, c0, cn, f2, s, g.tile));
+    // chunk c + 1 is enqueued for assembly before chunk c is reduced, so the
+    // workers build it while the main stream reduces (also when the
+    // reduction waits on the host, as the LOBPCG progress checks do)
+    const int ncells = (int)g.cells.size();
+    TRY_LAUNCH(fork_workers(g, s));
+    TRY_LAUNCH(assemble_chunk(B, g, 0, std::min(g.chunk, ncells), 0));
+    for (int c = 0, c0 = 0; c0 < ncells; ++c, c0 += g.chunk) {
+      const int cn = std::min(g.chunk, ncells - c0);
+      if (c0 + g.chunk < ncells)
+        TRY_LAUNCH(assemble_chunk(B, g, c0 + g.chunk, std::min(g.chunk, ncells - c0 - g.chunk),
+                                  (c + 1) & 1));
+      TRY_LAUNCH(reduce_chunk(B, g, c0, cn, c & 1, f2, s, g.tile));
     }
   }
   return BS_OK;
