@@ -129,3 +129,25 @@ def test_lobpcg_batch_start_validation(batch):
     with pytest.raises(bs.BSError) as ei:
         bs.bs_batch_set_start(b, U, 1)
     assert ei.value.code == bs.BS_EINVAL
+
+
+def test_lobpcg_batch_single_cell_single_k():
+    """The smallest batch: one cell, one wavevector, on both solvers."""
+    c = cells.config3_cell(40)
+    Q = np.ascontiguousarray(c["Q"][7:8][None])
+    b = bs.bs_batch_create([_args(c["cell"], c["M"])], 1, NB)
+    try:
+        out = []
+        for solver in (bs.BS_SOLVER_DENSE, bs.BS_SOLVER_LOBPCG, bs.BS_SOLVER_FP64):
+            bs.bs_batch_set_solver(b, solver)
+            w = np.empty((1, 1, NB))
+            st = np.empty((1, 1), np.int32)
+            bs.bs_batch_solve(b, Q, w, st)
+            assert not st.any()
+            out.append(w)
+    finally:
+        bs.bs_batch_destroy(b)
+    oc = mv.OracleCell(c["cell"], c["M"])
+    ref = oc.omega(Q[0, 0], NB)
+    for w in out:
+        assert omega_rel_err(w[0, 0], ref, omega_floor(c["cell"])).max() <= TOL

@@ -156,3 +156,41 @@ def test_lobpcg_rejects_bad_arguments():
         assert ei.value.code == bs.BS_EINVAL
     finally:
         bs.bs_destroy_cell(h)
+
+
+def test_lobpcg_edge_cases():
+    """No wavevectors; a single band; the smallest cell (M = 1, n = 18)."""
+    cell = cells.voronoi_cell(8, 3, seed=3)
+    h = make(cell, 1)
+    try:
+        w0 = np.empty((0, 4))
+        bs.bs_solve_k_lobpcg(h, np.zeros((0, 2)), 4, w0)          # nk = 0: nothing to do
+        Q = QS[:4]
+        for nb in (1, 4, 13):                                    # nbands + 5 <= n = 18
+            w, st, it, fb, _ = lobpcg(h, Q, nb)
+            oc = mv.OracleCell(cell, 1)
+            ref = np.array([oc.omega(q, nb) for q in Q])
+            assert omega_rel_err(w, ref, omega_floor(cell)).max() <= TOL, nb
+            assert not st.any()
+        with pytest.raises(bs.BSError) as ei:                    # nbands + 5 > n
+            bs.bs_solve_k_lobpcg(h, Q, 14, np.empty((4, 14)))
+        assert ei.value.code == bs.BS_EINVAL
+    finally:
+        bs.bs_destroy_cell(h)
+
+
+@pytest.mark.slow
+def test_lobpcg_largest_truncation():
+    """M = 15 (n = 1922, the largest the library takes) on a 64 x 64 Voronoi cell."""
+    cell = cells.voronoi_cell(64, 12, seed=77)
+    M, nb = 15, 10
+    h = make(cell, M)
+    try:
+        Q = QS[1:3]
+        w, st, it, fb, _ = lobpcg(h, Q, nb)
+    finally:
+        bs.bs_destroy_cell(h)
+    assert not st.any()
+    oc = mv.OracleCell(cell, M)
+    ref = np.array([oc.omega(q, nb) for q in Q])
+    assert omega_rel_err(w, ref, omega_floor(cell)).max() <= TOL
