@@ -166,14 +166,14 @@ def test_lobpcg_edge_cases():
         w0 = np.empty((0, 4))
         bs.bs_solve_k_lobpcg(h, np.zeros((0, 2)), 4, w0)          # nk = 0: nothing to do
         Q = QS[:4]
-        for nb in (1, 4, 13):                                    # nbands + 5 <= n = 18
+        for nb in (1, 4, 12):                                    # 3b = 48 > n = 18
             w, st, it, fb, _ = lobpcg(h, Q, nb)
             oc = mv.OracleCell(cell, 1)
             ref = np.array([oc.omega(q, nb) for q in Q])
             assert omega_rel_err(w, ref, omega_floor(cell)).max() <= TOL, nb
             assert not st.any()
-        with pytest.raises(bs.BSError) as ei:                    # nbands + 5 > n
-            bs.bs_solve_k_lobpcg(h, Q, 14, np.empty((4, 14)))
+        with pytest.raises(bs.BSError) as ei:                    # above BS_LOB_MAX_BANDS
+            bs.bs_solve_k_lobpcg(h, Q, 13, np.empty((4, 13)))
         assert ei.value.code == bs.BS_EINVAL
     finally:
         bs.bs_destroy_cell(h)
