@@ -15,7 +15,8 @@ step by step, in the paper's notation, in float64 / complex128:
   * index maps I1, I2, I3 (alpha-major) ............. Sec. IV.A
   * H, Omega, Phi entries ........................... Eqs. (eh), (eo), (ep)
   * isotropic plane-strain compliance D_jkmn ........ Sec. IV, constitutive law
-  * centroid quadrature over subdomains ............. Sec. III (int F = sum F_i V_i)
+  * centroid quadrature over subdomains ............. Sec. III (int F = sum F_i V_i),
+    pixels of a phase map or the elements of a mesh (centroid, area, phase)
   * eigenproblem A U = lambda Omega U, A = H Phi^-1 H^*,
     omega = sqrt(lambda) ............................ Eq. (eigenvalueproblem)
 
@@ -39,7 +40,7 @@ import numpy as np
 import scipy.linalg as sla
 
 __all__ = [
-    "reciprocal_basis", "plane_wave_indices", "wavevectors", "quadrature",
+    "reciprocal_basis", "plane_wave_indices", "wavevectors", "quadrature", "subdomains",
     "compliance", "form_factors", "toeplitz", "integrals_literal", "OracleCell",
     "bands",
 ]
@@ -82,6 +83,18 @@ def quadrature(cell):
     x = H1.reshape(-1, 1) * cell.h1 + H2.reshape(-1, 1) * cell.h2
     V = abs(np.linalg.det(np.array([cell.h1, cell.h2])))
     return x, np.full(P * P, V / (P * P))
+
+
+def subdomains(cell):
+    """Centroids x_i (nel, 2), areas V_i and phase index of every subdomain
+    (Sec. III): the pixels of a pixel cell, or the elements of a mesh cell
+    (centroid given in fractional coordinates, x = s h1 + t h2)."""
+    if hasattr(cell, "centroid"):
+        c = np.asarray(cell.centroid, float)
+        x = c[:, :1] * np.asarray(cell.h1, float) + c[:, 1:] * np.asarray(cell.h2, float)
+        return x, np.asarray(cell.area, float), np.asarray(cell.phase).astype(np.int64)
+    x, w = quadrature(cell)
+    return x, w, cell.phase.reshape(-1).astype(np.int64)
 
 
 def compliance(lam, mu):
@@ -155,13 +168,12 @@ class OracleCell:
     """k-independent integrals of one cell, and the per-k pencil."""
 
     def __init__(self, cell, M, paper_conj=False):
-        if 2 * M + 1 > cell.P:
+        if not hasattr(cell, "centroid") and 2 * M + 1 > cell.P:
             raise ValueError("truncation needs 2M+1 <= P")
         self.cell, self.M, self.paper_conj = cell, M, paper_conj
         N = (2 * M + 1) ** 2
         self.N = N
-        x, w = quadrature(cell)
-        ph = cell.phase.reshape(-1).astype(np.int64)
+        x, w, ph = subdomains(cell)
         rho = cell.rho[ph]
         D = compliance(cell.lam, cell.mu)[ph]          # (npix, 2,2,2,2)
         fields = [np.ones_like(rho), rho]

@@ -23,6 +23,8 @@ __all__ = [
     "Cell", "square", "hexagonal", "homogeneous_cell", "circle_cell",
     "bilayer_cell", "voronoi_cell", "ellipse_cell", "steel_epoxy_hex_cell",
     "ibz_path", "config0", "config1", "config3_cell", "CONFIGS",
+    "MeshCell", "jittered_triangles", "mesh_circle_cell", "mesh_voronoi_cell", "pixel_mesh",
+    "steel_epoxy_hex_mesh",
 ]
 
 
@@ -184,6 +186,143 @@ def steel_epoxy_hex_cell(P=64):
     epoxy = (7.54e9 - 2 * 1.48e9, 1.48e9, 1142.0)
     return circle_cell(P, r=2.0e-3 / a, matrix=epoxy, inclusion=steel, lattice="hex",
                        a=a, name="steel_epoxy_hex")
+
+
+# ---------------------------------------------------------------- meshes
+@dataclass
+class MeshCell:
+    """A multi-phase 2-D unit cell given as a mesh (the paper's subdomains,
+    Sec. III): each element carries its centroid in fractional coordinates
+    (x = s h1 + t h2), its Cartesian area and a phase index."""
+
+    h1: np.ndarray
+    h2: np.ndarray
+    centroid: np.ndarray      # (nel, 2) fractional (s, t)
+    area: np.ndarray          # (nel,) Cartesian areas, summing to |det[h1; h2]|
+    phase: np.ndarray         # (nel,) uint16
+    lam: np.ndarray
+    mu: np.ndarray
+    rho: np.ndarray
+    name: str = "mesh"
+    lattice: str = "square"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nel(self) -> int:
+        return int(self.phase.shape[0])
+
+    @property
+    def nphase(self) -> int:
+        return int(self.lam.shape[0])
+
+    def translated(self, ds: float, dt: float) -> "MeshCell":
+        """The same mesh moved by (ds, dt) in fractional coordinates."""
+        return MeshCell(self.h1.copy(), self.h2.copy(), self.centroid + np.array([ds, dt]),
+                        self.area.copy(), self.phase.copy(), self.lam.copy(), self.mu.copy(),
+                        self.rho.copy(), self.name + f"+({ds},{dt})", self.lattice,
+                        dict(self.meta))
+
+    def with_props(self, lam=None, mu=None, rho=None) -> "MeshCell":
+        return MeshCell(self.h1.copy(), self.h2.copy(), self.centroid.copy(), self.area.copy(),
+                        self.phase.copy(),
+                        self.lam.copy() if lam is None else np.asarray(lam, np.float64),
+                        self.mu.copy() if mu is None else np.asarray(mu, np.float64),
+                        self.rho.copy() if rho is None else np.asarray(rho, np.float64),
+                        self.name, self.lattice, dict(self.meta))
+
+
+def jittered_triangles(n: int, jitter: float = 0.3, seed: int = 0):
+    """A periodic triangulation of the unit torus in fractional coordinates:
+    vertices ((i + dx)/n, (j + dy)/n) with dx, dy uniform in
+    [-jitter/2, jitter/2] (one draw per vertex, shared by every triangle that
+    uses it), each grid square split into two triangles along alternating
+    diagonals.  Returns the vertices (2 n^2, 3, 2) of every triangle, with
+    coordinates unwrapped so each triangle is contiguous.  jitter < 1/2 keeps
+    every triangle positively oriented."""
+    if not 0.0 <= jitter < 0.5:
+        raise ValueError("jitter must lie in [0, 1/2)")
+    rng = np.random.default_rng(seed)
+    d = (rng.random((n, n, 2)) - 0.5) * jitter
+
+    def v(i, j):
+        return (np.array([i, j], float) + d[i % n, j % n]) / n
+
+    tris = []
+    for i in range(n):
+        for j in range(n):
+            a, b, c, e = v(i, j), v(i + 1, j), v(i + 1, j + 1), v(i, j + 1)
+            if (i + j) % 2 == 0:
+                tris += [(a, b, c), (a, c, e)]
+            else:
+                tris += [(a, b, e), (b, c, e)]
+    return np.array(tris)
+
+
+def _mesh_from_triangles(tris, h1, h2):
+    """Centroids (fractional) and Cartesian areas of triangles (nel, 3, 2)."""
+    cen = tris.mean(axis=1)
+    e1, e2 = tris[:, 1] - tris[:, 0], tris[:, 2] - tris[:, 0]
+    frac_area = 0.5 * (e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+    if (frac_area <= 0).any():
+        raise ValueError("a triangle is not positively oriented")
+    V = abs(h1[0] * h2[1] - h1[1] * h2[0])
+    return cen, frac_area * V
+
+
+def mesh_circle_cell(n=22, r=0.3, matrix=(4.0, 1.5, 1.2), inclusion=(110.0, 80.0, 7.8),
+                     lattice="square", a=1.0, jitter=0.3, seed=0, name="mesh_circle"):
+    """A circular inclusion on a jittered triangle mesh: an element is in the
+    inclusion iff its centroid lies within r*a of the cell centre (minimum
+    image), the rule of circle_cell."""
+    h1, h2 = square(a) if lattice == "square" else hexagonal(a)
+    cen, area = _mesh_from_triangles(jittered_triangles(n, jitter, seed), h1, h2)
+    x = cen[:, :1] * h1 + cen[:, 1:] * h2
+    inside = _min_image_dist2(h1, h2, x, 0.5 * h1 + 0.5 * h2) <= (r * a) ** 2
+    lam, mu, rho = (np.array([matrix[i], inclusion[i]], float) for i in range(3))
+    return MeshCell(h1, h2, cen, area, inside.astype(np.uint16), lam, mu, rho, name, lattice,
+                    {"n": n, "jitter": jitter, "seed": seed})
+
+
+def mesh_voronoi_cell(n=24, nseeds=40, seed=5, lattice="square", a=1.0, jitter=0.3):
+    """Periodic Voronoi phases (the rule of voronoi_cell) on a jittered
+    triangle mesh; properties drawn per phase as there."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    h1, h2 = square(a) if lattice == "square" else hexagonal(a)
+    frac = rng.random((nseeds, 2))
+    lam, mu, rho = _draw_props(rng, nseeds)
+    cen, area = _mesh_from_triangles(jittered_triangles(n, jitter, seed + 1), h1, h2)
+    pts = frac[:, :1] * h1 + frac[:, 1:] * h2
+    images = np.concatenate([pts + i * h1 + j * h2 for i in (-1, 0, 1) for j in (-1, 0, 1)])
+    x = cen[:, :1] * h1 + cen[:, 1:] * h2
+    _, idx = cKDTree(images).query(x)
+    return MeshCell(h1, h2, cen, area, (idx % nseeds).astype(np.uint16), lam, mu, rho,
+                    "mesh_voronoi", lattice, {"n": n, "seed": seed, "nseeds": nseeds})
+
+
+def pixel_mesh(cell: Cell) -> MeshCell:
+    """A pixel cell as a mesh of square elements (centroid = pixel centre,
+    area = V / P^2): the same subdomains, so the same quadrature."""
+    P = cell.P
+    f = (np.arange(P) + 0.5) / P
+    S, T = np.meshgrid(f, f, indexing="ij")
+    V = abs(cell.h1[0] * cell.h2[1] - cell.h1[1] * cell.h2[0])
+    return MeshCell(cell.h1.copy(), cell.h2.copy(), np.stack([S.ravel(), T.ravel()], axis=1),
+                    np.full(P * P, V / (P * P)), cell.phase.reshape(-1).astype(np.uint16),
+                    cell.lam.copy(), cell.mu.copy(), cell.rho.copy(), cell.name + "_as_mesh",
+                    cell.lattice)
+
+
+def steel_epoxy_hex_mesh(n=22):
+    """The hexagonal steel/epoxy cell (Sec. "Example: hexagonal unit cell")
+    on a jittered triangle mesh of 2 n^2 elements (968 for n = 22, the size
+    of the paper's 964-triangle mesh)."""
+    a = 6.023e-3
+    steel = (264e9 - 2 * 81e9, 81e9, 7780.0)
+    epoxy = (7.54e9 - 2 * 1.48e9, 1.48e9, 1142.0)
+    return mesh_circle_cell(n, r=2.0e-3 / a, matrix=epoxy, inclusion=steel, lattice="hex", a=a,
+                            name="steel_epoxy_hex_mesh")
 
 
 # High-symmetry points in fractional coordinates Q (k = Q1 q1 + Q2 q2).
