@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4", "modes"])
     ap.add_argument("--cells", type=int, default=None,
                     help="cells of the config-3 batch (4096) or config-4 evaluation set (1024)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1310_6380_gb300", "data",
@@ -872,10 +872,246 @@ def run_c4(args):
     rep.close()
 
 
+# ---------------------------------------------------------------- mode shapes
+MODES_METRIC = "Bloch mode shapes/sec (stress coefficients + u, sigma on the cell's pixel grid)"
+
+
+def modes_workload():
+    from paper_1310_6380_gb300 import cells
+    cfg = cells.config1()
+    nvec, G = 12, cfg["cell"].P
+    N = (2 * cfg["M"] + 1) ** 2
+    config = {
+        "workload": f"modes: the 256x256 periodic Voronoi cell (1132 phases, seed 1310), "
+                    f"M={cfg['M']} ({N} plane waves), {len(cfg['Q'])} k on G-X-M-G, the lowest "
+                    f"{nvec} modes of each from bs_solve_k_lobpcg; one step = stress "
+                    f"coefficients S = -Phi^-1 H^* U (FP64) and the 5 fields u1, u2, S11, S22, "
+                    f"S12 of every mode on the {G}x{G} pixel-centre grid (complex64)",
+        "cells": 1, "k_points": len(cfg["Q"]), "modes_per_k": nvec, "grid": G,
+        "plane_waves": N, "l2": "outputs (2.8 GB) larger than L2; L2 flushed between steps",
+    }
+    return cfg, config, nvec, G
+
+
+def modes_oracle_sample(cfg, nvec, G, idx):
+    """The oracle on the sampled wavevectors idx: its own lowest nvec modes U
+    (eigh of the pencil, untimed), then the timed stress coefficients and the
+    five fields of every mode on the G x G grid.  Returns (U, S, F, seconds)."""
+    import scipy.linalg as sla
+    from oracle import mixed_variational as mv
+    from oracle import mode_shapes as ms
+    oc = mv.OracleCell(cfg["cell"], cfg["M"])
+    Us = []
+    for i in idx:
+        A, Om = oc.pencil(cfg["Q"][i])
+        Us.append(np.ascontiguousarray(sla.eigh(A, Om, subset_by_index=[0, nvec - 1])[1].T))
+    t0 = time.perf_counter()
+    oc = mv.OracleCell(cfg["cell"], cfg["M"])
+    S, F = [], []
+    N = oc.N
+    for j, i in enumerate(idx):
+        q = cfg["Q"][i]
+        Si = ms.stress_coefficients(oc, q, Us[j])
+        coef = np.concatenate([Us[j].reshape(2 * nvec, N), Si.reshape(3 * nvec, N)])
+        S.append(Si)
+        F.append(ms.field_on_grid(cfg["cell"], cfg["M"], q, coef, G))
+    return Us, S, F, time.perf_counter() - t0
+
+
+def run_modes(args):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    rep = Replicas("nccl", torch.device("cuda", local))
+    world, rank = rep.world, rep.rank
+    from paper_1310_6380_gb300 import binding as bs
+
+    cfg, config, nvec, G = modes_workload()
+    cell, M = cfg["cell"], cfg["M"]
+    Q = np.ascontiguousarray(cfg["Q"])
+    nk, N = len(Q), (2 * M + 1) ** 2
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    stream = torch.cuda.current_stream()
+    h = bs.bs_create_cell(cell.h1, cell.h2, dev(cell.phase.astype(np.uint16)), dev(cell.lam),
+                          dev(cell.mu), dev(cell.rho), M, bs.BS_PREC_MIXED)
+    bs.bs_assemble(h, stream)
+    Qd = dev(Q)
+    # the modes (input of the step, computed once): LOBPCG vectors
+    w = torch.empty((nk, nvec), dtype=torch.float64, device="cuda")
+    vec = torch.empty((nk, nvec, 2 * N), dtype=torch.complex64, device="cuda")
+    bs.bs_solve_k_lobpcg(h, Qd, nvec, w, vec_out=vec, stream=stream)
+    Ud = vec.to(torch.complex128).contiguous()
+    Sd = torch.empty((nk, nvec, 3 * N), dtype=torch.complex128, device="cuda")
+    Fu = torch.empty((nk, 2 * nvec, G, G), dtype=torch.complex64, device="cuda")
+    Fs = torch.empty((nk, 3 * nvec, G, G), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    Uv, Sv = Ud.view(nk, 2 * nvec, N), Sd.view(nk, 3 * nvec, N)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step():
+        ev[0].record(stream)
+        bs.bs_stress_coefficients(h, Qd, Ud, Sd, stream)
+        ev[1].record(stream)
+        bs.bs_mode_field(h, Qd, Uv, G, Fu, stream)
+        ev[2].record(stream)
+        bs.bs_mode_field(h, Qd, Sv, G, Fs, stream)
+        ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(device_bus_id(torch))
+    parts = {"stress": [], "field_u": [], "field_sigma": []}
+    step_ms = []
+    rep.barrier()
+    launches0 = bs.bs_launch_count()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+        ev[3].synchronize()
+        step_ms.append(ev[0].elapsed_time(ev[3]))
+        parts["stress"].append(ev[0].elapsed_time(ev[1]))
+        parts["field_u"].append(ev[1].elapsed_time(ev[2]))
+        parts["field_sigma"].append(ev[2].elapsed_time(ev[3]))
+    rep.barrier()
+    clocks = sampler.stop()
+    launches = bs.bs_launch_count() - launches0
+    ms = rep.max(statistics.mean(step_ms))
+    pm = {k: statistics.mean(v) for k, v in parts.items()}
+    units = nk * nvec
+    value = rep.value(units, ms)
+
+    # rooflines of the two kinds of work; the JSON roofline is the dominant one
+    W = 2 * M + 1
+    stress_flops = units * 3 * 8.0 * N * N          # three Gram solves, two triangular products
+    fld = nk * 5 * nvec
+    field_flops = fld * (8.0 * W * G * G + 8.0 * W * W * G)
+    field_bytes = fld * G * G * 8.0 + fld * N * 16.0
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    hbm_peak, _, note = measured_peaks()
+    t_field = (pm["field_u"] + pm["field_sigma"]) / 1e3
+    rl_stress = {"bound": "alu", "kernel": "bs_stress_coefficients (stress_rhs_kernel, "
+                                           "zgemm_kernel x4, stress_combine_kernel)",
+                 "achieved": stress_flops / (pm["stress"] / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                 "unit": "TFLOP/s", "traffic": None,
+                 "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                 "algorithmic": "3 Gram solves per mode, each two triangular products: 24 N^2 "
+                                "real flops per mode"}
+    rl_stress["frac"] = rl_stress["achieved"] / rl_stress["peak"]
+    rl_field = {"bound": "alu", "kernel": "field_kernel<24> (+ field_table_kernel)",
+                "achieved": field_flops / t_field / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "traffic": None,
+                "peak_source": "nominal FP32 CUDA-core rate: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                "algorithmic": "8 W G^2 + 8 W^2 G real flops per field (W = 2M+1 = 21, G = 256); "
+                               f"stores {field_bytes / 1e9:.2f} GB per step",
+                "hbm_gbs": field_bytes / t_field / 1e9, "hbm_frac": field_bytes / t_field / 1e9
+                / hbm_peak, "hbm_peak_source": "copy bandwidth, " + note}
+    rl_field["frac"] = rl_field["achieved"] / rl_field["peak"]
+    roofline = rl_stress if pm["stress"] >= pm["field_u"] + pm["field_sigma"] else rl_field
+
+    # end to end: host modes in, host stress and fields out (pinned)
+    hQ = torch.from_numpy(Q).pin_memory()
+    hU = Ud.cpu().pin_memory()
+    hS = torch.empty_like(Sd, device="cpu").pin_memory()
+    hFu = torch.empty(tuple(Fu.shape), dtype=torch.complex64).pin_memory()
+    hFs = torch.empty(tuple(Fs.shape), dtype=torch.complex64).pin_memory()
+
+    def e2e_step():
+        bs.bs_stress_coefficients(h, hQ, hU, hS, stream)
+        bs.bs_mode_field(h, hQ, hU.view(nk, 2 * nvec, N), G, hFu, stream)
+        bs.bs_mode_field(h, hQ, hS.view(nk, 3 * nvec, N), G, hFs, stream)
+
+    e2e_step()
+    rep.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = rep.max((time.perf_counter() - t0) / args.steps)
+    e2e = {"value": world * units / e2e_s, "unit": "modes/s",
+           "h2d_bytes_per_step": hQ.numel() * 8 + hU.numel() * 16 + hS.numel() * 16,
+           "d2h_bytes_per_step": hS.numel() * 16 + (hFu.numel() + hFs.numel()) * 8,
+           "api": "bs_stress_coefficients (host U in, host S out) + bs_mode_field x2 (host "
+                  "coefficients in, host fields out)"}
+
+    out = {
+        "metric": MODES_METRIC, "value": value, "unit": "modes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 stress solves, f32 field contractions (complex64 fields)",
+        "data": "synthetic", "config": config, "e2e": e2e, "gpu_launches": launches,
+        "gpu_launches_per_step": launches // max(1, args.steps), "roofline": roofline,
+        "rooflines": {"stress": rl_stress, "fields": rl_field},
+        "parts_ms": {k: round(v, 3) for k, v in pm.items()}, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on two wavevectors with its own modes; the library run on
+        # the same modes for the parity figures
+        idx = [nk // 9, nk // 3]
+        Us, S_ref, F_ref, secs = modes_oracle_sample(cfg, nvec, G, idx)
+        U2 = np.ascontiguousarray(np.stack(Us))
+        S2 = np.empty((len(idx), nvec, 3 * N), np.complex128)
+        bs.bs_stress_coefficients(h, Q[idx], U2, S2)
+        coef2 = np.ascontiguousarray(np.concatenate(
+            [U2.reshape(len(idx), 2 * nvec, N), S2.reshape(len(idx), 3 * nvec, N)], axis=1))
+        F2 = np.empty((len(idx), 5 * nvec, G, G), np.complex64)
+        bs.bs_mode_field(h, Q[idx], coef2, G, F2)
+        err_s = max(float(np.abs(S2[j] - S_ref[j]).max() / np.abs(S_ref[j]).max())
+                    for j in range(len(idx)))
+        err_f = 0.0
+        for j in range(len(idx)):
+            coef = np.concatenate([Us[j].reshape(2 * nvec, N), S_ref[j].reshape(3 * nvec, N)])
+            bound = (2 * W + 4) * 2.0 ** -24 * np.abs(coef).sum(axis=1)
+            err_f = max(err_f, float((np.abs(F2[j] - F_ref[j]).max(axis=(1, 2)) / bound).max()))
+        out["cpu_baseline"] = {"value": len(idx) * nvec / secs, "unit": "modes/s",
+                               "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                               "sample": f"k {idx} of {nk}, the oracle's own lowest {nvec} modes "
+                                         f"each: oracle cell set-up, stress and the 5 fields on "
+                                         f"the grid ({secs:.1f} s)"}
+        out["max_rel_err_stress_vs_oracle"] = err_s
+        out["max_field_err_over_bound"] = err_f
+    bs.bs_destroy_cell(h)
+    if rank == 0:
+        print(json.dumps(out))
+    rep.close()
+
+
+def run_reference_modes(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    cfg, config, nvec, G = modes_workload()
+    nk = len(cfg["Q"])
+    times = []
+    for i in range(args.warmup + args.steps):
+        secs = modes_oracle_sample(cfg, nvec, G, [(i * 7) % nk])[3]
+        if i >= args.warmup:
+            times.append(secs)
+    value = nvec / statistics.mean(times)
+    desc = (f"each step: oracle cell set-up, stress and the 5 fields of the oracle's own lowest "
+            f"{nvec} modes at one k")
+    print(json.dumps({
+        "impl": "reference", "metric": MODES_METRIC, "value": value, "unit": "modes/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": "modes/s", "cores": len(os.sched_getaffinity(0)),
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "modes/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
-        run_reference(args)
+        if args.config == "modes":
+            run_reference_modes(args)
+        else:
+            run_reference(args)
+    elif args.config == "modes":
+        run_modes(args)
     elif args.config == "c3":
         args.cells = args.cells or 4096
         run_batch(args)
