@@ -100,6 +100,50 @@ typedef struct bs_cell_desc {
 int bs_create_cell(const bs_cell_desc* desc, bs_cell** out);
 
 /*
+ * bs_mesh_desc - a unit cell given as a mesh of subdomains (the paper's
+ * triangle meshes, Sec. III and the hexagonal example of Sec. V), each
+ * integrated by the centroid rule int F = sum_e F(c_e) A_e.
+ *   h1, h2    : as bs_cell_desc.
+ *   nel       : elements; (2M+1)^2 <= nel <= 2^26.
+ *   centroid  : nel x 2 doubles, fractional centroid (s, t) of each
+ *               element, c_e = s h1 + t h2 (any periodic image); host or
+ *               device.
+ *   area      : nel doubles, Cartesian areas (> 0); host or device.
+ *   phase     : nel uint16 phase indices (< nphase); host or device.
+ *   nphase, lam, mu, rho, M, precision : as bs_cell_desc.
+ * The caller keeps ownership of every array.
+ */
+typedef struct bs_mesh_desc {
+    double h1[2];
+    double h2[2];
+    int32_t nel;
+    const double* centroid;
+    const double* area;
+    const uint16_t* phase;
+    int32_t nphase;
+    const double* lam;
+    const double* mu;
+    const double* rho;
+    int32_t M;
+    int32_t precision;
+} bs_mesh_desc;
+
+/*
+ * bs_create_cell_mesh - bs_create_cell for a mesh.  The form factors are
+ * the centroid sums of Eqs. (eo), (ep) over the elements, and H of Eq. (eh)
+ * keeps its integral I1 = int conj(f_a) f_b (the plane waves are orthogonal
+ * under the pixel rule, not under a general mesh), so C(k) uses L_R^-1 I1
+ * where the pixel path uses V L_R^-1.  Every other call takes the cell as
+ * it takes a pixel cell (bs_assemble, bs_solve_k, bs_bands,
+ * bs_solve_k_lobpcg, bs_stress_coefficients, bs_mode_field); the ragged
+ * batch (bs_batch_*) takes pixel cells only.  Errors: BS_EINVAL (any
+ * constraint above), BS_ENOMEM, BS_ECUDA; a mesh too coarse for M makes a
+ * Gram matrix singular, reported as BS_ENOTPD after bs_assemble.
+ * Synchronous.
+ */
+int bs_create_cell_mesh(const bs_mesh_desc* desc, bs_cell** out);
+
+/*
  * bs_assemble - everything that does not depend on k, on `stream`:
  *   material fields 1/(lam+mu), 1/mu, rho per pixel (Sec. IV, the
  *   compliance D_jkmn), their form factors ghat(d) = sum_i g_i V_i
@@ -377,6 +421,45 @@ int bs_cnn_train_step(bs_cnn* net, const uint16_t* phase, const double* table, c
 
 /* bs_cell_dims - N (plane waves) and n = 2N (eigen dimension). */
 int bs_cell_dims(const bs_cell* cell, int* N, int* n);
+
+/*
+ * bs_stress_coefficients - stress coefficients of Bloch modes (Sec. IV, the
+ * second block row of Eq. (equationshomogeneousMatrix): Phi S + H^* U = 0,
+ * so S = -Phi^-1 H^* U, as stated after Eq. (eigenvalueproblem)).
+ *   Q     : nk*2 doubles (Q1, Q2), host or device.
+ *   U     : nk x nvec x 2N complex128 (interleaved re, im) displacement
+ *           coefficients, index I*N + a with component I in {u1, u2} and
+ *           plane wave a in the alpha-major order of bs_cell_desc's M (the
+ *           layout of bs_solve_k_lobpcg's vectors); host or device.
+ *   S_out : nk x nvec x 3N complex128, index J*N + a with J in
+ *           {S11, S22, S12}; host or device.
+ * FP64 throughout, with the k-independent Gram factors of bs_assemble (any
+ * precision); U need not be an eigenvector (the map is linear).  Requires
+ * bs_assemble (BS_ESTATE otherwise); 1 <= nvec <= 16384.  Asynchronous when
+ * U and S_out are both device pointers; nk = 0 does nothing.
+ */
+int bs_stress_coefficients(bs_cell* cell, const double* Q, int nk, int nvec,
+                           const double* U, double* S_out, void* stream);
+
+/*
+ * bs_mode_field - fields of plane-wave expansions (Eq. (approximation2d)) on
+ * a G x G grid of the unit cell: for every wavevector k and field f,
+ *   out[k][f][p][q] = sum_a coef[k][f][a] exp(i K_a . x_pq),
+ *   K_a = (Q1 + alpha_a) q^1 + (Q2 + beta_a) q^2  (Eq. (1)),
+ *   x_pq = ((p + 1/2)/G) h1 + ((q + 1/2)/G) h2,  0 <= p, q < G
+ * (the pixel centres when G = P; p runs along h1).  Displacement modes are
+ * nfield = 2*nvec fields of U (u1, u2 of each mode), stress modes 3*nvec
+ * fields of S from bs_stress_coefficients.
+ *   Q     : nk*2 doubles, host or device.
+ *   coef  : nk x nfield x N complex128 (interleaved), host or device.
+ *   out   : nk x nfield x G x G complex64 (interleaved), host or device.
+ * The phases are reduced exactly and evaluated in FP64, the two separable
+ * contractions in FP32: |error| <= (2(2M+1) + 4) 2^-24 sum_a |coef_a| per
+ * point.  1 <= G <= 8192, nfield >= 1.  Asynchronous when coef and out are
+ * both device pointers; nk = 0 does nothing.
+ */
+int bs_mode_field(bs_cell* cell, const double* Q, int nk, int nfield,
+                  const double* coef, int G, float* out, void* stream);
 
 /*
  * bs_set_profiling - when `on` is non-zero, bs_assemble and bs_solve_k

@@ -38,6 +38,13 @@ class bs_cell_desc(ctypes.Structure):
                 ("M", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
+class bs_mesh_desc(ctypes.Structure):
+    _fields_ = [("h1", ctypes.c_double * 2), ("h2", ctypes.c_double * 2), ("nel", ctypes.c_int32),
+                ("centroid", ctypes.c_void_p), ("area", ctypes.c_void_p), ("phase", ctypes.c_void_p),
+                ("nphase", ctypes.c_int32), ("lam", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("rho", ctypes.c_void_p), ("M", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libbs.so is not built ({LIB_PATH}); run "
@@ -46,6 +53,7 @@ def _load():
     vp, i32, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
     sig = {
         "bs_create_cell": [ctypes.POINTER(bs_cell_desc), ctypes.POINTER(vp)],
+        "bs_create_cell_mesh": [ctypes.POINTER(bs_mesh_desc), ctypes.POINTER(vp)],
         "bs_assemble": [vp, vp],
         "bs_solve_k": [vp, dp, i32, i32, dp, dp, vp],
         "bs_bands": [vp, i32, i32, i32, dp, dp, vp],
@@ -74,6 +82,8 @@ def _load():
         "bs_batch_set_vectors": [vp, i32],
         "bs_batch_vectors": [vp, dp],
         "bs_batch_set_tile": [vp, i32],
+        "bs_stress_coefficients": [vp, dp, i32, i32, dp, dp, vp],
+        "bs_mode_field": [vp, dp, i32, i32, dp, i32, dp, vp],
         "bs_cnn_create": [i32, i32, i32, i32, ctypes.POINTER(vp)],
         "bs_cnn_destroy": [vp],
         "bs_cnn_num_params": [vp, ctypes.POINTER(ctypes.c_longlong)],
@@ -103,7 +113,8 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_batch_phase_times", "bs_solve_k_lobpcg", "bs_batch_set_solver",
             "bs_batch_set_start", "bs_batch_stats", "bs_batch_set_vectors", "bs_batch_vectors",
             "bs_batch_set_tile", "bs_cnn_create", "bs_cnn_destroy", "bs_cnn_num_params", "bs_cnn_set_params",
-            "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step"]
+            "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step", "bs_stress_coefficients",
+            "bs_mode_field", "bs_create_cell_mesh"]
 BS_SOLVER_DENSE, BS_SOLVER_LOBPCG, BS_SOLVER_FP64 = 0, 1, 2
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
 
@@ -129,7 +140,7 @@ def _ptr(x, dtype):
         import torch
         tdt = {np.float64: torch.float64, np.uint16: torch.uint16, np.int32: torch.int32,
                np.float32: torch.float32, np.complex64: torch.complex64,
-               np.int64: torch.int64}[dtype]
+               np.complex128: torch.complex128, np.int64: torch.int64}[dtype]
         if x.dtype != tdt or not x.is_contiguous():
             raise TypeError(f"expected a contiguous {tdt} tensor")
         return x.data_ptr()
@@ -159,6 +170,23 @@ def bs_create_cell(h1, h2, phase, lam, mu, rho, M: int, precision: int = BS_PREC
     return out
 
 
+def bs_create_cell_mesh(h1, h2, centroid, area, phase, lam, mu, rho, M: int,
+                        precision: int = BS_PREC_FP64):
+    """Handle of a new mesh cell (see bs_mesh_desc in include/bandstructure.h):
+    centroid (nel, 2) fractional, area (nel,), phase (nel,) uint16."""
+    d = bs_mesh_desc()
+    d.h1[0], d.h1[1] = float(h1[0]), float(h1[1])
+    d.h2[0], d.h2[1] = float(h2[0]), float(h2[1])
+    d.nel, d.M, d.precision = int(phase.shape[0]), int(M), int(precision)
+    d.nphase = int(lam.shape[0])
+    d.centroid, d.area = _ptr(centroid, np.float64), _ptr(area, np.float64)
+    d.phase = _ptr(phase, np.uint16)
+    d.lam, d.mu, d.rho = _ptr(lam, np.float64), _ptr(mu, np.float64), _ptr(rho, np.float64)
+    out = ctypes.c_void_p()
+    _check(_lib.bs_create_cell_mesh(ctypes.byref(d), ctypes.byref(out)))
+    return out
+
+
 def bs_assemble(cell, stream=None):
     _check(_lib.bs_assemble(cell, _stream(stream)))
 
@@ -182,6 +210,24 @@ def bs_solve_k_lobpcg(cell, Q, nbands: int, omega_out, X0=None, status_out=None,
                                   _ptr(iters_out, np.int32), _ptr(fallback_out, np.int32),
                                   _ptr(vec_out, np.complex64), _stream(stream)))
     return omega_out
+
+
+def bs_stress_coefficients(cell, Q, U, S_out, stream=None):
+    """U: (nk, nvec, 2N) complex128 displacement coefficients; S_out: (nk, nvec, 3N)
+    complex128 (S11, S22, S12 blocks)."""
+    nk, nvec = int(U.shape[0]), int(U.shape[1])
+    _check(_lib.bs_stress_coefficients(cell, _ptr(Q, np.float64), nk, nvec,
+                                       _ptr(U, np.complex128), _ptr(S_out, np.complex128),
+                                       _stream(stream)))
+    return S_out
+
+
+def bs_mode_field(cell, Q, coef, G: int, out, stream=None):
+    """coef: (nk, nfield, N) complex128; out: (nk, nfield, G, G) complex64."""
+    nk, nfield = int(coef.shape[0]), int(coef.shape[1])
+    _check(_lib.bs_mode_field(cell, _ptr(Q, np.float64), nk, nfield, _ptr(coef, np.complex128),
+                              int(G), _ptr(out, np.complex64), _stream(stream)))
+    return out
 
 
 def bs_bands(cell, path: int, nk: int, nbands: int, Q_out, omega_out, stream=None):

@@ -236,6 +236,97 @@ static int k_batch_cap(const bs_cell* c) {
 static double omega_floor2(const bs_cell* c);
 
 // ------------------------------------------------------------------ create
+// Device storage of a validated cell (pixel map when cen == nullptr, else a
+// mesh of nel elements with fractional centroids cen and areas area).
+static int create_common(const double h1[2], const double h2[2], double det, int P, int nel, int M,
+                         int np, int precision, const std::vector<double>& raw,
+                         const std::vector<uint16_t>& ph, const std::vector<double>* cen,
+                         const std::vector<double>* area, bs_cell** out) {
+  bs_cell* c = new bs_cell;
+  memset(c, 0, sizeof(*c));
+  c->P = P;
+  c->mesh = cen != nullptr;
+  c->nel = nel;
+  c->M = M;
+  c->N = (2 * M + 1) * (2 * M + 1);
+  c->n = 2 * c->N;
+  c->D = 4 * M + 1;
+  c->nphase = np;
+  c->precision = precision;
+  for (int i = 0; i < 2; ++i) {
+    c->h1[i] = h1[i];
+    c->h2[i] = h2[i];
+  }
+  c->V = fabs(det);
+  // reciprocal basis of Eq. (1) in 2-D: q^1 = 2 pi (h2y, -h2x)/det, q^2 = 2 pi (-h1y, h1x)/det
+  c->q1[0] = 2.0 * M_PI * h2[1] / det;
+  c->q1[1] = -2.0 * M_PI * h2[0] / det;
+  c->q2[0] = -2.0 * M_PI * h1[1] / det;
+  c->q2[1] = 2.0 * M_PI * h1[0] / det;
+
+  const size_t NN = (size_t)c->N * c->N, nn = (size_t)c->n * c->n;
+  int r = BS_OK;
+  if (!r) r = dalloc(&c->d_phase, ph.size(), "phase");
+  if (!r) r = dalloc(&c->d_table, 6 * (size_t)np, "table");
+  if (!r) r = dalloc(&c->d_E, (size_t)c->D * P, "E");
+  if (!r) r = dalloc(&c->d_Y, 3 * (size_t)P * c->D, "Y");
+  if (!r) r = dalloc(&c->d_ghat, (c->mesh ? 4 : 3) * (size_t)c->D * c->D, "ghat");
+  if (!r && c->mesh) r = dalloc(&c->d_cen, 2 * (size_t)nel, "mesh centroids");
+  if (!r && c->mesh) r = dalloc(&c->d_area, (size_t)nel, "mesh areas");
+  if (!r && c->mesh) r = dalloc(&c->d_I1, NN, "mesh Gram matrix of the plane waves");
+  if (!r && c->mesh) r = dalloc(&c->d_mpart, bs_mesh_partial_elems(M, nel), "mesh partials");
+  if (!r) r = dalloc(&c->d_T, 3 * NN, "T");
+  if (!r) r = dalloc(&c->d_Linv, 3 * NN, "Linv");
+  if (!r) r = dalloc(&c->d_G, 2 * (size_t)c->N, "G");
+  if (!r) r = dalloc(&c->d_F, 6 * NN, "F");
+  if (!r) r = dalloc(&c->d_Pp, 12 * NN, "P");
+  if (!r) r = dalloc(&c->d_Cm, 6 * nn, "Cm");
+  if (!r) r = dalloc(&c->d_info, 4, "info");
+  size_t sa = 0, sb = 0, sd = 0;
+  bs_fields_tc_elems(P, c->D, &sa, &sb, &sd);
+  if (!r) r = dalloc(&c->d_sliceA, sa, "field digit planes");
+  if (!r) r = dalloc(&c->d_sliceB, sb, "exponential digit planes");
+  if (!r) r = dalloc(&c->d_sliceD, sd, "digit-pair products");
+  if (!r) r = dalloc(&c->d_expA, 3 * (size_t)P, "field exponents");
+  if (!r) r = dalloc(&c->d_expB, 2 * (size_t)c->D, "table exponents");
+  size_t ma = 0, mb = 0, md = 0;
+  bs_zgemm_tc_elems(c->N, 2, &ma, &mb, &md);
+  if (!r) r = dalloc(&c->d_mA, ma, "monomial digit planes A");
+  if (!r) r = dalloc(&c->d_mB, mb, "monomial digit planes B");
+  if (!r) r = dalloc(&c->d_mD, md, "monomial digit-pair products");
+  if (!r) r = dalloc(&c->d_meA, 2 * (size_t)c->N, "monomial exponents A");
+  if (!r) r = dalloc(&c->d_meB, 2 * (size_t)c->N, "monomial exponents B");
+  if (!r) r = dalloc(&c->d_LinvR2, 2 * NN, "L_R^-1 pair");
+  if (r) {
+    bs_destroy_cell(c);
+    return r;
+  }
+  std::vector<double> G(2 * (size_t)c->N);
+  for (int a = 0; a < c->N; ++a) {
+    const int al = a / (2 * M + 1) - M, be = a % (2 * M + 1) - M;
+    G[a] = al * c->q1[0] + be * c->q2[0];
+    G[c->N + a] = al * c->q1[1] + be * c->q2[1];
+  }
+  cudaError_t e = cudaMemcpy(c->d_phase, ph.data(), ph.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_table + 3 * np, raw.data(), raw.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_G, G.data(), G.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_info, 0, 4 * sizeof(int));
+  if (e == cudaSuccess && c->mesh)
+    e = cudaMemcpy(c->d_cen, cen->data(), cen->size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c->mesh)
+    e = cudaMemcpy(c->d_area, area->data(), area->size() * 8, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    r = bs_cuda_status(e, "bs_create_cell upload");
+    bs_destroy_cell(c);
+    return r;
+  }
+  c->tol = 1e-6;
+  c->floor2 = omega_floor2(c);
+  *out = c;
+  return BS_OK;
+}
+
 extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
   if (!d || !out) {
     bs_set_error("bs_create_cell: NULL argument");
@@ -279,85 +370,69 @@ extern "C" int bs_create_cell(const bs_cell_desc* d, bs_cell** out) {
       return BS_EINVAL;
     }
 
-  bs_cell* c = new bs_cell;
-  memset(c, 0, sizeof(*c));
-  c->P = P;
-  c->M = M;
-  c->N = (2 * M + 1) * (2 * M + 1);
-  c->n = 2 * c->N;
-  c->D = 4 * M + 1;
-  c->nphase = np;
-  c->precision = d->precision;
-  for (int i = 0; i < 2; ++i) {
-    c->h1[i] = d->h1[i];
-    c->h2[i] = d->h2[i];
-  }
-  c->V = fabs(det);
-  // reciprocal basis of Eq. (1) in 2-D: q^1 = 2 pi (h2y, -h2x)/det, q^2 = 2 pi (-h1y, h1x)/det
-  c->q1[0] = 2.0 * M_PI * d->h2[1] / det;
-  c->q1[1] = -2.0 * M_PI * d->h2[0] / det;
-  c->q2[0] = -2.0 * M_PI * d->h1[1] / det;
-  c->q2[1] = 2.0 * M_PI * d->h1[0] / det;
-
-  const size_t NN = (size_t)c->N * c->N, nn = (size_t)c->n * c->n;
-  int r = BS_OK;
-  if (!r) r = dalloc(&c->d_phase, (size_t)P * P, "phase");
-  if (!r) r = dalloc(&c->d_table, 6 * (size_t)np, "table");
-  if (!r) r = dalloc(&c->d_E, (size_t)c->D * P, "E");
-  if (!r) r = dalloc(&c->d_Y, 3 * (size_t)P * c->D, "Y");
-  if (!r) r = dalloc(&c->d_ghat, 3 * (size_t)c->D * c->D, "ghat");
-  if (!r) r = dalloc(&c->d_T, 3 * NN, "T");
-  if (!r) r = dalloc(&c->d_Linv, 3 * NN, "Linv");
-  if (!r) r = dalloc(&c->d_G, 2 * (size_t)c->N, "G");
-  if (!r) r = dalloc(&c->d_F, 6 * NN, "F");
-  if (!r) r = dalloc(&c->d_Pp, 12 * NN, "P");
-  if (!r) r = dalloc(&c->d_Cm, 6 * nn, "Cm");
-  if (!r) r = dalloc(&c->d_info, 4, "info");
-  size_t sa = 0, sb = 0, sd = 0;
-  bs_fields_tc_elems(P, c->D, &sa, &sb, &sd);
-  if (!r) r = dalloc(&c->d_sliceA, sa, "field digit planes");
-  if (!r) r = dalloc(&c->d_sliceB, sb, "exponential digit planes");
-  if (!r) r = dalloc(&c->d_sliceD, sd, "digit-pair products");
-  if (!r) r = dalloc(&c->d_expA, 3 * (size_t)P, "field exponents");
-  if (!r) r = dalloc(&c->d_expB, 2 * (size_t)c->D, "table exponents");
-  size_t ma = 0, mb = 0, md = 0;
-  bs_zgemm_tc_elems(c->N, 2, &ma, &mb, &md);
-  if (!r) r = dalloc(&c->d_mA, ma, "monomial digit planes A");
-  if (!r) r = dalloc(&c->d_mB, mb, "monomial digit planes B");
-  if (!r) r = dalloc(&c->d_mD, md, "monomial digit-pair products");
-  if (!r) r = dalloc(&c->d_meA, 2 * (size_t)c->N, "monomial exponents A");
-  if (!r) r = dalloc(&c->d_meB, 2 * (size_t)c->N, "monomial exponents B");
-  if (!r) r = dalloc(&c->d_LinvR2, 2 * NN, "L_R^-1 pair");
-  if (r) {
-    bs_destroy_cell(c);
-    return r;
-  }
-  std::vector<double> G(2 * (size_t)c->N);
-  for (int a = 0; a < c->N; ++a) {
-    const int al = a / (2 * M + 1) - M, be = a % (2 * M + 1) - M;
-    G[a] = al * c->q1[0] + be * c->q2[0];
-    G[c->N + a] = al * c->q1[1] + be * c->q2[1];
-  }
-  cudaError_t e = cudaMemcpy(c->d_phase, ph.data(), ph.size() * 2, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(c->d_table + 3 * np, raw.data(), raw.size() * 8, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->d_G, G.data(), G.size() * 8, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(c->d_info, 0, 4 * sizeof(int));
-  if (e != cudaSuccess) {
-    r = bs_cuda_status(e, "bs_create_cell upload");
-    bs_destroy_cell(c);
-    return r;
-  }
-  c->tol = 1e-6;
-  c->floor2 = omega_floor2(c);
-  *out = c;
-  return BS_OK;
+  return create_common(d->h1, d->h2, det, P, P * P, M, np, d->precision, raw, ph, nullptr, nullptr,
+                       out);
 }
+
+extern "C" int bs_create_cell_mesh(const bs_mesh_desc* d, bs_cell** out) {
+  if (!d || !out) {
+    bs_set_error("bs_create_cell_mesh: NULL argument");
+    return BS_EINVAL;
+  }
+  *out = nullptr;
+  const int nel = d->nel, M = d->M, np = d->nphase;
+  const long N = (2L * M + 1) * (2L * M + 1);
+  if (M < 0 || M > 15 || nel < N || nel > (1 << 26) || np < 1 || np > 65536 || !d->centroid ||
+      !d->area || !d->phase || !d->lam || !d->mu || !d->rho) {
+    bs_set_error("bs_create_cell_mesh: need 0 <= M <= 15, (2M+1)^2 <= nel <= 2^26, 1 <= nphase "
+                 "<= 65536 and non-NULL arrays (nel=%d M=%d nphase=%d)", nel, M, np);
+    return BS_EINVAL;
+  }
+  if (d->precision != BS_PREC_FP64 && d->precision != BS_PREC_MIXED) {
+    bs_set_error("bs_create_cell_mesh: unknown precision %d", d->precision);
+    return BS_EINVAL;
+  }
+  const double det = d->h1[0] * d->h2[1] - d->h1[1] * d->h2[0];
+  if (!(fabs(det) > 0.0) || !isfinite(det)) {
+    bs_set_error("bs_create_cell_mesh: h1, h2 are not a basis");
+    return BS_EINVAL;
+  }
+  std::vector<double> raw(3 * (size_t)np);
+  TRY(fetch_to_host(raw.data(), d->lam, np * sizeof(double)));
+  TRY(fetch_to_host(raw.data() + np, d->mu, np * sizeof(double)));
+  TRY(fetch_to_host(raw.data() + 2 * np, d->rho, np * sizeof(double)));
+  for (int i = 0; i < np; ++i) {
+    const double lam = raw[i], mu = raw[np + i], rho = raw[2 * np + i];
+    if (!isfinite(lam) || !isfinite(mu) || !isfinite(rho) || !(mu > 0.0) || !(lam + mu > 0.0) ||
+        !(rho > 0.0)) {
+      bs_set_error("bs_create_cell_mesh: phase %d has lam=%g mu=%g rho=%g (need mu > 0, "
+                   "lam + mu > 0, rho > 0, finite)", i, lam, mu, rho);
+      return BS_EINVAL;
+    }
+  }
+  std::vector<uint16_t> ph((size_t)nel);
+  std::vector<double> cen(2 * (size_t)nel), area((size_t)nel);
+  TRY(fetch_to_host(ph.data(), d->phase, ph.size() * sizeof(uint16_t)));
+  TRY(fetch_to_host(cen.data(), d->centroid, cen.size() * sizeof(double)));
+  TRY(fetch_to_host(area.data(), d->area, area.size() * sizeof(double)));
+  for (int i = 0; i < nel; ++i) {
+    if (ph[i] >= np || !(area[i] > 0.0) || !isfinite(area[i]) || !isfinite(cen[2 * i]) ||
+        !isfinite(cen[2 * i + 1])) {
+      bs_set_error("bs_create_cell_mesh: element %d has phase %u (nphase %d), area %g, "
+                   "centroid (%g, %g) (need phase < nphase, area > 0, finite)", i, ph[i], np,
+                   area[i], cen[2 * i], cen[2 * i + 1]);
+      return BS_EINVAL;
+    }
+  }
+  return create_common(d->h1, d->h2, det, 0, nel, M, np, d->precision, raw, ph, &cen, &area, out);
+}
+
 
 extern "C" int bs_destroy_cell(bs_cell* c) {
   if (!c) return BS_OK;
   bs_set_profiling(c, 0);
   free_workspace(c);
+  bs_free_mode_workspace(c);
   free_lob_workspace(c);
   cudaFree(c->d_phase);
   cudaFree(c->d_table);
@@ -382,6 +457,10 @@ extern "C" int bs_destroy_cell(bs_cell* c) {
   cudaFree(c->d_meA);
   cudaFree(c->d_meB);
   cudaFree(c->d_LinvR2);
+  cudaFree(c->d_cen);
+  cudaFree(c->d_area);
+  cudaFree(c->d_I1);
+  cudaFree(c->d_mpart);
   delete c;
   return BS_OK;
 }
@@ -407,7 +486,10 @@ extern "C" int bs_assemble(bs_cell* c, void* stream) {
   CK(cudaMemsetAsync(c->d_info, 0, 2 * sizeof(int), s), "bs_assemble");
   for (int i = 0; i < PH_COUNT; ++i) c->prof_ready[i] = false;
   bs_phase_begin(c, PH_ASM, s);
-  TRY(bs_launch_assembly(c, s));                                   // a1 + a2
+  if (c->mesh)
+    TRY(bs_launch_mesh_assembly(c, s));                            // a1 + a2 on mesh elements
+  else
+    TRY(bs_launch_assembly(c, s));                                 // a1 + a2
   bs_phase_end(c, PH_ASM, s);
   bs_phase_begin(c, PH_GRAM, s);
   TRY(bs_launch_toeplitz(c, s));                                   // a3 expansion

@@ -57,11 +57,11 @@ __global__ void stage2_kernel(int P, int D, double w, const zd* __restrict__ E,
 }
 
 // T[f][a + b N] = ghat[f][alpha_a - alpha_b + 2M][beta_a - beta_b + 2M]
-__global__ void toeplitz_kernel(const zd* __restrict__ ghat, int M, int N, int D,
+__global__ void toeplitz_kernel(const zd* __restrict__ ghat, int M, int N, int D, int nf,
                                 zd* __restrict__ T) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t NN = (size_t)N * N;
-  if (i >= 3 * NN) return;
+  if (i >= (size_t)nf * NN) return;
   int f = (int)(i / NN);
   size_t r = i % NN;
   int a = (int)(r % N), b = (int)(r / N);
@@ -90,9 +90,15 @@ int bs_launch_assembly(bs_cell* c, cudaStream_t s) {
 }
 
 int bs_launch_toeplitz(bs_cell* c, cudaStream_t s) {
-  size_t tot = 3 * (size_t)c->N * c->N;
-  toeplitz_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->d_ghat, c->M, c->N, c->D,
+  const size_t NN = (size_t)c->N * c->N, tot = 3 * NN;
+  toeplitz_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->d_ghat, c->M, c->N, c->D, 3,
                                                                  c->d_T);
   BS_CHECK_LAUNCH("toeplitz_kernel");
+  if (c->mesh) {
+    // the Gram matrix of the plane waves under the centroid rule (the 4th field, 1)
+    toeplitz_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(
+        c->d_ghat + 3 * (size_t)c->D * c->D, c->M, c->N, c->D, 1, c->d_I1);
+    BS_CHECK_LAUNCH("toeplitz_kernel I1");
+  }
   return BS_OK;
 }

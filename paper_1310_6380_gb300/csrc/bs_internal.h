@@ -94,13 +94,19 @@ struct bs_cell {
   bool assembled;
 
   // inputs (device copies)
-  uint16_t* d_phase;   // P*P
+  uint16_t* d_phase;   // P*P pixel phases, or nel element phases of a mesh
+  bool mesh;           // subdomains are mesh elements (bs_create_cell_mesh)
+  int nel;             // subdomains: P*P pixels or mesh elements
+  double* d_cen;       // mesh: nel x 2 fractional centroids
+  double* d_area;      // mesh: nel Cartesian areas
+  zd* d_I1;            // mesh: N x N Gram matrix int conj(f_a) f_b (V I on a pixel grid)
+  zd* d_mpart;         // mesh: per-chunk partial form factors
   double* d_table;     // 3*nphase: 1/(lam+mu), 1/mu, rho
 
   // assembly
   zd* d_E;             // D x P separable exponential table, row-major [d][p]
   zd* d_Y;             // 3 x P x D first-stage contraction
-  zd* d_ghat;          // 3 x D x D form factors [f][da][db]
+  zd* d_ghat;          // 3 x D x D form factors [f][da][db] (4 for a mesh: the 4th is of 1)
 
   // k-independent Gram factors
   zd* d_T;             // 3 x N x N Toeplitz blocks (kappa, mu, rho), Cholesky in place
@@ -161,6 +167,8 @@ struct bs_cell {
   int* d_stat;         // kcap
   int wcap;            // capacity of d_w per k
   // LOBPCG workspace (grown on demand)
+  double* d_mode;      // mode-shape workspace (stress solves, field tables, staging)
+  size_t mode_cap;     // its bytes
   int lcap;            // k the LOBPCG workspace holds
   int lbcap;           // block size it was sized for
   zf* d_lS;
@@ -366,3 +374,14 @@ int bs_launch_rr_tail(const MixedWs& w, int n, int kb, int nbands, int b, double
 // writes omega = sqrt(max(lambda, 0)) when want_omega, else lambda
 int bs_launch_bisect(const double* de, int n, int batch, int nbands, double* omega, int* stat,
                      cudaStream_t s, bool want_omega = true, double stop_rel = 0.0);
+
+// modes.cu: stress coefficients and plane-wave fields on a grid
+void bs_free_mode_workspace(bs_cell* c);
+int bs_launch_stress(bs_cell* c, const zd* U, const double* Q, int kc, int nvec, zd* Zk, zd* Zm,
+                     zd* Y, zd* S, cudaStream_t s);
+int bs_launch_mode_field(const zd* coef, const double* Q, long kbase, int nkt, long f0, long nf,
+                         int fpk, int M, int G, zf* E, zf* out, cudaStream_t s);
+
+// mesh.cu: form factors of a mesh cell (centroid rule over its elements)
+size_t bs_mesh_partial_elems(int M, int nel);
+int bs_launch_mesh_assembly(bs_cell* c, cudaStream_t s);

@@ -382,9 +382,19 @@ int bs_launch_monomials(bs_cell* c, cudaStream_t s) {
   int* err = c->d_info + 1;
   // F_X^a = L_R^-1 diag(s_a) L_X^-dagger for X in {kappa, mu} (batch of 2), a = 0, 1, 2,
   // as exact-slice tensor-core contractions (FP64 accuracy)
-  cudaError_t e = cudaMemcpyAsync(c->d_LinvR2, LinvR, NN * sizeof(zd), cudaMemcpyDeviceToDevice, s);
+  // On a mesh, H = i I1 diag(K) with I1 = int conj(f_a) f_b under the centroid
+  // rule (V I on a pixel grid), so L_R^-1 I1 takes the place of V L_R^-1
+  // (I1 is Hermitian: L_R^-1 I1 = L_R^-1 I1^dagger).
+  cudaError_t e = cudaSuccess;
+  if (c->mesh) {
+    TRY_LAUNCH(bs_launch_zgemm_tc(LinvR, 0, nullptr, c->d_I1, 0, c->d_LinvR2, (long)NN, N, 1,
+                                  c->d_mA, c->d_mB, c->d_mD, c->d_meA, c->d_meB, err, s));
+  } else {
+    e = cudaMemcpyAsync(c->d_LinvR2, LinvR, NN * sizeof(zd), cudaMemcpyDeviceToDevice, s);
+  }
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->d_LinvR2 + NN, LinvR, NN * sizeof(zd), cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyAsync(c->d_LinvR2 + NN, c->d_LinvR2, NN * sizeof(zd), cudaMemcpyDeviceToDevice,
+                        s);
   if (e != cudaSuccess) return bs_cuda_status(e, "monomials copy");
   for (int a = 0; a < 3; ++a) {
     const double* sc = a == 0 ? nullptr : c->d_G + (size_t)(a - 1) * N;
@@ -401,7 +411,8 @@ int bs_launch_monomials(bs_cell* c, cudaStream_t s) {
                                   c->d_mD, c->d_meA, c->d_meB, err, s));
   }
   const size_t tot = (size_t)c->n * c->n;
-  monomial_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->d_Pp, N, c->V * c->V, c->d_Cm);
+  const double V2 = c->mesh ? 1.0 : c->V * c->V;
+  monomial_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->d_Pp, N, V2, c->d_Cm);
   BS_CHECK_LAUNCH("monomial_kernel");
   return BS_OK;
 }
