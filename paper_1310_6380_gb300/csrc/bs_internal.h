@@ -221,7 +221,8 @@ int bs_launch_toeplitz(bs_cell* c, cudaStream_t s);
 // dense.cu
 int bs_launch_cholesky(zd* A, int n, int batch, long stride, int* info, cudaStream_t s);
 int bs_launch_trinv(const zd* L, zd* X, int n, int batch, long stride, cudaStream_t s);
-// C[b] = alpha * opA(A[b]) * diag(sc) * opB(B[b]); tri bit0: opA lower, bit1: opB upper
+// C[b] = alpha * opA(A[b]) * diag(sc) * opB(B[b]); tri bit0: opA lower, bit1: opB upper,
+// bit2: opA upper
 int bs_launch_zgemm(bool conjA, bool conjB, int m, int nn, int k, zd alpha,
                     const zd* A, int lda, long sA, const zd* B, int ldb, long sB,
                     const double* sc, long sS, zd* C, int ldc, long sC, int batch,

@@ -236,13 +236,14 @@ __global__ void zgemm_kernel(int m, int nn, int k, zd alpha, const zd* __restric
   if (sc) sc += (size_t)b * sS;
   const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
   const int tid = threadIdx.x, tx = tid % 32, ty = tid / 32;
-  int kend = k;
+  int kend = k, kbeg = 0;
   if (tri & 1) kend = min(kend, r0 + BM);
   if (tri & 2) kend = min(kend, c0 + BN);
+  if (tri & 4) kbeg = r0 / BK * BK;      // opA upper triangular: row r needs k >= r only
   zd acc[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc[i] = zmake(0.0, 0.0);
-  for (int k0 = 0; k0 < kend; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
     for (int e = tid; e < BM * BK; e += 256) {
       int r, kk;
       if (!CA) { r = e % BM; kk = e / BM; } else { kk = e % BK; r = e / BK; }

@@ -273,11 +273,11 @@ int bs_launch_stress(bs_cell* c, const zd* U, const double* Q, int kc, int nvec,
   TRY_LAUNCH(bs_launch_zgemm(false, false, N, m, N, one, Lk, N, 0, Zk, N, 0, nullptr, 0, Y, N, 0,
                              1, 1, s));
   TRY_LAUNCH(bs_launch_zgemm(true, false, N, m, N, one, Lk, N, 0, Y, N, 0, nullptr, 0, Zk, N, 0,
-                             1, 0, s));
+                             1, 4, s));
   TRY_LAUNCH(bs_launch_zgemm(false, false, N, 2 * m, N, one, Lm, N, 0, Zm, N, 0, nullptr, 0, Y,
                              N, 0, 1, 1, s));
   TRY_LAUNCH(bs_launch_zgemm(true, false, N, 2 * m, N, one, Lm, N, 0, Y, N, 0, nullptr, 0, Zm, N,
-                             0, 1, 0, s));
+                             0, 1, 4, s));
   stress_combine_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Zk, Zm, N, m,
                                                                      c->mesh ? 1.0 : c->V, S);
   BS_CHECK_LAUNCH("stress_combine_kernel");
