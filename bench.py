@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--no-graph", action="store_true",
                     help="config 3: time the plain solve only (no CUDA graph record/replay)")
     ap.add_argument("--cpu-sample-k", type=int, default=6)
+    ap.add_argument("--kpoints", type=int, default=None,
+                    help="mode shapes: use the first K wavevectors only (small profiling runs)")
     return ap.parse_args()
 
 
@@ -967,6 +969,10 @@ def run_modes(args):
     from paper_1310_6380_gb300 import binding as bs
 
     cfg, config, nvec, G = modes_workload()
+    if args.kpoints:
+        cfg["Q"] = cfg["Q"][:args.kpoints]
+        config["k_points"] = len(cfg["Q"])
+        config["workload"] += f" (first {len(cfg['Q'])} wavevectors only)"
     cell, M = cfg["cell"], cfg["M"]
     Q = np.ascontiguousarray(cfg["Q"])
     nk, N = len(Q), (2 * M + 1) ** 2

@@ -15,6 +15,7 @@ step by step, in the paper's notation, in float64 / complex128:
   * index maps I1, I2, I3 (alpha-major) ............. Sec. IV.A
   * H, Omega, Phi entries ........................... Eqs. (eh), (eo), (ep)
   * isotropic plane-strain compliance D_jkmn ........ Sec. IV, constitutive law
+    (or the compliance of a general in-plane stiffness per phase)
   * centroid quadrature over subdomains ............. Sec. III (int F = sum F_i V_i),
     pixels of a phase map or the elements of a mesh (centroid, area, phase)
   * eigenproblem A U = lambda Omega U, A = H Phi^-1 H^*,
@@ -41,7 +42,7 @@ import scipy.linalg as sla
 
 __all__ = [
     "reciprocal_basis", "plane_wave_indices", "wavevectors", "quadrature", "subdomains",
-    "compliance", "form_factors", "toeplitz", "integrals_literal", "OracleCell",
+    "compliance", "compliance_from_stiffness", "form_factors", "toeplitz", "integrals_literal", "OracleCell",
     "bands",
 ]
 
@@ -106,6 +107,25 @@ def compliance(lam, mu):
     sym = 0.5 * (np.einsum("jm,kn->jkmn", d, d) + np.einsum("jn,km->jkmn", d, d))
     vol = np.einsum("jk,mn->jkmn", d, d)
     return (sym - lam / (2.0 * (mu + lam)) * vol) / (2.0 * mu)
+
+
+def compliance_from_stiffness(C):
+    """D_jkmn (..., 2,2,2,2) of in-plane Voigt stiffness C (..., 3, 3)
+    (sigma = C (e11, e22, 2 e12)): with S = C^-1, D1111 = S11, D2222 = S22,
+    D1122 = S12, D11_12 = S13 / 2, D22_12 = S23 / 2, D12_12 = S33 / 4 and the
+    minor and major symmetries of the compliance tensor (Sec. IV, the general
+    constitutive law behind Eq. (ep))."""
+    S = np.linalg.inv(np.asarray(C, float))
+    D = np.zeros(S.shape[:-2] + (2, 2, 2, 2))
+    pairs = [(0, 0), (1, 1), (0, 1)]
+    fac = [1.0, 1.0, 0.5]
+    for a, (j, k) in enumerate(pairs):
+        for b, (m, n) in enumerate(pairs):
+            v = S[..., a, b] * fac[a] * fac[b]
+            for (jj, kk) in {(j, k), (k, j)}:
+                for (mm, nn) in {(m, n), (n, m)}:
+                    D[..., jj, kk, mm, nn] = v
+    return D
 
 
 # ---------------------------------------------------------------- integrals
@@ -175,7 +195,10 @@ class OracleCell:
         self.N = N
         x, w, ph = subdomains(cell)
         rho = cell.rho[ph]
-        D = compliance(cell.lam, cell.mu)[ph]          # (npix, 2,2,2,2)
+        if getattr(cell, "stiffness", None) is not None:
+            D = compliance_from_stiffness(cell.stiffness)[ph]
+        else:
+            D = compliance(cell.lam, cell.mu)[ph]      # (npix, 2,2,2,2)
         fields = [np.ones_like(rho), rho]
         for (j, k) in _COMP:
             for (m, n) in _COMP:

@@ -24,7 +24,8 @@ __all__ = [
     "bilayer_cell", "voronoi_cell", "ellipse_cell", "steel_epoxy_hex_cell",
     "ibz_path", "config0", "config1", "config3_cell", "CONFIGS",
     "MeshCell", "jittered_triangles", "mesh_circle_cell", "mesh_voronoi_cell", "pixel_mesh",
-    "steel_epoxy_hex_mesh",
+    "steel_epoxy_hex_mesh", "isotropic_stiffness", "rotate_stiffness", "rotated_orthotropic", "with_stiffness",
+    "anisotropic_cell",
 ]
 
 
@@ -41,6 +42,7 @@ class Cell:
     name: str = "cell"
     lattice: str = "square"   # "square" or "hex": selects the IBZ path
     meta: dict = field(default_factory=dict)
+    stiffness: np.ndarray = None   # optional (nphase, 3, 3) in-plane Voigt stiffness
 
     @property
     def P(self) -> int:
@@ -206,6 +208,7 @@ class MeshCell:
     name: str = "mesh"
     lattice: str = "square"
     meta: dict = field(default_factory=dict)
+    stiffness: np.ndarray = None   # optional (nphase, 3, 3) in-plane Voigt stiffness
 
     @property
     def nel(self) -> int:
@@ -323,6 +326,59 @@ def steel_epoxy_hex_mesh(n=22):
     epoxy = (7.54e9 - 2 * 1.48e9, 1.48e9, 1142.0)
     return mesh_circle_cell(n, r=2.0e-3 / a, matrix=epoxy, inclusion=steel, lattice="hex", a=a,
                             name="steel_epoxy_hex_mesh")
+
+
+# ---------------------------------------------------------------- anisotropy
+# In-plane Voigt notation: sigma = (s11, s22, s12), strain = (e11, e22, 2 e12),
+# sigma = C strain with C symmetric positive definite (plane strain).
+def isotropic_stiffness(lam, mu):
+    """(n, 3, 3) Voigt stiffness of isotropic phases."""
+    lam, mu = np.atleast_1d(np.asarray(lam, float)), np.atleast_1d(np.asarray(mu, float))
+    C = np.zeros((lam.shape[0], 3, 3))
+    C[:, 0, 0] = C[:, 1, 1] = lam + 2 * mu
+    C[:, 0, 1] = C[:, 1, 0] = lam
+    C[:, 2, 2] = mu
+    return C
+
+
+def rotate_stiffness(C, theta):
+    """Voigt stiffness (3, 3) of a material turned by theta in the plane."""
+    c, s = np.cos(theta), np.sin(theta)
+    T = np.array([[c * c, s * s, 2 * s * c], [s * s, c * c, -2 * s * c],
+                  [-s * c, s * c, c * c - s * s]])          # sigma' = T sigma
+    R = np.diag([1.0, 1.0, 2.0])                            # strain Voigt <-> tensor
+    Te = R @ T @ np.linalg.inv(R)                           # strain' = Te strain
+    return T @ np.asarray(C, float) @ np.linalg.inv(Te)     # sigma' = T C Te^-1 strain'
+
+
+def rotated_orthotropic(c11, c22, c12, c66, theta):
+    """Voigt stiffness of an orthotropic material whose axes are turned by
+    theta in the plane: C' = T^-T C T^-1 with the stress transformation T of
+    a rotation by theta."""
+    return rotate_stiffness(np.array([[c11, c12, 0.0], [c12, c22, 0.0], [0.0, 0.0, c66]]), theta)
+
+
+def with_stiffness(cell, C):
+    """A copy of a pixel or mesh cell with per-phase Voigt stiffness C (nphase, 3, 3)."""
+    import copy
+    out = copy.copy(cell)
+    out.stiffness = np.asarray(C, float).copy()
+    return out
+
+
+def anisotropic_cell(cell, seed=0):
+    """The cell with every phase replaced by a rotated orthotropic material:
+    c11, c22 ~ U[20, 200], c66 ~ U[5, 60], c12 ~ U[0, 0.4 sqrt(c11 c22)],
+    orientation ~ U[0, pi); densities kept."""
+    rng = np.random.default_rng(seed)
+    C = []
+    for _ in range(cell.nphase):
+        u = rng.random(5)
+        c11, c22 = 20 + 180 * u[0], 20 + 180 * u[1]
+        c66 = 5 + 55 * u[2]
+        c12 = 0.4 * np.sqrt(c11 * c22) * u[3]
+        C.append(rotated_orthotropic(c11, c22, c12, c66, np.pi * u[4]))
+    return with_stiffness(cell, np.array(C))
 
 
 # High-symmetry points in fractional coordinates Q (k = Q1 q1 + Q2 q2).

@@ -9,6 +9,10 @@ def omega_floor(cell):
     A = np.array([cell.h1, cell.h2], float)
     qm = 2 * np.pi * np.linalg.inv(A)
     qmin = min(np.linalg.norm(qm[:, 0]), np.linalg.norm(qm[:, 1]))
+    if getattr(cell, "stiffness", None) is not None:
+        # slowest shear-like speed: smallest eigenvalue of the Voigt stiffness over rho
+        c2 = min(np.linalg.eigvalsh(C)[0] / r for C, r in zip(cell.stiffness, cell.rho))
+        return np.sqrt(c2) * qmin / 2
     return np.sqrt(np.min(cell.mu / cell.rho)) * qmin / 2
 
 
