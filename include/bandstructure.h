@@ -144,6 +144,22 @@ typedef struct bs_mesh_desc {
 int bs_create_cell_mesh(const bs_mesh_desc* desc, bs_cell** out);
 
 /*
+ * bs_set_stiffness - give every phase a general in-plane stiffness instead of
+ * the isotropic (lam, mu) of the cell's description (pixel or mesh cell).
+ *   C6 : nphase x 6 doubles per phase, the Voigt entries C11, C22, C12, C16,
+ *        C26, C66 of sigma = C (e11, e22, 2 e12) (plane strain); host or
+ *        device.  Each C must be symmetric positive definite (BS_EINVAL).
+ * The compliance Gram matrix of Eq. (ep) then has all its blocks, Phi =
+ * [T[S_rc]] with S = C^-1 (the paper's factors 2 and 4 are those of the
+ * Voigt compliance), and bs_assemble factors it as one 3N x 3N matrix.  The
+ * densities stay those of the description.  Call before bs_assemble (the
+ * cell needs a new bs_assemble afterwards); bs_form_factors then returns 7
+ * fields (S11, S22, rho, S12, S13, S23, S33) instead of 3.  Every
+ * single-cell call takes the cell; the ragged batch does not.  Synchronous.
+ */
+int bs_set_stiffness(bs_cell* cell, const double* C6);
+
+/*
  * bs_assemble - everything that does not depend on k, on `stream`:
  *   material fields 1/(lam+mu), 1/mu, rho per pixel (Sec. IV, the
  *   compliance D_jkmn), their form factors ghat(d) = sum_i g_i V_i
@@ -219,7 +235,8 @@ int bs_solve_k_lobpcg(bs_cell* cell, const double* Q, int nk, int nbands,
 
 /*
  * bs_form_factors - copy the assembled form factors to `out`
- * (host or device): 3 fields (1/(lam+mu), 1/mu, rho) x D x D complex
+ * (host or device): 3 fields (1/(lam+mu), 1/mu, rho), or the 7 of a cell
+ * given bs_set_stiffness (S11, S22, rho, S12, S13, S23, S33), x D x D complex
  * (interleaved re, im), D = 4M+1, index [f][da+2M][db+2M].
  * Synchronises `stream` when `out` is a host pointer.
  */

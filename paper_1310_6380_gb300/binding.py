@@ -54,6 +54,7 @@ def _load():
     sig = {
         "bs_create_cell": [ctypes.POINTER(bs_cell_desc), ctypes.POINTER(vp)],
         "bs_create_cell_mesh": [ctypes.POINTER(bs_mesh_desc), ctypes.POINTER(vp)],
+        "bs_set_stiffness": [vp, dp],
         "bs_assemble": [vp, vp],
         "bs_solve_k": [vp, dp, i32, i32, dp, dp, vp],
         "bs_bands": [vp, i32, i32, i32, dp, dp, vp],
@@ -114,7 +115,7 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_batch_set_start", "bs_batch_stats", "bs_batch_set_vectors", "bs_batch_vectors",
             "bs_batch_set_tile", "bs_cnn_create", "bs_cnn_destroy", "bs_cnn_num_params", "bs_cnn_set_params",
             "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step", "bs_stress_coefficients",
-            "bs_mode_field", "bs_create_cell_mesh"]
+            "bs_mode_field", "bs_create_cell_mesh", "bs_set_stiffness"]
 BS_SOLVER_DENSE, BS_SOLVER_LOBPCG, BS_SOLVER_FP64 = 0, 1, 2
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
 
@@ -185,6 +186,11 @@ def bs_create_cell_mesh(h1, h2, centroid, area, phase, lam, mu, rho, M: int,
     out = ctypes.c_void_p()
     _check(_lib.bs_create_cell_mesh(ctypes.byref(d), ctypes.byref(out)))
     return out
+
+
+def bs_set_stiffness(cell, C6):
+    """C6: (nphase, 6) float64 Voigt entries C11, C22, C12, C16, C26, C66 per phase."""
+    _check(_lib.bs_set_stiffness(cell, _ptr(C6, np.float64)))
 
 
 def bs_assemble(cell, stream=None):

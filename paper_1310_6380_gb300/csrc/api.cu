@@ -252,6 +252,7 @@ static int create_common(const double h1[2], const double h2[2], double det, int
   c->n = 2 * c->N;
   c->D = 4 * M + 1;
   c->nphase = np;
+  c->nf = 3;
   c->precision = precision;
   for (int i = 0; i < 2; ++i) {
     c->h1[i] = h1[i];
@@ -274,7 +275,7 @@ static int create_common(const double h1[2], const double h2[2], double det, int
   if (!r && c->mesh) r = dalloc(&c->d_cen, 2 * (size_t)nel, "mesh centroids");
   if (!r && c->mesh) r = dalloc(&c->d_area, (size_t)nel, "mesh areas");
   if (!r && c->mesh) r = dalloc(&c->d_I1, NN, "mesh Gram matrix of the plane waves");
-  if (!r && c->mesh) r = dalloc(&c->d_mpart, bs_mesh_partial_elems(M, nel), "mesh partials");
+  if (!r && c->mesh) r = dalloc(&c->d_mpart, bs_mesh_partial_elems(M, nel, 4), "mesh partials");
   if (!r) r = dalloc(&c->d_T, 3 * NN, "T");
   if (!r) r = dalloc(&c->d_Linv, 3 * NN, "Linv");
   if (!r) r = dalloc(&c->d_G, 2 * (size_t)c->N, "G");
@@ -283,7 +284,7 @@ static int create_common(const double h1[2], const double h2[2], double det, int
   if (!r) r = dalloc(&c->d_Cm, 6 * nn, "Cm");
   if (!r) r = dalloc(&c->d_info, 4, "info");
   size_t sa = 0, sb = 0, sd = 0;
-  bs_fields_tc_elems(P, c->D, &sa, &sb, &sd);
+  bs_fields_tc_elems(P, c->D, 3, &sa, &sb, &sd);
   if (!r) r = dalloc(&c->d_sliceA, sa, "field digit planes");
   if (!r) r = dalloc(&c->d_sliceB, sb, "exponential digit planes");
   if (!r) r = dalloc(&c->d_sliceD, sd, "digit-pair products");
@@ -428,6 +429,114 @@ extern "C" int bs_create_cell_mesh(const bs_mesh_desc* d, bs_cell** out) {
 }
 
 
+// Re-size the field-dependent storage of a cell for nf material fields.
+static int realloc_fields(bs_cell* c, int nf) {
+  const size_t NN = (size_t)c->N * c->N, D2 = (size_t)c->D * c->D;
+  const int P = c->P, np = c->nphase;
+  std::vector<double> raw(3 * (size_t)np);
+  CK(cudaMemcpy(raw.data(), c->d_table + (size_t)c->nf * np, raw.size() * 8,
+                cudaMemcpyDeviceToHost), "bs_set_stiffness raw");
+  zd** zbufs[] = {&c->d_Y, &c->d_ghat, &c->d_T, &c->d_mpart, &c->d_Phi, &c->d_LPhi, &c->d_Yw,
+                  &c->d_Wk, &c->d_Pab};
+  for (zd** b : zbufs) {
+    cudaFree(*b);
+    *b = nullptr;
+  }
+  cudaFree(c->d_table);
+  cudaFree(c->d_sliceA);
+  cudaFree(c->d_sliceD);
+  cudaFree(c->d_expA);
+  c->d_table = nullptr;
+  c->d_sliceA = nullptr;
+  c->d_sliceD = nullptr;
+  c->d_expA = nullptr;
+  int r = BS_OK;
+  if (!r) r = dalloc(&c->d_table, (size_t)(nf + 3) * np, "table");
+  if (!r) r = dalloc(&c->d_Y, (size_t)nf * P * c->D, "Y");
+  if (!r) r = dalloc(&c->d_ghat, (size_t)(nf + (c->mesh ? 1 : 0)) * D2, "ghat");
+  if (!r) r = dalloc(&c->d_T, (size_t)nf * NN, "T");
+  if (!r && c->mesh)
+    r = dalloc(&c->d_mpart, bs_mesh_partial_elems(c->M, c->nel, nf + 1), "mesh partials");
+  size_t sa = 0, sb = 0, sd = 0;
+  bs_fields_tc_elems(P, c->D, nf, &sa, &sb, &sd);
+  if (!r) r = dalloc(&c->d_sliceA, sa, "field digit planes");
+  if (!r) r = dalloc(&c->d_sliceD, sd, "digit-pair products");
+  if (!r) r = dalloc(&c->d_expA, (size_t)nf * P, "field exponents");
+  if (!r) r = dalloc(&c->d_Phi, 9 * NN, "Phi");
+  if (!r) r = dalloc(&c->d_LPhi, 9 * NN, "Phi inverse factor");
+  if (!r) r = dalloc(&c->d_Yw, 18 * NN, "H_i Z");
+  if (!r) r = dalloc(&c->d_Wk, 18 * NN, "W_i");
+  if (!r) r = dalloc(&c->d_Pab, 24 * NN, "W_a W_b^dagger");
+  if (r) return r;
+  CK(cudaMemcpy(c->d_table + (size_t)nf * np, raw.data(), raw.size() * 8, cudaMemcpyHostToDevice),
+     "bs_set_stiffness raw");
+  c->nf = nf;
+  return BS_OK;
+}
+
+extern "C" int bs_set_stiffness(bs_cell* c, const double* C6) {
+  if (!c || !C6) {
+    bs_set_error("bs_set_stiffness: NULL argument");
+    return BS_EINVAL;
+  }
+  const int np = c->nphase;
+  std::vector<double> cv(6 * (size_t)np);
+  TRY(fetch_to_host(cv.data(), C6, cv.size() * sizeof(double)));
+  std::vector<double> raw(3 * (size_t)np);
+  CK(cudaMemcpy(raw.data(), c->d_table + (size_t)c->nf * np, raw.size() * 8,
+                cudaMemcpyDeviceToHost), "bs_set_stiffness raw");
+  // derived rows: S11, S22, rho, S12, S13, S23, S33 of S = C^-1 (Voigt)
+  std::vector<double> tab(7 * (size_t)np);
+  double c2min = 1e300;
+  for (int i = 0; i < np; ++i) {
+    const double* v = &cv[6 * (size_t)i];
+    const double C[3][3] = {{v[0], v[2], v[3]}, {v[2], v[1], v[4]}, {v[3], v[4], v[5]}};
+    // positive definite by its leading minors; inverse by cofactors
+    const double m1 = C[0][0], m2 = C[0][0] * C[1][1] - C[0][1] * C[1][0];
+    const double co00 = C[1][1] * C[2][2] - C[1][2] * C[2][1];
+    const double co01 = -(C[1][0] * C[2][2] - C[1][2] * C[2][0]);
+    const double co02 = C[1][0] * C[2][1] - C[1][1] * C[2][0];
+    const double det = C[0][0] * co00 + C[0][1] * co01 + C[0][2] * co02;
+    bool ok = true;
+    for (int k = 0; k < 6; ++k) ok = ok && isfinite(v[k]);
+    if (!ok || !(m1 > 0.0) || !(m2 > 0.0) || !(det > 0.0)) {
+      bs_set_error("bs_set_stiffness: phase %d stiffness is not symmetric positive definite", i);
+      return BS_EINVAL;
+    }
+    const double S00 = co00 / det, S01 = co01 / det, S02 = co02 / det;
+    const double S11 = (C[0][0] * C[2][2] - C[0][2] * C[2][0]) / det;
+    const double S12 = -(C[0][0] * C[2][1] - C[0][1] * C[2][0]) / det;
+    const double S22 = m2 / det;
+    const double rho = raw[2 * (size_t)np + i];
+    const double row[7] = {S00, S11, rho, S01, S02, S12, S22};
+    for (int f = 0; f < 7; ++f) tab[(size_t)f * np + i] = row[f];
+    // smallest eigenvalue of C by bisection on "C - x I is positive definite"
+    // (leading minors), a monotone test on [0, min diagonal]; the slowest
+    // shear-like speed squared of the phase is taken as lo / rho
+    double lo = 0.0, hi = std::min(std::min(C[0][0], C[1][1]), C[2][2]);
+    auto pd = [&](double x) {
+      const double a = C[0][0] - x, b = C[1][1] - x, e = C[2][2] - x;
+      const double d3 = a * (b * e - C[1][2] * C[2][1]) - C[0][1] * (C[1][0] * e - C[1][2] * C[2][0]) +
+                        C[0][2] * (C[1][0] * C[2][1] - b * C[2][0]);
+      return a > 0.0 && a * b - C[0][1] * C[1][0] > 0.0 && d3 > 0.0;
+    };
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (pd(mid)) lo = mid; else hi = mid;
+    }
+    c2min = std::min(c2min, lo / rho);
+  }
+  if (!c->aniso) TRY(realloc_fields(c, 7));
+  c->aniso = true;
+  CK(cudaMemcpy(c->d_table, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice),
+     "bs_set_stiffness table");
+  const double q2 = std::min(c->q1[0] * c->q1[0] + c->q1[1] * c->q1[1],
+                             c->q2[0] * c->q2[0] + c->q2[1] * c->q2[1]);
+  c->floor2 = c2min * q2 / 4.0;
+  c->assembled = false;
+  return BS_OK;
+}
+
 extern "C" int bs_destroy_cell(bs_cell* c) {
   if (!c) return BS_OK;
   bs_set_profiling(c, 0);
@@ -461,6 +570,11 @@ extern "C" int bs_destroy_cell(bs_cell* c) {
   cudaFree(c->d_area);
   cudaFree(c->d_I1);
   cudaFree(c->d_mpart);
+  cudaFree(c->d_Phi);
+  cudaFree(c->d_LPhi);
+  cudaFree(c->d_Yw);
+  cudaFree(c->d_Wk);
+  cudaFree(c->d_Pab);
   delete c;
   return BS_OK;
 }
@@ -493,11 +607,18 @@ extern "C" int bs_assemble(bs_cell* c, void* stream) {
   bs_phase_end(c, PH_ASM, s);
   bs_phase_begin(c, PH_GRAM, s);
   TRY(bs_launch_toeplitz(c, s));                                   // a3 expansion
-  TRY(bs_launch_cholesky(c->d_T, c->N, 3, (long)NN, c->d_info, s)); // a3 factors
-  TRY(bs_launch_trinv(c->d_T, c->d_Linv, c->N, 3, (long)NN, s));
+  if (c->aniso) {
+    TRY(bs_launch_gram_aniso(c, s));                               // R and the full Phi
+  } else {
+    TRY(bs_launch_cholesky(c->d_T, c->N, 3, (long)NN, c->d_info, s)); // a3 factors
+    TRY(bs_launch_trinv(c->d_T, c->d_Linv, c->N, 3, (long)NN, s));
+  }
   bs_phase_end(c, PH_GRAM, s);
   bs_phase_begin(c, PH_MONO, s);
-  TRY(bs_launch_monomials(c, s));                                  // a3/a4 coefficients
+  if (c->aniso)
+    TRY(bs_launch_monomials_aniso(c, s));
+  else
+    TRY(bs_launch_monomials(c, s));                                // a3/a4 coefficients
   bs_phase_end(c, PH_MONO, s);
   c->assembled = true;
   return BS_OK;
@@ -532,7 +653,8 @@ extern "C" int bs_sync(bs_cell* c, void* stream) {
 // in absolute terms (the acoustic branches vanish at Gamma)
 static double omega_floor2(const bs_cell* c) {
   std::vector<double> raw(3 * (size_t)c->nphase);
-  cudaMemcpy(raw.data(), c->d_table + 3 * c->nphase, raw.size() * 8, cudaMemcpyDeviceToHost);
+  cudaMemcpy(raw.data(), c->d_table + (size_t)c->nf * c->nphase, raw.size() * 8,
+             cudaMemcpyDeviceToHost);
   double ct2 = 1e300;
   for (int i = 0; i < c->nphase; ++i) ct2 = std::min(ct2, raw[c->nphase + i] / raw[2 * c->nphase + i]);
   const double q2 = std::min(c->q1[0] * c->q1[0] + c->q1[1] * c->q1[1],
@@ -1024,7 +1146,7 @@ extern "C" int bs_form_factors(bs_cell* c, double* out, void* stream) {
   }
   cudaStream_t s = (cudaStream_t)stream;
   const bool dev = is_device_ptr(out);
-  CK(cudaMemcpyAsync(out, c->d_ghat, 3 * (size_t)c->D * c->D * sizeof(zd),
+  CK(cudaMemcpyAsync(out, c->d_ghat, (size_t)c->nf * c->D * c->D * sizeof(zd),
                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
      "bs_form_factors");
   if (!dev) CK(cudaStreamSynchronize(s), "bs_form_factors sync");

@@ -72,32 +72,40 @@ __global__ void toeplitz_kernel(const zd* __restrict__ ghat, int M, int N, int D
 
 }  // namespace
 
-int bs_launch_assembly(bs_cell* c, cudaStream_t s) {
-  int P = c->P, D = c->D;
-  // the raw lam/mu/rho copies sit right after the derived table
-  const double* raw = c->d_table + 3 * c->nphase;
+// Per-phase fields of an isotropic cell (an anisotropic cell's table is
+// written by bs_set_stiffness): the raw lam/mu/rho copies sit right after
+// the nf derived rows.
+int bs_launch_table(bs_cell* c, cudaStream_t s) {
+  if (c->aniso) return BS_OK;
+  const double* raw = c->d_table + (size_t)c->nf * c->nphase;
   table_kernel<<<(c->nphase + 127) / 128, 128, 0, s>>>(raw, raw + c->nphase, raw + 2 * c->nphase,
                                                        c->nphase, c->d_table);
   BS_CHECK_LAUNCH("table_kernel");
+  return BS_OK;
+}
+
+int bs_launch_assembly(bs_cell* c, cudaStream_t s) {
+  int P = c->P, D = c->D;
+  TRY_LAUNCH(bs_launch_table(c, s));
   exp_table_kernel<<<(D * P + 255) / 256, 256, 0, s>>>(P, c->M, D, c->d_E);
   BS_CHECK_LAUNCH("exp_table_kernel");
-  // first stage (the bulk: 3 P^2 D complex-by-real products) on the tensor cores
+  // first stage (the bulk: nf P^2 D complex-by-real products) on the tensor cores
   TRY_LAUNCH(bs_launch_fields_tc(c, s));
-  stage2_kernel<<<dim3(D, 3), 64, 0, s>>>(P, D, c->V / ((double)P * P), c->d_E, c->d_Y,
-                                          c->d_ghat);
+  stage2_kernel<<<dim3(D, c->nf), 64, 0, s>>>(P, D, c->V / ((double)P * P), c->d_E, c->d_Y,
+                                              c->d_ghat);
   BS_CHECK_LAUNCH("stage2_kernel");
   return BS_OK;
 }
 
 int bs_launch_toeplitz(bs_cell* c, cudaStream_t s) {
-  const size_t NN = (size_t)c->N * c->N, tot = 3 * NN;
-  toeplitz_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->d_ghat, c->M, c->N, c->D, 3,
-                                                                 c->d_T);
+  const size_t NN = (size_t)c->N * c->N, tot = (size_t)c->nf * NN;
+  toeplitz_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->d_ghat, c->M, c->N, c->D,
+                                                                 c->nf, c->d_T);
   BS_CHECK_LAUNCH("toeplitz_kernel");
   if (c->mesh) {
-    // the Gram matrix of the plane waves under the centroid rule (the 4th field, 1)
+    // the Gram matrix of the plane waves under the centroid rule (the last field, 1)
     toeplitz_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(
-        c->d_ghat + 3 * (size_t)c->D * c->D, c->M, c->N, c->D, 1, c->d_I1);
+        c->d_ghat + (size_t)c->nf * c->D * c->D, c->M, c->N, c->D, 1, c->d_I1);
     BS_CHECK_LAUNCH("toeplitz_kernel I1");
   }
   return BS_OK;

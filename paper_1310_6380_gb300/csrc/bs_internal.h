@@ -101,6 +101,16 @@ struct bs_cell {
   double* d_area;      // mesh: nel Cartesian areas
   zd* d_I1;            // mesh: N x N Gram matrix int conj(f_a) f_b (V I on a pixel grid)
   zd* d_mpart;         // mesh: per-chunk partial form factors
+  // material fields: nf = 3 (isotropic: 1/(lam+mu), 1/mu, rho) or 7 (a general
+  // in-plane stiffness: Voigt compliance S11, S22, rho, S12, S13, S23, S33);
+  // d_table holds nf derived rows then the raw lam, mu, rho rows
+  int nf;
+  bool aniso;
+  zd* d_Phi;           // aniso: 3N x 3N compliance Gram matrix, Cholesky in place
+  zd* d_LPhi;          // aniso: its triangular inverse
+  zd* d_Yw;            // aniso: 3 x 2N x 3N rows of H_i Z (Z = L_Phi^-dagger)
+  zd* d_Wk;            // aniso: 3 x 2N x 3N W_i = L_Omega^-1 H_i Z
+  zd* d_Pab;           // aniso: 6 x 2N x 2N products W_a W_b^dagger
   double* d_table;     // 3*nphase: 1/(lam+mu), 1/mu, rho
 
   // assembly
@@ -236,7 +246,7 @@ int bs_launch_monomials(bs_cell* c, cudaStream_t s);
 int bs_launch_slice_gemm(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
                          int batch, long sA, long sB, long ldd, long sD, int* err, cudaStream_t s);
 int bs_launch_fields_tc(bs_cell* c, cudaStream_t s);
-size_t bs_fields_tc_elems(int P, int D, size_t* nA, size_t* nB, size_t* nD);
+size_t bs_fields_tc_elems(int P, int D, int nf, size_t* nA, size_t* nB, size_t* nD);
 int bs_launch_cx_tc(const zd* C, const zd* X, int n, int b, int kb, uint16_t* sA, uint16_t* sB,
                     float* sD, int* eA, int* eB, zd* Y, int* err, cudaStream_t s);
 void bs_cx_tc_elems(int n, int b, int kb, size_t* nA, size_t* nB, size_t* nD);
@@ -384,5 +394,14 @@ int bs_launch_mode_field(const zd* coef, const double* Q, long kbase, int nkt, l
                          int fpk, int M, int G, zf* E, zf* out, cudaStream_t s);
 
 // mesh.cu: form factors of a mesh cell (centroid rule over its elements)
-size_t bs_mesh_partial_elems(int M, int nel);
+size_t bs_mesh_partial_elems(int M, int nel, int nfields);
 int bs_launch_mesh_assembly(bs_cell* c, cudaStream_t s);
+
+// assemble.cu: per-phase derived table of an isotropic cell
+int bs_launch_table(bs_cell* c, cudaStream_t s);
+
+// aniso.cu: a general in-plane stiffness per phase (the full Phi of Eq. (ep))
+int bs_launch_gram_aniso(bs_cell* c, cudaStream_t s);
+int bs_launch_monomials_aniso(bs_cell* c, cudaStream_t s);
+int bs_launch_stress_aniso(bs_cell* c, const zd* U, const double* Q, int kc, int nvec, zd* R3,
+                           zd* Y3, zd* S, cudaStream_t s);

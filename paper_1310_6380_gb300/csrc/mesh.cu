@@ -1,15 +1,16 @@
 // Form factors of a mesh cell: the centroid rule of Sec. III over arbitrary
 // elements (the paper's triangle meshes) instead of pixels,
 //   ghat_f(d) = sum_e w_f(e) exp(-i G_d . c_e),  d in [-2M, 2M]^2,
-// with w = area/(lam+mu), area/mu, area*rho and area (the fourth field gives
-// I1 = int conj(f_a) f_b, which a mesh does not make diagonal).  With the
-// centroid c_e = s_e h1 + t_e h2 the phase separates into
+// with w = area times each per-phase material field (1/(lam+mu), 1/mu, rho,
+// or the seven of an anisotropic cell) and w = area for a last field, whose
+// form factors give I1 = int conj(f_a) f_b (a mesh does not make it
+// diagonal).  With the centroid c_e = s_e h1 + t_e h2 the phase separates into
 // exp(-2 pi i da s_e) exp(-2 pi i db t_e), so each field is the contraction
 // over elements of a (2M+1) x nel table (da >= 0 only: ghat(-d) = conj ghat(d)
 // for real fields) with a D x nel table.  It runs in FP64 on the CUDA cores:
 // element chunks per CTA, tables staged per tile of elements in shared
-// memory, a fixed-order reduction over chunks; the cost is 4 (2M+1) D nel
-// complex products (7 MFLOP for a 1000-element mesh at M = 5).
+// memory, a fixed-order reduction over chunks; the cost is (nf + 1)(2M+1) D nel
+// complex products (7 MFLOP for a 1000-element isotropic mesh at M = 5).
 #include <algorithm>
 
 #include "bs_internal.h"
@@ -25,8 +26,8 @@ int mesh_chunks(int nel) { return std::max(1, std::min(152, (nel + 255) / 256));
 // part[f][ch][r][db] = sum_{e in chunk ch} w_f(e) exp(-2 pi i (r s_e + (db - 2M) t_e)), r = 0..2M
 __global__ void __launch_bounds__(MT)
 mesh_partial_kernel(const double* __restrict__ cen, const double* __restrict__ area,
-                    const uint16_t* __restrict__ phase, const double* __restrict__ raw, int np,
-                    int nel, int M, int nch, zd* __restrict__ part) {
+                    const uint16_t* __restrict__ phase, const double* __restrict__ tab, int np,
+                    int nf, int nel, int M, int nch, zd* __restrict__ part) {
   extern __shared__ zd sm[];
   const int R = 2 * M + 1, D = 4 * M + 1, npair = R * D;
   zd* Ea = sm;              // [TE][R]: w_f exp(-2 pi i r s)
@@ -45,10 +46,8 @@ mesh_partial_kernel(const double* __restrict__ cen, const double* __restrict__ a
       if (e < e1) {
         double w = 1.0, x;
         if (row < R) {
-          const int p = phase[e];
           const double a = area[e];
-          const double lam = raw[p], mu = raw[np + p], rho = raw[2 * np + p];
-          w = f == 0 ? a / (lam + mu) : f == 1 ? a / mu : f == 2 ? a * rho : a;
+          w = f < nf ? a * tab[(size_t)f * np + phase[e]] : a;
           x = 2.0 * row * cen[2 * e];
         } else {
           x = 2.0 * (row - R - 2 * M) * cen[2 * e + 1];
@@ -105,8 +104,8 @@ __global__ void mesh_reduce_kernel(const zd* __restrict__ part, int M, int nch,
 
 }  // namespace
 
-size_t bs_mesh_partial_elems(int M, int nel) {
-  return (size_t)4 * mesh_chunks(nel) * (2 * M + 1) * (4 * M + 1);
+size_t bs_mesh_partial_elems(int M, int nel, int nfields) {
+  return (size_t)nfields * mesh_chunks(nel) * (2 * M + 1) * (4 * M + 1);
 }
 
 int bs_launch_mesh_assembly(bs_cell* c, cudaStream_t s) {
@@ -118,11 +117,14 @@ int bs_launch_mesh_assembly(bs_cell* c, cudaStream_t s) {
   const size_t smem = (size_t)TE * (R + D) * sizeof(zd);
   cudaFuncSetAttribute(mesh_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  const double* raw = c->d_table + 3 * c->nphase;
-  mesh_partial_kernel<<<dim3(nch, 4), MT, smem, s>>>(c->d_cen, c->d_area, c->d_phase, raw,
-                                                    c->nphase, c->nel, M, nch, c->d_mpart);
+  TRY_LAUNCH(bs_launch_table(c, s));
+  const int nfl = c->nf + 1;     // the material fields and the constant 1
+  mesh_partial_kernel<<<dim3(nch, nfl), MT, smem, s>>>(c->d_cen, c->d_area, c->d_phase,
+                                                      c->d_table, c->nphase, c->nf, c->nel, M,
+                                                      nch, c->d_mpart);
   BS_CHECK_LAUNCH("mesh_partial_kernel");
-  mesh_reduce_kernel<<<dim3((R * D + 127) / 128, 4), 128, 0, s>>>(c->d_mpart, M, nch, c->d_ghat);
+  mesh_reduce_kernel<<<dim3((R * D + 127) / 128, nfl), 128, 0, s>>>(c->d_mpart, M, nch,
+                                                                   c->d_ghat);
   BS_CHECK_LAUNCH("mesh_reduce_kernel");
   return BS_OK;
 }

@@ -299,18 +299,18 @@ extern "C" int bs_stress_coefficients(bs_cell* c, const double* Q, int nk, int n
   const int N = c->N;
   const bool u_dev = dev_ptr(U), s_dev = dev_ptr(S_out), q_dev = dev_ptr(Q);
   // columns per chunk: whole wavevectors, each N x m block about 2^21 complex
-  // entries (ten such blocks, ~320 MB) and m <= 16384 (the product's grid)
+  // entries (eleven such blocks, ~350 MB) and m <= 16384 (the product's grid)
   long kcl = std::min<long>((1L << 21) / ((long)N * nvec), 16384 / nvec);
   const int kc = (int)std::max<long>(1, std::min<long>(nk, kcl));
   const size_t m = (size_t)kc * nvec;
   const size_t zq = 2 * (size_t)kc, zu = 2 * (size_t)N * m, zs = 3 * (size_t)N * m;
-  const size_t need = (zq + 2 * (5 * (size_t)N * m + zu + zs)) * sizeof(double);
+  const size_t need = (zq + 2 * (6 * (size_t)N * m + zu + zs)) * sizeof(double);
   TRY_LAUNCH(mode_ws(c, need));
   double* dQ = c->d_mode;
-  zd* Zk = (zd*)(dQ + zq);
+  zd* Zk = (zd*)(dQ + zq);             // Zk, Zm: 3 N m contiguous (R3 of the anisotropic path)
   zd* Zm = Zk + (size_t)N * m;
-  zd* Y = Zm + 2 * (size_t)N * m;
-  zd* dU = Y + 2 * (size_t)N * m;
+  zd* Y = Zm + 2 * (size_t)N * m;      // 3 N m
+  zd* dU = Y + 3 * (size_t)N * m;
   zd* dS = dU + (size_t)2 * N * m;
   for (int k0 = 0; k0 < nk; k0 += kc) {
     const int kb = std::min(kc, nk - k0);
@@ -325,7 +325,17 @@ extern "C" int bs_stress_coefficients(bs_cell* c, const double* Q, int nk, int n
       uk = dU;
     }
     zd* sk = s_dev ? (zd*)S_out + (size_t)k0 * nvec * 3 * N : dS;
-    TRY_LAUNCH(bs_launch_stress(c, uk, dQ, kb, nvec, Zk, Zm, Y, sk, s));
+    if (c->aniso) {
+      const zd* ui = uk;
+      if (c->mesh) {   // I1 U first (U as an N x 2 kb nvec matrix)
+        TRY_LAUNCH(bs_launch_zgemm(false, false, N, 2 * (int)mb, N, zmake(1.0, 0.0), c->d_I1, N,
+                                   0, uk, N, 0, nullptr, 0, Y, N, 0, 1, 0, s));
+        ui = Y;
+      }
+      TRY_LAUNCH(bs_launch_stress_aniso(c, ui, dQ, kb, nvec, Zk, Y, sk, s));
+    } else {
+      TRY_LAUNCH(bs_launch_stress(c, uk, dQ, kb, nvec, Zk, Zm, Y, sk, s));
+    }
     if (!s_dev)
       MCK(cudaMemcpyAsync((zd*)S_out + (size_t)k0 * nvec * 3 * N, dS, mb * 3 * N * sizeof(zd),
                           cudaMemcpyDeviceToHost, s),

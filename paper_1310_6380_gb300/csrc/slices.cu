@@ -102,7 +102,7 @@ __device__ __forceinline__ void put_digits(double x, int e, int S, uint16_t* out
 }
 
 // ---- assembly operands
-// A rows (f, s, p): grid (P, 3), block 128
+// A rows (f, s, p): grid (P, nf), block 128
 __global__ void pack_fields_kernel(const uint16_t* __restrict__ phase,
                                    const double* __restrict__ tab, int nphase, int P, int S,
                                    int Kp, uint16_t* __restrict__ A, int* __restrict__ eA) {
@@ -148,12 +148,12 @@ __global__ void pack_exp_kernel(const zd* __restrict__ E, int P, int D, int S, i
 // Y[f][p][d] = sum_{s,t} 2^(eA+eB-12-7(s+t)) Dm[(t,d,c)][(f,s,p)]
 template <int S>
 __global__ void recombine_fields_kernel(const float* __restrict__ Dm, const int* __restrict__ eA,
-                                        const int* __restrict__ eB, int P, int D,
+                                        const int* __restrict__ eB, int P, int D, int nf,
                                         zd* __restrict__ Y) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)3 * P * D) return;
+  if (i >= (size_t)nf * P * D) return;
   const int d = (int)(i % D), p = (int)((i / D) % P), f = (int)(i / ((size_t)P * D));
-  const size_t M = (size_t)3 * S * P;
+  const size_t M = (size_t)nf * S * P;
   OrderSums<S> o;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
@@ -249,27 +249,27 @@ __global__ void recombine_cx_kernel(const float* __restrict__ Dm, const int* __r
 }  // namespace
 
 int bs_launch_fields_tc(bs_cell* c, cudaStream_t s) {
-  const int P = c->P, D = c->D, S = BS_SLICES_ASM, Kp = (P + 7) / 8 * 8;
-  pack_fields_kernel<<<dim3(P, 3), 128, 0, s>>>(c->d_phase, c->d_table, c->nphase, P, S, Kp,
-                                                c->d_sliceA, c->d_expA);
+  const int P = c->P, D = c->D, S = BS_SLICES_ASM, Kp = (P + 7) / 8 * 8, nf = c->nf;
+  pack_fields_kernel<<<dim3(P, nf), 128, 0, s>>>(c->d_phase, c->d_table, c->nphase, P, S, Kp,
+                                                 c->d_sliceA, c->d_expA);
   BS_CHECK_LAUNCH("pack_fields_kernel");
   pack_exp_kernel<<<2 * D, 128, 0, s>>>(c->d_E, P, D, S, Kp, c->d_sliceB, c->d_expB);
   BS_CHECK_LAUNCH("pack_exp_kernel");
-  const int M = 3 * S * P, N = 2 * S * D;
+  const int M = nf * S * P, N = 2 * S * D;
   TRY_LAUNCH(bs_launch_slice_gemm(c->d_sliceA, c->d_sliceB, c->d_sliceD, M, N, Kp, 1,
                                   (long)M * Kp, (long)N * Kp, M, (long)M * N, c->d_info + 1, s));
-  const size_t tot = (size_t)3 * P * D;
+  const size_t tot = (size_t)nf * P * D;
   recombine_fields_kernel<BS_SLICES_ASM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      c->d_sliceD, c->d_expA, c->d_expB, P, D, c->d_Y);
+      c->d_sliceD, c->d_expA, c->d_expB, P, D, nf, c->d_Y);
   BS_CHECK_LAUNCH("recombine_fields_kernel");
   return BS_OK;
 }
 
-size_t bs_fields_tc_elems(int P, int D, size_t* nA, size_t* nB, size_t* nD) {
+size_t bs_fields_tc_elems(int P, int D, int nf, size_t* nA, size_t* nB, size_t* nD) {
   const int S = BS_SLICES_ASM, Kp = (P + 7) / 8 * 8;
-  *nA = (size_t)3 * S * P * Kp;
+  *nA = (size_t)nf * S * P * Kp;
   *nB = (size_t)2 * S * D * Kp;
-  *nD = (size_t)3 * S * P * 2 * S * D;
+  *nD = (size_t)nf * S * P * 2 * S * D;
   return *nA + *nB;
 }
 
