@@ -45,7 +45,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4", "modes",
-                                                          "mesh"])
+                                                          "mesh", "aniso"])
     ap.add_argument("--cells", type=int, default=None,
                     help="cells of the config-3 batch (4096) or config-4 evaluation set (1024)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1310_6380_gb300", "data",
@@ -76,6 +76,19 @@ def workload(name):
             "cells": 1, "elements": cell.nel, "k_points": 70, "plane_waves": 121, "n": 242,
             "nbands": 18, "precision": "fp64",
             "l2": "flushed between timed steps (256 MiB write, untimed)",
+        }
+        return cfg, config, 0
+    if name == "aniso":
+        cfg = cells.config1()
+        cfg["cell"] = cells.anisotropic_cell(cfg["cell"], seed=6380)
+        config = {
+            "workload": "aniso: the c1 cell (256x256 periodic Voronoi, 1132 phases, seed 1310) "
+                        "with every phase a rotated orthotropic material (c11, c22 ~ U[20, 200], "
+                        "c66 ~ U[5, 60], c12 ~ U[0, 0.4 sqrt(c11 c22)], orientation ~ U[0, pi), "
+                        "seed 6380), full 3N x 3N compliance Gram matrix, M=10 (441 plane "
+                        "waves, n=882), 90 k on G-X-M-G, lowest 18 branches, FP64 path",
+            "cells": 1, "k_points": 90, "plane_waves": 441, "n": 882, "nbands": 18,
+            "precision": "fp64", "l2": "flushed between timed steps (256 MiB write, untimed)",
         }
         return cfg, config, 0
     cfg = cells.config0() if name == "c0" else cells.config1()
@@ -255,8 +268,11 @@ def cpu_oracle_sample(cfg, nk_sample):
 def rel_err(w, ref, cell):
     A = np.array([cell.h1, cell.h2])
     qm = 2 * np.pi * np.linalg.inv(A)
-    floor = np.sqrt(np.min(cell.mu / cell.rho)) * min(np.linalg.norm(qm[:, 0]),
-                                                       np.linalg.norm(qm[:, 1])) / 2
+    if getattr(cell, "stiffness", None) is not None:
+        c2 = min(np.linalg.eigvalsh(C)[0] / r for C, r in zip(cell.stiffness, cell.rho))
+    else:
+        c2 = np.min(cell.mu / cell.rho)
+    floor = np.sqrt(c2) * min(np.linalg.norm(qm[:, 0]), np.linalg.norm(qm[:, 1])) / 2
     return np.abs(w ** 2 - ref ** 2) / (2 * np.maximum(ref ** 2, floor ** 2))
 
 
@@ -557,13 +573,23 @@ def run_ours(args):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     is_mesh = hasattr(cell, "centroid")
 
+    C6 = None
+    if getattr(cell, "stiffness", None) is not None:
+        Cs = cell.stiffness
+        C6 = np.ascontiguousarray(np.stack([Cs[:, 0, 0], Cs[:, 1, 1], Cs[:, 0, 1], Cs[:, 0, 2],
+                                            Cs[:, 1, 2], Cs[:, 2, 2]], axis=1))
+
     def create(conv):
         if is_mesh:
-            return bs.bs_create_cell_mesh(cell.h1, cell.h2, conv(cell.centroid), conv(cell.area),
-                                          conv(cell.phase.astype(np.uint16)), conv(cell.lam),
-                                          conv(cell.mu), conv(cell.rho), M, prec)
-        return bs.bs_create_cell(cell.h1, cell.h2, conv(cell.phase.astype(np.uint16)),
-                                 conv(cell.lam), conv(cell.mu), conv(cell.rho), M, prec)
+            c = bs.bs_create_cell_mesh(cell.h1, cell.h2, conv(cell.centroid), conv(cell.area),
+                                       conv(cell.phase.astype(np.uint16)), conv(cell.lam),
+                                       conv(cell.mu), conv(cell.rho), M, prec)
+        else:
+            c = bs.bs_create_cell(cell.h1, cell.h2, conv(cell.phase.astype(np.uint16)),
+                                  conv(cell.lam), conv(cell.mu), conv(cell.rho), M, prec)
+        if C6 is not None:
+            bs.bs_set_stiffness(c, conv(C6))
+        return c
 
     h = create(dev)
     bs.bs_set_profiling(h, True)
@@ -642,13 +668,20 @@ def run_ours(args):
                                             if is_mesh else ()):
         host_bufs[name] = pin(arr)
 
+    if C6 is not None:
+        host_bufs["stiffness"] = pin(C6)
+
     def e2e_create():
         b = host_bufs
         if is_mesh:
-            return bs.bs_create_cell_mesh(cell.h1, cell.h2, b["centroid"], b["area"], b["phase"],
-                                          b["lam"], b["mu"], b["rho"], M, prec)
-        return bs.bs_create_cell(cell.h1, cell.h2, b["phase"], b["lam"], b["mu"], b["rho"], M,
-                                 prec)
+            c = bs.bs_create_cell_mesh(cell.h1, cell.h2, b["centroid"], b["area"], b["phase"],
+                                       b["lam"], b["mu"], b["rho"], M, prec)
+        else:
+            c = bs.bs_create_cell(cell.h1, cell.h2, b["phase"], b["lam"], b["mu"], b["rho"], M,
+                                  prec)
+        if C6 is not None:
+            bs.bs_set_stiffness(c, b["stiffness"])
+        return c
 
     def e2e_step():
         c = e2e_create()
