@@ -25,7 +25,8 @@ __all__ = [
     "ibz_path", "config0", "config1", "config3_cell", "CONFIGS",
     "MeshCell", "jittered_triangles", "mesh_circle_cell", "mesh_voronoi_cell", "pixel_mesh",
     "steel_epoxy_hex_mesh", "isotropic_stiffness", "rotate_stiffness", "rotated_orthotropic", "with_stiffness",
-    "anisotropic_cell",
+    "anisotropic_cell", "Cell3", "sphere_cell3", "voronoi_cell3", "extruded_cell3",
+    "ibz_path_cubic",
 ]
 
 
@@ -379,6 +380,101 @@ def anisotropic_cell(cell, seed=0):
         c12 = 0.4 * np.sqrt(c11 * c22) * u[3]
         C.append(rotated_orthotropic(c11, c22, c12, c66, np.pi * u[4]))
     return with_stiffness(cell, np.array(C))
+
+
+# ---------------------------------------------------------------- 3-D cells
+@dataclass
+class Cell3:
+    """A voxelated multi-phase 3-D unit cell: phase[p, q, r] along h1, h2, h3,
+    voxel (p, q, r) centred at ((p + 1/2)/P, (q + 1/2)/P, (r + 1/2)/P) in
+    fractional coordinates."""
+
+    h1: np.ndarray            # (3,)
+    h2: np.ndarray
+    h3: np.ndarray
+    phase: np.ndarray         # (P, P, P) uint16
+    lam: np.ndarray
+    mu: np.ndarray
+    rho: np.ndarray
+    name: str = "cell3"
+    lattice: str = "cubic"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def P(self) -> int:
+        return int(self.phase.shape[0])
+
+    @property
+    def nphase(self) -> int:
+        return int(self.lam.shape[0])
+
+
+def _cubic(a=1.0):
+    return np.array([a, 0.0, 0.0]), np.array([0.0, a, 0.0]), np.array([0.0, 0.0, a])
+
+
+def _voxel_centres(h1, h2, h3, P):
+    f = (np.arange(P) + 0.5) / P
+    S, T, U = np.meshgrid(f, f, f, indexing="ij")
+    return S[..., None] * h1 + T[..., None] * h2 + U[..., None] * h3
+
+
+def sphere_cell3(P=16, r=0.3, matrix=(4.0, 1.5, 1.2), inclusion=(110.0, 80.0, 7.8), a=1.0):
+    """A spherical inclusion of radius r*a at the centre of a simple cubic
+    cell: a voxel is inside iff its centre lies within r*a of the centre."""
+    h1, h2, h3 = _cubic(a)
+    x = _voxel_centres(h1, h2, h3, P)
+    c = 0.5 * (h1 + h2 + h3)
+    inside = np.sum((x - c) ** 2, axis=-1) <= (r * a) ** 2
+    lam, mu, rho = (np.array([matrix[i], inclusion[i]], float) for i in range(3))
+    return Cell3(h1, h2, h3, inside.astype(np.uint16), lam, mu, rho, "sphere")
+
+
+def voronoi_cell3(P=16, nseeds=12, seed=3, a=1.0):
+    """Periodic 3-D Voronoi phases (nearest seed over the 27 periodic images)
+    on a simple cubic cell; properties drawn per phase as in 2-D."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    h1, h2, h3 = _cubic(a)
+    frac = rng.random((nseeds, 3))
+    lam, mu, rho = _draw_props(rng, nseeds)
+    pts = frac @ np.array([h1, h2, h3])
+    images = np.concatenate([pts + i * h1 + j * h2 + k * h3
+                             for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)])
+    x = _voxel_centres(h1, h2, h3, P).reshape(-1, 3)
+    _, idx = cKDTree(images).query(x)
+    return Cell3(h1, h2, h3, (idx % nseeds).astype(np.uint16).reshape(P, P, P), lam, mu, rho,
+                 "voronoi3", "cubic", {"seed": seed})
+
+
+def extruded_cell3(cell: Cell, a3=1.0):
+    """A 2-D pixel cell extruded along x3 (uniform in the third direction),
+    h3 = (0, 0, a3), P voxels along h3."""
+    h1 = np.array([cell.h1[0], cell.h1[1], 0.0])
+    h2 = np.array([cell.h2[0], cell.h2[1], 0.0])
+    h3 = np.array([0.0, 0.0, a3])
+    P = cell.P
+    ph = np.repeat(cell.phase[:, :, None], P, axis=2).astype(np.uint16)
+    return Cell3(h1, h2, h3, ph, cell.lam.copy(), cell.mu.copy(), cell.rho.copy(),
+                 cell.name + "_extruded", "tetragonal")
+
+
+def ibz_path_cubic(nk: int, a=1.0) -> np.ndarray:
+    """nk fractional wavevectors (nk, 3) uniform in arc length along
+    Gamma-X-M-R-Gamma of the simple cubic lattice (first and last Gamma)."""
+    corners = np.array([(0, 0, 0), (0.5, 0, 0), (0.5, 0.5, 0), (0.5, 0.5, 0.5), (0, 0, 0)],
+                       float)
+    kc = corners * (2 * np.pi / a)
+    seg = np.linalg.norm(np.diff(kc, axis=0), axis=1)
+    cum = np.concatenate([[0.0], np.cumsum(seg)])
+    out = np.empty((nk, 3))
+    for i in range(nk):
+        s_ = cum[-1] * i / (nk - 1)
+        j = min(int(np.searchsorted(cum, s_, side="right")) - 1, len(seg) - 1)
+        t = 0.0 if seg[j] == 0 else (s_ - cum[j]) / seg[j]
+        out[i] = corners[j] + min(max(t, 0.0), 1.0) * (corners[j + 1] - corners[j])
+    return out
 
 
 # High-symmetry points in fractional coordinates Q (k = Q1 q1 + Q2 q2).
