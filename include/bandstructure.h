@@ -479,6 +479,74 @@ int bs_mode_field(bs_cell* cell, const double* Q, int nk, int nfield,
                   const double* coef, int G, float* out, void* stream);
 
 /*
+ * 3-D cells (the paper's outlook: three displacement and six stress
+ * components, 9 (2M+1)^3 unknowns), FP64 path.
+ *
+ * bs_cell3_desc - a voxelated cubic, tetragonal or any other 3-D cell:
+ *   h1, h2, h3 : Cartesian cell vectors (a basis).
+ *   P          : voxels per side, 1 <= P <= 128; phase is P x P x P uint16,
+ *                phase[p][q][r] with p along h1, q along h2, r along h3
+ *                (r fastest); voxel centres ((p+1/2)/P, (q+1/2)/P, (r+1/2)/P).
+ *   nphase, lam, mu, rho : isotropic phases (mu > 0, 3 lam + 2 mu > 0, rho > 0).
+ *   M          : plane waves |a|, |b|, |c| <= M, 0 <= M <= 5, 2M+1 <= P;
+ *                N = (2M+1)^3, n = 3N, wave index (a+M)(2M+1)^2 + (b+M)(2M+1) + c+M.
+ * All arrays host or device; the caller keeps ownership.
+ */
+typedef struct bs_cell3_desc {
+    double h1[3];
+    double h2[3];
+    double h3[3];
+    int32_t P;
+    const uint16_t* phase;
+    int32_t nphase;
+    const double* lam;
+    const double* mu;
+    const double* rho;
+    int32_t M;
+} bs_cell3_desc;
+
+typedef struct bs_cell3 bs_cell3;
+
+/* bs_create_cell3 - validate and copy a 3-D cell (BS_EINVAL, BS_ENOMEM). Synchronous. */
+int bs_create_cell3(const bs_cell3_desc* desc, bs_cell3** out);
+
+/*
+ * bs_assemble3 - the k-independent part on `stream`: form factors of
+ * 1/(3 lam + 2 mu), 1/mu and rho over the voxels (Eqs. (eo), (ep) with the
+ * centroid rule, three separable stages), their Toeplitz Gram blocks and
+ * Cholesky factors (the isotropic Phi is block diagonal in the hydrostatic,
+ * deviatoric and shear stress directions), and the ten k-monomial matrices
+ * of C(k) (their twenty complex N^3 products as exact-slice tensor-core
+ * contractions).  A failed Cholesky is reported as BS_ENOTPD by the next
+ * synchronising call.
+ */
+int bs_assemble3(bs_cell3* cell, void* stream);
+
+/*
+ * bs_solve_k3 - lowest `nbands` angular frequencies at `nk` wavevectors
+ * k = Q1 q^1 + Q2 q^2 + Q3 q^3 (Q: nk x 3 doubles), FP64 Householder
+ * reduction and Sturm bisection of C(k) (n = 3N).  omega_out nk x nbands,
+ * status_out nk or NULL; host or device.  Requires bs_assemble3
+ * (BS_ESTATE); 1 <= nbands <= n.
+ */
+int bs_solve_k3(bs_cell3* cell, const double* Q, int nk, int nbands, double* omega_out,
+                int* status_out, void* stream);
+
+/* bs_form_factors3 - the 3 x D^3 form factors (1/(3 lam + 2 mu), 1/mu, rho),
+ * complex, index [f][da+2M][db+2M][dc+2M], D = 4M+1. Synchronises `stream`. */
+int bs_form_factors3(bs_cell3* cell, double* out, void* stream);
+
+/* bs_reduced_matrix3 - C(k) (n x n complex, column-major, lower triangle
+ * valid) for one wavevector Q (3 doubles). Synchronises `stream`. */
+int bs_reduced_matrix3(bs_cell3* cell, const double* Q, double* out, void* stream);
+
+/* bs_cell3_dims - N = (2M+1)^3 and n = 3N of a 3-D cell. */
+int bs_cell3_dims(const bs_cell3* cell, int* N, int* n);
+
+/* bs_destroy_cell3 - free a 3-D cell. NULL is a no-op. */
+int bs_destroy_cell3(bs_cell3* cell);
+
+/*
  * bs_set_profiling - when `on` is non-zero, bs_assemble and bs_solve_k
  * record CUDA events on their stream around each phase; bs_phase_times
  * then returns the elapsed milliseconds of the most recent call (the last

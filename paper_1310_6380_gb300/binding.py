@@ -45,6 +45,13 @@ class bs_mesh_desc(ctypes.Structure):
                 ("rho", ctypes.c_void_p), ("M", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
+class bs_cell3_desc(ctypes.Structure):
+    _fields_ = [("h1", ctypes.c_double * 3), ("h2", ctypes.c_double * 3),
+                ("h3", ctypes.c_double * 3), ("P", ctypes.c_int32), ("phase", ctypes.c_void_p),
+                ("nphase", ctypes.c_int32), ("lam", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("rho", ctypes.c_void_p), ("M", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libbs.so is not built ({LIB_PATH}); run "
@@ -55,6 +62,13 @@ def _load():
         "bs_create_cell": [ctypes.POINTER(bs_cell_desc), ctypes.POINTER(vp)],
         "bs_create_cell_mesh": [ctypes.POINTER(bs_mesh_desc), ctypes.POINTER(vp)],
         "bs_set_stiffness": [vp, dp],
+        "bs_create_cell3": [ctypes.POINTER(bs_cell3_desc), ctypes.POINTER(vp)],
+        "bs_assemble3": [vp, vp],
+        "bs_solve_k3": [vp, dp, i32, i32, dp, dp, vp],
+        "bs_form_factors3": [vp, dp, vp],
+        "bs_reduced_matrix3": [vp, dp, dp, vp],
+        "bs_cell3_dims": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "bs_destroy_cell3": [vp],
         "bs_assemble": [vp, vp],
         "bs_solve_k": [vp, dp, i32, i32, dp, dp, vp],
         "bs_bands": [vp, i32, i32, i32, dp, dp, vp],
@@ -115,7 +129,9 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_batch_set_start", "bs_batch_stats", "bs_batch_set_vectors", "bs_batch_vectors",
             "bs_batch_set_tile", "bs_cnn_create", "bs_cnn_destroy", "bs_cnn_num_params", "bs_cnn_set_params",
             "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step", "bs_stress_coefficients",
-            "bs_mode_field", "bs_create_cell_mesh", "bs_set_stiffness"]
+            "bs_mode_field", "bs_create_cell_mesh", "bs_set_stiffness", "bs_create_cell3",
+            "bs_assemble3", "bs_solve_k3", "bs_form_factors3", "bs_reduced_matrix3",
+            "bs_cell3_dims", "bs_destroy_cell3"]
 BS_SOLVER_DENSE, BS_SOLVER_LOBPCG, BS_SOLVER_FP64 = 0, 1, 2
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
 
@@ -191,6 +207,53 @@ def bs_create_cell_mesh(h1, h2, centroid, area, phase, lam, mu, rho, M: int,
 def bs_set_stiffness(cell, C6):
     """C6: (nphase, 6) float64 Voigt entries C11, C22, C12, C16, C26, C66 per phase."""
     _check(_lib.bs_set_stiffness(cell, _ptr(C6, np.float64)))
+
+
+def bs_create_cell3(h1, h2, h3, phase, lam, mu, rho, M: int):
+    """Handle of a new 3-D cell (see bs_cell3_desc): phase (P, P, P) uint16."""
+    d = bs_cell3_desc()
+    for i in range(3):
+        d.h1[i], d.h2[i], d.h3[i] = float(h1[i]), float(h2[i]), float(h3[i])
+    d.P, d.M = int(phase.shape[0]), int(M)
+    d.nphase = int(lam.shape[0])
+    d.phase = _ptr(phase, np.uint16)
+    d.lam, d.mu, d.rho = _ptr(lam, np.float64), _ptr(mu, np.float64), _ptr(rho, np.float64)
+    out = ctypes.c_void_p()
+    _check(_lib.bs_create_cell3(ctypes.byref(d), ctypes.byref(out)))
+    return out
+
+
+def bs_assemble3(cell, stream=None):
+    _check(_lib.bs_assemble3(cell, _stream(stream)))
+
+
+def bs_solve_k3(cell, Q, nbands: int, omega_out, status_out=None, stream=None):
+    """Q: (nk, 3) float64; omega_out: (nk, nbands)."""
+    _check(_lib.bs_solve_k3(cell, _ptr(Q, np.float64), int(Q.shape[0]), int(nbands),
+                            _ptr(omega_out, np.float64), _ptr(status_out, np.int32),
+                            _stream(stream)))
+    return omega_out
+
+
+def bs_form_factors3(cell, out, stream=None):
+    _check(_lib.bs_form_factors3(cell, _ptr(out, np.float64), _stream(stream)))
+    return out
+
+
+def bs_reduced_matrix3(cell, Q, out, stream=None):
+    _check(_lib.bs_reduced_matrix3(cell, _ptr(Q, np.float64), _ptr(out, np.float64),
+                                   _stream(stream)))
+    return out
+
+
+def bs_cell3_dims(cell):
+    N, n = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.bs_cell3_dims(cell, ctypes.byref(N), ctypes.byref(n)))
+    return N.value, n.value
+
+
+def bs_destroy_cell3(cell):
+    _check(_lib.bs_destroy_cell3(cell))
 
 
 def bs_assemble(cell, stream=None):
