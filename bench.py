@@ -45,7 +45,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="c1", choices=["c0", "c1", "c2", "c3", "c4", "modes",
-                                                          "mesh", "aniso"])
+                                                          "mesh", "aniso", "3d"])
     ap.add_argument("--cells", type=int, default=None,
                     help="cells of the config-3 batch (4096) or config-4 evaluation set (1024)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1310_6380_gb300", "data",
@@ -1182,13 +1182,179 @@ def run_reference_modes(args):
                 "d2h_bytes_per_step": 0}}))
 
 
+# ---------------------------------------------------------------- 3-D cells
+def workload3d():
+    from paper_1310_6380_gb300 import cells
+    cell = cells.sphere_cell3(32, 0.3)
+    M, nb, nk = 3, 12, 30
+    Q = cells.ibz_path_cubic(nk)
+    config = {
+        "workload": "3d: simple cubic cell a=1, 32^3 voxels, one spherical inclusion r=0.3a "
+                    "(matrix lam=4, mu=1.5, rho=1.2; inclusion 110, 80, 7.8), M=3 (343 plane "
+                    "waves, n=1029), 30 k on G-X-M-R-G, lowest 12 branches, FP64 path",
+        "cells": 1, "k_points": nk, "plane_waves": 343, "n": 1029, "nbands": nb,
+        "precision": "fp64", "l2": "flushed between timed steps (256 MiB write, untimed)",
+    }
+    return dict(cell=cell, M=M, Q=Q, nbands=nb), config
+
+
+def oracle3d_sample(cfg, idx):
+    from oracle import mixed_variational_3d as mv3
+    t0 = time.perf_counter()
+    oc = mv3.OracleCell3(cfg["cell"], cfg["M"])
+    ws = [oc.omega(cfg["Q"][i], cfg["nbands"]) for i in idx]
+    return np.array(ws), time.perf_counter() - t0
+
+
+def run_3d(args):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    rep = Replicas("nccl", torch.device("cuda", local))
+    world, rank = rep.world, rep.rank
+    from paper_1310_6380_gb300 import binding as bs
+
+    cfg, config = workload3d()
+    cell, M, nb = cfg["cell"], cfg["M"], cfg["nbands"]
+    Q = np.ascontiguousarray(cfg["Q"])
+    nk = len(Q)
+    n = 3 * (2 * M + 1) ** 3
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    stream = torch.cuda.current_stream()
+    h = bs.bs_create_cell3(cell.h1, cell.h2, cell.h3, dev(cell.phase.astype(np.uint16)),
+                           dev(cell.lam), dev(cell.mu), dev(cell.rho), M)
+    Qd = dev(Q)
+    w = torch.empty((nk, nb), dtype=torch.float64, device="cuda")
+    st = torch.empty(nk, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step():
+        ev[0].record(stream)
+        bs.bs_assemble3(h, stream)
+        ev[1].record(stream)
+        bs.bs_solve_k3(h, Qd, nb, w, st, stream)
+        ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(device_bus_id(torch))
+    step_ms, asm_ms, sol_ms = [], [], []
+    rep.barrier()
+    launches0 = bs.bs_launch_count()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+        ev[2].synchronize()
+        step_ms.append(ev[0].elapsed_time(ev[2]))
+        asm_ms.append(ev[0].elapsed_time(ev[1]))
+        sol_ms.append(ev[1].elapsed_time(ev[2]))
+    rep.barrier()
+    clocks = sampler.stop()
+    launches = bs.bs_launch_count() - launches0
+    assert not st.cpu().numpy().any(), "a wavevector did not converge"
+    ms = rep.max(statistics.mean(step_ms))
+    value = rep.value(nk, ms)
+    omega = w.cpu().numpy()
+    t_sol = statistics.mean(sol_ms)
+    flops = nk * 16.0 / 3.0 * n ** 3
+    achieved = flops / (t_sol / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "tridiag_step_kernel<double> (with the per-k builder "
+                                          "and bisection: bs_solve_k3 of one step)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}"}
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hp, hl, hm, hr, hQ = (pin(cell.phase.astype(np.uint16)), pin(cell.lam), pin(cell.mu),
+                          pin(cell.rho), pin(Q))
+    hw = torch.empty((nk, nb), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        c = bs.bs_create_cell3(cell.h1, cell.h2, cell.h3, hp, hl, hm, hr, M)
+        try:
+            bs.bs_assemble3(c, stream)
+            bs.bs_solve_k3(c, hQ, nb, hw, None, stream)
+        finally:
+            bs.bs_destroy_cell3(c)
+
+    e2e_step()
+    rep.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = rep.max((time.perf_counter() - t0) / args.steps)
+    e2e = {"value": world * nk / e2e_s, "unit": "k-solves/s",
+           "h2d_bytes_per_step": hp.numel() * 2 + 3 * hl.numel() * 8 + hQ.numel() * 8,
+           "d2h_bytes_per_step": hw.numel() * 8,
+           "api": "bs_create_cell3 + bs_assemble3 + bs_solve_k3 + bs_destroy_cell3, pinned host "
+                  "buffers"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config, "e2e": e2e, "gpu_launches": launches,
+        "gpu_launches_per_step": launches // max(1, args.steps), "roofline": roofline,
+        "phases_ms": {"assemble3": round(statistics.mean(asm_ms), 3),
+                      "solve_k3": round(t_sol, 3)},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        idx = [4, 17]
+        ws, secs = oracle3d_sample(cfg, idx)
+        A = np.array([cell.h1, cell.h2, cell.h3])
+        qm = 2 * np.pi * np.linalg.inv(A)
+        fl = np.sqrt(np.min(cell.mu / cell.rho)) * min(np.linalg.norm(qm[:, i]) for i in range(3)) / 2
+        err = np.abs(omega[idx] ** 2 - ws ** 2) / (2 * np.maximum(ws ** 2, fl ** 2))
+        out["cpu_baseline"] = {"value": len(idx) / secs, "unit": "k-solves/s",
+                               "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                               "sample": f"oracle cell set-up + wavevectors {idx} of {nk} "
+                                         f"({secs:.1f} s); value = their k-solves / time"}
+        out["max_rel_err_vs_oracle"] = float(err.max())
+    bs.bs_destroy_cell3(h)
+    if rank == 0:
+        print(json.dumps(out))
+    rep.close()
+
+
+def run_reference_3d(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    cfg, config = workload3d()
+    nk = len(cfg["Q"])
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, secs = oracle3d_sample(cfg, [(i * 7) % nk])
+        if i >= args.warmup:
+            times.append(secs)
+    value = 1.0 / statistics.mean(times)
+    desc = "each step: oracle cell set-up and one wavevector"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "k-solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": "k-solves/s", "cores": len(os.sched_getaffinity(0)),
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "k-solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         if args.config == "modes":
             run_reference_modes(args)
+        elif args.config == "3d":
+            run_reference_3d(args)
         else:
             run_reference(args)
+    elif args.config == "3d":
+        run_3d(args)
     elif args.config == "modes":
         run_modes(args)
     elif args.config == "c3":
