@@ -649,7 +649,7 @@ extern "C" int bs_sync(bs_cell* c, void* stream) {
 
 // ------------------------------------------------------------------ solve
 // Solve a chunk of kb wavevectors already in c->d_Q; results in c->d_w / d_stat.
-// omega_floor^2 = (c_T,min |q|_min / 2)^2: below it frequencies are judged
+// omega_floor^2 = (c_T,min |q|_min / 2)^2: below it frequencies are compared
 // in absolute terms (the acoustic branches vanish at Gamma)
 static double omega_floor2(const bs_cell* c) {
   std::vector<double> raw(3 * (size_t)c->nphase);

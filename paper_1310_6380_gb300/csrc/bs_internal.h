@@ -361,10 +361,10 @@ int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int M, int Mp
 // inertia.cu: eigenvalue-count certificate (FP32 LDL^dagger of the scaled
 // C - sigma I, sigma in a gap above the wanted Ritz values); A (lower part of
 // C(k), overwritten), sigma (kb), sc (kb x n) floats and iwork (3 kb ints)
-// scratch; stat[k] = BS_ENOCONV where the count fails; verdict optional
+// scratch; stat[k] = BS_ENOCONV where the count fails; outcome optional
 int bs_launch_inertia_check(zf* A, int n, int kb, const double* theta, int b, int nb,
                             double floor2, float* sigma, float* sc, int* iwork, int* stat,
-                            int* verdict, cudaStream_t s);
+                            int* outcome, cudaStream_t s);
 // dense FP64 solve of nf host wavevectors on an assembled cell (host outputs)
 int bs_cell_dense_fp64(bs_cell* c, const double* Q, int nf, int nbands, double* om, int* st,
                        cudaStream_t s);

@@ -211,13 +211,13 @@ __global__ void ldl_update_kernel(zf* __restrict__ A, int n, int j0) {
   }
 }
 
-__global__ void inertia_judge_kernel(const int* __restrict__ neg, const int* __restrict__ expect,
+__global__ void inertia_decide_kernel(const int* __restrict__ neg, const int* __restrict__ expect,
                                      const int* __restrict__ flag, int kb, int* __restrict__ stat,
-                                     int* __restrict__ verdict) {
+                                     int* __restrict__ outcome) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= kb) return;
   const int bad = flag[k] || neg[k] != expect[k];
-  if (verdict) verdict[k] = flag[k] ? 2 : (neg[k] != expect[k] ? 1 : 0);
+  if (outcome) outcome[k] = flag[k] ? 2 : (neg[k] != expect[k] ? 1 : 0);
   if (bad && stat[k] == 0) stat[k] = BS_ENOCONV;
 }
 
@@ -226,11 +226,11 @@ __global__ void inertia_judge_kernel(const int* __restrict__ neg, const int* __r
 // Count check of kb problems: A (kb x n x n FP32, lower triangle of C(k)) is
 // overwritten with the factors; theta (kb x b FP64 Ritz values); sigma (kb)
 // and sc (kb x n) floats and iwork (3 kb ints) are scratch; stat[k] becomes
-// BS_ENOCONV where the count does not match or cannot be trusted; verdict
+// BS_ENOCONV where the count does not match or cannot be trusted; outcome
 // (optional, kb) 0 ok, 1 count mismatch, 2 unreliable.
 int bs_launch_inertia_check(zf* A, int n, int kb, const double* theta, int b, int nb,
                             double floor2, float* sigma, float* sc, int* iwork, int* stat,
-                            int* verdict, cudaStream_t s) {
+                            int* outcome, cudaStream_t s) {
   int* neg = iwork;
   int* expect = iwork + kb;
   int* flag = iwork + 2 * kb;
@@ -254,7 +254,7 @@ int bs_launch_inertia_check(zf* A, int n, int kb, const double* theta, int b, in
       BS_CHECK_LAUNCH("ldl_update_kernel");
     }
   }
-  inertia_judge_kernel<<<(kb + 127) / 128, 128, 0, s>>>(neg, expect, flag, kb, stat, verdict);
-  BS_CHECK_LAUNCH("inertia_judge_kernel");
+  inertia_decide_kernel<<<(kb + 127) / 128, 128, 0, s>>>(neg, expect, flag, kb, stat, outcome);
+  BS_CHECK_LAUNCH("inertia_decide_kernel");
   return BS_OK;
 }
