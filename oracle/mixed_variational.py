@@ -165,8 +165,10 @@ def integrals_literal(cell, M, Q, g=None):
     [f]_ijk = exp([A1(j) - B1(k)] c(i,1) + [A2(j) - B2(k)] c(i,2)),
     I_jk = sum_i g_i [f]_ijk A_i, with A1, A2, B1, B2 built from T = A^-1
     as in that section.  Returns the N x N matrix I (paper sign convention).
-    Only for tiny cells: the tensor [f] has N_el * N^2 entries."""
-    x, w = quadrature(cell)
+    Only for tiny cells: the tensor [f] has N_el * N^2 entries.  The
+    elements are the cell's subdomains: pixels, or the elements of a mesh
+    (the paper's own case, centroids c(i, :) and areas A_i)."""
+    x, w, _ = subdomains(cell)
     if g is None:
         g = np.ones(len(w))
     A = np.array([cell.h1, cell.h2])

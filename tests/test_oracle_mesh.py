@@ -78,3 +78,17 @@ def test_planted_vertex_for_centroid_fails():
                          good.lam, good.mu, good.rho)
     assert homogeneous_error(good, 2) <= 1e-5
     assert homogeneous_error(bad, 2) > 1e-4
+
+
+def test_paper_integrand_on_a_mesh():
+    """The paper's own GPU formulation (Eq. (eExp): the integrand tensor from
+    element centroids and areas, T = A^-1) on a triangle mesh equals the
+    mesh form factors expanded to plane-wave pairs (paper sign convention)."""
+    m = cells.mesh_voronoi_cell(6, 4, seed=3, lattice="hex")
+    M = 2
+    Q = np.array([0.31, -0.17])
+    x, w, ph = mv.subdomains(m)
+    rho = m.rho[ph]
+    lit = mv.integrals_literal(m, M, Q, rho)
+    T = mv.toeplitz(mv.form_factors(rho[None], x, w, m.h1, m.h2, M, paper_conj=True)[0], M)
+    assert np.allclose(lit, T, atol=1e-14 * np.abs(T).max())
