@@ -2,6 +2,8 @@
 against the oracle: form factors, the reduced matrix, frequencies on the
 FP64, mixed and LOBPCG paths, stress coefficients, the pixel mesh against
 the pixel path, and argument errors."""
+import os
+
 import numpy as np
 import pytest
 
@@ -173,3 +175,26 @@ def test_mesh_argument_errors():
         assert ei.value.code == bs.BS_ENOTPD
     finally:
         bs.bs_destroy_cell(h)
+
+
+def test_gpu_mesh_reproduces_the_papers_stop_bands():
+    """The paper's worked example on a 968-triangle mesh through the GPU FP64
+    path: the stop bands of the first 12 branches (M = 5) match the printed
+    120-262 kHz and 427-473 kHz to 1 % (tests/golden, Sec. IV.B)."""
+    ref = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden",
+                                  "hex_steel_epoxy_stop_bands.txt"))
+    m = cells.steel_epoxy_hex_mesh(22)
+    Qs = np.ascontiguousarray(cells.ibz_path("hex", 46, m.h1, m.h2))
+    h = make(m, 5)
+    try:
+        w = np.empty((len(Qs), 12))
+        st = np.empty(len(Qs), np.int32)
+        bs.bs_solve_k(h, Qs, 12, w, st)
+    finally:
+        bs.bs_destroy_cell(h)
+    assert not st.any()
+    f = w / (2 * np.pi) / 1e3
+    gaps = [(f[:, i].max(), f[:, i + 1].min()) for i in range(11)
+            if f[:, i + 1].min() - f[:, i].max() > 10.0]
+    assert np.array(gaps).shape == ref.shape
+    assert np.allclose(gaps, ref, rtol=0.01)
