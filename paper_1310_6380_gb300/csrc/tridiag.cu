@@ -316,6 +316,33 @@ static int launch_steps(typename Cplx<R>::T* A, int n, int batch, typename Cplx<
   return BS_OK;
 }
 
+// FP64: 64-tiles while a step has enough of them to fill the GPU, then
+// 32-tiles (four times as many CTAs) for the small trailing blocks of the
+// last steps.  Each step writes and reduces its own partial sums, so the
+// tile edge may change from one step to the next.
+static int launch_steps_fp64(zd* A, int n, int batch, zd* vec, zd* part, double* de, double* tau,
+                             zd* beta, unsigned* count, cudaStream_t s) {
+  tridiag_init_kernel<double><<<batch, NT, 0, s>>>(A, n, vec, de, tau, beta, count);
+  BS_CHECK_LAUNCH("tridiag_init_kernel");
+  const long fill = 2L * 2 * 152;   // two waves of the 64-tile kernel (2 CTAs per SM)
+  const int nt64 = (n + 63) / 64, nt32 = (n + 31) / 32;
+  for (int j = 0; j + 1 < n; ++j) {
+    const int m64 = nt64 - (j + 1) / 64;
+    const int ntl64 = m64 * (m64 + 1) / 2;
+    if ((long)ntl64 * batch >= fill) {
+      tridiag_step_kernel<double, 64><<<dim3(ntl64, batch), NT, 0, s>>>(A, n, j, vec, part, de,
+                                                                         tau, beta, count, ntl64);
+    } else {
+      const int m32 = nt32 - (j + 1) / 32;
+      const int ntl32 = m32 * (m32 + 1) / 2;
+      tridiag_step_kernel<double, 32><<<dim3(ntl32, batch), NT, 0, s>>>(A, n, j, vec, part, de,
+                                                                         tau, beta, count, ntl32);
+    }
+    BS_CHECK_LAUNCH("tridiag_step_kernel");
+  }
+  return BS_OK;
+}
+
 template <typename R>
 int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
                       typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
@@ -333,6 +360,8 @@ int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>
   // launch and epilogue latency then repeats once per group.)
   if (tile == 32)
     return launch_steps<R, 32>(A, n, batch, vec, part, de, tau, beta, count, s);
+  if constexpr (sizeof(R) == 8)
+    return launch_steps_fp64(A, n, batch, vec, part, de, tau, beta, count, s);
   return launch_steps<R, 64>(A, n, batch, vec, part, de, tau, beta, count, s);
 }
 
