@@ -316,12 +316,14 @@ static int launch_steps(typename Cplx<R>::T* A, int n, int batch, typename Cplx<
   return BS_OK;
 }
 
-// FP64: 64-tiles while a step has enough of them to fill the GPU, then
-// 32-tiles (four times as many CTAs) for the small trailing blocks of the
-// last steps.  Each step writes and reduces its own partial sums, so the
-// tile edge may change from one step to the next.
+// FP64, n <= 600: 64-tiles while a step has enough of them to fill the GPU,
+// then 32-tiles (four times as many CTAs) for the small trailing blocks of
+// the last steps.  Each step writes and reduces its own partial sums, so the
+// tile edge may change from one step to the next.  Larger matrices keep
+// 64-tiles throughout (their tail is a negligible share of the steps).
 static int launch_steps_fp64(zd* A, int n, int batch, zd* vec, zd* part, double* de, double* tau,
                              zd* beta, unsigned* count, cudaStream_t s) {
+  if (n > 600) return launch_steps<double, 64>(A, n, batch, vec, part, de, tau, beta, count, s);
   tridiag_init_kernel<double><<<batch, NT, 0, s>>>(A, n, vec, de, tau, beta, count);
   BS_CHECK_LAUNCH("tridiag_init_kernel");
   const long fill = 2L * 2 * 152;   // two waves of the 64-tile kernel (2 CTAs per SM)
