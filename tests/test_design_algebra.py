@@ -61,22 +61,26 @@ def test_isotropic_2d_blocks(mesh):
         assert np.abs(C - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-def test_anisotropic_2d_w_form():
+@pytest.mark.parametrize("mesh", [False, True])
+def test_anisotropic_2d_w_form(mesh):
     """Phi = [T[S_rc]] factored whole, W_i = L_Omega^-1 H_i L_Phi^-dagger and
     C(k) = W W^dagger with W = k1 W1 + k2 W2 + W0 (the header of the
-    anisotropic kernels)."""
-    cell = cells.anisotropic_cell(cells.voronoi_cell(16, 4, seed=6, lattice="hex"), seed=2)
+    anisotropic kernels); A_R = L_R^-1 I1 on a mesh."""
+    base = (cells.mesh_voronoi_cell(12, 4, seed=6, lattice="hex") if mesh
+            else cells.voronoi_cell(16, 4, seed=6, lattice="hex"))
+    cell = cells.anisotropic_cell(base, seed=2)
     M = 2
     oc = mv.OracleCell(cell, M)
     S = np.linalg.inv(cell.stiffness)
     T = gram(cell, M, [S[:, 0, 0], S[:, 1, 1], cell.rho, S[:, 0, 1], S[:, 0, 2], S[:, 1, 2],
-                       S[:, 2, 2]])
+                       S[:, 2, 2], np.ones_like(cell.rho)])
     f = {(0, 0): 0, (1, 1): 1, (2, 2): 6, (0, 1): 3, (0, 2): 4, (1, 2): 5}
     Phi = np.block([[T[f[(min(r, c), max(r, c))]] for c in range(3)] for r in range(3)])
     Z = np.linalg.inv(np.linalg.cholesky(Phi)).conj().T
     N = oc.N
     V = abs(np.linalg.det(np.array([cell.h1, cell.h2])))
-    AR = V * np.linalg.inv(np.linalg.cholesky(T[2]))
+    LRi = np.linalg.inv(np.linalg.cholesky(T[2]))
+    AR = LRi @ T[7] if mesh else V * LRi
     Zr = [Z[r * N:(r + 1) * N] for r in range(3)]
     G = gvec(cell, M)
     W1 = np.vstack([AR @ Zr[0], AR @ Zr[2]])
