@@ -291,14 +291,19 @@ int bs_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, i
  * for callers that cannot call cudaMalloc/cudaFree, such as code whose
  * device memory is owned by another allocator that reserved it up front,
  * or pipelined code that cannot let cudaFree wait for the whole device.
- *   d, e, lam_out : DEVICE pointers with the layout of
- *                   bs_tridiag_eigenvalues (host pointers: BS_EINVAL).
- *   Limit: batch * 2n <= 1048576 (the scratch is a fixed 8 MiB array in the
+ *   d, e, lam_out : DEVICE pointers on the current device, with the layout
+ *                   of bs_tridiag_eigenvalues (host pointers or memory of
+ *                   another GPU: BS_EINVAL).
+ *   Limits: batch * 2n <= 1048576 (the scratch is a fixed 8 MiB array in the
  *   library's device image, held by every GPU that loads the library until
  *   the process exits); larger batches return BS_EINVAL - split them.
+ *   n <= (the device's opt-in shared memory per block) / 24 bytes, since
+ *   one matrix's tridiagonal is staged in shared memory: n <= 9685 on a
+ *   GB300 (227 KB); larger n returns BS_EINVAL.
  * The first call on a device looks up the array's device address with the
  * runtime (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
+ * capture.  First calls from several host threads at once are safe (the
+ * per-device address cache is atomic).  All calls share the one array and it keeps the last call's
  * contents, so calls that overlap on the GPU (different streams, or
  * different host threads) race: serialise them.  Asynchronous on `stream`.
  */
@@ -323,18 +328,16 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   certify) or
  *   NULL; host or device pointers.  The first call times the two tile
  *   edges of the per-step reduction per truncation group and keeps the
- *   faster (autotuning; the cluster-resident variant is only used when
- *   bs_batch_set_tile selects it).
+ *   faster (autotuning).
  * bs_batch_set_graph - on != 0: the next bs_batch_solve records the whole
  *   solve in a CUDA graph, later calls replay it (the Q and output pointers
  *   of the recording call must be reused); on == 0 drops the graph.
  * bs_batch_tiles - the reduction variant chosen for each truncation group
  *   and the group's eigen dimension n: 64 or 32 (tile edge of the
- *   per-step kernel) or 0 (the whole matrix resident in the shared memory
- *   of a thread-block cluster, n up to about 600).
- * bs_batch_set_tile - force that choice for every group (0, 32 or 64; 0
- *   falls back to 64 where n does not fit a cluster) or, with -1, return to
- *   timing all of them on the next solve.  Drops a recorded graph.
+ *   per-step kernel).
+ * bs_batch_set_tile - force that choice for every group (32 or 64) or,
+ *   with -1, return to timing both on the next solve (BS_EINVAL for any
+ *   other value).  Drops a recorded graph.
  * bs_batch_set_profiling / bs_batch_phase_times - with profiling on, a
  *   solve that does not replay a graph records CUDA events around each
  *   chunk's phases; phase_times returns milliseconds summed over chunks:

@@ -21,7 +21,7 @@ step by step, in the paper's notation, in float64 / complex128:
   * eigenproblem A U = lambda Omega U, A = H Phi^-1 H^*,
     omega = sqrt(lambda) ............................ Eq. (eigenvalueproblem)
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
   * subdomain = pixel, centroid = pixel centre, weight V / P^2;
   * H is 2N x 3N (rows u1, u2; columns S11, S22, S12) and H^* = H^dagger;
   * H uses the wavevector of the trial (column) plane wave;

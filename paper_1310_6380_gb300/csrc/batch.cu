@@ -55,6 +55,11 @@ bool dev_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// dst[0] |= src[0], dst[1] |= src[1]: a worker cell's status flags into the group's
+__global__ void or_flags_kernel(const int* __restrict__ src, int* __restrict__ dst) {
+  if (threadIdx.x < 2 && src[threadIdx.x]) atomicOr(dst + threadIdx.x, src[threadIdx.x]);
+}
+
 // rows [k][0..w) of src go to dst rows idx[k]: per-cell outputs back in caller order
 __global__ void scatter_rows_kernel(const double* __restrict__ src, const int* __restrict__ idx,
                                     int rows, int w, double* __restrict__ dst) {
@@ -143,6 +148,11 @@ struct BatchGroup {
   int* fbrow;
   zd* vec64;                  // FP64 solver: reduction vectors and partial sums
   zd* part64;
+  // [0] tensor-core pipeline timeout of a main-stream product, [1] a Gram
+  // Cholesky failed, [2] a tensor-core timeout during a cell's assembly
+  // (the workers' own flags are reset by every assembly, so each assembly's
+  // flags are OR-ed in here right after it)
+  int* d_err;
 };
 
 struct bs_batch {
@@ -209,7 +219,7 @@ static void free_group(BatchGroup& g) {
                 g.phase, g.X32, g.X64, g.CX, g.G, g.H, g.W, g.theta, g.cxA, g.cxB, g.cxD, g.cxeA,
                 g.cxeB, g.w, g.st, g.d_rowidx, g.d_Gall, g.lS, g.lCS, g.lA, g.lpart, g.lZ, g.lY,
                 g.lst, g.lndone, g.liters, g.lsig, g.lsc, g.liw, g.fbw,
-                g.fbst, g.fbrow, g.vec64, g.part64};
+                g.fbst, g.fbrow, g.vec64, g.part64, g.d_err};
   for (void* p : ps) cudaFree(p);
 }
 
@@ -281,6 +291,9 @@ static int alloc_group(BatchGroup& g, int nk, int nbands) {
   if (!r) r = balloc(&g.st, K, "batch status");
   if (!r) r = balloc(&g.d_rowidx, g.cells.size() * (size_t)nk, "batch row index");
   if (!r) r = balloc(&g.d_Gall, g.cells.size() * 2 * (size_t)g.N, "batch G vectors");
+  if (!r) r = balloc(&g.d_err, 3, "batch error flags");
+  if (!r && cudaMemset(g.d_err, 0, 3 * sizeof(int)) != cudaSuccess)
+    r = bs_cuda_status(cudaGetLastError(), "batch error flag");
   return r;
 }
 
@@ -355,6 +368,11 @@ static int assemble_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, int p) {
     const bool lob = B->solver == BS_SOLVER_LOBPCG;
     int r = load_cell(B, g, wk, c0 + i, ws);
     if (!r) r = bs_assemble(wk, ws);
+    if (!r) {
+      or_flags_kernel<<<1, 32, 0, ws>>>(wk->d_info, g.d_err + 1);
+      r = cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA;
+      if (r) bs_set_error("or_flags_kernel launch failed");
+    }
     if (!r && B->d_vec)
       r = cudaMemcpyAsync(g.lLinv + (size_t)i * g.N * g.N, wk->d_Linv + 2 * (size_t)g.N * g.N,
                           (size_t)g.N * g.N * sizeof(zd), cudaMemcpyDeviceToDevice, ws) == cudaSuccess
@@ -447,7 +465,7 @@ static int reduce_chunk_body(bs_batch* B, BatchGroup& g, int c0, int cn, int p, 
     memset(&w, 0, sizeof(w));
     w.C64 = g.C64; w.X64 = g.X64; w.CX = g.CX; w.G = g.G; w.H = g.H; w.W = g.W;
     w.theta = g.theta; w.lamT = nullptr; w.cxA = g.cxA; w.cxB = g.cxB; w.cxD = g.cxD;
-    w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
+    w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.d_err;
     CK(cudaMemsetAsync(g.st, 0, K * sizeof(int), s), "batch status");
     TRY_LAUNCH(bs_launch_rr_tail(w, n, K, B->nbands, lb, 1e-6, floor2, g.w, g.st, s));
     TRY_LAUNCH(bs_launch_inertia_check(g.C32, n, K, g.theta, lb, B->nbands, floor2, g.lsig, g.lsc,
@@ -486,7 +504,7 @@ static int reduce_chunk_body(bs_batch* B, BatchGroup& g, int c0, int cn, int p, 
   w.C64 = g.C64; w.C32 = g.C32; w.de = g.de; w.tau = g.tau; w.beta = g.beta; w.lamT = g.lamT;
   w.scratch = g.scr; w.Y = g.Y; w.phase = g.phase; w.X32 = g.X32; w.X64 = g.X64; w.CX = g.CX;
   w.G = g.G; w.H = g.H; w.W = g.W; w.theta = g.theta; w.cxA = g.cxA; w.cxB = g.cxB;
-  w.cxD = g.cxD; w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
+  w.cxD = g.cxD; w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.d_err;
   TRY_LAUNCH(bs_launch_mixed_refine(w, n, K, B->nbands, b, 1e-6, floor2, g.w, g.st, s));
   if (B->d_vec)
     TRY_LAUNCH(bs_launch_lob_vectors(g.X64, g.W, g.lLinv, (long)g.N * g.N, nk, g.N, g.M, B->vecMp, b,
@@ -878,18 +896,9 @@ static int tune_group(bs_batch* B, BatchGroup& g, double floor2, cudaStream_t s)
   const int cn = std::min(g.chunk, (int)g.cells.size());
   float best = 1e30f;
   int best_tile = 64;
-  // the cluster-resident variant (tile 0) is not timed here: measured 5x
-  // slower than the per-step kernel on ragged batches (n = 242..578), its
-  // steps are serial chains of cluster barriers; bs_batch_set_tile selects it
   for (int tile : {64, 32}) {
     CK(cudaEventRecord(e0, s), "tune");
-    const int r = run_chunk(B, g, 0, cn, floor2, s, tile);
-    if (r != BS_OK && tile == 0) {   // the cluster path could not be scheduled: skip it
-      cudaGetLastError();
-      cudaStreamSynchronize(s);
-      continue;
-    }
-    TRY_LAUNCH(r);
+    TRY_LAUNCH(run_chunk(B, g, 0, cn, floor2, s, tile));
     CK(cudaEventRecord(e1, s), "tune");
     CK(cudaEventSynchronize(e1), "tune");
     float ms = 0.f;
@@ -909,8 +918,8 @@ static int tune_group(bs_batch* B, BatchGroup& g, double floor2, cudaStream_t s)
 static void drop_graph(bs_batch* B);
 
 extern "C" int bs_batch_set_tile(bs_batch* B, int tile) {
-  if (!B || (tile != -1 && tile != 0 && tile != 32 && tile != 64)) {
-    bs_set_error("bs_batch_set_tile: NULL batch or tile not in {-1, 0, 32, 64}");
+  if (!B || (tile != -1 && tile != 32 && tile != 64)) {
+    bs_set_error("bs_batch_set_tile: NULL batch or tile not in {-1, 32, 64}");
     return BS_EINVAL;
   }
   drop_graph(B);
@@ -918,7 +927,7 @@ extern "C" int bs_batch_set_tile(bs_batch* B, int tile) {
     if (tile == -1) {
       g.tuned = false;
     } else {
-      g.tile = (tile == 0 && !bs_tridiag_cluster_fits(g.n)) ? 64 : tile;
+      g.tile = tile;
       g.tuned = true;
     }
   }
@@ -986,7 +995,7 @@ static int mixed_rescue(bs_batch* B, BatchGroup& g, int c0, const std::vector<in
   w.C64 = g.C64; w.C32 = g.C32; w.de = g.de; w.tau = g.tau; w.beta = g.beta; w.lamT = g.lamT;
   w.scratch = g.scr; w.Y = g.Y; w.phase = g.phase; w.X32 = g.X32; w.X64 = g.X64; w.CX = g.CX;
   w.G = g.G; w.H = g.H; w.W = g.W; w.theta = g.theta; w.cxA = g.cxA; w.cxB = g.cxB;
-  w.cxD = g.cxD; w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.workers[0]->d_info + 1;
+  w.cxD = g.cxD; w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.d_err;
   TRY_LAUNCH(bs_launch_mixed_refine(w, n, nf, B->nbands, g.b, 1e-6, floor2, g.fbw, g.fbst, s));
   scatter_rows_kernel<<<(nf * B->nbands + 255) / 256, 256, 0, s>>>(g.fbw, g.fbrow, nf,
                                                                    B->nbands, B->d_w);
@@ -1048,6 +1057,7 @@ static int solve_all(bs_batch* B, const std::vector<double>& floors, cudaStream_
   for (auto& g : B->groups) {
     double f2 = 1e300;
     for (int ci : g.cells) f2 = std::min(f2, floors[ci]);
+    CK(cudaMemsetAsync(g.d_err, 0, 3 * sizeof(int), s), "batch error flags");
     // chunk c + 1 is enqueued for assembly before chunk c is reduced, so the
     // workers build it while the main stream reduces (also when the
     // reduction waits on the host, as the LOBPCG progress checks do)
@@ -1133,15 +1143,14 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
        "bs_batch_solve status");
   if (!dev_ptr(omega_out) || (status_out && !dev_ptr(status_out))) {
     CK(cudaStreamSynchronize(s), "bs_batch_solve sync");
-    for (auto& g : B->groups)
-      for (int wi = 0; wi < g.nworkers; ++wi) {
-      int info[2] = {0, 0};
-      CK(cudaMemcpy(info, g.workers[wi]->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost), "info");
-      if (info[0]) {
+    for (auto& g : B->groups) {
+      int err[3] = {0, 0, 0};
+      CK(cudaMemcpy(err, g.d_err, 3 * sizeof(int), cudaMemcpyDeviceToHost), "info");
+      if (err[1]) {
         bs_set_error("bs_batch_solve: a Gram matrix was not positive definite");
         return BS_ENOTPD;
       }
-      if (info[1]) {
+      if (err[0] || err[2]) {
         bs_set_error("bs_batch_solve: a tensor-core pipeline wait reached its limit");
         return BS_ECUDA;
       }

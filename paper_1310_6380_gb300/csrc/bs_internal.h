@@ -266,13 +266,8 @@ int bs_launch_builder(const zd* Cm, int n, const double* Q, int nk, double q1x, 
 // (j+1, j) entry of the unitarily reduced (complex) tridiagonal.
 size_t bs_tridiag_vec_elems(int n);
 size_t bs_tridiag_part_elems(int n);
-// tridiag_cluster.cu: FP32 reduction with each matrix resident in one
-// cluster's shared memory (n up to ~600); same outputs as bs_launch_tridiag
-bool bs_tridiag_cluster_fits(int n);
-int bs_launch_tridiag_cluster(zf* A, int n, int batch, double* de, double* tau, zd* beta,
-                              cudaStream_t s);
 // tile: 64 (default) or 32 (tile edge of the fused update + matrix-vector
-// step); 0 (FP32 only): the cluster-resident kernel where n fits, else 64
+// step); 0 means 64
 template <typename R>
 int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
                       typename Cplx<R>::T* part, double* de, double* tau, zd* beta,

@@ -349,13 +349,6 @@ template <typename R>
 int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>::T* vec,
                       typename Cplx<R>::T* part, double* de, double* tau, zd* beta,
                       unsigned* count, cudaStream_t s, int tile) {
-  // tile 0: FP32 matrices small enough for a cluster's shared memory
-  if constexpr (sizeof(R) == 4) {
-    if (tile == 0) {
-      if (bs_tridiag_cluster_fits(n)) return bs_launch_tridiag_cluster(A, n, batch, de, tau, beta, s);
-      tile = 64;
-    }
-  }
   if (tile == 0) tile = 64;
   // The whole batch runs in every step launch.  (Reducing it in L2-sized
   // groups one after another was measured slower for FP32: the per-step

@@ -99,16 +99,19 @@ def test_batch_rejects_mixed_grids_and_fp64():
         bs.bs_batch_create([tuple(fp64)], 2, 4)
 
 
-def test_batch_cluster_reduction_matches_per_step_kernel():
-    """The cluster-resident FP32 reduction (tile 0) and the per-step kernel
-    (tile 64) give the same certified bands on every (cell, k)."""
+def test_batch_tile_edges_agree():
+    """Both tile edges of the per-step FP32 reduction (32 and 64) give the
+    same certified bands on every (cell, k); other tile values are refused."""
     cfgs = [cells.config3_cell(i) for i in range(20, 28)]
     nk, nb = 6, 10
     Qs = np.ascontiguousarray(np.stack([c["Q"][::5][:nk] for c in cfgs]))
     b = bs.bs_batch_create([_args(c["cell"], c["M"]) for c in cfgs], nk, nb)
     try:
+        with pytest.raises(bs.BSError) as ei:
+            bs.bs_batch_set_tile(b, 0)
+        assert ei.value.code == bs.BS_EINVAL
         out = {}
-        for tile in (0, 64):
+        for tile in (32, 64):
             bs.bs_batch_set_tile(b, tile)
             w = np.empty((len(cfgs), nk, nb))
             st = np.empty((len(cfgs), nk), np.int32)
@@ -117,10 +120,10 @@ def test_batch_cluster_reduction_matches_per_step_kernel():
             out[tile] = (w, st, fb, bs.bs_batch_tiles(b))
     finally:
         bs.bs_batch_destroy(b)
-    assert set(out[0][3].values()) == {0}
+    assert set(out[32][3].values()) == {32} and set(out[64][3].values()) == {64}
     for i, c in enumerate(cfgs):
-        assert omega_rel_err(out[0][0][i], out[64][0][i], omega_floor(c["cell"])).max() <= 2 * TOL
-    assert not out[0][1].any() and out[0][2].sum() <= 2
+        assert omega_rel_err(out[32][0][i], out[64][0][i], omega_floor(c["cell"])).max() <= 2 * TOL
+    assert not out[32][1].any() and not out[64][1].any()
 
 
 def test_batch_fp64_solver_matches_single_cell_fp64():

@@ -46,6 +46,7 @@ def test_static_matches_allocating_on_two_calls():
 
 
 def test_static_rejects_oversize_and_host_pointers():
+    # every case is rejected by the host-side checks before any copy or launch
     n, batch = 1000, 600                       # batch * 2n > 2^20
     d = torch.zeros((batch, n), dtype=torch.float64, device="cuda")
     e = torch.ones((batch, n - 1), dtype=torch.float64, device="cuda")
@@ -53,6 +54,14 @@ def test_static_rejects_oversize_and_host_pointers():
     with pytest.raises(bs.BSError) as ei:
         bs.bs_tridiag_eigenvalues_static(d, e, 4, out)
     assert ei.value.code == bs.BS_EINVAL and "fixed scratch" in str(ei.value)
+    # within the array, but one matrix's tridiagonal exceeds shared memory
+    n = 10000
+    d = torch.zeros((1, n), dtype=torch.float64, device="cuda")
+    e = torch.ones((1, n - 1), dtype=torch.float64, device="cuda")
+    out = torch.empty((1, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(bs.BSError) as ei:
+        bs.bs_tridiag_eigenvalues_static(d, e, 4, out)
+    assert ei.value.code == bs.BS_EINVAL and "shared memory" in str(ei.value)
     dh, eh = _tridiag(3, 2, 10)
     with pytest.raises(bs.BSError) as ei:
         bs.bs_tridiag_eigenvalues_static(dh, eh, 3, np.empty((2, 3)))
