@@ -24,27 +24,22 @@ namespace {
 constexpr int NB = 32;   // block size of the blocked factorisations
 
 // ---------------------------------------------------------------- Cholesky
-// Factor the diagonal block of panel j0 in shared memory (every CTA of the
-// panel does it); the CTA with blockIdx.x == 0 stores it, the others solve
-// their block row X := A_ij L_jj^-dagger.
-__global__ void chol_panel_kernel(zd* __restrict__ A, int n, long stride, int j0,
-                                  int* __restrict__ info) {
-  __shared__ zd L[NB][NB + 1];
-  __shared__ zd X[NB][NB + 1];
-  zd* a = A + (size_t)blockIdx.y * stride;
+// Blocked right-looking Cholesky, panels of NB columns.  The factor of a
+// diagonal block is computed and stored by exactly one CTA, in a launch
+// whose other CTAs do not read that block: the first block by
+// chol_diag_kernel, block j + 1 by the CTA of chol_update_kernel(j) that
+// owns it (it holds the block's last update).  chol_panel_kernel(j) then
+// reads the stored factor of block j, never a block being rewritten.
+
+// In-place Cholesky of the jb x jb lower triangle in shared memory; a
+// pivot that is not positive sets *info and is replaced by 1.
+__device__ void chol_block_smem(zd (*L)[NB + 1], int jb, int* info) {
   const int tid = threadIdx.x;
-  const int jb = min(NB, n - j0);
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e % NB, c = e / NB;
-    L[r][c] = (r < jb && c < jb && r >= c) ? a[(size_t)(j0 + r) + (size_t)(j0 + c) * n]
-                                           : zmake(0.0, 0.0);
-  }
-  __syncthreads();
   for (int c = 0; c < jb; ++c) {
     if (tid == 0) {
       double piv = L[c][c].x;
       if (!(piv > 0.0) || !isfinite(piv)) {
-        if (blockIdx.x == 0) atomicOr(info, 1);
+        atomicOr(info, 1);
         piv = 1.0;
       }
       L[c][c] = zmake(sqrt(piv), 0.0);
@@ -60,18 +55,49 @@ __global__ void chol_panel_kernel(zd* __restrict__ A, int n, long stride, int j0
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0) {
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      int r = e % NB, c = e / NB;
-      if (r < jb && c < jb && r >= c) a[(size_t)(j0 + r) + (size_t)(j0 + c) * n] = L[r][c];
-    }
-    return;
+}
+
+// load / store the lower triangle of the diagonal block at (j0, j0)
+__device__ void diag_load(const zd* a, int n, int j0, int jb, zd (*L)[NB + 1]) {
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int r = e % NB, c = e / NB;
+    L[r][c] = (r < jb && c < jb && r >= c) ? a[(size_t)(j0 + r) + (size_t)(j0 + c) * n]
+                                           : zmake(0.0, 0.0);
   }
-  const int i0 = j0 + NB * blockIdx.x;
+  __syncthreads();
+}
+__device__ void diag_store(zd* a, int n, int j0, int jb, const zd (*L)[NB + 1]) {
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int r = e % NB, c = e / NB;
+    if (r < jb && c < jb && r >= c) a[(size_t)(j0 + r) + (size_t)(j0 + c) * n] = L[r][c];
+  }
+}
+
+// the first diagonal block of each matrix
+__global__ void chol_diag_kernel(zd* __restrict__ A, int n, long stride, int* __restrict__ info) {
+  __shared__ zd L[NB][NB + 1];
+  zd* a = A + (size_t)blockIdx.x * stride;
+  const int jb = min(NB, n);
+  diag_load(a, n, 0, jb, L);
+  chol_block_smem(L, jb, info);
+  diag_store(a, n, 0, jb, L);
+}
+
+// block row i = j + 1 + blockIdx.x of panel j0: X L_jj^dagger = A_ij with
+// L_jj the stored factor of the diagonal block
+__global__ void chol_panel_kernel(zd* __restrict__ A, int n, long stride, int j0) {
+  __shared__ zd L[NB][NB + 1];
+  __shared__ zd X[NB][NB + 1];
+  zd* a = A + (size_t)blockIdx.y * stride;
+  const int tid = threadIdx.x;
+  const int jb = min(NB, n - j0);
+  const int i0 = j0 + NB * (blockIdx.x + 1);
   if (i0 >= n) return;
   const int ib = min(NB, n - i0);
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     int r = e % NB, c = e / NB;
+    L[r][c] = (r < jb && c < jb && r >= c) ? a[(size_t)(j0 + r) + (size_t)(j0 + c) * n]
+                                           : zmake(0.0, 0.0);
     X[r][c] = (r < ib && c < jb) ? a[(size_t)(i0 + r) + (size_t)(j0 + c) * n] : zmake(0.0, 0.0);
   }
   __syncthreads();
@@ -102,8 +128,11 @@ __device__ __forceinline__ void tri_index(int l, int& bi, int& bk) {
   bk = l - r * (r + 1) / 2;
 }
 
-// Trailing update A_ik -= L_ij L_kj^dagger for block rows i >= k > j.
-__global__ void chol_update_kernel(zd* __restrict__ A, int n, long stride, int j0) {
+// Trailing update A_ik -= L_ij L_kj^dagger for block rows i >= k > j; the
+// CTA of the first trailing diagonal block then factors that block (the
+// next panel's diagonal block, which no other CTA of this launch reads).
+__global__ void chol_update_kernel(zd* __restrict__ A, int n, long stride, int j0,
+                                   int* __restrict__ info) {
   __shared__ zd Li[NB][NB + 1];
   __shared__ zd Lk[NB][NB + 1];
   zd* a = A + (size_t)blockIdx.y * stride;
@@ -128,6 +157,13 @@ __global__ void chol_update_kernel(zd* __restrict__ A, int n, long stride, int j
       size_t o = (size_t)(i0 + r) + (size_t)(k0 + cc) * n;
       a[o] = zsub(a[o], acc);
     }
+  }
+  if (bi == 0 && bk == 0) {
+    __syncthreads();   // the block's updated entries, written by this CTA
+    const int nb = min(NB, n - i0);
+    diag_load(a, n, i0, nb, Li);
+    chol_block_smem(Li, nb, info);
+    diag_store(a, n, i0, nb, Li);
   }
 }
 
@@ -337,14 +373,15 @@ __global__ void monomial_kernel(const zd* __restrict__ Pp, int N, double V2, zd*
 
 int bs_launch_cholesky(zd* A, int n, int batch, long stride, int* info, cudaStream_t s) {
   const int nt = (n + NB - 1) / NB;
-  for (int j = 0; j < nt; ++j) {
-    chol_panel_kernel<<<dim3(nt - j, batch), 256, 0, s>>>(A, n, stride, j * NB, info);
-    BS_CHECK_LAUNCH("chol_panel_kernel");
+  chol_diag_kernel<<<batch, 256, 0, s>>>(A, n, stride, info);
+  BS_CHECK_LAUNCH("chol_diag_kernel");
+  for (int j = 0; j + 1 < nt; ++j) {
     const int rem = nt - j - 1;
-    if (rem > 0) {
-      chol_update_kernel<<<dim3(rem * (rem + 1) / 2, batch), 256, 0, s>>>(A, n, stride, j * NB);
-      BS_CHECK_LAUNCH("chol_update_kernel");
-    }
+    chol_panel_kernel<<<dim3(rem, batch), 256, 0, s>>>(A, n, stride, j * NB);
+    BS_CHECK_LAUNCH("chol_panel_kernel");
+    chol_update_kernel<<<dim3(rem * (rem + 1) / 2, batch), 256, 0, s>>>(A, n, stride, j * NB,
+                                                                        info);
+    BS_CHECK_LAUNCH("chol_update_kernel");
   }
   return BS_OK;
 }

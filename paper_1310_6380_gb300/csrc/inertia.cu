@@ -11,9 +11,10 @@
 // scaled matrix S (C - sigma I) S, S = diag(C)^-1/2 (congruence keeps the
 // inertia; the scaling evens out the rows).  A pivot smaller than 1e-5 of the
 // scaled unit diagonal makes the count unreliable and is reported as such.
-// Blocked right-looking, panels of 32: a panel kernel (diagonal block in
-// shared memory, then the block rows below) and a trailing-update kernel
-// over the lower-triangular tiles, for a batch of matrices.
+// Blocked right-looking, panels of 32: a panel kernel for the block rows
+// below each diagonal block and a trailing-update kernel over the
+// lower-triangular tiles (whose first tile's CTA also factors the next
+// diagonal block), for a batch of matrices.
 #include <float.h>
 #include <math.h>
 
@@ -78,28 +79,22 @@ __global__ void inertia_scale_kernel(zf* __restrict__ A, int n, const float* __r
   ak[e] = make_float2(v.x * s, v.y * s);
 }
 
-// Panel j0: every CTA factors the diagonal block A11 = L11 D1 L11^dagger in
-// shared memory; CTA 0 stores it (D on the diagonal) and counts the negative
-// pivots, the others form their block row L_i1 = A_i1 L11^-dagger D1^-1.
-__global__ void ldl_panel_kernel(zf* __restrict__ A, int n, int j0, int* __restrict__ neg,
-                                 int* __restrict__ flag) {
-  __shared__ zf L[NB][NB + 1];
-  __shared__ zf X[NB][NB + 1];
-  __shared__ float d[NB];
-  zf* a = A + (size_t)blockIdx.y * n * n;
-  const int tid = threadIdx.x, k = blockIdx.y;
-  const int jb = min(NB, n - j0);
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int r = e % NB, c = e / NB;
-    L[r][c] = (r < jb && c < jb && r >= c) ? a[(size_t)(j0 + r) + (size_t)(j0 + c) * n]
-                                           : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
+// Blocked right-looking LDL^dagger, panels of NB columns.  As in the FP64
+// Cholesky, each diagonal block is factored and stored by exactly one CTA,
+// in a launch whose other CTAs do not read it: the first by
+// ldl_diag_kernel, block j + 1 by the CTA of ldl_update_kernel(j) that
+// owns it.  That CTA also counts the block's negative pivots.
+
+// In-place A11 = L11 D1 L11^dagger of the jb x jb lower triangle in shared
+// memory (unit L11 below the diagonal, D1 in d); a pivot below TINY_PIVOT
+// in magnitude flags the count of matrix k as unreliable.
+__device__ void ldl_block_smem(zf (*L)[NB + 1], float* d, int jb, int* flag) {
+  const int tid = threadIdx.x;
   for (int c = 0; c < jb; ++c) {
     if (tid == 0) {
       float p = L[c][c].x;
       if (!(fabsf(p) >= TINY_PIVOT)) {
-        if (blockIdx.x == 0) flag[k] = 1;
+        *flag = 1;
         p = p < 0.f ? -TINY_PIVOT : TINY_PIVOT;
       }
       d[c] = p;
@@ -125,28 +120,60 @@ __global__ void ldl_panel_kernel(zf* __restrict__ A, int n, int j0, int* __restr
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0) {
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      const int r = e % NB, c = e / NB;
-      if (r < jb && c < jb && r >= c)
-        a[(size_t)(j0 + r) + (size_t)(j0 + c) * n] =
-            r == c ? make_float2(d[r], 0.f) : L[r][c];
-    }
-    if (tid == 0) {
-      int cnt = 0;
-      for (int c = 0; c < jb; ++c) cnt += d[c] < 0.f;
-      atomicAdd(neg + k, cnt);
-    }
-    return;
+}
+
+// load the lower triangle of the diagonal block at (j0, j0), factor it,
+// store L (strictly lower) and D (on the diagonal), add its negative pivots
+__device__ void ldl_diag(zf* a, int n, int j0, int k, zf (*L)[NB + 1], float* d, int* neg,
+                         int* flag) {
+  const int jb = min(NB, n - j0);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e % NB, c = e / NB;
+    L[r][c] = (r < jb && c < jb && r >= c) ? a[(size_t)(j0 + r) + (size_t)(j0 + c) * n]
+                                           : make_float2(0.f, 0.f);
   }
-  const int i0 = j0 + NB * blockIdx.x;
+  __syncthreads();
+  ldl_block_smem(L, d, jb, flag + k);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e % NB, c = e / NB;
+    if (r < jb && c < jb && r >= c)
+      a[(size_t)(j0 + r) + (size_t)(j0 + c) * n] = r == c ? make_float2(d[r], 0.f) : L[r][c];
+  }
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int c = 0; c < jb; ++c) cnt += d[c] < 0.f;
+    atomicAdd(neg + k, cnt);
+  }
+}
+
+__global__ void ldl_diag_kernel(zf* __restrict__ A, int n, int* __restrict__ neg,
+                                int* __restrict__ flag) {
+  __shared__ zf L[NB][NB + 1];
+  __shared__ float d[NB];
+  const int k = blockIdx.x;
+  ldl_diag(A + (size_t)k * n * n, n, 0, k, L, d, neg, flag);
+}
+
+// block row i = j + 1 + blockIdx.x of panel j0: L_i1 = A_i1 L11^-dagger D1^-1
+// from the stored factor of the diagonal block
+__global__ void ldl_panel_kernel(zf* __restrict__ A, int n, int j0) {
+  __shared__ zf L[NB][NB + 1];
+  __shared__ zf X[NB][NB + 1];
+  __shared__ float d[NB];
+  zf* a = A + (size_t)blockIdx.y * n * n;
+  const int tid = threadIdx.x;
+  const int jb = min(NB, n - j0);
+  const int i0 = j0 + NB * (blockIdx.x + 1);
   if (i0 >= n) return;
   const int ib = min(NB, n - i0);
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     const int r = e % NB, c = e / NB;
+    L[r][c] = (r < jb && c < jb && r > c) ? a[(size_t)(j0 + r) + (size_t)(j0 + c) * n]
+                                          : make_float2(0.f, 0.f);
     X[r][c] = (r < ib && c < jb) ? a[(size_t)(i0 + r) + (size_t)(j0 + c) * n]
                                  : make_float2(0.f, 0.f);
   }
+  if (tid < NB) d[tid] = tid < jb ? a[(size_t)(j0 + tid) * (n + 1)].x : 1.f;
   __syncthreads();
   // Y L11^dagger = A_i1 (unit L11), then L_i1 = Y D1^-1
   if (tid < ib) {
@@ -174,8 +201,10 @@ __device__ __forceinline__ void tile_of(int l, int& bi, int& bk) {
   bk = l - r * (r + 1) / 2;
 }
 
-// trailing update A_ik -= L_i1 D1 L_k1^dagger for block rows i >= k > panel
-__global__ void ldl_update_kernel(zf* __restrict__ A, int n, int j0) {
+// trailing update A_ik -= L_i1 D1 L_k1^dagger for block rows i >= k > panel;
+// the CTA of the first trailing diagonal block then factors that block
+__global__ void ldl_update_kernel(zf* __restrict__ A, int n, int j0, int* __restrict__ neg,
+                                  int* __restrict__ flag) {
   __shared__ zf Li[NB][NB + 1];
   __shared__ zf Lk[NB][NB + 1];
   __shared__ float d[NB];
@@ -208,6 +237,10 @@ __global__ void ldl_update_kernel(zf* __restrict__ A, int n, int j0) {
       a[o].x -= ax;
       a[o].y -= ay;
     }
+  }
+  if (bi == 0 && bk == 0) {
+    __syncthreads();   // the block's updated entries, written by this CTA
+    ldl_diag(a, n, i0, blockIdx.y, Li, d, neg, flag);
   }
 }
 
@@ -245,14 +278,14 @@ int bs_launch_inertia_check(zf* A, int n, int kb, const double* theta, int b, in
   inertia_scale_kernel<<<dim3((unsigned)((nn + 255) / 256), kb), 256, 0, s>>>(A, n, sigma, sc);
   BS_CHECK_LAUNCH("inertia_scale_kernel");
   const int nt = (n + NB - 1) / NB;
-  for (int j = 0; j < nt; ++j) {
-    ldl_panel_kernel<<<dim3(nt - j, kb), 256, 0, s>>>(A, n, j * NB, neg, flag);
-    BS_CHECK_LAUNCH("ldl_panel_kernel");
+  ldl_diag_kernel<<<kb, 256, 0, s>>>(A, n, neg, flag);
+  BS_CHECK_LAUNCH("ldl_diag_kernel");
+  for (int j = 0; j + 1 < nt; ++j) {
     const int rem = nt - j - 1;
-    if (rem > 0) {
-      ldl_update_kernel<<<dim3(rem * (rem + 1) / 2, kb), 256, 0, s>>>(A, n, j * NB);
-      BS_CHECK_LAUNCH("ldl_update_kernel");
-    }
+    ldl_panel_kernel<<<dim3(rem, kb), 256, 0, s>>>(A, n, j * NB);
+    BS_CHECK_LAUNCH("ldl_panel_kernel");
+    ldl_update_kernel<<<dim3(rem * (rem + 1) / 2, kb), 256, 0, s>>>(A, n, j * NB, neg, flag);
+    BS_CHECK_LAUNCH("ldl_update_kernel");
   }
   inertia_decide_kernel<<<(kb + 127) / 128, 128, 0, s>>>(neg, expect, flag, kb, stat, outcome);
   BS_CHECK_LAUNCH("inertia_decide_kernel");
