@@ -810,11 +810,13 @@ static int solve_chunk_lobpcg(bs_cell* c, int kb, int nbands, int b, const float
   m.cxeA = c->d_cxeA;
   m.cxeB = c->d_cxeB;
   m.err = c->d_info + 1;
+  m.csig = c->d_lsig;         // the count check's shift and expected count
+  m.cexp = c->d_liw + kb;
   CK(cudaMemsetAsync(c->d_stat, 0, kb * sizeof(int), s), "status");
   TRY(bs_launch_rr_tail(m, n, kb, nbands, b, c->tol, c->floor2, c->d_w, c->d_stat, s));
   // no eigenvalue skipped below the wanted ones (C32 is free after the iterations)
   TRY(bs_launch_inertia_check(c->d_C32, n, kb, c->d_theta, b, nbands, c->floor2, c->d_lsig,
-                              c->d_lsc, c->d_liw, c->d_stat, nullptr, s));
+                              c->d_lsc, c->d_liw, c->d_stat, nullptr, s, true));
   if (want_vec)
     TRY(bs_launch_lob_vectors(c->d_X64, c->d_W, c->d_Linv + 2 * (size_t)N * N, 0, kb, N, c->M, -1,
                               b, nbands, kb, nullptr, c->d_lvec, s));

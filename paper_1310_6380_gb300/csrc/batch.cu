@@ -466,10 +466,11 @@ static int reduce_chunk_body(bs_batch* B, BatchGroup& g, int c0, int cn, int p, 
     w.C64 = g.C64; w.X64 = g.X64; w.CX = g.CX; w.G = g.G; w.H = g.H; w.W = g.W;
     w.theta = g.theta; w.lamT = nullptr; w.cxA = g.cxA; w.cxB = g.cxB; w.cxD = g.cxD;
     w.cxeA = g.cxeA; w.cxeB = g.cxeB; w.err = g.d_err;
+    w.csig = g.lsig; w.cexp = g.liw + K;   // the count check's shift and expected count
     CK(cudaMemsetAsync(g.st, 0, K * sizeof(int), s), "batch status");
     TRY_LAUNCH(bs_launch_rr_tail(w, n, K, B->nbands, lb, 1e-6, floor2, g.w, g.st, s));
     TRY_LAUNCH(bs_launch_inertia_check(g.C32, n, K, g.theta, lb, B->nbands, floor2, g.lsig, g.lsc,
-                                       g.liw, g.st, nullptr, s));
+                                       g.liw, g.st, nullptr, s, true));
     if (B->d_vec)
       TRY_LAUNCH(bs_launch_lob_vectors(g.X64, g.W, g.lLinv, (long)g.N * g.N, nk, g.N, g.M, B->vecMp,
                                        lb, B->nbands, K, rows, B->d_vec, s));

@@ -275,28 +275,31 @@ int bs_launch_tridiag(typename Cplx<R>::T* A, int n, int batch, typename Cplx<R>
 
 // mixed.cu: FP32 reduction + FP64 Rayleigh-Ritz refinement
 struct MixedWs {
-  zd* C64;        // kb x n x n full Hermitian C(k)
-  zf* C32;        // kb x n x n, lower triangle; reflectors after the reduction
-  double* de;     // kb x 2n tridiagonal
-  double* tau;    // kb x n
-  zd* beta;       // kb x n
-  double* lamT;   // kb x (b+1) eigenvalues of T
-  double* scratch;// kb x b x 5n inverse-iteration factors
-  double* Y;      // kb x b x n tridiagonal eigenvectors
-  zd* phase;      // kb x n diagonal unitary scaling
-  zf* X32;        // kb x b x n back-transformed vectors (FP32)
-  zd* X64;        // kb x n x b (column-major) FP64 copy
-  zd* CX;         // kb x n x b
-  zd* G;          // kb x b x b
-  zd* H;          // kb x b x b
-  zd* W;          // kb x b x b Ritz coefficients
-  double* theta;  // kb x b Ritz values
-  uint16_t* cxA;  // C X digit planes and products (tensor cores)
-  uint16_t* cxB;
-  float* cxD;
-  int* cxeA;
-  int* cxeB;
-  int* err;       // tensor-core pipeline timeout flag
+  zd* C64 = nullptr;        // kb x n x n full Hermitian C(k)
+  zf* C32 = nullptr;        // kb x n x n, lower triangle; reflectors after the reduction
+  double* de = nullptr;     // kb x 2n tridiagonal
+  double* tau = nullptr;    // kb x n
+  zd* beta = nullptr;       // kb x n
+  double* lamT = nullptr;   // kb x (b+1) eigenvalues of T
+  double* scratch = nullptr;// kb x b x 5n inverse-iteration factors
+  double* Y = nullptr;      // kb x b x n tridiagonal eigenvectors
+  zd* phase = nullptr;      // kb x n diagonal unitary scaling
+  zf* X32 = nullptr;        // kb x b x n back-transformed vectors (FP32)
+  zd* X64 = nullptr;        // kb x n x b (column-major) FP64 copy
+  zd* CX = nullptr;         // kb x n x b
+  zd* G = nullptr;          // kb x b x b
+  zd* H = nullptr;          // kb x b x b
+  zd* W = nullptr;          // kb x b x b Ritz coefficients
+  double* theta = nullptr;  // kb x b Ritz values
+  uint16_t* cxA = nullptr;  // C X digit planes and products (tensor cores)
+  uint16_t* cxB = nullptr;
+  float* cxD = nullptr;
+  int* cxeA = nullptr;
+  int* cxeB = nullptr;
+  int* err = nullptr;       // tensor-core pipeline timeout flag
+  double* errb = nullptr;   // optional: kb x nbands certified error bounds of theta
+  float* csig = nullptr;    // LOBPCG tail: kb count shifts chosen by the certificate
+  int* cexp = nullptr;      // and the eigenvalue counts expected below them (-1: none)
 };
 #define BS_MIXED_MAX_BANDS 24
 int bs_mixed_guard(int nbands, int n);
@@ -353,13 +356,40 @@ int bs_launch_lob_export(const LobWs& w, int n, int kb, int b, zd* X64, int* ite
 // |alpha|, |beta| <= Mp, 2 (2Mp+1)^2 per vector
 int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int M, int Mp, int kb, int nvec,
                              float2* y, cudaStream_t s);
+// Shift of the eigenvalue-count certificate in the gap above Ritz value i
+// (theta ascending, FP64): usable when theta_{i+1} - theta_i >= 2e-3 of its
+// size; sigma sits in that gap, at most 1% above theta_i, rounded to FP32
+// (the precision of the count), and i + 1 eigenvalues should lie below it.
+__host__ __device__ inline bool bs_shift_at(const double* t, int i, double floor2, float* sigma) {
+  const double g = t[i + 1] - t[i];
+  if (!(g == g && g < 1e308 && g >= 2e-3 * (t[i + 1] > floor2 ? t[i + 1] : floor2))) return false;
+  const double h = 0.02 * (t[i] > floor2 ? t[i] : floor2);
+  *sigma = (float)(t[i] + 0.5 * (g < h ? g : h));
+  return true;
+}
+// The default shift: the highest usable gap with i in [nb - 1, b - 2];
+// *expect = i + 1, or -1 (returns false) when there is none.
+__host__ __device__ inline bool bs_count_shift(const double* t, int b, int nb, double floor2,
+                                               float* sigma, int* expect) {
+  for (int i = b - 2; i >= nb - 1; --i)
+    if (bs_shift_at(t, i, floor2, sigma)) {
+      *expect = i + 1;
+      return true;
+    }
+  *sigma = 0.f;
+  *expect = -1;
+  return false;
+}
 // inertia.cu: eigenvalue-count certificate (FP32 LDL^dagger of the scaled
 // C - sigma I, sigma in a gap above the wanted Ritz values); A (lower part of
 // C(k), overwritten), sigma (kb), sc (kb x n) floats and iwork (3 kb ints)
 // scratch; stat[k] = BS_ENOCONV where the count fails; outcome optional
+// shift_given: sigma (kb) and iwork[kb..2kb) (expected counts, -1 for none)
+// are already set (by the residual certificate of the Rayleigh-Ritz tail,
+// which picks the cut), else they are taken from bs_count_shift
 int bs_launch_inertia_check(zf* A, int n, int kb, const double* theta, int b, int nb,
                             double floor2, float* sigma, float* sc, int* iwork, int* stat,
-                            int* outcome, cudaStream_t s);
+                            int* outcome, cudaStream_t s, bool shift_given = false);
 // dense FP64 solve of nf host wavevectors on an assembled cell (host outputs)
 int bs_cell_dense_fp64(bs_cell* c, const double* Q, int nf, int nbands, double* om, int* st,
                        cudaStream_t s);
@@ -370,8 +400,10 @@ int bs_launch_lob_vectors(const zd* X64, const zd* Wc, const zd* LinvR, long lst
                           int N, int M, int Mp, int b, int nbands, int kb, const int* rows,
                           float2* out, cudaStream_t s);
 // mixed.cu: the FP64 Rayleigh-Ritz tail on a given FP64 block X64 (CX, G, H,
-// small eigenproblem, residual bound); gap reference lambda_{b+1} of T
-// (lamT) or, when lamT is null, the largest Ritz value of the block
+// small eigenproblem, Lehmann lower bounds from the residual Gram); the
+// bound on the next eigenvalue comes from the eigenvalues of T (lamT) or,
+// when lamT is null, from the shift of the count certificate, which the
+// caller must then run (bs_launch_inertia_check)
 int bs_launch_rr_tail(const MixedWs& w, int n, int kb, int nbands, int b, double tol,
                       double floor2, double* omega, int* stat, cudaStream_t s);
 

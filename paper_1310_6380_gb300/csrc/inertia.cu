@@ -25,34 +25,18 @@ namespace {
 constexpr int NB = 32;
 constexpr float TINY_PIVOT = 1e-5f;
 
-// sigma and the expected count per k from the FP64 Ritz values theta
-// (b ascending per k): the first index i >= nb - 1 whose gap to the next Ritz
-// value is at least 2e-3 of its size; sigma in that gap (at most 1% above
-// theta_i), expected count i + 1.  No usable gap: flag (count unreliable).
+// sigma and the expected count per k (bs_count_shift); no usable gap: flag
+// (count unreliable)
 __global__ void inertia_shift_kernel(const double* __restrict__ theta, int b, int nb, int kb,
                                      double floor2, float* __restrict__ sigma,
-                                     int* __restrict__ expect, int* __restrict__ flag) {
+                                     int* __restrict__ expect, int* __restrict__ flag,
+                                     bool given) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= kb) return;
-  const double* t = theta + (size_t)k * b;
-  int pick = -1;
-  for (int i = nb - 1; i < b - 1; ++i) {
-    const double g = t[i + 1] - t[i];
-    if (isfinite(g) && g >= 2e-3 * fmax(t[i + 1], floor2)) {
-      pick = i;
-      break;
-    }
-  }
-  if (pick < 0) {
-    sigma[k] = 0.f;
-    expect[k] = -1;
-    flag[k] = 1;
-    return;
-  }
-  const double g = t[pick + 1] - t[pick];
-  sigma[k] = (float)(t[pick] + 0.5 * fmin(g, 0.02 * fmax(t[pick], floor2)));
-  expect[k] = pick + 1;
-  flag[k] = 0;
+  if (given)
+    flag[k] = expect[k] < 0 ? 1 : 0;
+  else
+    flag[k] = bs_count_shift(theta + (size_t)k * b, b, nb, floor2, sigma + k, expect + k) ? 0 : 1;
 }
 
 // sc[k][r] = diag(C)_r^-1/2
@@ -263,12 +247,12 @@ __global__ void inertia_decide_kernel(const int* __restrict__ neg, const int* __
 // (optional, kb) 0 ok, 1 count mismatch, 2 unreliable.
 int bs_launch_inertia_check(zf* A, int n, int kb, const double* theta, int b, int nb,
                             double floor2, float* sigma, float* sc, int* iwork, int* stat,
-                            int* outcome, cudaStream_t s) {
+                            int* outcome, cudaStream_t s, bool shift_given) {
   int* neg = iwork;
   int* expect = iwork + kb;
   int* flag = iwork + 2 * kb;
   inertia_shift_kernel<<<(kb + 127) / 128, 128, 0, s>>>(theta, b, nb, kb, floor2, sigma, expect,
-                                                        flag);
+                                                        flag, shift_given);
   BS_CHECK_LAUNCH("inertia_shift_kernel");
   cudaError_t e = cudaMemsetAsync(neg, 0, kb * sizeof(int), s);
   if (e != cudaSuccess) return bs_cuda_status(e, "inertia counters");

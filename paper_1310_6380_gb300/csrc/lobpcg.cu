@@ -1056,15 +1056,16 @@ __global__ void __launch_bounds__(UT, 2) lob_update_kernel(LobWs w, int n, int k
     int na = 0;
     unsigned mask = 0u;
     float rmax = 0.f;
-    const float top = st.theta[b - 1];
+    // the FP64 certificate bounds the error of theta_c by about
+    // ||r_c||^2 / (rho - theta_c), rho a shift in a gap near the block's top
+    // (at most theta_{b-2} + 1%), against 2 tolb max(theta_c, floor2): wanted
+    // columns meet that with theta_{b-2} for rho and a factor 8 to spare
+    const float top = st.theta[b - 2];
     for (int c = 0; c < b; ++c) {
       const float scale = fmaxf(fabsf(st.theta[c]), floor2);
       const float ratio = sqrtf(rn2[c]) / scale;
-      // wanted columns must also meet the residual bound the FP64 stage
-      // checks, ||r||^2 / (theta_top - theta) <= 2 tolb max(theta, floor2),
-      // with a factor 4 to spare
       const bool ok = ratio <= tol &&
-                      (c >= nb || rn2[c] <= 0.5f * tolb * scale * fmaxf(top - st.theta[c], 0.f));
+                      (c >= nb || rn2[c] <= 0.25f * tolb * scale * fmaxf(top - st.theta[c], 0.f));
       if (c < nb) {
         wanted = wanted && ok;
         rmax = fmaxf(rmax, ratio);

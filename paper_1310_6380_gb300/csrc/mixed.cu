@@ -8,12 +8,14 @@
 //   T --FP64 inverse iteration + MGS--> y_1..y_b
 //   y --phases of beta, FP32 reflectors--> X (n x b)
 //   X --FP64: C X, X^dagger X, X^dagger C X, Cholesky + Jacobi--> Ritz pairs
-//   Ritz pairs --FP64 residual ||C x - theta x||--> error bound and status
+//   Ritz pairs --FP64 residuals R, E = R^dagger R--> Lehmann lower bounds
 //
 // b = nbands + guard vectors, so clusters at the edge of the wanted band
-// stay inside the subspace.  The bound |theta - lambda| <= ||r||^2 / gap
-// (gap = distance to lambda_{b+1} of T) is checked against the requested
-// tolerance; wavevectors that miss it are reported with BS_ENOCONV.
+// stay inside the subspace.  Each Ritz value is an upper bound of its
+// eigenvalue; Lehmann's method (certify_kernel) gives a lower bound from
+// E and a bound rho on the next eigenvalue (from T's eigenvalues), and the
+// difference is checked against the requested tolerance; wavevectors that
+// miss it are reported with BS_ENOCONV.
 #include <float.h>
 #include <math.h>
 
@@ -437,45 +439,319 @@ __global__ void small_eig_kernel(const zd* __restrict__ Gg, const zd* __restrict
   if (tid == 0 && fail) stat[k] = BS_ENOTPD;
 }
 
-// ------------------------------------------------------------ residuals and output
-// r_i = C X w_i - theta_i X w_i; bound_i = ||r_i||^2 / (lambda_{b+1}(T) - theta_i).
-__global__ void residual_kernel(const zd* __restrict__ CX, const zd* __restrict__ X,
-                                const zd* __restrict__ W, const double* __restrict__ theta,
-                                const double* __restrict__ lamT, int lstride, int n, int b,
-                                int nbands, double tol, double floor2, double* __restrict__ omega,
-                                int* __restrict__ stat) {
-  __shared__ int bad;
-  const int k = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  const zd* cx = CX + (size_t)k * n * b;
-  const zd* x = X + (size_t)k * n * b;
-  const zd* w = W + (size_t)k * b * b;
-  // lambda_{b+1} of T, or (no T: the LOBPCG block) the largest Ritz value,
-  // which lies at or below lambda_{b+1} once the block has converged
-  const double gapref = lamT ? lamT[(size_t)k * lstride + b] : theta[(size_t)k * b + b - 1];
-  for (int i = warp; i < nbands; i += nw) {
-    const double th = theta[(size_t)k * b + i];
-    double s2 = 0.0;
-    for (int r = lane; r < n; r += 32) {
-      zd acc = zmake(0.0, 0.0);
-      for (int l = 0; l < b; ++l) {
-        const zd wl = w[l + (size_t)i * b];
-        acc = zfma(zsub(cx[r + (size_t)l * n], zscale(x[r + (size_t)l * n], th)), wl, acc);
-      }
-      s2 = fma(acc.x, acc.x, fma(acc.y, acc.y, s2));
+// ------------------------------------------------------------ certificate
+// Guaranteed lower bounds for the lowest eigenvalues from the Rayleigh-Ritz
+// data, by Lehmann's method.  The Ritz vectors y_i = X w_i (i < m) are
+// orthonormal with Ritz values theta_i and residuals r_i = C y_i - theta_i y_i
+// (orthogonal to every y_j); let E = R^dagger R.  For any rho with
+// theta_i < rho <= lambda_{m+1}(C), the Rayleigh-Ritz method applied to
+// (C - rho)^-1 on the trial space (C - rho) span(Y) gives the Ritz values
+// -1/nu_i, with nu_1 <= ... <= nu_m the eigenvalues of
+//     K = D + D^-1/2 E D^-1/2,   D = diag(rho - theta_i),
+// and, (C - rho)^-1 having exactly m eigenvalues 1/(lambda_j - rho) < 0,
+// min-max turns them into  lambda_{m+1-i} >= rho - nu_i.  Only the distance
+// of each Ritz value to rho enters: a cluster of close Ritz values inside
+// the block needs no gap of its own.  Upper bounds are the Ritz values
+// themselves (lambda_i <= theta_i), so theta_j - (rho - nu_{m+1-j}) bounds
+// the error of theta_j.
+//
+// rho comes from an eigenvalue count: the Sturm count of the FP32
+// tridiagonal T of the mixed path (rho from lambda_{m+1}(T)) or the FP32
+// LDL^dagger count of the LOBPCG path (rho = its shift sigma, m = the
+// expected count, which that check verifies).  Both counts are exact for an
+// FP32 perturbation of C(k); the margin 2^-20 max_r C_rr subtracted from rho
+// covers that perturbation (FP32 rounding of C and of the reduction).
+
+constexpr int RCH = 8;   // rows of C X and X staged per step of the residual Gram
+
+// Hermitian eigenvalues of the m x m matrix K (shared, row stride BMAX + 1)
+// by cyclic Jacobi with the round-robin pairing of small_eig_kernel; m even
+// (callers pad with a decoupled zero); eigenvalues left on the diagonal.
+__device__ void jacobi_eigenvalues(zd (*K)[BMAX + 1], int m, double* red) {
+  __shared__ double cs_[BMAX / 2], sn_[BMAX / 2];
+  __shared__ zd ph_[BMAX / 2];
+  __shared__ int pp_[BMAX / 2], qq_[BMAX / 2];
+  __shared__ double offn, totn;
+  const int tid = threadIdx.x, nt = blockDim.x, np = m / 2;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double o = 0.0, t = 0.0;
+    for (int e = tid; e < m * m; e += nt) {
+      const int r = e % m, c = e / m;
+      const double m2 = K[r][c].x * K[r][c].x + K[r][c].y * K[r][c].y;
+      t += m2;
+      if (r != c) o += m2;
     }
-    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    if (lane == 0) {
-      const double gap = fmax(gapref - th, 1e-300);
-      const double bound = s2 / gap;
-      if (!(bound <= tol * 2.0 * fmax(th, floor2)) || !isfinite(th)) atomicOr(&bad, 1);
-      omega[(size_t)k * nbands + i] = sqrt(fmax(th, 0.0));
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      o += __shfl_xor_sync(0xffffffffu, o, sh);
+      t += __shfl_xor_sync(0xffffffffu, t, sh);
+    }
+    if ((tid & 31) == 0) {
+      red[2 * (tid >> 5)] = o;
+      red[2 * (tid >> 5) + 1] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double so = 0.0, st = 0.0;
+      for (int w = 0; w < nt / 32; ++w) {
+        so += red[2 * w];
+        st += red[2 * w + 1];
+      }
+      offn = so;
+      totn = st;
+    }
+    __syncthreads();
+    if (offn <= 1e-26 * totn) break;
+    for (int rd = 0; rd < m - 1; ++rd) {
+      if (tid < np) {
+        int p, q;
+        if (tid == 0) {
+          p = rd % (m - 1);
+          q = m - 1;
+        } else {
+          p = (rd + tid) % (m - 1);
+          q = (rd - tid + (m - 1)) % (m - 1);
+        }
+        if (p > q) {
+          const int tq = p;
+          p = q;
+          q = tq;
+        }
+        const zd c = K[p][q];
+        const double ca = hypot(c.x, c.y);
+        double cs = 1.0, sn = 0.0;
+        zd ph = zmake(1.0, 0.0);
+        if (ca > 0.0) {
+          ph = zmake(c.x / ca, c.y / ca);
+          const double zeta = (K[q][q].x - K[p][p].x) / (2.0 * ca);
+          const double tt = zeta >= 0.0 ? 1.0 / (zeta + sqrt(1.0 + zeta * zeta))
+                                        : -1.0 / (-zeta + sqrt(1.0 + zeta * zeta));
+          cs = 1.0 / sqrt(1.0 + tt * tt);
+          sn = tt * cs;
+        }
+        pp_[tid] = p;
+        qq_[tid] = q;
+        cs_[tid] = cs;
+        sn_[tid] = sn;
+        ph_[tid] = ph;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * m; e += nt) {
+        const int u = e / m, r = e % m, p = pp_[u], q = qq_[u];
+        const double cs = cs_[u], sn = sn_[u];
+        const zd ap = K[r][p], aq = zmul(K[r][q], zconj(ph_[u]));
+        K[r][p] = zsub(zscale(ap, cs), zscale(aq, sn));
+        K[r][q] = zadd(zscale(ap, sn), zscale(aq, cs));
+      }
+      __syncthreads();
+      for (int e = tid; e < np * m; e += nt) {
+        const int u = e / m, c = e % m, p = pp_[u], q = qq_[u];
+        const double cs = cs_[u], sn = sn_[u];
+        const zd ap = K[p][c], aq = zmul(K[q][c], ph_[u]);
+        K[p][c] = zsub(zscale(ap, cs), zscale(aq, sn));
+        K[q][c] = zadd(zscale(ap, sn), zscale(aq, cs));
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Lehmann lower bounds of the wanted eigenvalues for one cut (m Ritz
+// vectors, bound rho on lambda_{m+1}); lower[j] = max(lower[j], bound).
+__device__ void lehmann_cut(const double* th, zd (*E)[BMAX + 1], zd (*K)[BMAX + 1], int m,
+                            double rho, int nbands, double* lower, double* red, double* nu) {
+  const int tid = threadIdx.x;
+  const int me = m + (m & 1);   // even size for the round-robin sweeps
+  for (int e = tid; e < me * me; e += blockDim.x) {
+    const int r = e % me, c = e / me;
+    zd v = zmake(0.0, 0.0);
+    if (r < m && c < m) {
+      const double dr = rho - th[r], dc = rho - th[c];
+      v = zscale(E[r][c], 1.0 / sqrt(dr * dc));
+      if (r == c) v = zmake(v.x + dr, 0.0);
+    }
+    K[r][c] = v;
+  }
+  __syncthreads();
+  jacobi_eigenvalues(K, me, red);
+  if (tid == 0) {
+    // ascending eigenvalues of K; the padding zero (if any) is the smallest
+    for (int i = 0; i < me; ++i) nu[i] = K[i][i].x;
+    for (int i = 1; i < me; ++i) {
+      const double v = nu[i];
+      int j = i - 1;
+      while (j >= 0 && nu[j] > v) {
+        nu[j + 1] = nu[j];
+        --j;
+      }
+      nu[j + 1] = v;
+    }
+    const int off = me - m;
+    // lambda_{j+1} >= rho - nu_(m - j)  (0-based j, ascending nu of the m real ones)
+    for (int j = 0; j < nbands && j < m; ++j) {
+      const double lb = rho - nu[off + m - 1 - j];
+      if (lb == lb) lower[j] = fmax(lower[j], lb);
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && stat[k] == 0 && bad) stat[k] = BS_ENOCONV;
+}
+
+// One CTA (256 threads) per problem: the residual Gram E = R^dagger R of the
+// Ritz vectors (R = C X W - X W Theta, from the FP64 C X), then the Lehmann
+// bounds for up to two cuts and the status: certified when every wanted
+// theta_j is within 2 tol max(theta_j, floor2) of its lower bound.
+__global__ void __launch_bounds__(256) certify_kernel(
+    const zd* __restrict__ C64, const zd* __restrict__ CX, const zd* __restrict__ X,
+    const zd* __restrict__ W, const double* __restrict__ theta, const double* __restrict__ lamT,
+    int lstride, int n, int b, int nbands, double tol, double floor2, double* __restrict__ omega,
+    int* __restrict__ stat, double* __restrict__ errb, float* __restrict__ csig,
+    int* __restrict__ cexp) {
+  __shared__ zd Ws[BMAX][BMAX + 1];        // W, later K
+  __shared__ zd Es[BMAX][BMAX + 1];        // E
+  __shared__ zd CXs[RCH][BMAX + 1], Xs[RCH][BMAX + 1];
+  __shared__ double th[BMAX], lower[BMAX], nu[BMAX + 1], red[16];
+  __shared__ double cmax_s;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const zd* cx = CX + (size_t)k * n * b;
+  const zd* x = X + (size_t)k * n * b;
+  const zd* wk = W + (size_t)k * b * b;
+  for (int e = tid; e < b * b; e += blockDim.x) Ws[e % b][e / b] = wk[e];
+  if (tid < b) {
+    th[tid] = theta[(size_t)k * b + tid];
+    lower[tid] = -1e300;
+  }
+  // max_r C_rr: the scale of the FP32 perturbation margin
+  double cm = 0.0;
+  for (int r = tid; r < n; r += blockDim.x)
+    cm = fmax(cm, C64[(size_t)k * n * n + (size_t)r * n + r].x);
+  for (int o = 16; o > 0; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+  if ((tid & 31) == 0) red[tid >> 5] = cm;
+  __syncthreads();
+  if (tid == 0) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v = fmax(v, red[w]);
+    cmax_s = v;
+  }
+  // residual Gram: thread t owns entries p = t, t + 256, ... of the b x b E
+  zd acc[(BMAX * BMAX + 255) / 256];
+#pragma unroll
+  for (int q = 0; q < (BMAX * BMAX + 255) / 256; ++q) acc[q] = zmake(0.0, 0.0);
+  const int rr = tid / 32, ci = tid % 32;   // staging: row rr, column ci of the chunk
+  for (int r0 = 0; r0 < n; r0 += RCH) {
+    __syncthreads();
+    if (ci < b) {
+      const int r = r0 + rr;
+      CXs[rr][ci] = r < n ? cx[(size_t)ci * n + r] : zmake(0.0, 0.0);
+      Xs[rr][ci] = r < n ? x[(size_t)ci * n + r] : zmake(0.0, 0.0);
+    }
+    __syncthreads();
+    // R[rr][ci] = sum_l (CX[rr][l] - theta_ci X[rr][l]) W[l][ci]
+    zd rv = zmake(0.0, 0.0);
+    if (ci < b) {
+      const double t = th[ci];
+      for (int l = 0; l < b; ++l)
+        rv = zfma(zsub(CXs[rr][l], zscale(Xs[rr][l], t)), Ws[l][ci], rv);
+    }
+    __syncthreads();
+    if (ci < b) CXs[rr][ci] = rv;   // the chunk of R replaces the chunk of C X
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < (BMAX * BMAX + 255) / 256; ++q) {
+      const int p = tid + 256 * q;
+      if (p < b * b) {
+        const int i = p % b, j = p / b;
+        zd a = acc[q];
+        for (int u = 0; u < RCH; ++u) a = zfma(zconj(CXs[u][i]), CXs[u][j], a);
+        acc[q] = a;
+      }
+    }
+  }
+  __syncthreads();
+  // the FP64 product C X carries an error of order 2^-41 |C| |X| per entry:
+  // allow for it in the residual norms (a negligible widening)
+  const double ecx = 0x1p-36 * cmax_s;
+#pragma unroll
+  for (int q = 0; q < (BMAX * BMAX + 255) / 256; ++q) {
+    const int p = tid + 256 * q;
+    if (p < b * b) {
+      const int i = p % b, j = p / b;
+      zd v = acc[q];
+      if (i == j) v = zmake(v.x + ecx * ecx * n, 0.0);
+      Es[i][j] = v;
+    }
+  }
+  __syncthreads();
+  const double margin = 0x1p-20 * cmax_s;
+  if (lamT) {
+    // cuts where T's spectrum has a gap above the m-th Ritz value, rho just
+    // below lambda_{m+1}(T): the highest and the lowest such m in
+    // [nbands, b] (degenerate eigenvalues rule out the cuts inside a multiplet)
+    const double* lt = lamT + (size_t)k * lstride;
+    int mhi = 0, mlo = 0;
+    for (int m = b; m >= nbands; --m)
+      if (lt[m] - margin > th[m - 1]) {
+        if (!mhi) mhi = m;
+        mlo = m;
+      }
+    if (mhi) lehmann_cut(th, Es, Ws, mhi, lt[mhi] - margin, nbands, lower, red, nu);
+    if (mlo && mlo != mhi) lehmann_cut(th, Es, Ws, mlo, lt[mlo] - margin, nbands, lower, red, nu);
+  } else if (csig) {
+    // The count certificate checks one shift sigma per problem; choose it
+    // here: the cuts i = b - 2 .. nbands - 1 with a usable gap (bs_shift_at),
+    // top-down, each with its own Lehmann bounds (Ritz vectors above a cut
+    // do not enter, so poorly converged guard vectors can be left out); the
+    // first cut that certifies every wanted band, else the one with the
+    // smallest worst ratio of error bound to tolerance.
+    __shared__ double lowc[BMAX], ratio_s;
+    __shared__ float best_sig;
+    __shared__ int best_m;
+    double best = 1e300;
+    if (tid == 0) {
+      best_sig = 0.f;
+      best_m = -1;
+    }
+    for (int i = b - 2; i >= nbands - 1; --i) {
+      float sig;
+      if (!bs_shift_at(th, i, floor2, &sig)) continue;
+      const double rho = (double)sig - margin;
+      if (!(rho > th[i])) continue;
+      if (tid < BMAX) lowc[tid] = -1e300;
+      __syncthreads();
+      lehmann_cut(th, Es, Ws, i + 1, rho, nbands, lowc, red, nu);
+      if (tid == 0) {
+        double r = 0.0;
+        for (int j = 0; j < nbands; ++j)
+          r = fmax(r, (th[j] - lowc[j]) / (tol * 2.0 * fmax(th[j], floor2)));
+        ratio_s = r == r ? r : 1e300;
+      }
+      __syncthreads();
+      const double r = ratio_s;
+      if (r < best) {
+        best = r;
+        if (tid < nbands) lower[tid] = lowc[tid];
+        if (tid == 0) {
+          best_sig = sig;
+          best_m = i + 1;
+        }
+      }
+      __syncthreads();
+      if (best <= 1.0) break;
+    }
+    if (tid == 0 && csig) {
+      csig[k] = best_sig;
+      cexp[k] = best_m;
+    }
+  }
+  if (tid == 0) {
+    int bad = 0;
+    for (int j = 0; j < nbands; ++j) {
+      const double t = th[j];
+      const double err = t - lower[j];
+      if (!(err <= tol * 2.0 * fmax(t, floor2)) || !isfinite(t)) bad = 1;
+      omega[(size_t)k * nbands + j] = sqrt(fmax(t, 0.0));
+      if (errb) errb[(size_t)k * nbands + j] = err;
+    }
+    if (stat[k] == 0 && bad) stat[k] = BS_ENOCONV;
+  }
 }
 
 // C32 (lower triangle, FP32) from the full FP64 C, batch of kb
@@ -549,8 +825,8 @@ int bs_launch_rr_tail(const MixedWs& w, int n, int kb, int nbands, int b, double
                              w.H, b, bb, kb, 0, s));
   small_eig_kernel<<<kb, 128, 0, s>>>(w.G, w.H, b, w.theta, w.W, stat);
   BS_CHECK_LAUNCH("small_eig_kernel");
-  residual_kernel<<<kb, 256, 0, s>>>(w.CX, w.X64, w.W, w.theta, w.lamT, b + 1, n, b, nbands, tol,
-                                     floor2, omega, stat);
-  BS_CHECK_LAUNCH("residual_kernel");
+  certify_kernel<<<kb, 256, 0, s>>>(w.C64, w.CX, w.X64, w.W, w.theta, w.lamT, b + 1, n, b,
+                                    nbands, tol, floor2, omega, stat, w.errb, w.csig, w.cexp);
+  BS_CHECK_LAUNCH("certify_kernel");
   return BS_OK;
 }
