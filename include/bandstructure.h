@@ -179,7 +179,9 @@ int bs_assemble(bs_cell* cell, void* stream);
  *              (Eq. (eigenvalueproblem)); host or device.
  *   status_out: nk ints (0 = converged) or NULL; host or device.
  * Requires bs_assemble first (BS_ESTATE otherwise); 1 <= nbands <= 2N.
- * Asynchronous when every output is a device pointer.
+ * Asynchronous when every output is a device pointer.  Otherwise it
+ * synchronises `stream` and returns BS_ENOCONV when a wavevector did not
+ * converge (its status entry, if status_out is given, says which).
  */
 int bs_solve_k(bs_cell* cell, const double* Q, int nk, int nbands,
                double* omega_out, int* status_out, void* stream);
@@ -232,6 +234,22 @@ int bs_bands(bs_cell* cell, int path, int nk, int nbands,
 int bs_solve_k_lobpcg(bs_cell* cell, const double* Q, int nk, int nbands,
                       const float* X0, int nvec, double* omega_out, int* status_out,
                       int* iters_out, int* fallback_out, float* vec_out, void* stream);
+
+/*
+ * bs_set_iteration_limits - the iteration caps of the iterative steps, for
+ * tests and diagnostics (the paper has no counterpart; its eigensolve is a
+ * direct one).  lobpcg_maxit: LOBPCG iterations per wavevector (default
+ * BS_LOB_MAXIT, at most 1000); bisect_sweeps: FP64 multisection sweeps per
+ * eigenvalue of the Sturm bisection (default 128, at most 128; the FP32
+ * pre-sweeps are capped at min(64, bisect_sweeps)).  A value <= 0 restores
+ * the default.  Process-wide; takes effect at the next solve (a CUDA graph
+ * recorded earlier keeps the limits it was recorded with).  When the LOBPCG
+ * cap runs out the wavevector goes to the certificate as it is and, if not
+ * certified, to the dense fallbacks; when the sweep cap runs out before an
+ * eigenvalue's bracket reaches FP64 accuracy, that wavevector's status is
+ * BS_ENOCONV.  Errors: BS_EINVAL above the maxima.
+ */
+int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps);
 
 /*
  * bs_form_factors - copy the assembled form factors to `out`

@@ -42,6 +42,21 @@ extern "C" const char* bs_last_error(void) { return g_err; }
 
 // ------------------------------------------------------------------ profiling
 static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_lob_maxit{BS_LOB_MAXIT};
+static std::atomic<int> g_bisect_sweeps{128};
+
+int bs_lob_maxit() { return g_lob_maxit.load(std::memory_order_relaxed); }
+int bs_bisect_sweeps() { return g_bisect_sweeps.load(std::memory_order_relaxed); }
+
+extern "C" int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps) {
+  if (lobpcg_maxit > 1000 || bisect_sweeps > 128) {
+    bs_set_error("bs_set_iteration_limits: need lobpcg_maxit <= 1000 and bisect_sweeps <= 128");
+    return BS_EINVAL;
+  }
+  g_lob_maxit.store(lobpcg_maxit > 0 ? lobpcg_maxit : BS_LOB_MAXIT, std::memory_order_relaxed);
+  g_bisect_sweeps.store(bisect_sweeps > 0 ? bisect_sweeps : 128, std::memory_order_relaxed);
+  return BS_OK;
+}
 
 void bs_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -730,12 +745,17 @@ extern "C" int bs_solve_k(bs_cell* c, const double* Q, int nk, int nbands, doubl
   const bool st_dev = status_out && is_device_ptr(status_out);
   const int cap = k_batch_cap(c);
   TRY(ensure_workspace(c, std::min(nk, cap), nbands));
+  // synchronous call without a status array: the statuses still decide the return code
+  std::vector<int> hst(!w_dev && !status_out ? nk : 0);
   for (int k0 = 0; k0 < nk; k0 += cap) {
     const int kb = std::min(cap, nk - k0);
     CK(cudaMemcpyAsync(c->d_Q, Q + 2 * (size_t)k0, 2 * kb * sizeof(double),
                        q_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
        "bs_solve_k Q");
     TRY(solve_chunk(c, kb, nbands, s));
+    if (!hst.empty())
+      CK(cudaMemcpyAsync(hst.data() + k0, c->d_stat, kb * sizeof(int), cudaMemcpyDeviceToHost, s),
+         "bs_solve_k status");
     CK(cudaMemcpyAsync(omega_out + (size_t)k0 * nbands, c->d_w, (size_t)kb * nbands * sizeof(double),
                        w_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
        "bs_solve_k omega");
@@ -746,9 +766,10 @@ extern "C" int bs_solve_k(bs_cell* c, const double* Q, int nk, int nbands, doubl
   }
   if (!w_dev || (status_out && !st_dev)) {
     TRY(check_info(c, s));
-    if (status_out && !st_dev)
+    const int* hs = status_out && !st_dev ? status_out : (hst.empty() ? nullptr : hst.data());
+    if (hs)
       for (int k = 0; k < nk; ++k)
-        if (status_out[k]) {
+        if (hs[k]) {
           bs_set_error("bs_solve_k: wavevector %d did not converge", k);
           return BS_ENOCONV;
         }
@@ -789,7 +810,7 @@ static int solve_chunk_lobpcg(bs_cell* c, int kb, int nbands, int b, const float
   w.nvec = nvec;
   w.ndone = c->d_lndone;
   const float tol32 = (float)std::max(sqrt(c->tol), 3e-4);
-  TRY(bs_launch_lobpcg(w, n, kb, b, nbands, BS_LOB_MAXIT, tol32, (float)c->tol, (float)c->floor2,
+  TRY(bs_launch_lobpcg(w, n, kb, b, nbands, bs_lob_maxit(), tol32, (float)c->tol, (float)c->floor2,
                        4, s));
   TRY(bs_launch_lob_export(w, n, kb, b, c->d_X64, c->d_liters, s));
   bs_phase_end(c, PH_TRID, s);

@@ -456,7 +456,7 @@ static int reduce_chunk_body(bs_batch* B, BatchGroup& g, int c0, int cn, int p, 
     lw.ndone = g.lndone;
     // a graph replays a fixed sequence: no early exit there (finished k
     // return at once from every later launch)
-    TRY_LAUNCH(bs_launch_lobpcg(lw, n, K, lb, B->nbands, BS_LOB_MAXIT, 1e-3f, 1e-6f, (float)floor2,
+    TRY_LAUNCH(bs_launch_lobpcg(lw, n, K, lb, B->nbands, bs_lob_maxit(), 1e-3f, 1e-6f, (float)floor2,
                                 B->capturing ? 0 : 4, s));
     TRY_LAUNCH(bs_launch_lob_export(lw, n, K, lb, g.X64, g.liters, s));
     prof_mark(B, s);

@@ -90,7 +90,7 @@ __device__ void sweep(T& lo, T& hi, int i, int l, unsigned mask, CountFn cnt) {
 __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ de, int n,
                                                      int nbands, double* __restrict__ omega,
                                                      int* __restrict__ stat, int want_omega,
-                                                     double stop_rel) {
+                                                     double stop_rel, int maxsweep) {
   extern __shared__ double sm[];
   double* d = sm;
   double* e2 = sm + n;
@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ 
       float flo = (float)gl, fhi = (float)gu;
       flo = fminf(flo, (float)gl - (float)w32);
       fhi = fmaxf(fhi, (float)gu + (float)w32);
-      for (int it = 0; it < 64 && (double)fhi - (double)flo > w32; ++it) sweep(flo, fhi, i, l, mask, c32);
+      for (int it = 0; it < min(64, maxsweep) && (double)fhi - (double)flo > w32; ++it)
+        sweep(flo, fhi, i, l, mask, c32);
       // widen by the FP32 count margin and verify in FP64
       double vlo = fmax(gl, (double)flo - w32), vhi = fmin(gu, (double)fhi + w32);
       const double x = l == 0 ? vlo : vhi;
@@ -153,13 +154,15 @@ __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ 
         hi = vhi;
       }
     }
-    for (int it = 0; it < 128; ++it) {
+    bool conv = false;
+    for (int it = 0; it <= maxsweep; ++it) {
       const double tol = fmax(atol, 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)));
-      if (hi - lo <= tol) break;
+      conv = hi - lo <= tol;
+      if (conv || it == maxsweep) break;
       sweep(lo, hi, i, l, mask, c64);
     }
     const double lam = 0.5 * (lo + hi);
-    if (!isfinite(lam)) bad = 1;
+    if (!isfinite(lam) || !conv) bad = 1;   // sweep limit reached: not converged
     if (l == 0) omega[(size_t)b * nbands + i] = want_omega ? sqrt(fmax(lam, 0.0)) : lam;
   }
   bad = __syncthreads_or(bad);
@@ -177,7 +180,7 @@ int bs_launch_bisect(const double* de, int n, int batch, int nbands, double* ome
     if (e != cudaSuccess) return bs_cuda_status(e, "bisect smem");
   }
   bisect_kernel<<<batch, NTB, smem, s>>>(de, n, nbands, omega, stat, want_omega ? 1 : 0,
-                                         stop_rel);
+                                         stop_rel, bs_bisect_sweeps());
   BS_CHECK_LAUNCH("bisect_kernel");
   return BS_OK;
 }

@@ -356,6 +356,10 @@ int bs_launch_lob_export(const LobWs& w, int n, int kb, int b, zd* X64, int* ite
 // |alpha|, |beta| <= Mp, 2 (2Mp+1)^2 per vector
 int bs_launch_lob_to_reduced(const float2* u, const zd* LR, int N, int M, int Mp, int kb, int nvec,
                              float2* y, cudaStream_t s);
+// Iteration limits (bs_set_iteration_limits): LOBPCG iterations and FP64
+// multisection sweeps of the Sturm bisection (defaults BS_LOB_MAXIT, 128)
+int bs_lob_maxit();
+int bs_bisect_sweeps();
 // Shift of the eigenvalue-count certificate in the gap above Ritz value i
 // (theta ascending, FP64): usable when theta_{i+1} - theta_i >= 2e-3 of its
 // size; sigma sits in that gap, at most 1% above theta_i, rounded to FP32
