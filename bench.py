@@ -32,10 +32,6 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-# Nominal FP64 peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
-# (An FMA-loop probe measured 1.19 TFLOP/s at 2.0 GHz.)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-
 METRIC = "k-point solves/sec at <=1e-6 rel omega err vs FP64 oracle"
 
 
@@ -53,6 +49,8 @@ def parse_args():
                     help="trained warm-start network (config 4)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="config 1: skip the reduced config-3 and config-4 measurements")
     ap.add_argument("--no-graph", action="store_true",
                     help="config 3: time the plain solve only (no CUDA graph record/replay)")
     ap.add_argument("--cpu-sample-k", type=int, default=6)
@@ -232,6 +230,32 @@ def measured_peaks():
         return 6800.0, 1900.0, "fallback (no MEASURED_PEAKS.json)"
 
 
+def device_peaks(torch, bs=None):
+    """SM count and maximum SM clock of this device (queried, not assumed),
+    the nominal FP64 and FP32 CUDA-core peaks from them (GB300: 2 FP64 FMA
+    and 128 FP32 FMA per SM per clock), and, with the library, the FP64
+    peak measured by its FMA-chain probe."""
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = int(p.multi_processor_count)
+    mhz = None
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        try:
+            q = subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()),
+                                "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                               capture_output=True, text=True, timeout=10)
+            mhz = float(q.stdout.strip().splitlines()[0])
+        except Exception:
+            mhz = 2070.0
+    out = {"sms": sms, "sm_max_mhz": mhz,
+           "fp64_nominal_tflops": sms * 2 * 2 * mhz * 1e6 / 1e12,
+           "fp32_nominal_tflops": sms * 128 * 2 * mhz * 1e6 / 1e12}
+    if bs is not None:
+        out["fp64_probe_tflops"] = bs.bs_probe_fp64(4, 20000)
+    return out
+
+
 def traffic_record(kernel):
     """DRAM bytes per step of `kernel` from the committed ncu summary, if the
     kernel's source is unchanged since the counters were taken."""
@@ -339,7 +363,7 @@ def measure_mixed(bs, torch, args, cell, M, nb, nk, Qd, stream, flush, barrier, 
             "speedup_vs_fp64_path": ms_fp64 / mms,
             "status_nonzero": int(np.count_nonzero(stm.cpu().numpy())),
             "phases_ms": {k: round(statistics.mean(p[k] for p in phs), 3)
-                          for k in phs[0] if k != "reserved"},
+                          for k in phs[0]},
             "max_rel_err_vs_fp64_path": float(rel_err(om, omega_fp64, cell).max()),
             "_omega": om}
 
@@ -374,17 +398,13 @@ def measure_tensor(bs, torch, stream, nk, n):
             "peak_source": "bf16 burst, " + note, "frac": tflops / bf16_peak}
 
 
-def run_batch(args):
-    """Config 3: a ragged batch of cells on the mixed path (bs_batch_*)."""
-    import torch
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    rep = Replicas("nccl", torch.device("cuda", local))
-    world, rank = rep.world, rep.rank
-    from paper_1310_6380_gb300 import binding as bs
+def measure_c3(bs, torch, rep, args, ncell, steps, warmup, graph=True, oracle_cells=8,
+               cpu_baseline=True):
+    """Config 3: a ragged batch of `ncell` cells on the dense mixed path
+    (bs_batch_*); returns the JSON dict of its measurement."""
     from paper_1310_6380_gb300 import cells
-
-    ncell, nk, nb = args.cells, 30, 10
+    world, rank = rep.world, rep.rank
+    nk, nb = 30, 10
     cfgs = [cells.config3_cell(i) for i in range(ncell)]
     cargs = [(c["cell"].h1, c["cell"].h2, np.ascontiguousarray(c["cell"].phase, np.uint16),
               c["cell"].lam, c["cell"].mu, c["cell"].rho, c["M"], bs.BS_PREC_MIXED) for c in cfgs]
@@ -396,17 +416,16 @@ def run_batch(args):
     st = torch.empty((ncell, nk), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
     barrier = rep.barrier
 
     def timed(graph):
         bs.bs_batch_set_graph(b, graph)
         bs.bs_batch_set_profiling(b, not graph)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             bs.bs_batch_solve(b, Qd, w, st, stream)
         barrier()
         times, phs = [], []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -425,8 +444,8 @@ def run_batch(args):
     sampler.start()
     ms_plain, phs = timed(False)
     clocks = sampler.stop()
-    launches = (bs.bs_launch_count() - launches0) // max(1, args.steps + args.warmup)
-    ms_graph = None if args.no_graph else timed(True)[0]
+    launches = (bs.bs_launch_count() - launches0) // max(1, steps + warmup)
+    ms_graph = timed(True)[0] if graph else None
     ms = ms_plain if ms_graph is None else min(ms_plain, ms_graph)
     ms = rep.max(ms)
     omega = w.cpu().numpy()
@@ -444,46 +463,31 @@ def run_batch(args):
     hs = torch.empty((ncell, nk), dtype=torch.int32).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         b2 = bs.bs_batch_create(cargs, nk, nb)
         bs.bs_batch_solve(b2, hQ, hw, hs, stream)
         bs.bs_batch_destroy(b2)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = rep.max((time.perf_counter() - t0) / steps)
     h2d = sum(a[2].nbytes + 3 * a[3].nbytes for a in cargs) + hQ.numel() * 8
     e2e = {"value": world * ncell * nk / e2e_s, "unit": "k-solves/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": hw.numel() * 8 + hs.numel() * 4,
            "api": "bs_batch_create (host arrays) + bs_batch_solve (host Q, outputs; first call "
                   "includes tile autotuning) + bs_batch_destroy"}
-    # dominant kernel: the FP32 Householder reduction.  Cluster-resident
-    # variant (tile 0): matrices stay on chip, so its roofline is the FP32
-    # ALU rate on (16/3) n^3 real flops per matrix; per-step variant: HBM
-    # on the read + write of every trailing triangle.
-    tiles = {} if not phs else tiles_chosen
+    # dominant kernel: the FP32 Householder reduction, bound by HBM on the
+    # read + write of every trailing triangle
     hbm_peak, _, note = measured_peaks()
-    if tiles and all(t == 0 for t in tiles.values()):
-        flops = sum(nk * 16.0 / 3.0 * float(n) ** 3 for n in ns)
-        achieved = flops / (ph["reduction"] / 1e3) / 1e12
-        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        roofline = {"bound": "alu", "kernel": "tridiag_cluster_kernel (one launch per chunk)",
-                    "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp32_peak, "traffic": None,
-                    "peak_source": "nominal FP32 CUDA-core rate: 152 SMs x 128 FMA/clk x 2 x "
-                                   "2.07 GHz",
-                    "algorithmic": f"(16/3) n^3 real flops per matrix, {ncell * nk} matrices "
-                                   "(n = 242..578)"}
-    else:
-        tri_bytes = sum(nk * sum(m * (m + 1) // 2 for m in range(1, int(n))) * 16.0 for n in ns)
-        achieved = tri_bytes / (ph["reduction"] / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "tridiag_step_kernel<float> (all launches of one step)",
-                    "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                    "traffic": None, "peak_source": "copy bandwidth, " + note,
-                    "algorithmic": "read + write (8 B each) of every trailing lower triangle of "
-                                   f"{ncell * nk} matrices (n = 242..578)"}
+    tri_bytes = sum(nk * sum(m * (m + 1) // 2 for m in range(1, int(n))) * 16.0 for n in ns)
+    achieved = tri_bytes / (ph["reduction"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "tridiag_step_kernel<float> (all launches of one step)",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "peak_source": "copy bandwidth, " + note,
+                "algorithmic": "read + write (8 B each) of every trailing lower triangle of "
+                               f"{ncell * nk} matrices (n = 242..578)"}
     value = world * ncell * nk / (ms / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 reduction, bf16 exact-slice tensor products, f64 refinement",
         "data": "synthetic",
@@ -497,11 +501,11 @@ def run_batch(args):
         "tiles": tiles_chosen, "phases_ms": {k: round(v, 1) for k, v in ph.items()},
         "status_nonzero": int(np.count_nonzero(status)),
         "fp64_fallbacks": int((fb_flags == 1).sum()), "gpu_launches_per_step": launches,
-        "gpu_launches": launches * args.steps, "e2e": e2e, "roofline": roofline, "clocks": clocks,
+        "gpu_launches": launches * steps, "e2e": e2e, "roofline": roofline, "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and cpu_baseline and oracle_cells > 0:
         from oracle import mixed_variational as mv
-        samp = list(range(0, ncell, max(1, ncell // 8)))[:8]
+        samp = list(range(0, ncell, max(1, ncell // oracle_cells)))[:oracle_cells]
         t0 = time.perf_counter()
         errs = []
         for i in samp:
@@ -516,7 +520,69 @@ def run_batch(args):
                                          f"({secs:.1f} s); value = their k-solves / time"}
         out["max_rel_err_vs_oracle"] = float(max(errs))
         out["oracle_sampled_cells"] = samp
-    if rank == 0:
+    return out
+
+
+def measure_assembly(bs, torch, stream, cell, M, ph_c1):
+    """The form-factor assembly's tensor-core launch (the first separable
+    stage, exact-slice digit planes on tcgen05) alone: on the c1 cell (its
+    time from the c1 steps' profiling) and on c3-shaped cells (64 x 64
+    pixels, M = 8 and M = 5, assembled alone, L2 flushed before each)."""
+    from paper_1310_6380_gb300 import cells
+    _, bf16_peak, note = measured_peaks()
+    S = 7   # digit planes per operand in the assembly
+
+    def figures(P, Mt, ms):
+        D = 4 * Mt + 1
+        Kp = (P + 7) // 8 * 8
+        issued = 2.0 * (3 * S * P) * (2 * S * D) * Kp
+        algo = 3.0 * (4.0 * D * P * P + 8.0 * D * D * P)
+        return {"P": P, "M": Mt, "gemm": f"[{3 * S * P} x {2 * S * D} x {Kp}] BF16 digit planes",
+                "ms_per_launch": ms, "issued_bf16_flops": issued,
+                "algorithmic_flops_per_cell": algo,
+                "issued_tflops": issued / (ms / 1e3) / 1e12,
+                "frac_of_bf16_peak": issued / (ms / 1e3) / 1e12 / bf16_peak,
+                "algorithmic_tflops": algo / (ms / 1e3) / 1e12}
+
+    out = {"kernel": "slice_gemm_kernel (tcgen05.mma kind::f16, TMA, TMEM), first stage of the "
+                     "form factors", "peak_tflops": bf16_peak,
+           "peak_source": "bf16 burst, " + note,
+           "algorithmic": "3 [4 D P^2 + 8 D^2 P] real flops per cell (both separable stages; the "
+                          "second runs in FP64 on CUDA cores); issued = 2 x digit-plane GEMM "
+                          "flops of the tensor-core launch",
+           "c1": figures(cell.P, M, ph_c1["assembly_tc"])}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for Mt in (8, 5):
+        i = next(i for i in range(200) if cells.config3_cell(i)["M"] == Mt)
+        c = cells.config3_cell(i)["cell"]
+        h = bs.bs_create_cell(c.h1, c.h2, np.ascontiguousarray(c.phase, np.uint16), c.lam.copy(),
+                              c.mu.copy(), c.rho.copy(), Mt, bs.BS_PREC_MIXED)
+        try:
+            bs.bs_set_profiling(h, True)
+            ts = []
+            for r in range(8):
+                flush.zero_()
+                bs.bs_assemble(h, stream)
+                t = bs.bs_phase_times(h)["assembly_tc"]
+                if r >= 3:
+                    ts.append(t)
+        finally:
+            bs.bs_destroy_cell(h)
+        out[f"c3_M{Mt}"] = figures(c.P, Mt, statistics.mean(ts))
+    return out
+
+
+def run_batch(args):
+    """Config 3 on its own line (bench.py --config c3)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    rep = Replicas("nccl", torch.device("cuda", local))
+    from paper_1310_6380_gb300 import binding as bs
+    out = measure_c3(bs, torch, rep, args, args.cells, args.steps, args.warmup,
+                     graph=not args.no_graph, oracle_cells=8,
+                     cpu_baseline=not args.no_cpu_baseline)
+    if rep.rank == 0:
         print(json.dumps(out))
     rep.close()
 
@@ -638,14 +704,19 @@ def run_ours(args):
 
     # dominant kernel: the Householder tridiagonalisation
     ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+    peaks = device_peaks(torch, bs)
     if prec == 0:
         trid_flops = nk * 16.0 / 3.0 * n ** 3
         achieved = trid_flops / (ph["tridiag"] / 1e3) / 1e12
+        fp64_peak = peaks["fp64_nominal_tflops"]
         roofline = {"bound": "alu", "kernel": "tridiag_step_kernel<double> (all launches of one step)",
-                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS,
+                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak,
                     "traffic": traffic_record("tridiag_step_kernel") if args.config == "c1" else None,
-                    "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                    "peak_source": f"nominal FP64: {peaks['sms']} SMs (queried) x 2 FMA/clk x 2 "
+                                   f"flop x {peaks['sm_max_mhz']:.0f} MHz",
+                    "peak_measured_fma_probe": peaks["fp64_probe_tflops"],
+                    "frac_of_probe": achieved / peaks["fp64_probe_tflops"],
                     "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}"}
     else:
         hbm_peak, _, note = measured_peaks()
@@ -706,13 +777,21 @@ def run_ours(args):
            "d2h_bytes_per_step": d2h,
            "api": "bs_create_cell + bs_assemble + bs_solve_k + bs_destroy_cell, pinned host buffers"}
 
-    # on config 1, also measure config 2 (the same cell on the mixed path) and the
-    # tensor-core utilisation of the exact-slice contraction
-    mixed = tensor = None
+    # on config 1, also measure config 2 (the same cell on the mixed path), the
+    # tensor-core utilisation of the exact-slice contraction, the assembly's
+    # tensor-core launch, and (reduced cell counts) configs 3 and 4
+    mixed = tensor = assembly = sub3 = sub4 = None
     if args.config == "c1":
         mixed = measure_mixed(bs, torch, args, cell, M, nb, nk, Qd, stream, flush, barrier, dev,
                               ms, omega, world)
         tensor = measure_tensor(bs, torch, stream, nk, n)
+        assembly = measure_assembly(bs, torch, stream, cell, M, ph)
+        if not args.no_sub:
+            sub_steps, sub_warm = min(args.steps, 3), 3
+            sub3 = measure_c3(bs, torch, rep, args, 512, sub_steps, sub_warm, graph=False,
+                              oracle_cells=3, cpu_baseline=not args.no_cpu_baseline)
+            sub4 = measure_c4(bs, torch, rep, args, 256, sub_steps, sub_warm, oracle_cells=2,
+                              fp64_cells=64, cpu_baseline=not args.no_cpu_baseline)
 
     out = {
         "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
@@ -721,18 +800,26 @@ def run_ours(args):
         "dtype": "f64" if prec == 0 else "f32 reduction, bf16 exact-slice tensor products, f64 refinement",
         "data": "synthetic", "config": config, "e2e": e2e, "gpu_launches": launches,
         "gpu_launches_per_step": launches // max(1, args.steps), "roofline": roofline,
-        "phases_ms": {k: round(v, 3) for k, v in ph.items() if k != "reserved" and v > 0},
+        "phases_ms": {k: round(v, 3) for k, v in ph.items() if v > 0},
         "wall_s_timed_region": t_wall, "clocks": clocks,
     }
     if args.config == "mesh":
         out["paper_context"] = ("the paper's run of this workload (1000-element steel/epoxy mesh, "
                                 "M=5, 70 k, 18 branches) took 90 s on a Quadro K2000 desktop GPU, "
                                 "about 0.78 k-solves/s; other hardware and mesh, context only")
+    out["device"] = peaks
     omega_mixed = None
     if mixed is not None:
         omega_mixed = mixed.pop("_omega")
         out["mixed_path"] = mixed
         out["tensor_core"] = tensor
+        out["assembly"] = assembly
+    for key, sub in (("c3", sub3), ("c4", sub4)):
+        if sub is not None:
+            for drop in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data",
+                         "clocks"):
+                sub.pop(drop, None)
+            out[key] = sub
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, idx, ws, desc, _ = cpu_oracle_sample(cfg, args.cpu_sample_k)
         out["cpu_baseline"] = {"value": v, "unit": "k-solves/s",
@@ -749,19 +836,16 @@ def run_ours(args):
     rep.close()
 
 
-def run_c4(args):
+def measure_c4(bs, torch, rep, args, ncell, steps, warmup, oracle_cells=6, fp64_cells=128,
+               cpu_baseline=True):
     """Config 4: the learned warm start.  Held-out cells (seeds 2e6 + i), 30 k
     each, 10 branches, batch LOBPCG from (a) the cold start and (b) the trained
     network's 12-vector starting subspaces; one step = network inference for
     every (cell, k) + the batch solve (assembly, LOBPCG, FP64 Rayleigh-Ritz,
-    count certificate, dense fallback).  The plain FP64 dense GPU path is timed
-    on a sample of the same cells for comparison."""
-    import torch
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    rep = Replicas("nccl", torch.device("cuda", local))
+    certificate, count check, dense rescues).  The plain FP64 dense GPU path
+    is timed on a sample of the same cells for comparison.  Returns the JSON
+    dict of the measurement."""
     world, rank = rep.world, rep.rank
-    from paper_1310_6380_gb300 import binding as bs
     from paper_1310_6380_gb300 import cells
     from paper_1310_6380_gb300 import warmstart as ws
 
@@ -770,7 +854,7 @@ def run_c4(args):
                          "python -m paper_1310_6380_gb300.train_warmstart --out <file>")
     saved = np.load(args.weights)
     meta = json.loads(str(saved["meta"]))
-    ncell, nk, nb, Mp, nvec = args.cells or 1024, 30, 10, meta["Mp"], meta["nvec"]
+    nk, nb, Mp, nvec = 30, 10, meta["Mp"], meta["nvec"]
     cfgs = [cells.config4_eval_cell(i) for i in range(ncell)]
     cl = [c["cell"] for c in cfgs]
     Ms = [c["M"] for c in cfgs]
@@ -799,11 +883,11 @@ def run_c4(args):
         bs.bs_batch_solve(b, Qd, w, st, stream)
 
     def timed(warm):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step(warm)
         barrier()
         times = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -823,7 +907,7 @@ def run_c4(args):
     sampler.start()
     ms_warm, it_warm, fb_warm, om_warm, st_warm = timed(True)
     clocks = sampler.stop()
-    launches = (bs.bs_launch_count() - launches0) // max(1, args.steps + args.warmup)
+    launches = (bs.bs_launch_count() - launches0) // max(1, steps + warmup)
     bs.bs_batch_set_profiling(b, True)
     step(True)
     torch.cuda.synchronize()
@@ -836,7 +920,7 @@ def run_c4(args):
     # the plain FP64 dense GPU path (FP64 C(k), Householder reduction, Sturm
     # multisection), batched over the cells like the other solvers, on a
     # sample of the cells
-    samp = list(range(0, ncell, max(1, ncell // 128)))[:128]
+    samp = list(range(0, ncell, max(1, ncell // fp64_cells)))[:fp64_cells]
     bf = bs.bs_batch_create([cargs[i] for i in samp], nk, nb)
     bs.bs_batch_set_solver(bf, bs.BS_SOLVER_FP64)
     Qf = torch.tensor(Qh[samp], device="cuda")
@@ -861,14 +945,14 @@ def run_c4(args):
     hQ = torch.from_numpy(Qh).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         b2 = bs.bs_batch_create(cargs, nk, nb)
         bs.bs_batch_set_solver(b2, bs.BS_SOLVER_LOBPCG)
         bs.bs_batch_set_start(b2, net.predict(pack, Qh), Mp)
         bs.bs_batch_solve(b2, hQ, hw, hs, stream)
         bs.bs_batch_destroy(b2)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = rep.max((time.perf_counter() - t0) / steps)
     h2d = (sum(a[2].nbytes + 3 * a[3].nbytes for a in cargs) + Qh.nbytes + pack.phase.nbytes
            + pack.table.nbytes + ncell * nk * nvec * 2 * (2 * Mp + 1) ** 2 * 8)
     e2e = {"value": world * ncell * nk / e2e_s, "unit": "k-solves/s", "h2d_bytes_per_step": h2d,
@@ -883,16 +967,17 @@ def run_c4(args):
     b_lob = 16
     cw_flops = float(np.sum(it_warm.reshape(ncell, nk) * (8.0 * ns[:, None] ** 2 * b_lob)))
     achieved = cw_flops / (ph["reduction"] / 1e3) / 1e12
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    fp32_peak = device_peaks(torch)["fp32_nominal_tflops"]
     roofline = {"bound": "alu", "kernel": "LOBPCG iterations (lob_cw_kernel + lob_eig_kernel + "
                                           "lob_update_kernel, one step)",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": "nominal FP32 CUDA-core rate: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                "peak_source": "nominal FP32 CUDA-core rate: SMs x 128 FMA/clk x 2 x max SM clock "
+                               "(queried)",
                 "algorithmic": "8 n^2 b flops (C W, b = 16) per LOBPCG iteration per (cell, k)"}
     out = {
         "metric": METRIC, "value": value, "unit": "k-solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 network and LOBPCG, bf16 exact-slice tensor products, f64 Rayleigh-Ritz",
         "data": "synthetic",
@@ -918,14 +1003,16 @@ def run_c4(args):
                                      "on BS_SOLVER_FP64 (assembly, FP64 C(k), FP64 Householder "
                                      "reduction, Sturm multisection)",
                            "speedup_of_value": value / fp64_rate},
+        "speedup_vs_fp64_batched": value / fp64_rate,
+        "speedup_target": 10.0,
         "status_nonzero": int(np.count_nonzero(st_warm)),
         "phases_ms": {k: round(v, 1) for k, v in ph.items()},
-        "gpu_launches_per_step": launches, "gpu_launches": launches * args.steps,
+        "gpu_launches_per_step": launches, "gpu_launches": launches * steps,
         "e2e": e2e, "roofline": roofline, "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and cpu_baseline and oracle_cells > 0:
         from oracle import mixed_variational as mv
-        osamp = list(range(0, ncell, max(1, ncell // 6)))[:6]
+        osamp = list(range(0, ncell, max(1, ncell // oracle_cells)))[:oracle_cells]
         t0 = time.perf_counter()
         errs = []
         for i in osamp:
@@ -942,7 +1029,19 @@ def run_c4(args):
         out["oracle_sampled_cells"] = osamp
     bs.bs_batch_destroy(b)
     net.close()
-    if rank == 0:
+    return out
+
+
+def run_c4(args):
+    """Config 4 on its own line (bench.py --config c4)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    rep = Replicas("nccl", torch.device("cuda", local))
+    from paper_1310_6380_gb300 import binding as bs
+    out = measure_c4(bs, torch, rep, args, args.cells or 1024, args.steps, args.warmup,
+                     cpu_baseline=not args.no_cpu_baseline)
+    if rep.rank == 0:
         print(json.dumps(out))
     rep.close()
 
@@ -1068,21 +1167,23 @@ def run_modes(args):
     fld = nk * 5 * nvec
     field_flops = fld * (8.0 * W * G * G + 8.0 * W * W * G)
     field_bytes = fld * G * G * 8.0 + fld * N * 16.0
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    dpk = device_peaks(torch)
+    fp32_peak = dpk["fp32_nominal_tflops"]
     hbm_peak, _, note = measured_peaks()
     t_field = (pm["field_u"] + pm["field_sigma"]) / 1e3
     rl_stress = {"bound": "alu", "kernel": "bs_stress_coefficients (stress_rhs_kernel, "
                                            "zgemm_kernel x4, stress_combine_kernel)",
-                 "achieved": stress_flops / (pm["stress"] / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                 "unit": "TFLOP/s", "traffic": None,
-                 "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                 "achieved": stress_flops / (pm["stress"] / 1e3) / 1e12,
+                 "peak": dpk["fp64_nominal_tflops"], "unit": "TFLOP/s", "traffic": None,
+                 "peak_source": "nominal FP64: SMs (queried) x 2 FMA/clk x 2 flop x max SM clock",
                  "algorithmic": "3 Gram solves per mode, each two triangular products: 24 N^2 "
                                 "real flops per mode"}
     rl_stress["frac"] = rl_stress["achieved"] / rl_stress["peak"]
     rl_field = {"bound": "alu", "kernel": "field_kernel<24> (+ field_table_kernel)",
                 "achieved": field_flops / t_field / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                 "traffic": None,
-                "peak_source": "nominal FP32 CUDA-core rate: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                "peak_source": "nominal FP32 CUDA-core rate: SMs (queried) x 128 FMA/clk x 2 x max "
+                               "SM clock",
                 "algorithmic": "8 W G^2 + 8 W^2 G real flops per field (W = 2M+1 = 21, G = 256); "
                                f"stores {field_bytes / 1e9:.2f} GB per step",
                 "hbm_gbs": field_bytes / t_field / 1e9, "hbm_frac": field_bytes / t_field / 1e9
@@ -1263,10 +1364,11 @@ def run_3d(args):
     achieved = flops / (t_sol / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "tridiag_step_kernel<double> (with the per-k builder "
                                           "and bisection: bs_solve_k3 of one step)",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz",
+                "achieved": achieved, "peak": device_peaks(torch)["fp64_nominal_tflops"],
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "nominal FP64: SMs (queried) x 2 FMA/clk x 2 flop x max SM clock",
                 "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}"}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hp, hl, hm, hr, hQ = (pin(cell.phase.astype(np.uint16)), pin(cell.lam), pin(cell.mu),
                           pin(cell.rho), pin(Q))

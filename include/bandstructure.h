@@ -579,11 +579,23 @@ int bs_destroy_cell3(bs_cell3* cell);
  *   ms[4] Householder tridiagonalisation
  *   ms[5] bisection and omega
  *   ms[6] FP64 Rayleigh-Ritz refinement (mixed path)
- *   ms[7] reserved (0)
+ *   ms[7] the tensor-core contraction of the form factors alone (the
+ *         first separable stage of Eqs. (eo), (ep), inside ms[0])
  * Phases that did not run in the last call report 0.
  */
 int bs_set_profiling(bs_cell* cell, int on);
 int bs_phase_times(bs_cell* cell, double ms[8]);
+
+/*
+ * bs_probe_fp64 - a measurement aid, not a step of the method (the paper
+ * has no counterpart): the device's FP64 FMA throughput, from a kernel of
+ * independent fused multiply-add chains on every SM (`blocks_per_sm` CTAs
+ * of 256 threads per SM, `iters` iterations of 8 chains per thread), timed
+ * with CUDA events on `stream`.  Writes TFLOP/s (2 flops per FMA) to
+ * *tflops.  Synchronises `stream`.  BS_EINVAL for iters < 1 or
+ * blocks_per_sm outside [1, 8].
+ */
+int bs_probe_fp64(int blocks_per_sm, int iters, double* tflops, void* stream);
 
 /*
  * bs_launch_count - number of CUDA kernels this library has launched in

@@ -96,6 +96,7 @@ def _load():
         "bs_batch_stats": [vp, dp, dp],
         "bs_batch_set_vectors": [vp, i32],
         "bs_batch_vectors": [vp, dp],
+        "bs_probe_fp64": [i32, i32, dp, vp],
         "bs_set_iteration_limits": [i32, i32],
         "bs_batch_set_tile": [vp, i32],
         "bs_stress_coefficients": [vp, dp, i32, i32, dp, dp, vp],
@@ -132,7 +133,7 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step", "bs_stress_coefficients",
             "bs_mode_field", "bs_create_cell_mesh", "bs_set_stiffness", "bs_create_cell3",
             "bs_assemble3", "bs_solve_k3", "bs_form_factors3", "bs_reduced_matrix3",
-            "bs_cell3_dims", "bs_destroy_cell3", "bs_set_iteration_limits"]
+            "bs_cell3_dims", "bs_destroy_cell3", "bs_set_iteration_limits", "bs_probe_fp64"]
 BS_SOLVER_DENSE, BS_SOLVER_LOBPCG, BS_SOLVER_FP64 = 0, 1, 2
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
 
@@ -378,6 +379,13 @@ def bs_batch_destroy(batch):
     _check(_lib.bs_batch_destroy(batch))
 
 
+def bs_probe_fp64(blocks_per_sm: int = 4, iters: int = 20000, stream=None) -> float:
+    """Measured FP64 FMA throughput of the device in TFLOP/s (a measurement aid)."""
+    out = np.zeros(1)
+    _check(_lib.bs_probe_fp64(int(blocks_per_sm), int(iters), out.ctypes.data, _stream(stream)))
+    return float(out[0])
+
+
 def bs_set_iteration_limits(lobpcg_maxit: int = 0, bisect_sweeps: int = 0):
     """Process-wide iteration caps (tests and diagnostics); 0 restores the defaults."""
     _check(_lib.bs_set_iteration_limits(int(lobpcg_maxit), int(bisect_sweeps)))
@@ -451,7 +459,7 @@ def bs_set_profiling(cell, on: bool):
     _check(_lib.bs_set_profiling(cell, int(bool(on))))
 
 
-PHASES = ("assembly", "gram", "monomials", "builder", "tridiag", "bisect", "refine", "reserved")
+PHASES = ("assembly", "gram", "monomials", "builder", "tridiag", "bisect", "refine", "assembly_tc")
 
 
 def bs_phase_times(cell) -> dict:

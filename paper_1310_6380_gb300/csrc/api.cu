@@ -46,6 +46,23 @@ static std::atomic<int> g_lob_maxit{BS_LOB_MAXIT};
 static std::atomic<int> g_bisect_sweeps{128};
 
 int bs_lob_maxit() { return g_lob_maxit.load(std::memory_order_relaxed); }
+
+int bs_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
 int bs_bisect_sweeps() { return g_bisect_sweeps.load(std::memory_order_relaxed); }
 
 extern "C" int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps) {
@@ -1066,6 +1083,60 @@ extern "C" int bs_phase_times(bs_cell* c, double ms[8]) {
 }
 
 // ------------------------------------------------------------------ diagnostics
+namespace {
+// 8 independent FMA chains per thread; the sum is stored so that nothing is
+// optimised away
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters, double seed,
+                                                             double* __restrict__ out) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = seed + 1e-3 * (threadIdx.x + i);
+  const double x = 1.0 - 1e-9, y = 1e-12;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], x, y);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += a[i];
+  if (s == 12345.678) out[blockIdx.x] = s;   // never true; keeps the chains live
+}
+}  // namespace
+
+extern "C" int bs_probe_fp64(int blocks_per_sm, int iters, double* tflops, void* stream) {
+  if (!tflops || iters < 1 || blocks_per_sm < 1 || blocks_per_sm > 8) {
+    bs_set_error("bs_probe_fp64: need tflops, iters >= 1, 1 <= blocks_per_sm <= 8");
+    return BS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = blocks_per_sm * bs_sm_count();
+  double* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc((void**)&out, grid * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) {
+    fp64_fma_probe_kernel<<<grid, 256, 0, s>>>(iters, 1.0, out);   // warm-up
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    e = cudaEventRecord(e0, s);
+  }
+  if (e == cudaSuccess) {
+    fp64_fma_probe_kernel<<<grid, 256, 0, s>>>(iters, 2.0, out);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess) return bs_cuda_status(e, "bs_probe_fp64");
+  *tflops = 2.0 * 8.0 * iters * (double)grid * 256.0 / (ms * 1e-3) / 1e12;
+  return BS_OK;
+}
+
 extern "C" int bs_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
                             int batch, void* stream) {
   if (!A || !B || !D || M < 1 || N < 1 || K < 8 || K % 8 || K > 4096 || batch < 1 ||

@@ -81,8 +81,12 @@ template <> struct Cplx<float> {
 };
 
 // phase indices of bs_phase_times
+// PH_ASM_TC: the first-stage form-factor contraction on the tensor cores
+// alone (inside PH_ASM)
 enum { PH_ASM = 0, PH_GRAM = 1, PH_MONO = 2, PH_BUILD = 3, PH_TRID = 4, PH_BISECT = 5,
-       PH_REFINE = 6, PH_COUNT = 8 };
+       PH_REFINE = 6, PH_ASM_TC = 7, PH_COUNT = 8 };
+// number of SMs of the current device (queried once per device)
+int bs_sm_count();
 
 // ------------------------------------------------------------------ cell
 struct LobState;

@@ -256,8 +256,10 @@ int bs_launch_fields_tc(bs_cell* c, cudaStream_t s) {
   pack_exp_kernel<<<2 * D, 128, 0, s>>>(c->d_E, P, D, S, Kp, c->d_sliceB, c->d_expB);
   BS_CHECK_LAUNCH("pack_exp_kernel");
   const int M = nf * S * P, N = 2 * S * D;
+  bs_phase_begin(c, PH_ASM_TC, s);
   TRY_LAUNCH(bs_launch_slice_gemm(c->d_sliceA, c->d_sliceB, c->d_sliceD, M, N, Kp, 1,
                                   (long)M * Kp, (long)N * Kp, M, (long)M * N, c->d_info + 1, s));
+  bs_phase_end(c, PH_ASM_TC, s);
   const size_t tot = (size_t)nf * P * D;
   recombine_fields_kernel<BS_SLICES_ASM><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
       c->d_sliceD, c->d_expA, c->d_expB, P, D, nf, c->d_Y);

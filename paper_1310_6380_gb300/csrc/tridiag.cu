@@ -326,7 +326,7 @@ static int launch_steps_fp64(zd* A, int n, int batch, zd* vec, zd* part, double*
   if (n > 600) return launch_steps<double, 64>(A, n, batch, vec, part, de, tau, beta, count, s);
   tridiag_init_kernel<double><<<batch, NT, 0, s>>>(A, n, vec, de, tau, beta, count);
   BS_CHECK_LAUNCH("tridiag_init_kernel");
-  const long fill = 2L * 2 * 152;   // two waves of the 64-tile kernel (2 CTAs per SM)
+  const long fill = 2L * 2 * bs_sm_count();   // two waves of the 64-tile kernel (2 CTAs per SM)
   const int nt64 = (n + 63) / 64, nt32 = (n + 31) / 32;
   for (int j = 0; j + 1 < n; ++j) {
     const int m64 = nt64 - (j + 1) / 64;
