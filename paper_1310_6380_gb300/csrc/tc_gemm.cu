@@ -2,11 +2,14 @@
 //
 // D[z][n][m] = sum_k A[z][m][k] B[z][n][k] for BF16 A (M x K) and B (N x K),
 // both K-contiguous, with FP32 accumulation in tensor memory and FP32 D
-// stored n-major (column-major M x N).  One CTA computes a 128 x 128 tile:
-// a TMA producer thread streams 128 x 64 tiles of A and B through a
-// 4-stage shared-memory ring (128-byte swizzle, mbarrier completion), one
-// thread issues tcgen05.mma (kind::f16, M=128, N=128, K=16) into a TMEM
-// accumulator, and all four warps drain TMEM with tcgen05.ld.
+// stored n-major (column-major M x N).  One CTA computes a 128 x BN tile:
+// a TMA producer thread streams 128 x 64 tiles of A and BN x 64 tiles of B
+// through a 3-stage shared-memory ring (128-byte swizzle, mbarrier
+// completion), one thread issues tcgen05.mma (kind::f16, M=128, N=BN, K=16)
+// into a TMEM accumulator, and all four warps drain TMEM with tcgen05.ld.
+// The ring is sized so that two CTAs fit on an SM: one drains its
+// accumulator while the other's MMAs run.  BN (64..128, a multiple of 16)
+// is chosen per launch to pad N as little as possible.
 //
 // The library feeds it "digit planes": an FP64 operand x with per-row
 // scale 2^e is written as sum_s t_s 2^(e - 6 - 7s) with integer digits
@@ -23,9 +26,11 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
-constexpr int TILE_A = BM * BK * 2, TILE_B = BN * BK * 2;   // bytes per stage
-constexpr int SMEM_BYTES = STAGES * (TILE_A + TILE_B) + 1024;
+constexpr int BM = 128, BNMAX = 128, BK = 64, STAGES = 3;
+constexpr int TILE_A = BM * BK * 2;                    // bytes per stage
+__host__ __device__ constexpr int tile_b(int bn) { return bn * BK * 2; }
+__host__ __device__ constexpr int smem_bytes(int bn) { return STAGES * (TILE_A + tile_b(bn)) + 1024; }
+constexpr int TMEM_COLS = 128;                         // power of two >= BN
 constexpr long WAIT_LIMIT = 1L << 20;   // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -83,13 +88,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 }
 
 // instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
 
-__global__ void __launch_bounds__(128, 1)
+template <int BN>
+__global__ void __launch_bounds__(128, 2)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, float* __restrict__ D, int M,
                       int N, int K, long ldd, long strideD, int* __restrict__ err) {
+  constexpr int TILE_B = tile_b(BN);
+  constexpr uint32_t IDESC = idesc(BN);
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_base;
@@ -111,7 +121,7 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base)),
-                 "r"(BN));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -188,7 +198,8 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
   }
 }
 
@@ -227,6 +238,42 @@ int make_map(CUtensorMap* tm, const uint16_t* base, int K, int rows, int batch, 
   return BS_OK;
 }
 
+// the tile edge along N: the candidate that pads N least, the larger on a tie
+static int pick_bn(int N) {
+  static const int cand[] = {128, 112, 96, 80, 64};
+  int best = 128;
+  long waste = -1;
+  for (int bn : cand) {
+    const long w = (long)((N + bn - 1) / bn) * bn - N;
+    if (waste < 0 || w < waste) {
+      waste = w;
+      best = bn;
+    }
+  }
+  return best;
+}
+
+template <int BN>
+static int launch_bn(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
+                     int batch, long sA, long sB, long ldd, long sD, int* err, cudaStream_t s) {
+  CUtensorMap ta, tb;
+  int r = make_map(&ta, A, K, M, batch, sA, BM);
+  if (!r) r = make_map(&tb, B, K, N, batch, sB, BN);
+  if (r) return r;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes(BN));
+    if (e != cudaSuccess) return bs_cuda_status(e, "slice GEMM smem");
+    attr = true;
+  }
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, batch);
+  slice_gemm_kernel<BN><<<grid, 128, smem_bytes(BN), s>>>(ta, tb, D, M, N, K, ldd, sD, err);
+  BS_CHECK_LAUNCH("slice_gemm_kernel");
+  return BS_OK;
+}
+
 }  // namespace
 
 int bs_launch_slice_gemm(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
@@ -237,19 +284,11 @@ int bs_launch_slice_gemm(const uint16_t* A, const uint16_t* B, float* D, int M, 
     bs_set_error("slice GEMM: need K %% 8 == 0, K <= 4096, 16-byte aligned operands");
     return BS_EINVAL;
   }
-  CUtensorMap ta, tb;
-  int r = make_map(&ta, A, K, M, batch, sA, BM);
-  if (!r) r = make_map(&tb, B, K, N, batch, sB, BN);
-  if (r) return r;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return bs_cuda_status(e, "slice GEMM smem");
-    attr = true;
+  switch (pick_bn(N)) {
+    case 64: return launch_bn<64>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
+    case 80: return launch_bn<80>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
+    case 96: return launch_bn<96>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
+    case 112: return launch_bn<112>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
+    default: return launch_bn<128>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
   }
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, batch);
-  slice_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ta, tb, D, M, N, K, ldd, sD, err);
-  BS_CHECK_LAUNCH("slice_gemm_kernel");
-  return BS_OK;
 }
