@@ -55,7 +55,8 @@ def parse_args():
                     help="config 3: time the plain solve only (no CUDA graph record/replay)")
     ap.add_argument("--cpu-sample-k", type=int, default=6)
     ap.add_argument("--kpoints", type=int, default=None,
-                    help="mode shapes: use the first K wavevectors only (small profiling runs)")
+                    help="single-cell configs and mode shapes: use the first K wavevectors only "
+                         "(small profiling runs)")
     return ap.parse_args()
 
 
@@ -632,6 +633,10 @@ def run_ours(args):
     from paper_1310_6380_gb300 import binding as bs
 
     cfg, config, prec = workload(args.config)
+    if args.kpoints:   # a reduced case for profiling: the first K wavevectors only
+        cfg["Q"] = cfg["Q"][:args.kpoints]
+        config = dict(config, k_points=len(cfg["Q"]),
+                      workload=config["workload"] + f" (first {len(cfg['Q'])} wavevectors only)")
     cell, M, nb = cfg["cell"], cfg["M"], cfg["nbands"]
     Q = np.ascontiguousarray(cfg["Q"])
     nk = len(Q)

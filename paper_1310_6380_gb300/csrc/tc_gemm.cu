@@ -9,7 +9,7 @@
 // into a TMEM accumulator, and all four warps drain TMEM with tcgen05.ld.
 // The ring is sized so that two CTAs fit on an SM: one drains its
 // accumulator while the other's MMAs run.  BN (64..128, a multiple of 16)
-// is chosen per launch to pad N as little as possible.
+// is chosen per launch: the largest that pads N by at most 6 %.
 //
 // The library feeds it "digit planes": an FP64 operand x with per-row
 // scale 2^e is written as sum_s t_s 2^(e - 6 - 7s) with integer digits
@@ -238,9 +238,13 @@ int make_map(CUtensorMap* tm, const uint16_t* base, int K, int rows, int batch, 
   return BS_OK;
 }
 
-// the tile edge along N: the candidate that pads N least, the larger on a tie
+// the tile edge along N: the largest candidate that pads N by at most 6 %
+// (larger tiles read each A tile fewer times and issue larger MMAs), else
+// the one that pads least
 static int pick_bn(int N) {
   static const int cand[] = {128, 112, 96, 80, 64};
+  for (int bn : cand)
+    if ((long)((N + bn - 1) / bn) * bn - N <= 0.06 * N) return bn;
   int best = 128;
   long waste = -1;
   for (int bn : cand) {
