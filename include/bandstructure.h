@@ -346,7 +346,9 @@ int bs_tridiag_eigenvalues_static(const double* d, const double* e, int n, int b
  *   certify) or
  *   NULL; host or device pointers.  The first call times the two tile
  *   edges of the per-step reduction per truncation group and keeps the
- *   faster (autotuning).
+ *   faster (autotuning); the choice is remembered for the process, per
+ *   device, eigen dimension and batch-size class (powers of two of the
+ *   matrices per reduction launch), and reused by later batches.
  * bs_batch_set_graph - on != 0: the next bs_batch_solve records the whole
  *   solve in a CUDA graph, later calls replay it (the Q and output pointers
  *   of the recording call must be reused); on == 0 drops the graph.

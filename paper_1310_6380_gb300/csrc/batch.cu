@@ -18,6 +18,8 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "bs_internal.h"
@@ -916,6 +918,21 @@ static int tune_group(bs_batch* B, BatchGroup& g, double floor2, cudaStream_t s)
   return BS_OK;
 }
 
+// Tile choices of earlier batches in this process, per (device, eigen
+// dimension n, log2 of the matrices per reduction launch): a later batch of
+// the same shape reuses the choice instead of timing both tile edges again.
+static std::mutex g_tile_mu;
+static std::map<std::tuple<int, int, int>, int> g_tile_cache;
+
+static std::tuple<int, int, int> tile_key(const bs_batch* B, const BatchGroup& g) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+  const long mats = (long)std::min(g.chunk, (int)g.cells.size()) * B->nk;
+  int lg = 0;
+  while ((1L << (lg + 1)) <= mats) ++lg;
+  return std::make_tuple(dev, g.n, lg);
+}
+
 static void drop_graph(bs_batch* B);
 
 extern "C" int bs_batch_set_tile(bs_batch* B, int tile) {
@@ -1099,9 +1116,21 @@ extern "C" int bs_batch_solve(bs_batch* B, const double* Q, double* omega_out, i
   B->prof = false;   // not while tuning or recording a graph
   for (auto& g : B->groups) {
     if (g.tuned || B->solver != BS_SOLVER_DENSE) continue;
+    const auto key = tile_key(B, g);
+    {
+      std::lock_guard<std::mutex> lk(g_tile_mu);
+      auto it = g_tile_cache.find(key);
+      if (it != g_tile_cache.end()) {
+        g.tile = it->second;
+        g.tuned = true;
+        continue;
+      }
+    }
     double f2 = 1e300;
     for (int ci : g.cells) f2 = std::min(f2, floors[ci]);
     TRY_LAUNCH(tune_group(B, g, f2, s));
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    g_tile_cache[key] = g.tile;
   }
   if (B->use_graph) {
     // the caller's stream may be the legacy default stream, which cannot be
