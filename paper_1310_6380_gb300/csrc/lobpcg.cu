@@ -719,6 +719,22 @@ __global__ void __launch_bounds__(32) lob_eig_kernel(LobWs w, int n, int kb, int
         hi = hb;
         lo = fmaxf(lo, -16.f * FLT_EPSILON * tnorm);
       }
+      // The basis contains the previous Ritz block, so Ritz value c can only
+      // have decreased, and between iterations it moves little: try the
+      // bracket [theta_c - 1e-3 |theta_c|, theta_c] (slightly widened), kept
+      // when the pair's two counts confirm it (about a third of the
+      // trisection steps of the full bracket)
+      const float t = stp->theta[c];
+      const float slack = 16.f * FLT_EPSILON * tnorm;
+      const float l1 = fmaxf(lo, t - 1e-3f * fabsf(t) - slack);
+      const float h1 = fminf(hi, t + 1e-6f * fabsf(t) + slack);
+      const int mine = sturm(h ? h1 : l1);
+      const int other = __shfl_xor_sync((1u << c) | (1u << (c + LB)), mine, LB);
+      const int clo = h ? other : mine, chi = h ? mine : other;
+      if (l1 < h1 && clo <= c && chi > c) {
+        lo = l1;
+        hi = h1;
+      }
     }
     for (int it = 0; it < 48; ++it) {
       // 1e-6 relative: the FP64 Rayleigh-Ritz stage recomputes the values
