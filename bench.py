@@ -793,7 +793,7 @@ def run_ours(args):
         assembly = measure_assembly(bs, torch, stream, cell, M, ph)
         if not args.no_sub:
             sub_steps, sub_warm = min(args.steps, 3), 3
-            sub3 = measure_c3(bs, torch, rep, args, 512, sub_steps, sub_warm, graph=False,
+            sub3 = measure_c3(bs, torch, rep, args, 512, sub_steps, sub_warm, graph=True,
                               oracle_cells=3, cpu_baseline=not args.no_cpu_baseline)
             sub4 = measure_c4(bs, torch, rep, args, 256, sub_steps, sub_warm, oracle_cells=2,
                               fp64_cells=64, cpu_baseline=not args.no_cpu_baseline)

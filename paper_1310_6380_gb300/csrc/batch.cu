@@ -95,6 +95,15 @@ struct BatchGroup {
   zd* lLinvb[2];
   cudaEvent_t adone[2][kWorkers];   // worker w finished assembling into set p
   cudaEvent_t rdone[2];             // the reduction that read set p is done
+  // Gram factors of a whole chunk at once: the workers write each cell's
+  // three Toeplitz blocks into gT, one stream factors them all (Cholesky and
+  // triangular inverse, batched over cells x 3) and the workers take the
+  // factors back for the monomials
+  zd* gT;                           // chunk x 3 x N x N
+  zd* gLinv;                        // chunk x 3 x N x N
+  cudaStream_t gstream;
+  cudaEvent_t tdone[kWorkers];      // worker w wrote its cells' Toeplitz blocks
+  cudaEvent_t gdone;                // the chunk's factors are ready
   bool used[2];
   int nworkers;
   int chunk;                  // cells per reduction batch
@@ -208,6 +217,10 @@ static void free_group(BatchGroup& g) {
     if (g.wdone[w]) cudaEventDestroy(g.wdone[w]);
   }
   if (g.fork) cudaEventDestroy(g.fork);
+  for (int w = 0; w < kWorkers; ++w)
+    if (g.tdone[w]) cudaEventDestroy(g.tdone[w]);
+  if (g.gdone) cudaEventDestroy(g.gdone);
+  if (g.gstream) cudaStreamDestroy(g.gstream);
   for (int p = 0; p < 2; ++p) {
     for (int w = 0; w < kWorkers; ++w)
       if (g.adone[p][w]) cudaEventDestroy(g.adone[p][w]);
@@ -221,7 +234,7 @@ static void free_group(BatchGroup& g) {
                 g.phase, g.X32, g.X64, g.CX, g.G, g.H, g.W, g.theta, g.cxA, g.cxB, g.cxD, g.cxeA,
                 g.cxeB, g.w, g.st, g.d_rowidx, g.d_Gall, g.lS, g.lCS, g.lA, g.lpart, g.lZ, g.lY,
                 g.lst, g.lndone, g.liters, g.lsig, g.lsc, g.liw, g.fbw,
-                g.fbst, g.fbrow, g.vec64, g.part64, g.d_err};
+                g.fbst, g.fbrow, g.vec64, g.part64, g.d_err, g.gT, g.gLinv};
   for (void* p : ps) cudaFree(p);
 }
 
@@ -293,6 +306,8 @@ static int alloc_group(BatchGroup& g, int nk, int nbands) {
   if (!r) r = balloc(&g.st, K, "batch status");
   if (!r) r = balloc(&g.d_rowidx, g.cells.size() * (size_t)nk, "batch row index");
   if (!r) r = balloc(&g.d_Gall, g.cells.size() * 2 * (size_t)g.N, "batch G vectors");
+  if (!r) r = balloc(&g.gT, (size_t)g.chunk * 3 * g.N * g.N, "batch Gram blocks");
+  if (!r) r = balloc(&g.gLinv, (size_t)g.chunk * 3 * g.N * g.N, "batch Gram inverse factors");
   if (!r) r = balloc(&g.d_err, 3, "batch error flags");
   if (!r && cudaMemset(g.d_err, 0, 3 * sizeof(int)) != cudaSuccess)
     r = bs_cuda_status(cudaGetLastError(), "batch error flag");
@@ -355,28 +370,85 @@ static int fork_workers(BatchGroup& g, cudaStream_t s) {
 }
 
 // enqueue the assembly and C(k) build of chunk (c0, cn) into buffer set p on
-// the worker streams (after the reduction that last read set p)
+// the worker streams (after the reduction that last read set p), in three
+// passes: (1) each worker, for its cells, the material table, the form
+// factors and the Toeplitz blocks, copied into the chunk's Gram buffer;
+// (2) one stream factors the Gram blocks of the whole chunk (Cholesky and
+// triangular inverse batched over cells x 3: full launches instead of the
+// small per-cell ones, whose FP64 panels are latency-bound); (3) each worker,
+// for its cells, takes the factors back, forms the k-monomials, builds C(k)
+// and the starting vectors.
 static int assemble_chunk(bs_batch* B, BatchGroup& g, int c0, int cn, int p) {
   const int nk = B->nk, n = g.n;
-  const size_t nn = (size_t)n * n;
+  const size_t nn = (size_t)n * n, NN3 = 3 * (size_t)g.N * g.N;
   use_buffers(g, p);
   if (g.used[p])
     for (int w = 0; w < g.nworkers; ++w)
       CK(cudaStreamWaitEvent(g.wstream[w], g.rdone[p], 0), "batch buffer reuse");
+  // pass 1: form factors and Toeplitz blocks
+  for (int i = 0; i < cn; ++i) {
+    const int wi = i % g.nworkers;
+    bs_cell* wk = g.workers[wi];
+    cudaStream_t ws = g.wstream[wi];
+    int r = load_cell(B, g, wk, c0 + i, ws);
+    if (!r) r = cudaMemsetAsync(wk->d_info, 0, 2 * sizeof(int), ws) == cudaSuccess
+                    ? BS_OK
+                    : bs_cuda_status(cudaGetLastError(), "batch info");
+    if (!r) r = bs_launch_assembly(wk, ws);
+    if (!r) r = bs_launch_toeplitz(wk, ws);
+    if (!r) {   // a tensor-core timeout of the form factors, before the next cell clears it
+      or_flags_kernel<<<1, 32, 0, ws>>>(wk->d_info, g.d_err + 1);
+      r = cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA;
+      if (r) bs_set_error("or_flags_kernel launch failed");
+    }
+    if (!r)
+      r = cudaMemcpyAsync(g.gT + (size_t)i * NN3, wk->d_T, NN3 * sizeof(zd),
+                          cudaMemcpyDeviceToDevice, ws) == cudaSuccess
+              ? BS_OK
+              : bs_cuda_status(cudaGetLastError(), "batch Gram blocks");
+    if (r) return r;
+  }
+  // pass 2: the chunk's Gram factors at once
+  for (int w = 0; w < g.nworkers; ++w) {
+    CK(cudaEventRecord(g.tdone[w], g.wstream[w]), "batch Toeplitz done");
+    CK(cudaStreamWaitEvent(g.gstream, g.tdone[w], 0), "batch Toeplitz join");
+  }
+  TRY_LAUNCH(bs_launch_cholesky(g.gT, g.N, 3 * cn, (long)g.N * g.N, g.d_err + 1, g.gstream));
+  TRY_LAUNCH(bs_launch_trinv(g.gT, g.gLinv, g.N, 3 * cn, (long)g.N * g.N, g.gstream));
+  CK(cudaEventRecord(g.gdone, g.gstream), "batch Gram done");
+  for (int w = 0; w < g.nworkers; ++w)
+    CK(cudaStreamWaitEvent(g.wstream[w], g.gdone, 0), "batch Gram join");
+  // pass 3: monomials, C(k), starting vectors
   for (int i = 0; i < cn; ++i) {
     const int ci = g.cells[c0 + i], wi = i % g.nworkers;
     bs_cell* wk = g.workers[wi];
     cudaStream_t ws = g.wstream[wi];
     const bool lob = B->solver == BS_SOLVER_LOBPCG;
+    // the worker's own Linv slot is read by the monomials (and T's slot for
+    // L_R by the starting vectors); its host fields still describe cell i
+    // only if the worker has no later cell of this chunk, so reload them
     int r = load_cell(B, g, wk, c0 + i, ws);
-    if (!r) r = bs_assemble(wk, ws);
+    if (!r)
+      r = cudaMemcpyAsync(wk->d_Linv, g.gLinv + (size_t)i * NN3, NN3 * sizeof(zd),
+                          cudaMemcpyDeviceToDevice, ws) == cudaSuccess
+              ? BS_OK
+              : bs_cuda_status(cudaGetLastError(), "batch Gram factors");
+    if (!r && lob && B->d_U)
+      r = cudaMemcpyAsync(wk->d_T + 2 * (size_t)g.N * g.N, g.gT + (size_t)i * NN3 + 2 * (size_t)g.N * g.N,
+                          (size_t)g.N * g.N * sizeof(zd), cudaMemcpyDeviceToDevice, ws) == cudaSuccess
+              ? BS_OK
+              : bs_cuda_status(cudaGetLastError(), "batch L_R");
+    if (!r) r = cudaMemsetAsync(wk->d_info, 0, 2 * sizeof(int), ws) == cudaSuccess
+                    ? BS_OK
+                    : bs_cuda_status(cudaGetLastError(), "batch info");
+    if (!r) r = bs_launch_monomials(wk, ws);
     if (!r) {
       or_flags_kernel<<<1, 32, 0, ws>>>(wk->d_info, g.d_err + 1);
       r = cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA;
       if (r) bs_set_error("or_flags_kernel launch failed");
     }
     if (!r && B->d_vec)
-      r = cudaMemcpyAsync(g.lLinv + (size_t)i * g.N * g.N, wk->d_Linv + 2 * (size_t)g.N * g.N,
+      r = cudaMemcpyAsync(g.lLinv + (size_t)i * g.N * g.N, g.gLinv + (size_t)i * NN3 + 2 * (size_t)g.N * g.N,
                           (size_t)g.N * g.N * sizeof(zd), cudaMemcpyDeviceToDevice, ws) == cudaSuccess
               ? BS_OK
               : bs_cuda_status(cudaGetLastError(), "batch L_R stash");
@@ -670,6 +742,10 @@ extern "C" int bs_batch_create(const bs_cell_desc* descs, int ncells, int nk, in
     }
     if (!r) {
       cudaError_t e = cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.gstream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.gdone, cudaEventDisableTiming);
+      for (int w = 0; w < g.nworkers && e == cudaSuccess; ++w)
+        e = cudaEventCreateWithFlags(&g.tdone[w], cudaEventDisableTiming);
       for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
         e = cudaEventCreateWithFlags(&g.rdone[p], cudaEventDisableTiming);
         for (int w = 0; w < g.nworkers && e == cudaSuccess; ++w)
