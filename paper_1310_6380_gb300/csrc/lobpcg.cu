@@ -1015,8 +1015,12 @@ __global__ void __launch_bounds__(UT, 2) lob_update_kernel(LobWs w, int n, int k
         ax[c] = zf0();
         ap[c] = zf0();
       }
+      // the next basis entry is loaded while this one is used (the loop is
+      // otherwise one L2 round trip per step)
+      zf vn = m > 0 ? src[(size_t)sm.colA[0] * n + r] : zf0();
       for (int i = 0; i < m; ++i) {
-        const zf v = src[(size_t)sm.colA[i] * n + r];
+        const zf v = vn;
+        if (i + 1 < m) vn = src[(size_t)sm.colA[i + 1] * n + r];
         const float4* zr = reinterpret_cast<const float4*>(sm.Zs + i * LB);
         const float4* yr = reinterpret_cast<const float4*>(sm.Ys + i * LB);
 #pragma unroll
