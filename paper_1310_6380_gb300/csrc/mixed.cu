@@ -97,15 +97,22 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
 // pivoting of the tridiagonal), two solves from a pseudo-random start, then
 // modified Gram-Schmidt of the block in FP64.  Thread i < b owns vector i.
 // Also writes the diagonal unitary scaling D (T_complex = D T_real D^dagger).
+// in_smem: the b x n block lives in shared memory while it is built and
+// orthogonalised (the b (b + 1) / 2 dependent dot products of the
+// Gram-Schmidt sweep then run on shared memory), and is stored at the end;
+// used when there are few problems (one large CTA per SM), otherwise the
+// block stays in global memory and many small CTAs share each SM.
 __global__ void tri_eigvec_kernel(const double* __restrict__ de, const zd* __restrict__ beta,
                                   const double* __restrict__ lam, int n, int b, int lstride,
                                   double* __restrict__ scratch, double* __restrict__ Y,
-                                  zd* __restrict__ phase) {
-  __shared__ double red[64];
+                                  zd* __restrict__ phase, bool in_smem) {
+  extern __shared__ double ysh[];
+  __shared__ double red[32];
   const int k = blockIdx.x, tid = threadIdx.x;
   const double* d = de + (size_t)k * 2 * n;
   const double* e = d + n;
-  double* y = Y + (size_t)k * b * n;
+  double* yg = Y + (size_t)k * b * n;
+  double* y = in_smem ? ysh : yg;
   if (tid < b) {
     const int i = tid;
     double* u0 = scratch + ((size_t)k * b + i) * 5 * n;
@@ -199,6 +206,8 @@ __global__ void tri_eigvec_kernel(const double* __restrict__ de, const zd* __res
       __syncthreads();
     }
   }
+  if (in_smem)
+    for (int q = tid; q < b * n; q += blockDim.x) yg[q] = ysh[q];
 }
 
 // ------------------------------------------------------------ back-transformation
@@ -804,7 +813,25 @@ int bs_launch_mixed_refine(const MixedWs& w, int n, int kb, int nbands, int b, d
                            double floor2, double* omega, int* stat, cudaStream_t s) {
   zero_int_kernel<<<(kb + 255) / 256, 256, 0, s>>>(stat, kb);
   BS_CHECK_LAUNCH("zero_int_kernel");
-  tri_eigvec_kernel<<<kb, 64, 0, s>>>(w.de, w.beta, w.lamT, n, b, b + 1, w.scratch, w.Y, w.phase);
+  // the vector block in shared memory when it fits (n <= about 900 at b = 28)
+  const size_t ysm = (size_t)b * n * sizeof(double);
+  int smax = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    smax = 0;
+  }
+  // shared memory pays when the problems do not fill the GPU anyway (one
+  // large block per SM); with many problems, many small CTAs per SM win
+  const bool in_smem = ysm + 1024 <= (size_t)smax && kb <= 2 * bs_sm_count();
+  if (in_smem && ysm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(tri_eigvec_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)ysm);
+    if (e != cudaSuccess) return bs_cuda_status(e, "tri_eigvec smem");
+  }
+  tri_eigvec_kernel<<<kb, in_smem ? 256 : 64, in_smem ? ysm : 0, s>>>(
+      w.de, w.beta, w.lamT, n, b, b + 1, w.scratch, w.Y, w.phase, in_smem);
   BS_CHECK_LAUNCH("tri_eigvec_kernel");
   backtransform_kernel<<<dim3(kb, (b + 7) / 8), 256, 0, s>>>(w.C32, w.tau, w.phase, w.Y, n, b,
                                                               w.X32, w.X64);
