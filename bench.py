@@ -369,15 +369,27 @@ def measure_mixed(bs, torch, args, cell, M, nb, nk, Qd, stream, flush, barrier, 
             "_omega": om}
 
 
-def measure_tensor(bs, torch, stream, nk, n):
+def slice_slabs(S, Kp, slab_k=4032):
+    """Lengths of the slabs of an exact-slice product with S digit planes of
+    width Kp: digit order u spans (u + 1) Kp terms, cut at slab_k."""
+    out = []
+    for u in range(S):
+        n = (u + 1) * Kp
+        out += [min(slab_k, n - k0) for k0 in range(0, n, slab_k)]
+    return out
+
+
+def measure_tensor(bs, torch, stream, nk, n, b=28, S=7):
     """Tensor-core utilisation of the exact-slice contraction on the shape of the
-    mixed path's Rayleigh-Ritz products (nk x [6n x 336 x 2n])."""
-    rng = np.random.default_rng(0)
-    zb, Mg, Ng, Kg = nk, 6 * n, 2 * 6 * 28, (2 * n + 7) // 8 * 8
-    bits = lambda a: torch.from_numpy(
-        (np.asarray(a, np.float32).view(np.uint32) >> 16).astype(np.uint16)).cuda()
-    Ag = bits(rng.integers(-64, 65, (zb, Mg, Kg)))
-    Bg = bits(rng.integers(-64, 65, (zb, Ng, Kg)))
+    mixed path's Rayleigh-Ritz products: per wavevector, the slabs of the
+    digit orders of [n x 2b] over K = 2n (their mean length)."""
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    slabs = slice_slabs(S, (2 * n + 63) // 64 * 64)
+    zb, Mg, Ng, Kg = nk * len(slabs), n, 2 * b, sum(slabs) // len(slabs) // 64 * 64
+    digits = lambda shape: torch.randint(-64, 65, shape, generator=gen, device="cuda",
+                                         dtype=torch.int8).to(torch.bfloat16).view(torch.uint16)
+    Ag = digits((zb, Mg, Kg))
+    Bg = digits((zb, Ng, Kg))
     Dg = torch.empty((zb, Ng, Mg), dtype=torch.float32, device="cuda")
     for _ in range(2):
         bs.bs_gemm_bf16(Ag, Bg, Dg, stream)
@@ -394,7 +406,8 @@ def measure_tensor(bs, torch, stream, nk, n):
     _, bf16_peak, note = measured_peaks()
     tflops = 2.0 * zb * Mg * Ng * Kg / (tc_ms / 1e3) / 1e12
     return {"kernel": "slice_gemm_kernel (tcgen05.mma kind::f16, TMA, TMEM)",
-            "shape": f"{zb} x [{Mg} x {Ng} x {Kg}] BF16 -> FP32", "ms": tc_ms,
+            "shape": f"{zb} x [{Mg} x {Ng} x {Kg}] BF16 -> FP32 ({nk} wavevectors x "
+                     f"{len(slabs)} digit-order slabs of mean length {Kg})", "ms": tc_ms,
             "achieved_tflops": tflops, "peak_tflops": bf16_peak,
             "peak_source": "bf16 burst, " + note, "frac": tflops / bf16_peak}
 
@@ -535,10 +548,11 @@ def measure_assembly(bs, torch, stream, cell, M, ph_c1):
 
     def figures(P, Mt, ms):
         D = 4 * Mt + 1
-        Kp = (P + 7) // 8 * 8
-        issued = 2.0 * (3 * S * P) * (2 * S * D) * Kp
+        slabs = slice_slabs(S, (P + 63) // 64 * 64)
+        issued = 2.0 * (3 * P) * (2 * D) * sum(slabs)
         algo = 3.0 * (4.0 * D * P * P + 8.0 * D * D * P)
-        return {"P": P, "M": Mt, "gemm": f"[{3 * S * P} x {2 * S * D} x {Kp}] BF16 digit planes",
+        return {"P": P, "M": Mt, "gemm": f"{len(slabs)} digit-order slabs of [{3 * P} x {2 * D}], "
+                                         f"{sum(slabs)} BF16 terms in all",
                 "ms_per_launch": ms, "issued_bf16_flops": issued,
                 "algorithmic_flops_per_cell": algo,
                 "issued_tflops": issued / (ms / 1e3) / 1e12,

@@ -244,11 +244,39 @@ int bs_launch_zgemm(bool conjA, bool conjB, int m, int nn, int k, zd alpha,
 int bs_launch_monomials(bs_cell* c, cudaStream_t s);
 
 // tc_gemm.cu / slices.cu: exact-slice contractions on tcgen05
-#define BS_SLICES_ASM 7   // digit planes per operand in the assembly (~2^-48)
-#define BS_SLICES_RR 6    // digit planes per operand in C X (~2^-41)
+#define BS_SLICES_ASM 7   // digit planes per operand in the assembly (~2^-46)
+#define BS_SLICES_RR 7    // digit planes per operand in C X (~2^-46)
 // D[z][n][m] = sum_k A[z][m][k] B[z][n][k]; BF16 operands, K % 8 == 0, K <= 4096
 int bs_launch_slice_gemm(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
                          int batch, long sA, long sB, long ldd, long sD, int* err, cudaStream_t s);
+// Digit orders of an exact-slice product.  The operands hold their S digit
+// planes side by side along K, each Kp wide (Kp % 64 == 0): A row m is
+// [A_0 | A_1 | ... | A_{S-1}], B row n the reverse [B_{S-1} | ... | B_0].  The
+// order-u sum  sum_{s+t=u} A_s B_t^T  is then one contraction over A columns
+// [0, (u+1) Kp) against B columns [(S-1-u) Kp, S Kp); it is split into slabs
+// of at most BS_SLAB_K terms (the FP32 accumulator stays exact: every digit
+// product is at most 2^12 in magnitude).  Orders u >= S are dropped: order S
+// weighs at most (S - 1) 2^-7S of |A||B| per term, the size of the digits' own
+// truncation (2^-7S per operand), so S = 7 keeps about 2^-46.
+#define BS_SLAB_MAX 64
+#define BS_SLAB_K 4032
+struct SliceSlabs {
+  int nq;                    // slabs
+  int order[BS_SLAB_MAX];    // digit order u of slab q
+  int a0[BS_SLAB_MAX];       // first A column
+  int b0[BS_SLAB_MAX];       // first B column
+  int len[BS_SLAB_MAX];      // columns (a multiple of 64)
+};
+// the slabs of S digits of width Kp for an M x N product over `batch`
+// entries (cut finer while the launch would have fewer than two CTAs per
+// SM); false when they do not fit BS_SLAB_MAX
+bool bs_slice_slabs(int S, int Kp, int M, int N, int batch, SliceSlabs* q);
+// (entry, slab) output planes to allocate for any batch up to `batch`
+size_t bs_slice_planes(int S, int Kp, int M, int N, int batch);
+// D[z][q][n][m] = sum_{k < len_q} A[z][m][a0_q + k] B[z][n][b0_q + k] for every
+// slab q of (S, Kp); A: batch x M x S Kp, B: batch x N x S Kp
+int bs_launch_slice_orders(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int S,
+                           int Kp, int batch, int* err, cudaStream_t s);
 int bs_launch_fields_tc(bs_cell* c, cudaStream_t s);
 size_t bs_fields_tc_elems(int P, int D, int nf, size_t* nA, size_t* nB, size_t* nD);
 int bs_launch_cx_tc(const zd* C, const zd* X, int n, int b, int kb, uint16_t* sA, uint16_t* sB,

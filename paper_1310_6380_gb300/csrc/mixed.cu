@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(256) certify_kernel(
     }
   }
   __syncthreads();
-  // the FP64 product C X carries an error of order 2^-41 |C| |X| per entry:
+  // the FP64 product C X carries an error of order 2^-46 |C| |X| per term:
   // allow for it in the residual norms (a negligible widening)
   const double ecx = 0x1p-36 * cmax_s;
 #pragma unroll

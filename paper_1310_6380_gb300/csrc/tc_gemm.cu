@@ -14,10 +14,16 @@
 // The library feeds it "digit planes": an FP64 operand x with per-row
 // scale 2^e is written as sum_s t_s 2^(e - 6 - 7s) with integer digits
 // |t_s| <= 64 (balanced rounding, radix 2^7).  Every product of two digits
-// is an integer of magnitude <= 2^12 and every sum over K <= 4096 terms
-// stays below 2^24, so the FP32 accumulation is exact, and the FP64
-// recombination of the digit-pair products reproduces the FP64 contraction
-// to about 2^-47 of |A||B| (six digits) on the BF16 tensor pipe.
+// is an integer of magnitude <= 2^12 and every sum over at most 4032 terms
+// stays below 2^24, so the FP32 accumulation is exact.  The S digit planes
+// sit side by side along K (B's in reverse order), so one slab of the
+// contraction forms a whole digit order sum_{s+t=u} A_s B_t^T at once; the
+// slab table (order, first A and B column, length) rides in the kernel's
+// parameters and blockIdx.z picks the slab.  The FP64 recombination of the
+// orders u < S reproduces the FP64 contraction to about 2^-46 of |A||B|
+// (seven digits) on the BF16 tensor pipe.
+#include <atomic>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -26,7 +32,7 @@
 
 namespace {
 
-constexpr int BM = 128, BNMAX = 128, BK = 64, STAGES = 3;
+constexpr int BM = 128, BK = 64, STAGES = 3;
 constexpr int TILE_A = BM * BK * 2;                    // bytes per stage
 __host__ __device__ constexpr int tile_b(int bn) { return bn * BK * 2; }
 __host__ __device__ constexpr int smem_bytes(int bn) { return STAGES * (TILE_A + tile_b(bn)) + 1024; }
@@ -93,11 +99,14 @@ __host__ __device__ constexpr uint32_t idesc(int bn) {
          ((uint32_t)(BM >> 4) << 24);
 }
 
+// blockIdx.z = z * slabs.nq + q: batch entry z, slab q (one slab of the
+// whole K for a plain contraction)
 template <int BN>
 __global__ void __launch_bounds__(128, 2)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, float* __restrict__ D, int M,
-                      int N, int K, long ldd, long strideD, int* __restrict__ err) {
+                      int N, long ldd, long strideD, const SliceSlabs slabs,
+                      int* __restrict__ err) {
   constexpr int TILE_B = tile_b(BN);
   constexpr uint32_t IDESC = idesc(BN);
   extern __shared__ uint8_t smem_raw[];
@@ -107,8 +116,10 @@ __global__ void __launch_bounds__(128, 2)
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * TILE_A;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, z = blockIdx.z;
-  const int nk = (K + BK - 1) / BK;
+  const int q = blockIdx.z % slabs.nq, z = blockIdx.z / slabs.nq;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int ka = slabs.a0[q], kbb = slabs.b0[q];
+  const int nk = (slabs.len[q] + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -136,8 +147,8 @@ __global__ void __launch_bounds__(128, 2)
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
       if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, err)) break;
       mbar_expect_tx(&full[s], TILE_A + TILE_B);
-      tma_load_3d(sA + s * TILE_A, &tmA, kb * BK, m0, z, &full[s]);
-      tma_load_3d(sB + s * TILE_B, &tmB, kb * BK, n0, z, &full[s]);
+      tma_load_3d(sA + s * TILE_A, &tmA, ka + kb * BK, m0, z, &full[s]);
+      tma_load_3d(sB + s * TILE_B, &tmB, kbb + kb * BK, n0, z, &full[s]);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -173,7 +184,7 @@ __global__ void __launch_bounds__(128, 2)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
     const int m = m0 + warp * 32 + lane;
-    float* dz = D + (size_t)z * strideD;
+    float* dz = D + (size_t)blockIdx.z * strideD;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t v[16];
@@ -259,26 +270,98 @@ static int pick_bn(int N) {
 
 template <int BN>
 static int launch_bn(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
-                     int batch, long sA, long sB, long ldd, long sD, int* err, cudaStream_t s) {
+                     int batch, long sA, long sB, long ldd, long sD, const SliceSlabs& slabs,
+                     int* err, cudaStream_t s) {
   CUtensorMap ta, tb;
   int r = make_map(&ta, A, K, M, batch, sA, BM);
   if (!r) r = make_map(&tb, B, K, N, batch, sB, BN);
   if (r) return r;
-  static bool attr = false;
-  if (!attr) {
+  // the shared-memory opt-in is a per-device attribute of the kernel
+  static std::atomic<bool> attr[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!attr[dev].load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_bytes(BN));
     if (e != cudaSuccess) return bs_cuda_status(e, "slice GEMM smem");
-    attr = true;
+    attr[dev].store(true, std::memory_order_release);
   }
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, batch);
-  slice_gemm_kernel<BN><<<grid, 128, smem_bytes(BN), s>>>(ta, tb, D, M, N, K, ldd, sD, err);
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, batch * slabs.nq);
+  slice_gemm_kernel<BN><<<grid, 128, smem_bytes(BN), s>>>(ta, tb, D, M, N, ldd, sD, slabs, err);
   BS_CHECK_LAUNCH("slice_gemm_kernel");
   return BS_OK;
 }
 
+static int dispatch_bn(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
+                       int batch, long sA, long sB, long ldd, long sD, const SliceSlabs& slabs,
+                       int* err, cudaStream_t s) {
+  switch (pick_bn(N)) {
+    case 64: return launch_bn<64>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, slabs, err, s);
+    case 80: return launch_bn<80>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, slabs, err, s);
+    case 96: return launch_bn<96>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, slabs, err, s);
+    case 112: return launch_bn<112>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, slabs, err, s);
+    default: return launch_bn<128>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, slabs, err, s);
+  }
+}
+
 }  // namespace
+
+// slabs of at most L terms (L % 64 == 0); false when there are more than BS_SLAB_MAX
+static bool cut_slabs(int S, int Kp, int L, SliceSlabs* sl) {
+  sl->nq = 0;
+  for (int u = 0; u < S; ++u) {
+    const int len = (u + 1) * Kp;
+    for (int k0 = 0; k0 < len; k0 += L) {
+      if (sl->nq == BS_SLAB_MAX) return false;
+      const int q = sl->nq++;
+      sl->order[q] = u;
+      sl->a0[q] = k0;
+      sl->b0[q] = (S - 1 - u) * Kp + k0;
+      sl->len[q] = len - k0 < L ? len - k0 : L;
+    }
+  }
+  return true;
+}
+
+// The longest slabs (fewest FP32 partial products to store and add) unless
+// the launch would then leave SMs idle: while the CTAs number fewer than two
+// per SM, the slabs are halved (down to 128 terms), which trades a serial K
+// loop for parallel CTAs.  Small contractions (one cell's form factors) need
+// this; batched ones keep the longest slabs.
+bool bs_slice_slabs(int S, int Kp, int M, int N, int batch, SliceSlabs* sl) {
+  const int bn = pick_bn(N);
+  const long tiles = (long)((M + BM - 1) / BM) * ((N + bn - 1) / bn) * batch;
+  const long want = 2L * bs_sm_count();
+  int L = BS_SLAB_K;
+  if (!cut_slabs(S, Kp, L, sl)) return false;
+  while (tiles * sl->nq < want && L > 128) {
+    const int L2 = (L / 2) / 64 * 64 < 128 ? 128 : (L / 2) / 64 * 64;
+    SliceSlabs t;
+    if (!cut_slabs(S, Kp, L2, &t)) break;
+    *sl = t;
+    L = L2;
+  }
+  return true;
+}
+
+size_t bs_slice_planes(int S, int Kp, int M, int N, int batch) {
+  // a smaller batch may cut its slabs finer: take the largest count of
+  // (entry, slab) output planes over every batch size up to `batch`
+  SliceSlabs full, sl;
+  if (!cut_slabs(S, Kp, BS_SLAB_K, &full)) return (size_t)BS_SLAB_MAX * batch;
+  const int bn = pick_bn(N);
+  const long t1 = (long)((M + BM - 1) / BM) * ((N + bn - 1) / bn);
+  size_t best = (size_t)full.nq * batch;
+  // from the first batch size whose longest slabs already give two CTAs per
+  // SM on, nothing is cut and the count grows with the batch
+  for (int b = 1; b <= batch && t1 * full.nq * b < 2L * bs_sm_count(); ++b) {
+    if (!bs_slice_slabs(S, Kp, M, N, b, &sl)) return (size_t)BS_SLAB_MAX * batch;
+    const size_t v = (size_t)sl.nq * b;
+    if (v > best) best = v;
+  }
+  return best;
+}
 
 int bs_launch_slice_gemm(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
                          int batch, long sA, long sB, long ldd, long sD, int* err,
@@ -288,11 +371,24 @@ int bs_launch_slice_gemm(const uint16_t* A, const uint16_t* B, float* D, int M, 
     bs_set_error("slice GEMM: need K %% 8 == 0, K <= 4096, 16-byte aligned operands");
     return BS_EINVAL;
   }
-  switch (pick_bn(N)) {
-    case 64: return launch_bn<64>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
-    case 80: return launch_bn<80>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
-    case 96: return launch_bn<96>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
-    case 112: return launch_bn<112>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
-    default: return launch_bn<128>(A, B, D, M, N, K, batch, sA, sB, ldd, sD, err, s);
+  SliceSlabs one;
+  one.nq = 1;
+  one.order[0] = 0;
+  one.a0[0] = one.b0[0] = 0;
+  one.len[0] = K;
+  return dispatch_bn(A, B, D, M, N, K, batch, sA, sB, ldd, sD, one, err, s);
+}
+
+int bs_launch_slice_orders(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int S,
+                           int Kp, int batch, int* err, cudaStream_t s) {
+  SliceSlabs sl;
+  if (Kp % 64 != 0 || S < 1 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M < 1 || N < 1 ||
+      batch < 1 || !bs_slice_slabs(S, Kp, M, N, batch, &sl) || (long)batch * sl.nq > 65535) {
+    bs_set_error("slice orders: need Kp %% 64 == 0, 16-byte aligned operands, at most %d slabs",
+                 BS_SLAB_MAX);
+    return BS_EINVAL;
   }
+  const int K = S * Kp;
+  return dispatch_bn(A, B, D, M, N, K, batch, (long)M * K, (long)N * K, M, (long)M * N, sl, err,
+                     s);
 }
