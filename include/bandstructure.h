@@ -252,6 +252,30 @@ int bs_solve_k_lobpcg(bs_cell* cell, const double* Q, int nk, int nbands,
 int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps);
 
 /*
+ * bs_set_reduction - how the FP64 path (BS_PREC_FP64 cells, the batch's
+ * BS_SOLVER_FP64 and its FP64 fallback) reduces C(k) to real tridiagonal
+ * form before the Sturm multisection of Eq. (eigenvalueproblem)'s lowest
+ * eigenvalues.  The paper leaves the eigensolve to a host library; both
+ * modes are unitary similarity transformations, so the eigenvalues agree
+ * to rounding:
+ *   BS_REDUCE_ONESTAGE: Householder reflectors column by column, on the
+ *     FP64 pipe ((16/3) n^3 flops per k);
+ *   BS_REDUCE_TWOSTAGE: dense -> band of half-width 8 by blocked Householder
+ *     QR, the trailing two-sided updates as FP64-exact digit-plane products
+ *     on the tensor cores (8 digits of 7 bits per operand), then band ->
+ *     tridiagonal by bulge chasing in FP64 (O(n^2) work per k);
+ *   BS_REDUCE_AUTO (default): two-stage for n >= 400, one-stage below.
+ * Process-wide; takes effect at the next solve.  The two-stage reduction
+ * needs an n x 8 complex panel in shared memory (n up to about 1800 on
+ * GB300); larger n use the one-stage reduction in every mode.
+ * Errors: BS_EINVAL for any other mode.
+ */
+#define BS_REDUCE_AUTO     0
+#define BS_REDUCE_ONESTAGE 1
+#define BS_REDUCE_TWOSTAGE 2
+int bs_set_reduction(int mode);
+
+/*
  * bs_form_factors - copy the assembled form factors to `out`
  * (host or device): 3 fields (1/(lam+mu), 1/mu, rho), or the 7 of a cell
  * given bs_set_stiffness (S11, S22, rho, S12, S13, S23, S33), x D x D complex

@@ -98,6 +98,7 @@ def _load():
         "bs_batch_vectors": [vp, dp],
         "bs_probe_fp64": [i32, i32, dp, vp],
         "bs_set_iteration_limits": [i32, i32],
+        "bs_set_reduction": [i32],
         "bs_batch_set_tile": [vp, i32],
         "bs_stress_coefficients": [vp, dp, i32, i32, dp, dp, vp],
         "bs_mode_field": [vp, dp, i32, i32, dp, i32, dp, vp],
@@ -133,9 +134,11 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_cnn_get_params", "bs_cnn_forward", "bs_cnn_train_step", "bs_stress_coefficients",
             "bs_mode_field", "bs_create_cell_mesh", "bs_set_stiffness", "bs_create_cell3",
             "bs_assemble3", "bs_solve_k3", "bs_form_factors3", "bs_reduced_matrix3",
-            "bs_cell3_dims", "bs_destroy_cell3", "bs_set_iteration_limits", "bs_probe_fp64"]
+            "bs_cell3_dims", "bs_destroy_cell3", "bs_set_iteration_limits", "bs_probe_fp64",
+            "bs_set_reduction"]
 BS_SOLVER_DENSE, BS_SOLVER_LOBPCG, BS_SOLVER_FP64 = 0, 1, 2
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
+BS_REDUCE_AUTO, BS_REDUCE_ONESTAGE, BS_REDUCE_TWOSTAGE = 0, 1, 2
 
 
 def bs_last_error() -> str:
@@ -389,6 +392,11 @@ def bs_probe_fp64(blocks_per_sm: int = 4, iters: int = 20000, stream=None) -> fl
 def bs_set_iteration_limits(lobpcg_maxit: int = 0, bisect_sweeps: int = 0):
     """Process-wide iteration caps (tests and diagnostics); 0 restores the defaults."""
     _check(_lib.bs_set_iteration_limits(int(lobpcg_maxit), int(bisect_sweeps)))
+
+
+def bs_set_reduction(mode: int):
+    """Process-wide reduction to tridiagonal form of the FP64 path (BS_REDUCE_*)."""
+    _check(_lib.bs_set_reduction(int(mode)))
 
 
 def bs_batch_set_tile(batch, tile: int):

@@ -65,6 +65,28 @@ int bs_sm_count() {
 }
 int bs_bisect_sweeps() { return g_bisect_sweeps.load(std::memory_order_relaxed); }
 
+static std::atomic<int> g_reduction{BS_REDUCE_AUTO};
+
+// the reduction to tridiagonal form of the FP64 eigensolve for dimension n:
+// the two-stage (band) reduction from BS_BAND_AUTO_MIN on, where its
+// tensor-core products outrun the one-stage reduction's FP64 pipe
+bool bs_use_band(int n) {
+  const int mode = g_reduction.load(std::memory_order_relaxed);
+  if (!bs_band_supported(n)) return false;
+  if (mode == BS_REDUCE_TWOSTAGE) return true;
+  if (mode == BS_REDUCE_ONESTAGE) return false;
+  return n >= BS_BAND_AUTO_MIN;
+}
+
+extern "C" int bs_set_reduction(int mode) {
+  if (mode != BS_REDUCE_AUTO && mode != BS_REDUCE_ONESTAGE && mode != BS_REDUCE_TWOSTAGE) {
+    bs_set_error("bs_set_reduction: mode %d is not BS_REDUCE_AUTO, _ONESTAGE or _TWOSTAGE", mode);
+    return BS_EINVAL;
+  }
+  g_reduction.store(mode, std::memory_order_relaxed);
+  return BS_OK;
+}
+
 extern "C" int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps) {
   if (lobpcg_maxit > 1000 || bisect_sweeps > 128) {
     bs_set_error("bs_set_iteration_limits: need lobpcg_maxit <= 1000 and bisect_sweeps <= 128");
@@ -142,6 +164,11 @@ static int copy_in(void* ddst, const void* src, size_t bytes, cudaStream_t s) {
 }
 
 static void free_workspace(bs_cell* c) {
+  if (c->band) {
+    bs_band_ws_free(c->band);
+    delete c->band;
+    c->band = nullptr;
+  }
   void* mixed[] = {c->d_C32, c->d_vec32, c->d_part32, c->d_lamT, c->d_scr, c->d_mY, c->d_mphase,
                    c->d_X32, c->d_X64, c->d_CX, c->d_mG, c->d_H, c->d_W, c->d_theta, c->d_beta,
                    c->d_cxA, c->d_cxB, c->d_cxD, c->d_cxeA, c->d_cxeB};
@@ -727,8 +754,14 @@ static int solve_chunk(bs_cell* c, int kb, int nbands, cudaStream_t s) {
                         s));
   bs_phase_end(c, PH_BUILD, s);
   bs_phase_begin(c, PH_TRID, s);
-  TRY(bs_launch_tridiag<double>(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
-                                c->d_beta, c->d_count, s));
+  if (bs_use_band(c->n)) {
+    if (!c->band) c->band = new BandWs();
+    TRY(bs_band_ws_alloc(c->band, c->n, c->kcap, BS_SLICES_BAND));
+    TRY(bs_launch_eig_band(c->d_C, c->n, kb, *c->band, c->d_de, c->d_info + 1, s));
+  } else {
+    TRY(bs_launch_tridiag<double>(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
+                                  c->d_beta, c->d_count, s));
+  }
   bs_phase_end(c, PH_TRID, s);
   bs_phase_begin(c, PH_BISECT, s);
   TRY(bs_launch_bisect(c->d_de, c->n, kb, nbands, c->d_w, c->d_stat, s));

@@ -1,0 +1,602 @@
+// Two-stage reduction of batched Hermitian matrices to real tridiagonal
+// form, for the FP64 eigensolve of Eq. (eigenvalueproblem) once the pencil
+// is in standard form C(k) u = lambda u.
+//
+// The one-stage Householder reduction (tridiag.cu) spends half of its
+// (16/3) n^3 flops in a matrix-vector product per column, so it stays on
+// the FP64 pipe, which GB300 runs at 2 FMA per clock per SM.  Here the
+// O(n^3) work becomes matrix-matrix products for the tensor cores:
+//
+//  stage 1, dense -> band of half-width nb (nb = 8): for the panel of
+//    columns j .. j+nb-1, a Householder QR of its m x nb block below the
+//    band, P = Q R with Q = I - V T V^dagger (compact WY, T upper
+//    triangular), puts R in the band; the trailing block is updated as
+//    Q^dagger A22 Q = A22 - V W^dagger - W V^dagger with
+//      Y = A22 V T,  Z = V^dagger Y,  W = Y - (1/2) V T^dagger Z.
+//    A22 V and the rank-2nb update run as exact-slice digit-plane
+//    contractions on tcgen05 (slices.cu), the QR and W in FP64;
+//  stage 2, band -> tridiagonal by bulge chasing: sweep s annihilates
+//    column s below its subdiagonal with a reflector of length nb, applies
+//    it on both sides of the next diagonal block, and chases the bulge it
+//    makes one block further down with a new reflector per block.  One CTA
+//    per matrix, eight lanes per sweep in flight: sweep s + 1 starts three
+//    blocks behind sweep s, so the blocks that the sweeps touch in one step
+//    are disjoint, and a block-wide barrier separates the steps.
+//
+// The unitary similarity keeps the eigenvalues; the tridiagonal is returned
+// as (d, |e|) for the Sturm multisection (bisect.cu).
+#include <algorithm>
+
+#include "bs_internal.h"
+
+namespace {
+
+constexpr int QR_NT = 256;   // threads of the panel QR and W kernels
+constexpr int LAG = 3;       // blocks between consecutive sweeps
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- symmetrise
+// Upper triangle <- conjugate of the lower one, real diagonal; the builders
+// write the lower triangle only.  32 x 32 tiles through shared memory.
+__global__ void symmetrize_kernel(zd* __restrict__ A, int n) {
+  __shared__ zd tile[32][33];
+  const int bi = blockIdx.x, bj = blockIdx.y;
+  if (bi < bj) return;
+  zd* a = A + (size_t)blockIdx.z * n * n;
+  const int x = threadIdx.x;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int r = bi * 32 + x, c = bj * 32 + y;   // lower tile element (r, c)
+    if (r < n && c < n) tile[y][x] = a[r + (size_t)c * n];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int r = bj * 32 + x, c = bi * 32 + y;   // upper element (r, c) = conj(A[c, r])
+    if (r < n && c < n) {
+      if (r < c) {
+        const zd v = tile[x][y];
+        a[r + (size_t)c * n] = zconj(v);
+      } else if (r == c) {
+        a[r + (size_t)c * n].y = 0.0;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- panel QR
+// Block-wide sum of NV complex values held by every thread; the result is
+// left in out[0 .. NV).  sh: NV x (QR_NT/32) zd.
+template <int NV>
+__device__ void block_zsum(zd (&v)[NV], zd* sh, zd* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    v[q].x = warp_sum_d(v[q].x);
+    v[q].y = warp_sum_d(v[q].y);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q * (QR_NT / 32) + warp] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    zd t = zmake(0.0, 0.0);
+    for (int w = 0; w < QR_NT / 32; ++w) t = zadd(t, sh[threadIdx.x * (QR_NT / 32) + w]);
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// Householder QR of the panel A[j+NB : n, j : j+NB] (m x NB) of every
+// matrix of the batch, in shared memory.  Thread t owns rows t, t + QR_NT,
+// ... of the panel throughout.  Writes R (upper triangle) and zeros below
+// it back into the panel, V (m x NB, unit lower trapezoidal, leading
+// dimension ldv) and T (NB x NB upper triangular, column-major).
+template <int NB>
+__global__ void __launch_bounds__(QR_NT) panel_qr_kernel(zd* __restrict__ A, int n, int j,
+                                                         zd* __restrict__ V, int ldv, long sv,
+                                                         zd* __restrict__ T) {
+  extern __shared__ zd P[];   // [NB][m]
+  __shared__ zd red[NB * (QR_NT / 32)];
+  __shared__ zd dots[NB];
+  __shared__ zd G[NB][NB];    // G[a][i] = v_a^dagger v_i, a < i
+  __shared__ double tau_s[NB];
+  __shared__ zd beta_s[NB];
+  __shared__ zd alpha_s;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const int m = n - j - NB;
+  zd* a = A + (size_t)k * n * n;
+  for (int idx = tid; idx < NB * m; idx += QR_NT) {
+    const int i = idx / m, r = idx % m;
+    P[idx] = a[(size_t)(j + i) * n + j + NB + r];
+  }
+  __syncthreads();
+  const int kk = min(NB, m - 1);   // reflectors of length >= 2
+  for (int i = 0; i < kk; ++i) {
+    zd* pi = P + (size_t)i * m;
+    // ||x[1:]||^2 of x = P[i][i:]
+    double s = 0.0;
+    for (int r = tid; r < m; r += QR_NT) {
+      if (r > i) s = fma(pi[r].x, pi[r].x, fma(pi[r].y, pi[r].y, s));
+      if (r == i) alpha_s = pi[r];
+    }
+    zd sv1[1] = {zmake(s, 0.0)};
+    block_zsum<1>(sv1, red, dots);
+    const zd alpha = alpha_s;
+    const double aa = hypot(alpha.x, alpha.y);
+    const double nu = sqrt(fma(aa, aa, dots[0].x));
+    double tau = 0.0;
+    zd beta = zmake(0.0, 0.0), scale = zmake(0.0, 0.0);
+    if (nu > 0.0) {
+      beta = aa > 0.0 ? zscale(alpha, -nu / aa) : zmake(-nu, 0.0);
+      tau = (aa + nu) / nu;
+      const zd den = zsub(alpha, beta);
+      const double d2 = den.x * den.x + den.y * den.y;
+      scale = zmake(den.x / d2, -den.y / d2);
+    }
+    // v = x / (x0 - beta) below the diagonal, and the dot products
+    // z_c = v^dagger P[c] (c > i) and G[a][i] = v_a^dagger v (a < i)
+    zd acc[NB > 1 ? NB - 1 : 1];
+#pragma unroll
+    for (int q = 0; q < NB - 1; ++q) acc[q] = zmake(0.0, 0.0);
+    for (int r = tid; r < m; r += QR_NT) {
+      if (r < i) continue;
+      zd vr;
+      if (r == i) {
+        vr = zmake(1.0, 0.0);
+      } else {
+        vr = zmul(pi[r], scale);
+        pi[r] = vr;
+      }
+#pragma unroll
+      for (int q = 0; q < NB - 1; ++q) {
+        if (q < i) {
+          // G[q][i]: v_q[r] (v_q[q] = 1, stored below its diagonal)
+          const zd vq = P[(size_t)q * m + r];
+          acc[q] = zfmac(vr, vq, acc[q]);   // conj(v_q[r]) v[r]
+        } else {
+          const int c = q + 1;             // column c > i
+          if (c > i && c < NB) acc[q] = zfmac(P[(size_t)c * m + r], vr, acc[q]);
+        }
+      }
+    }
+    block_zsum<(NB > 1 ? NB - 1 : 1)>(acc, red, dots);
+    if (tid == 0) {
+      tau_s[i] = tau;
+      beta_s[i] = beta;
+      for (int q = 0; q < i; ++q) G[q][i] = dots[q];
+    }
+    // P[c] -= tau v (v^dagger P[c]) for c > i
+    for (int r = tid; r < m; r += QR_NT) {
+      if (r < i) continue;
+      const zd vr = r == i ? zmake(1.0, 0.0) : pi[r];
+#pragma unroll
+      for (int c = 1; c < NB; ++c) {
+        if (c <= i) continue;
+        const zd z = zscale(dots[c - 1], tau);
+        P[(size_t)c * m + r] = zsub(P[(size_t)c * m + r], zmul(vr, z));
+      }
+    }
+    __syncthreads();
+  }
+  // write back: R and zeros into the panel, V, then T
+  zd* vk = V + (size_t)k * sv;
+  for (int idx = tid; idx < NB * m; idx += QR_NT) {
+    const int i = idx / m, r = idx % m;
+    zd out, vv;
+    if (i < kk) {
+      out = r < i ? P[idx] : (r == i ? beta_s[i] : zmake(0.0, 0.0));
+      vv = r < i ? zmake(0.0, 0.0) : (r == i ? zmake(1.0, 0.0) : P[idx]);
+    } else {
+      out = P[idx];
+      vv = zmake(0.0, 0.0);
+    }
+    a[(size_t)(j + i) * n + j + NB + r] = out;
+    vk[(size_t)i * ldv + r] = vv;
+  }
+  if (tid == 0) {
+    // T (forward, columnwise): T[i][i] = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i];
+    // built in place of G's lower triangle and diagonal, column by column
+    zd* tk = T + (size_t)k * NB * NB;
+    for (int i = 0; i < NB; ++i) {
+      for (int r = 0; r < NB; ++r) {
+        zd t = zmake(0.0, 0.0);
+        if (i < kk) {
+          if (r == i) {
+            t = zmake(tau_s[i], 0.0);
+          } else if (r < i) {
+            for (int q = r; q < i; ++q) t = zfma(tk[r + q * NB], G[q][i], t);
+            t = zscale(t, -tau_s[i]);
+          }
+        }
+        tk[r + i * NB] = t;
+      }
+    }
+  }
+}
+
+// W = Y - (1/2) V (T^dagger Z), Y = X T, Z = V^dagger Y; one CTA per matrix
+// and dsc[i] = round((log2 max|W[:, i]| - log2 max|V[:, i]|) / 2), the
+// power of two that balances column i of V against column i of W in the
+// digit planes of the rank-2nb update
+template <int NB>
+__global__ void __launch_bounds__(QR_NT) wform_kernel(const zd* __restrict__ X,
+                                                      const zd* __restrict__ V,
+                                                      const zd* __restrict__ T, int ld, long sv,
+                                                      int m, zd* __restrict__ W,
+                                                      int* __restrict__ dsc) {
+  constexpr int NP = NB * NB, NG = QR_NT / NP > 0 ? QR_NT / NP : 1;
+  __shared__ zd Ts[NB][NB];
+  __shared__ zd Zp[NG][NP];
+  __shared__ zd M2[NB][NB];
+  __shared__ double cmax[2][NB][QR_NT / 32];
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const zd* xk = X + (size_t)k * sv;
+  const zd* vk = V + (size_t)k * sv;
+  zd* wk = W + (size_t)k * sv;
+  for (int idx = tid; idx < NP; idx += QR_NT) Ts[idx % NB][idx / NB] = T[(size_t)k * NP + idx];
+  __syncthreads();
+  for (int idx = tid; idx < m * NB; idx += QR_NT) {
+    const int r = idx % m, c = idx / m;
+    zd y = zmake(0.0, 0.0);
+    for (int q = 0; q <= c; ++q) y = zfma(xk[(size_t)q * ld + r], Ts[q][c], y);
+    wk[(size_t)c * ld + r] = y;
+  }
+  __syncthreads();
+  {
+    const int p = tid % NP, g = tid / NP;
+    if (g < NG) {
+      const int a = p % NB, c = p / NB;
+      zd z = zmake(0.0, 0.0);
+      for (int r = g; r < m; r += NG) z = zfmac(wk[(size_t)c * ld + r], vk[(size_t)a * ld + r], z);
+      Zp[g][p] = z;
+    }
+  }
+  __syncthreads();
+  if (tid < NP) {
+    zd z = zmake(0.0, 0.0);
+    for (int g = 0; g < NG; ++g) z = zadd(z, Zp[g][tid]);
+    Zp[0][tid] = z;   // Z[a][c] at index a + c NB
+  }
+  __syncthreads();
+  if (tid < NP) {
+    const int a = tid % NB, c = tid / NB;
+    zd t = zmake(0.0, 0.0);
+    for (int d = 0; d <= a; ++d) t = zfma(zconj(Ts[d][a]), Zp[0][d + c * NB], t);
+    M2[a][c] = t;
+  }
+  __syncthreads();
+  // thread -> (column c = tid % NB, rows r = tid / NB + i (QR_NT / NB)): the
+  // column maxima of V and W come out of the same pass
+  constexpr int RS = QR_NT / NB;
+  const int c = tid % NB;
+  double mv = 0.0, mw = 0.0;
+  for (int r = tid / NB; r < m; r += RS) {
+    zd t = zmake(0.0, 0.0);
+    for (int q = 0; q < NB; ++q) t = zfma(vk[(size_t)q * ld + r], M2[q][c], t);
+    zd y = wk[(size_t)c * ld + r];
+    y.x = fma(-0.5, t.x, y.x);
+    y.y = fma(-0.5, t.y, y.y);
+    wk[(size_t)c * ld + r] = y;
+    const zd v = vk[(size_t)c * ld + r];
+    mv = fmax(mv, fmax(fabs(v.x), fabs(v.y)));
+    mw = fmax(mw, fmax(fabs(y.x), fabs(y.y)));
+  }
+  // lanes l and l + NB, l + 2NB, ... of a warp share the column
+#pragma unroll
+  for (int o = NB; o < 32; o <<= 1) {
+    mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, o));
+    mw = fmax(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+  }
+  if ((tid & 31) < NB) {
+    cmax[0][c][tid >> 5] = mv;
+    cmax[1][c][tid >> 5] = mw;
+  }
+  __syncthreads();
+  if (tid < NB) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < QR_NT / 32; ++w) {
+      a = fmax(a, cmax[0][tid][w]);
+      b = fmax(b, cmax[1][tid][w]);
+    }
+    int ev = 0, ew = 0;
+    if (a > 0.0) frexp(a, &ev);
+    if (b > 0.0) frexp(b, &ew);
+    dsc[(size_t)k * NB + tid] = (a > 0.0 && b > 0.0) ? (ew - ev) / 2 : 0;
+  }
+}
+
+// ---------------------------------------------------------------- stage 2
+// Band storage: column c holds A[c + d, c] for d < 2 NB (d <= NB is the
+// band, the rest room for the bulges), complex, at bd[c 2NB + d].
+//
+// One sweep task works on an 8 x 8 block O (rows r0 .. r0+7 below the
+// columns C0 .. C0+7 of the previous reflector) and the diagonal block D
+// of rows r0 .. r0+7, on eight lanes, lane i holding row i of both, four
+// sweeps per warp.  Row sums are lane-local; column sums are a
+// reduce-scatter over the eight lanes (lane i ends with column i).  The
+// scalars of the reflector come from FP64 reciprocal square roots and one
+// reciprocal; GB300 issues FP64 at 2 operations per clock per SM, so every
+// redundant FP64 operation across lanes counts.
+constexpr int CH_NB = 8;                // band half-width of the chase
+constexpr int CH_WARPS = 16;            // warps per CTA
+constexpr int CH_SLOTS = CH_WARPS * 4;  // sweeps in flight per matrix
+
+__device__ __forceinline__ zd gshfl(zd v, int src) {
+  return zmake(__shfl_sync(0xffffffffu, v.x, src, 8), __shfl_sync(0xffffffffu, v.y, src, 8));
+}
+__device__ __forceinline__ zd gxor(zd v, int o) {
+  return zmake(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ zd sel(bool c, zd a, zd b) { return c ? a : b; }
+
+// sum over the eight lanes of a group of P[i] (lane i of the group): three
+// halving exchanges, 7 complex additions per lane
+__device__ __forceinline__ zd rscatter8(const zd (&P)[8], int i) {
+  const bool b2 = i & 4, b1 = i & 2, b0 = i & 1;
+  zd Q[4], R[2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Q[q] = zadd(sel(b2, P[q + 4], P[q]), gxor(sel(b2, P[q], P[q + 4]), 4));
+#pragma unroll
+  for (int q = 0; q < 2; ++q) R[q] = zadd(sel(b1, Q[q + 2], Q[q]), gxor(sel(b1, Q[q], Q[q + 2]), 2));
+  return zadd(sel(b0, R[1], R[0]), gxor(sel(b0, R[0], R[1]), 1));
+}
+
+__device__ __forceinline__ double gsum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+
+__global__ void __launch_bounds__(CH_WARPS * 32, 1)
+    bulge_kernel(const zd* __restrict__ A, int n, zd* __restrict__ band_g, int in_smem,
+                 double* __restrict__ de) {
+  constexpr int NB = CH_NB, W2 = 2 * NB;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int k = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int* T0 = reinterpret_cast<int*>(dsm);   // start step of each sweep
+  __shared__ int tend_s;
+  zd* bd = in_smem ? reinterpret_cast<zd*>(dsm + ((size_t)n * sizeof(int) + 15) / 16 * 16)
+                   : band_g + (size_t)k * n * W2;
+  const zd* a = A + (size_t)k * n * n;
+  for (int idx = tid; idx < n * W2; idx += CH_WARPS * 32) {
+    const int c = idx / W2, d = idx % W2;
+    zd v = zmake(0.0, 0.0);
+    if (d <= NB && c + d < n) v = a[(size_t)c * n + c + d];
+    if (d == 0) v.y = 0.0;
+    bd[idx] = v;
+  }
+  if (tid == 0) {
+    // sweep s runs on slot s mod CH_SLOTS, LAG steps after sweep s - 1
+    // started and once its slot's previous sweep has finished
+    int prev = -LAG, tend = 0;
+    for (int s = 0; s + 1 < n; ++s) {
+      const int nt = (n - 1 - s + NB - 1) / NB;
+      int t0 = prev + LAG;
+      if (s >= CH_SLOTS) {
+        const int sp = s - CH_SLOTS, ntp = (n - 1 - sp + NB - 1) / NB;
+        t0 = max(t0, T0[sp] + ntp);
+      }
+      T0[s] = t0;
+      prev = t0;
+      tend = max(tend, t0 + nt);
+    }
+    tend_s = tend;
+  }
+  __syncthreads();
+  const int tend = tend_s;
+  const int i = lane & 7;
+  int s = warp * 4 + (lane >> 3);   // this group's sweep
+  zd vp = zmake(0.0, 0.0);          // previous reflector of the sweep (row i)
+  double taup = 0.0;
+  const zd zero = zmake(0.0, 0.0);
+  for (int t = 0; t < tend; ++t) {
+    const bool act = s + 1 < n && t >= T0[s];
+    // the sweeps in flight are consecutive, so most warps have none: they
+    // skip the step's FP64 work (the pipe's issue slots are per warp)
+    if (!__any_sync(0xffffffffu, act)) {
+      __syncthreads();
+      continue;
+    }
+    const int kt = act ? t - T0[s] + 1 : 1;
+    const int C0 = kt == 1 ? s : s + 1 + (kt - 2) * NB;
+    const int Lc = kt == 1 ? 1 : NB;
+    const int r0 = C0 + Lc;
+    const int L = act ? min(r0 + NB - 1, n - 1) - r0 + 1 : 0;
+    const double tp = kt == 1 ? 0.0 : taup;
+    // O <- O H_prev (a no-op for the first task, whose O is column s)
+    zd O[8];
+    zd y = zero;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      O[j] = (i < L && j < Lc) ? bd[(size_t)(C0 + j) * W2 + (r0 + i - C0 - j)] : zero;
+      y = zfma(O[j], gshfl(vp, j), y);
+    }
+    const zd ty = zscale(y, tp);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) O[j] = zfnmac(ty, gshfl(vp, j), O[j]);
+    // reflector H = I - tau v v^dagger, H x = beta e1, x = column 0 of O
+    const zd x = O[0];
+    const double sq = gsum((i >= 1 && i < L) ? fma(x.x, x.x, x.y * x.y) : 0.0);
+    const zd al = gshfl(x, 0);
+    const double a2 = fma(al.x, al.x, al.y * al.y), s2 = a2 + sq;
+    double tau = 0.0;
+    zd beta = zero, scl = zero;
+    if (s2 > 0.0) {
+      const double rn = rsqrt(s2), nu = s2 * rn;
+      if (a2 > 0.0) {
+        const double ra = rsqrt(a2), aa = a2 * ra;
+        beta = zscale(al, -nu * ra);
+        tau = (aa + nu) * rn;
+        // 1 / (alpha - beta) = conj(alpha) ra / (|alpha| + nu)
+        scl = zscale(zconj(al), ra / (aa + nu));
+      } else {
+        beta = zmake(-nu, 0.0);
+        tau = 1.0;
+        scl = zmake(rn, 0.0);
+      }
+    }
+    const zd v = i == 0 ? zmake(1.0, 0.0) : ((i < L && tau != 0.0) ? zmul(x, scl) : zero);
+    // O <- H O: z_j = sum_i conj(v_i) O[i][j], O[i][j] -= tau v_i z_j
+    {
+      zd P[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) P[j] = zmul(zconj(v), O[j]);
+      const zd zi = rscatter8(P, i);
+      const zd tv = zscale(v, tau);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) O[j] = zsub(O[j], zmul(tv, gshfl(zi, j)));
+    }
+    O[0] = i == 0 ? beta : zero;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (i < L && j < Lc) bd[(size_t)(C0 + j) * W2 + (r0 + i - C0 - j)] = O[j];
+    // D <- H D H on rows and columns r0 .. r0+L-1
+    zd D[8];
+    zd p = zero;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      zd dv = zero;
+      if (i < L && j < L)
+        dv = i >= j ? bd[(size_t)(r0 + j) * W2 + (i - j)]
+                    : zconj(bd[(size_t)(r0 + i) * W2 + (j - i)]);
+      D[j] = dv;
+      p = zfma(dv, gshfl(v, j), p);
+    }
+    p = zscale(p, tau);
+    const zd q = zmul(zconj(v), p);
+    const double vhp = gsum(q.x);   // v^dagger p is real
+    const zd w = zsub(p, zscale(v, 0.5 * tau * vhp));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      // every lane takes part in the shuffles; the lower triangle is stored
+      const zd wj = gshfl(w, j), vj = gshfl(v, j);
+      zd dv = zfnmac(v, wj, D[j]);
+      dv = zfnmac(w, vj, dv);
+      if (i == j) dv.y = 0.0;
+      if (j <= i && i < L) bd[(size_t)(r0 + j) * W2 + (i - j)] = dv;
+    }
+    vp = v;
+    taup = tau;
+    if (act && kt == (n - 1 - s + NB - 1) / NB) s += CH_SLOTS;
+    __syncthreads();
+  }
+  double* dk = de + (size_t)k * 2 * n;
+  for (int c = tid; c < n; c += CH_WARPS * 32) {
+    dk[c] = bd[(size_t)c * W2].x;
+    const zd e = c + 1 < n ? bd[(size_t)c * W2 + 1] : zmake(0.0, 0.0);
+    dk[n + c] = hypot(e.x, e.y);
+  }
+}
+
+size_t bulge_smem(int n, bool in_smem) {
+  size_t b = ((size_t)n * sizeof(int) + 15) / 16 * 16;
+  if (in_smem) b += (size_t)n * 2 * CH_NB * sizeof(zd);
+  return b;
+}
+
+int max_optin_smem() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 48 * 1024;
+  return v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+bool bs_band_supported(int n) {
+  // the panel QR keeps an m x NB panel in shared memory
+  return n >= 2 && (size_t)BS_BAND_NB * n * sizeof(zd) + 8192 <= (size_t)max_optin_smem();
+}
+
+void bs_band_ws_free(BandWs* w) {
+  void* p[] = {w->V, w->X, w->W, w->T, w->wA, w->wB, w->wD, w->eA, w->eB, w->band, w->dsc};
+  for (void* q : p) cudaFree(q);
+  *w = BandWs();
+}
+
+int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
+  if (w->n == n && w->kb >= kb && w->S == S) return BS_OK;
+  bs_band_ws_free(w);
+  const int NB = BS_BAND_NB;
+  const int m = std::max(n - NB, 1);
+  size_t nA = 0, nB = 0, nD = 0, nE = 0;
+  bs_band_tc_elems(n, NB, kb, S, &nA, &nB, &nD, &nE);
+  const size_t pv = (size_t)kb * m * NB;
+  struct Item { void** p; size_t bytes; const char* what; } items[] = {
+      {(void**)&w->V, pv * sizeof(zd), "band reflectors"},
+      {(void**)&w->X, pv * sizeof(zd), "band A22 V"},
+      {(void**)&w->W, pv * sizeof(zd), "band W"},
+      {(void**)&w->T, (size_t)kb * NB * NB * sizeof(zd), "band T"},
+      {(void**)&w->wA, nA * sizeof(uint16_t), "band digit planes A"},
+      {(void**)&w->wB, nB * sizeof(uint16_t), "band digit planes B"},
+      {(void**)&w->wD, nD * sizeof(float), "band digit-order sums"},
+      {(void**)&w->eA, nE * sizeof(int), "band exponents A"},
+      {(void**)&w->eB, nE * sizeof(int), "band exponents B"},
+      {(void**)&w->band, (size_t)kb * n * 2 * NB * sizeof(zd), "band storage"},
+      {(void**)&w->dsc, (size_t)kb * NB * sizeof(int), "band balance exponents"},
+  };
+  for (auto& it : items) {
+    cudaError_t e = cudaMalloc(it.p, it.bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      bs_band_ws_free(w);
+      bs_set_error("out of device memory (%s, %zu bytes)", it.what, it.bytes);
+      return BS_ENOMEM;
+    }
+  }
+  w->n = n;
+  w->kb = kb;
+  w->S = S;
+  return BS_OK;
+}
+
+int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cudaStream_t s) {
+  constexpr int NB = BS_BAND_NB;
+  if (w.n != n || w.kb < kb || !bs_band_supported(n)) {
+    bs_set_error("band reduction: workspace for n = %d, %d matrices not set up", n, kb);
+    return BS_EINVAL;
+  }
+  const int nt = (n + 31) / 32;
+  symmetrize_kernel<<<dim3(nt, nt, kb), dim3(32, 8), 0, s>>>(A, n);
+  BS_CHECK_LAUNCH("symmetrize_kernel");
+  const int ld = std::max(n - NB, 1);
+  const long sv = (long)ld * NB;
+  if (n - NB > 1) {
+    // the shared-memory opt-in is a per-device attribute of the kernel
+    cudaError_t e = cudaFuncSetAttribute(panel_qr_kernel<NB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)NB * (n - NB) * sizeof(zd)));
+    if (e != cudaSuccess) return bs_cuda_status(e, "panel QR smem");
+  }
+  for (int j = 0; n - j - NB > 1; j += NB) {
+    const int m = n - j - NB;
+    const size_t smem = (size_t)NB * m * sizeof(zd);
+    panel_qr_kernel<NB><<<kb, QR_NT, smem, s>>>(A, n, j, w.V, ld, sv, w.T);
+    BS_CHECK_LAUNCH("panel_qr_kernel");
+    TRY_LAUNCH(bs_launch_band_av(A, n, j + NB, m, w.V, ld, sv, NB, kb, w.S, w.wA, w.wB, w.wD,
+                                 w.eA, w.eB, w.X, ld, sv, err, s));
+    wform_kernel<NB><<<kb, QR_NT, 0, s>>>(w.X, w.V, w.T, ld, sv, m, w.W, w.dsc);
+    BS_CHECK_LAUNCH("wform_kernel");
+    TRY_LAUNCH(bs_launch_band_rank2(w.V, w.W, ld, sv, w.dsc, m, NB, kb, w.S, w.wA, w.wB, w.eA, A,
+                                    n, j + NB, err, s));
+  }
+  static_assert(NB == CH_NB, "the bulge chase is written for a band half-width of 8");
+  const bool in_smem = bulge_smem(n, true) <= (size_t)max_optin_smem();
+  const size_t smem = bulge_smem(n, in_smem);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(bulge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return bs_cuda_status(e, "bulge chase smem");
+  }
+  bulge_kernel<<<kb, CH_WARPS * 32, smem, s>>>(A, n, w.band, in_smem ? 1 : 0, de);
+  BS_CHECK_LAUNCH("bulge_kernel");
+  return BS_OK;
+}

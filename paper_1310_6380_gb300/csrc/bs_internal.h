@@ -201,6 +201,8 @@ struct bs_cell {
   int* d_liw;
 
   // profiling: events around each phase of the last call
+  struct BandWs* band;  // two-stage reduction workspace (allocated on first use)
+
   bool prof;
   bool prof_ready[PH_COUNT];
   cudaEvent_t ev[PH_COUNT][2];
@@ -289,6 +291,40 @@ int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long
                        int* err, cudaStream_t s);
 
 // builder.cu
+// ---- two-stage reduction to tridiagonal form (band.cu)
+#define BS_BAND_NB 8        // half-width of the intermediate band
+#define BS_SLICES_BAND 8    // digit planes per operand in its contractions (~2^-53)
+struct BandWs {
+  int n = 0, kb = 0, S = 0;
+  zd* V = nullptr;          // kb x (n - nb) x nb reflectors of the current panel
+  zd* X = nullptr;          // kb x (n - nb) x nb: A22 V
+  zd* W = nullptr;          // kb x (n - nb) x nb
+  zd* T = nullptr;          // kb x nb x nb
+  uint16_t* wA = nullptr;   // digit planes
+  uint16_t* wB = nullptr;
+  float* wD = nullptr;      // digit-order sums
+  int* eA = nullptr;
+  int* eB = nullptr;
+  zd* band = nullptr;       // kb x n x 2nb band storage (when it does not fit in shared memory)
+  int* dsc = nullptr;       // kb x nb power-of-two balance of V against W per column
+};
+#define BS_BAND_AUTO_MIN 400   // BS_REDUCE_AUTO takes the two-stage reduction from this n on
+bool bs_band_supported(int n);
+bool bs_use_band(int n);
+int bs_band_ws_alloc(BandWs* w, int n, int kb, int S);
+void bs_band_ws_free(BandWs* w);
+int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cudaStream_t s);
+void bs_band_tc_elems(int n, int nb, int kb, int S, size_t* nA, size_t* nB, size_t* nD,
+                      size_t* nE);
+int bs_launch_band_av(const zd* A, int n, int o, int m, const zd* V, int ldv, long sv, int nb,
+                      int kb, int S, uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB,
+                      zd* X, int ldx, long sx, int* err, cudaStream_t s);
+int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex, int m, int kb,
+                           zd* A, int n, int o, int* err, cudaStream_t s);
+int bs_launch_band_rank2(const zd* V, const zd* W, int ld, long sv, const int* dsc, int m, int nb,
+                         int kb, int S, uint16_t* wA, uint16_t* wB, int* ex, zd* A, int n, int o,
+                         int* err, cudaStream_t s);
+
 int bs_launch_builder(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,
                       double q2x, double q2y, zd* C, cudaStream_t s);
 

@@ -66,11 +66,13 @@ __device__ __forceinline__ void order_sums(const float* __restrict__ Dm, size_t 
   *xi = fma(pow2(-12 - 7 * u), (double)ai, vi);
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(double t) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn((float)t));
-}
-__device__ __forceinline__ uint16_t bf16_bits(long long t) {   // exact for |t| <= 256
-  return __bfloat16_as_ushort(__int2bfloat16_rn((int)t));
+// BF16 bits of a small integer (|t| <= 256, exact): t is added to the bit
+// pattern of 1.5 2^23, whose unit in the last place is 1, and 1.5 2^23 is
+// subtracted again, so the conversion runs on the FP32 pipe instead of the
+// conversion unit; the BF16 value is the top half of the FP32 one
+__device__ __forceinline__ uint16_t bf16_bits(long long t) {
+  const float f = __int_as_float(0x4B400000 + (int)t) - 12582912.0f;
+  return (uint16_t)(__float_as_uint(f) >> 16);
 }
 
 __device__ __forceinline__ double warp_max(double v) {
@@ -96,25 +98,29 @@ __device__ __forceinline__ int row_exp(double m) {
 }
 
 // Digits by integer arithmetic on the FP64 bit pattern (FP64 arithmetic is
-// slow on GB300): X = round(x 2^(48-e)) as a signed 64-bit integer
-// (|X| <= 2^48), then t_0 = floor((X + 2^41) / 2^42), remainder r, and
-// t_s = floor((r + 2^(41-7s)) / 2^(42-7s)) for s >= 1, each in [-64, 64].
-// Digit s goes to out[s * plane] (plane < 0 for the reversed B layout).
+// slow on GB300): with B = 6 + 7 (S - 1) bits (48 for seven digits, 55 for
+// eight, enough for the whole FP64 mantissa of every x within a factor 4
+// of the row scale), X = round(x 2^(B-e)) as a signed 64-bit integer
+// (|X| <= 2^B), then t_0 = floor((X + 2^(B-7)) / 2^(B-6)), remainder r, and
+// t_s = floor((r + 2^(B-7-7s)) / 2^(B-6-7s)) for s >= 1 (the last digit is
+// the remainder itself), each in [-64, 64].  Digit s goes to
+// out[s * plane] (plane < 0 for the reversed B layout).
 __device__ __forceinline__ void put_digits(double x, int e, int S, uint16_t* out,
                                            ptrdiff_t plane) {
+  const int B = 6 + 7 * (S - 1);
   const long long bits = __double_as_longlong(x);
   const int E = (int)((bits >> 52) & 0x7FF);
   long long X = 0;
   if (E != 0) {
     const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-    const int sh = 1075 - E - 48 + e;   // X = m 2^-sh
-    if (sh <= 0) X = m << (-sh);        // not reached: |x| <= 2^e keeps sh >= 4
+    const int sh = 1075 - E - B + e;    // X = m 2^-sh; |x| <= 2^e keeps sh >= 52 - B
+    if (sh <= 0) X = m << (-sh);
     else if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
     if (bits < 0) X = -X;
   }
   long long r = X;
   for (int s = 0; s < S; ++s) {
-    const int sh = 42 - 7 * s;
+    const int sh = B - 6 - 7 * s;
     long long t;
     if (sh > 0) t = (r + (1LL << (sh - 1))) >> sh;
     else t = r;
@@ -390,4 +396,185 @@ int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long
       wD, sl, eA, eB, N, C, sC);
   BS_CHECK_LAUNCH("recombine_z_kernel");
   return BS_OK;
+}
+
+// ---- the two contractions of a dense-to-band reduction step
+// (band.cu): X = A22 V with A22 the Hermitian trailing block of A (full
+// storage, m x m at offset o, leading dimension n), and the two-sided
+// update A22 -= V W^dagger + W V^dagger.
+namespace {
+
+// A rows r of [Re A22[r, :] | Im A22[r, :]], read as the conjugate of
+// column r; grid (m, kb), block 128
+__global__ void pack_trail_kernel(const zd* __restrict__ A, int n, int o, int m, int S, int Kp,
+                                  uint16_t* __restrict__ out, int* __restrict__ ex) {
+  __shared__ double sh[4];
+  const int r = blockIdx.x, k = blockIdx.y;
+  const zd* col = A + (size_t)k * n * n + (size_t)(o + r) * n + o;
+  double mx = 0.0;
+  for (int c = threadIdx.x; c < m; c += 128) {
+    const zd v = col[c];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  const int e = row_exp(row_max(mx, sh));
+  uint16_t* base = out + ((size_t)k * m + r) * S * Kp;
+  for (int c = threadIdx.x; c < Kp; c += 128) {
+    double x = 0.0;
+    if (c < m) x = col[c].x;
+    else if (c < 2 * m) x = -col[c - m].y;
+    put_digits(x, e, S, base + c, Kp);
+  }
+  if (threadIdx.x == 0) ex[(size_t)k * m + r] = e;
+}
+
+// B rows (i, part) of the m x nb block V (leading dimension ldv, batch
+// stride sv), digits reversed: part 0 = [Vr; -Vi], part 1 = [Vi; Vr];
+// grid (nb, kb), block 128
+__global__ void pack_panel_kernel(const zd* __restrict__ V, int ldv, long sv, int m, int nb,
+                                  int S, int Kp, uint16_t* __restrict__ out,
+                                  int* __restrict__ ex) {
+  __shared__ double sh[4];
+  const int i = blockIdx.x, k = blockIdx.y;
+  const zd* x = V + (size_t)k * sv + (size_t)i * ldv;
+  double mx = 0.0;
+  for (int r = threadIdx.x; r < m; r += 128) mx = fmax(mx, fmax(fabs(x[r].x), fabs(x[r].y)));
+  const int e = row_exp(row_max(mx, sh));
+  uint16_t* base0 = out + ((size_t)k * 2 * nb + 2 * i) * S * Kp + (size_t)(S - 1) * Kp;
+  uint16_t* base1 = base0 + (size_t)S * Kp;
+  for (int c = threadIdx.x; c < Kp; c += 128) {
+    double v0 = 0.0, v1 = 0.0;
+    if (c < m) {
+      v0 = x[c].x;
+      v1 = x[c].y;
+    } else if (c < 2 * m) {
+      v0 = -x[c - m].y;
+      v1 = x[c - m].x;
+    }
+    put_digits(v0, e, S, base0 + c, -(ptrdiff_t)Kp);
+    put_digits(v1, e, S, base1 + c, -(ptrdiff_t)Kp);
+  }
+  if (threadIdx.x == 0) ex[(size_t)k * nb + i] = e;
+}
+
+// X[k][r + i ldx] = 2^(eA + eB) sum_u 2^(-12-7u) (slabs of order u)[(i, part)][r]
+__global__ void recombine_panel_kernel(const float* __restrict__ Dm, const SliceSlabs sl,
+                                       const int* __restrict__ eA, const int* __restrict__ eB,
+                                       int m, int nb, zd* __restrict__ X, int ldx, long sx) {
+  const int k = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * nb) return;
+  const int r = idx % m, i = idx / m;
+  const size_t M = (size_t)m, Nn = 2 * (size_t)nb;
+  const float* dk = Dm + (size_t)k * sl.nq * Nn * M;
+  double xr, xi;
+  order_sums(dk, Nn * M, (2 * (size_t)i) * M + r, (2 * (size_t)i + 1) * M + r, sl, &xr, &xi);
+  const int e = eA[(size_t)k * m + r] + eB[(size_t)k * nb + i];
+  X[(size_t)k * sx + (size_t)i * ldx + r] = zmake(ldexp(xr, e), ldexp(xi, e));
+}
+
+// Operands of the rank-2nb update V W^dagger + W V^dagger = X Y^dagger with
+// X = [V D, W D^-1], Y = [W D^-1, V D] (m x 2nb), D = diag(2^dsc_i) a
+// power-of-two balance of column i of V (entries at most 1) against
+// column i of W (of the size of the matrix norm), so that one row scale
+// serves both halves of a row without starving V of digits:
+// A rows r = [Re X[r, :] | Im X[r, :]], B rows (c, 0) = [Re Y[c, :] | Im Y[c, :]],
+// (c, 1) = [-Im Y[c, :] | Re Y[c, :]], K = 4 nb <= 64 (one 64-column block).
+// Row r of X and of Y hold the same numbers, so one exponent serves both,
+// and entries (r, c) and (c, r) of the product come from the same digits.
+// The scaling only shifts the digit exponents (no rounding); grid (m, kb),
+// block 64
+__global__ void pack_rank2_kernel(const zd* __restrict__ V, const zd* __restrict__ W, int ld,
+                                  long sv, const int* __restrict__ dsc, int m, int nb, int S,
+                                  uint16_t* __restrict__ oa, uint16_t* __restrict__ ob,
+                                  int* __restrict__ ex) {
+  __shared__ double sh[2];
+  const int r = blockIdx.x, k = blockIdx.y, t = threadIdx.x;
+  const zd* vk = V + (size_t)k * sv;
+  const zd* wk = W + (size_t)k * sv;
+  const int w2 = 2 * nb;
+  // column t of A: t < 2nb -> Re X[r, t], t < 4nb -> Im X[r, t - 2nb]
+  double a = 0.0, y0 = 0.0, y1 = 0.0;
+  int shx = 0, shy = 0;   // exponents of the balance of the X and Y entries
+  if (t < 2 * w2) {
+    const int c = t < w2 ? t : t - w2;
+    const int ci = c < nb ? c : c - nb;
+    const int d = dsc[(size_t)k * nb + ci];
+    shx = c < nb ? d : -d;
+    shy = -shx;
+    const zd xv = c < nb ? vk[(size_t)c * ld + r] : wk[(size_t)(c - nb) * ld + r];
+    const zd yv = c < nb ? wk[(size_t)c * ld + r] : vk[(size_t)(c - nb) * ld + r];
+    if (t < w2) {
+      a = xv.x;
+      y0 = yv.x;
+      y1 = -yv.y;
+    } else {
+      a = xv.y;
+      y0 = yv.y;
+      y1 = yv.x;
+    }
+  }
+  double mx = warp_max(fabs(a) * pow2(shx));
+  if ((t & 31) == 0) sh[t >> 5] = mx;
+  __syncthreads();
+  mx = fmax(sh[0], sh[1]);
+  const int e = row_exp(mx);
+  const size_t rowlen = (size_t)S * 64;
+  put_digits(a, e - shx, S, oa + ((size_t)k * m + r) * rowlen + t, 64);
+  uint16_t* b0 = ob + ((size_t)k * 2 * m + 2 * (size_t)r) * rowlen + (size_t)(S - 1) * 64 + t;
+  put_digits(y0, e - shy, S, b0, -64);
+  put_digits(y1, e - shy, S, b0 + rowlen, -64);
+  if (t == 0) ex[(size_t)k * m + r] = e;
+}
+
+}  // namespace
+
+void bs_band_tc_elems(int n, int nb, int kb, int S, size_t* nA, size_t* nB, size_t* nD,
+                      size_t* nE) {
+  const int m = n - nb > 1 ? n - nb : 1, Kp = (2 * m + 63) / 64 * 64;
+  const size_t aA = (size_t)kb * m * S * Kp, aB = (size_t)kb * 2 * nb * S * Kp;
+  const size_t hA = (size_t)kb * m * S * 64, hB = (size_t)kb * 2 * m * S * 64;
+  *nA = aA > hA ? aA : hA;
+  *nB = aB > hB ? aB : hB;
+  // the largest trailing block needs the most planes; smaller ones may cut
+  // their slabs finer, so take the maximum over the sizes a reduction visits
+  size_t d = 0;
+  for (int mm = m; mm > 1; mm -= nb) {
+    const int kp = (2 * mm + 63) / 64 * 64;
+    const size_t pa = bs_slice_planes(S, kp, mm, 2 * nb, kb) * mm * 2 * nb;
+    d = d > pa ? d : pa;
+  }
+  *nD = d;
+  *nE = (size_t)kb * (m + 2 * nb);
+}
+
+int bs_launch_band_av(const zd* A, int n, int o, int m, const zd* V, int ldv, long sv, int nb,
+                      int kb, int S, uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB,
+                      zd* X, int ldx, long sx, int* err, cudaStream_t s) {
+  const int Kp = (2 * m + 63) / 64 * 64;
+  SliceSlabs sl;
+  if (!bs_slice_slabs(S, Kp, m, 2 * nb, kb, &sl)) {
+    bs_set_error("band reduction: m = %d gives too many digit slabs", m);
+    return BS_EINVAL;
+  }
+  pack_trail_kernel<<<dim3(m, kb), 128, 0, s>>>(A, n, o, m, S, Kp, wA, eA);
+  BS_CHECK_LAUNCH("pack_trail_kernel");
+  pack_panel_kernel<<<dim3(nb, kb), 128, 0, s>>>(V, ldv, sv, m, nb, S, Kp, wB, eB);
+  BS_CHECK_LAUNCH("pack_panel_kernel");
+  TRY_LAUNCH(bs_launch_slice_orders(wA, wB, wD, m, 2 * nb, S, Kp, kb, err, s));
+  recombine_panel_kernel<<<dim3((m * nb + 255) / 256, kb), 256, 0, s>>>(wD, sl, eA, eB, m, nb, X,
+                                                                       ldx, sx);
+  BS_CHECK_LAUNCH("recombine_panel_kernel");
+  return BS_OK;
+}
+
+int bs_launch_band_rank2(const zd* V, const zd* W, int ld, long sv, const int* dsc, int m, int nb,
+                         int kb, int S, uint16_t* wA, uint16_t* wB, int* ex, zd* A, int n, int o,
+                         int* err, cudaStream_t s) {
+  if (S != 8 || 4 * nb > 64) {
+    bs_set_error("band reduction: needs 8 digits and band width <= 16 (nb = %d)", nb);
+    return BS_EINVAL;
+  }
+  pack_rank2_kernel<<<dim3(m, kb), 64, 0, s>>>(V, W, ld, sv, dsc, m, nb, S, wA, wB, ex);
+  BS_CHECK_LAUNCH("pack_rank2_kernel");
+  return bs_launch_rank2_update(wA, wB, ex, m, kb, A, n, o, err, s);
 }

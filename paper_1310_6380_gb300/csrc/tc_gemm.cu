@@ -214,6 +214,181 @@ __global__ void __launch_bounds__(128, 2)
   }
 }
 
+// ---- fused rank-2nb update of the dense-to-band reduction (band.cu):
+// A22 -= X Y^dagger with X = [V W], Y = [W V] given as eight digit planes
+// per operand (slices.cu, pack_rank2_kernel): A rows r [A_0 | .. | A_7],
+// B rows (c, part) reversed [B_7 | .. | B_0], each block 64 wide.  The CTA
+// keeps all eight digit orders u = s + t of its 128 x BN tile in tensor
+// memory (accumulator u at column u BN), streams A's digit blocks through
+// a ring while B's stay resident, and the epilogue combines the orders in
+// a 64-bit integer and subtracts the product from the FP64 matrix in place,
+// so no partial products go through global memory.  The update is
+// Hermitian: tiles above the diagonal exit at once, and the others write
+// A22[r, c] (r >= c) and, staged through shared memory so that the stores
+// run along columns, A22[c, r] = conj(A22[r, c]).
+//
+// Order sums: with at most 64 nonzero terms per digit block (K = 4 nb),
+// |o_u| <= (u + 1) 2^18, so hi = sum_{u<4} o_u 2^(7(3-u)) < 2^40 and
+// T = hi 2^21 + floor(lo / 2^7), lo = sum_{u>=4} o_u 2^(7(7-u)), is below
+// 2^62: sum_u 2^(-12-7u) o_u = 2^-54 T up to 2^-54 of the operands' scale,
+// the size of the digit truncation itself.  One conversion and one FMA per
+// real entry (GB300 issues 2 FP64 operations per clock per SM).
+constexpr int R2_S = 8, R2_STAGES = 4;
+
+template <int BN>
+__global__ void __launch_bounds__(128, 2)
+    rank2_update_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB, const int* __restrict__ ex,
+                        int m, zd* __restrict__ A, int n, int o, int* __restrict__ err) {
+  constexpr int TILE_B = tile_b(BN);
+  constexpr uint32_t IDESC = idesc(BN);
+  constexpr int TCOLS = R2_S * BN;   // 256 or 512
+  constexpr int CW = BN / 2;         // complex columns of the tile
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[R2_STAGES], empty[R2_STAGES], bfull, done;
+  __shared__ uint32_t tmem_base;
+  const int z = blockIdx.z;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, cc0 = n0 / 2;
+  if (cc0 > m0 + BM - 1) return;     // above the diagonal: the mirror tile writes it
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + R2_STAGES * TILE_A;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < R2_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(&bfull, 1);
+    mbar_init(&done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer: B's eight blocks once, then A's digit blocks through the ring
+    mbar_expect_tx(&bfull, R2_S * TILE_B);
+    for (int b = 0; b < R2_S; ++b) tma_load_3d(sB + b * TILE_B, &tmB, b * BK, n0, z, &bfull);
+    for (int sd = 0; sd < R2_S; ++sd) {
+      const int q = sd % R2_STAGES;
+      const uint32_t ph = (uint32_t)(sd / R2_STAGES) & 1u;
+      if (sd >= R2_STAGES && !mbar_wait(&empty[q], ph ^ 1u, err)) break;
+      mbar_expect_tx(&full[q], TILE_A);
+      tma_load_3d(sA + q * TILE_A, &tmA, sd * BK, m0, z, &full[q]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: digit s of A against digits t = 0 .. 7-s of B into order s + t
+    bool ok = mbar_wait(&bfull, 0u, err);
+    for (int sd = 0; ok && sd < R2_S; ++sd) {
+      const int q = sd % R2_STAGES;
+      const uint32_t ph = (uint32_t)(sd / R2_STAGES) & 1u;
+      if (!mbar_wait(&full[q], ph, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + q * TILE_A);
+      for (int t = 0; t + sd < R2_S; ++t) {
+        const uint32_t b0 = smem_u32(sB + (R2_S - 1 - t) * TILE_B);
+        const uint32_t acc_addr = tmem + (uint32_t)((sd + t) * BN);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t ad = sdesc(a0 + kk * 32), bd = sdesc(b0 + kk * 32);
+          const uint32_t acc = (sd > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr),
+              "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&empty[q]))
+          : "memory");
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&done))
+        : "memory");
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&done, 0u, err));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // the A ring is free once every MMA has completed: it stages the tile
+  // (BM x CW complex, row stride CW + 1) for the transposed stores
+  zd* stage = reinterpret_cast<zd*>(sA);
+  const int rl = warp * 32 + lane, r = m0 + rl;
+  const bool live = r < m;
+  zd* az = A + (size_t)z * n * n + (size_t)o * n + o;
+  if (ok) {
+    const int er = live ? ex[(size_t)z * m + r] : 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+#pragma unroll
+      for (int u = 0; u < R2_S; ++u) {
+        uint32_t v[16];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(u * BN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long d = __float2int_rn(__uint_as_float(v[j]));
+          if (u < 4) hi[j] = hi[j] * 128 + d;
+          else lo[j] = lo[j] * 128 + d;
+        }
+      }
+#pragma unroll
+      for (int jc = 0; jc < 8; ++jc) {
+        const int cl = c0 / 2 + jc, c = cc0 + cl;
+        zd val = zmake(0.0, 0.0);
+        if (live && c < m && c <= r) {
+          const long long tr = hi[2 * jc] * 2097152 + (lo[2 * jc] >> 7);
+          const long long ti = hi[2 * jc + 1] * 2097152 + (lo[2 * jc + 1] >> 7);
+          const int e = er + ex[(size_t)z * m + c] - 54;
+          const double w = __longlong_as_double((long long)(1023 + e) << 52);
+          zd* ap = az + (size_t)c * n + r;
+          val = *ap;
+          val.x = fma(-(double)tr, w, val.x);
+          val.y = r == c ? 0.0 : fma(-(double)ti, w, val.y);
+          *ap = val;
+        }
+        stage[rl * (CW + 1) + cl] = val;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TCOLS));
+  }
+  if (ok) {
+    // A22[c, r] = conj(A22[r, c]) for r > c: CW consecutive c per row r
+    for (int idx = threadIdx.x; idx < BM * CW; idx += 128) {
+      const int rr = idx / CW, cl = idx % CW;
+      const int rw = m0 + rr, c = cc0 + cl;
+      if (rw < m && c < m && rw > c) az[(size_t)rw * n + c] = zconj(stage[rr * (CW + 1) + cl]);
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -391,4 +566,36 @@ int bs_launch_slice_orders(const uint16_t* A, const uint16_t* B, float* D, int M
   const int K = S * Kp;
   return dispatch_bn(A, B, D, M, N, K, batch, (long)M * K, (long)N * K, M, (long)M * N, sl, err,
                      s);
+}
+
+// A22 (m x m at offset o of each n x n matrix) -= X Y^dagger from the digit
+// planes of pack_rank2_kernel; ex: row exponents (kb x m)
+int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex, int m, int kb,
+                           zd* A, int n, int o, int* err, cudaStream_t s) {
+  constexpr int BN = 32;
+  if (((uintptr_t)dA & 15) || ((uintptr_t)dB & 15) || m < 1 || kb < 1 || kb > 65535) {
+    bs_set_error("rank-2 update: bad operands (m = %d, batch = %d)", m, kb);
+    return BS_EINVAL;
+  }
+  const int K = R2_S * BK;
+  CUtensorMap ta, tb;
+  int r = make_map(&ta, dA, K, m, kb, (long)m * K, BM);
+  if (!r) r = make_map(&tb, dB, K, 2 * m, kb, (long)2 * m * K, BN);
+  if (r) return r;
+  const int smem = R2_STAGES * TILE_A + R2_S * tile_b(BN) + 1024;
+  static_assert(BM * (BN / 2 + 1) * (int)sizeof(zd) <= R2_STAGES * TILE_A,
+                "the staged tile fits in the A ring");
+  static std::atomic<bool> attr[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!attr[dev].load(std::memory_order_acquire)) {
+    cudaError_t e = cudaFuncSetAttribute(rank2_update_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return bs_cuda_status(e, "rank-2 update smem");
+    attr[dev].store(true, std::memory_order_release);
+  }
+  dim3 grid((m + BM - 1) / BM, (2 * m + BN - 1) / BN, kb);
+  rank2_update_kernel<BN><<<grid, 128, smem, s>>>(ta, tb, ex, m, A, n, o, err);
+  BS_CHECK_LAUNCH("rank2_update_kernel");
+  return BS_OK;
 }
