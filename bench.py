@@ -637,6 +637,71 @@ def run_reference_batch(args):
                 "d2h_bytes_per_step": 0}}))
 
 
+BAND_NB = 8
+
+
+def band_roofline(red, n, nk, ph, peaks):
+    """Roofline of the dominant kernel group of the two-stage reduction (live
+    event times per group, summed over the panel steps of one solve) and the
+    reduction's rate on the one-stage flop count (16/3) n^3 per k."""
+    hbm_peak, _, note = measured_peaks()
+    fp64_peak = peaks["fp64_nominal_tflops"]
+    nb = BAND_NB
+    ms = [n - j - nb for j in range(0, n, nb) if n - j - nb > 1]   # trailing sizes per step
+    # algorithmic work of each group for the nk matrices of one solve
+    rank2_bytes = nk * sum(32.0 * m * (m + 1) / 2 + 16.0 * m * (m - 1) / 2 for m in ms)
+    av_bytes = nk * sum(16.0 * m * m for m in ms)
+    tasks = sum((n - 1 - s + nb - 1) // nb for s in range(n - 1))
+    chase_flops = nk * tasks * 6.0 * nb * nb * 8.0
+    qr_flops = nk * sum(8.0 * 4.0 * m * nb * nb for m in ms)
+    w_flops = nk * sum(8.0 * 2.0 * m * nb * nb for m in ms)
+    groups = {
+        "rank2_update": {"bound": "hbm", "kernel": "pack_rank2_kernel + rank2_update_kernel "
+                         "(tcgen05, eight digit orders in TMEM, FP64 epilogue)",
+                         "work": rank2_bytes, "unit": "GB/s", "peak": hbm_peak,
+                         "peak_source": "copy bandwidth, " + note,
+                         "algorithmic": "read + write (16 B each) of the trailing lower "
+                                        "triangle and write of its mirror, per panel step"},
+        "a22_v": {"bound": "hbm", "kernel": "pack_trail_kernel + slice_gemm_kernel (A22 V) + "
+                  "recombine", "work": av_bytes, "unit": "GB/s", "peak": hbm_peak,
+                  "peak_source": "copy bandwidth, " + note,
+                  "algorithmic": "one read (16 B) of the trailing block per panel step"},
+        "bulge_chase": {"bound": "alu", "kernel": "bulge_kernel (band 8 -> tridiagonal, FP64)",
+                        "work": chase_flops, "unit": "TFLOP/s", "peak": fp64_peak,
+                        "peak_source": "nominal FP64", "algorithmic":
+                        "6 nb^2 complex multiply-adds per chase task (one-sided products of "
+                        "the off-diagonal block on both sides, two-sided diagonal block)"},
+        "panel_qr": {"bound": "alu", "kernel": "panel_qr_kernel (FP64)", "work": qr_flops,
+                     "unit": "TFLOP/s", "peak": fp64_peak, "peak_source": "nominal FP64",
+                     "algorithmic": "Householder QR of an m x 8 complex panel, 4 m nb^2 "
+                                    "complex multiply-adds"},
+        "w_form": {"bound": "alu", "kernel": "wz_kernel + wrow_kernel (FP64)", "work": w_flops,
+                   "unit": "TFLOP/s", "peak": fp64_peak, "peak_source": "nominal FP64",
+                   "algorithmic": "2 m nb^2 complex multiply-adds per panel"},
+    }
+    top = max(groups, key=lambda g: red[g])
+    g = groups[top]
+    t = red[top] / 1e3
+    scale = 1e9 if g["unit"] == "GB/s" else 1e12
+    achieved = g["work"] / t / scale
+    roofline = {"bound": g["bound"], "kernel": g["kernel"], "achieved": achieved,
+                "peak": g["peak"], "unit": g["unit"], "frac": achieved / g["peak"],
+                "traffic": None, "peak_source": g["peak_source"],
+                "algorithmic": g["algorithmic"] + f"; {nk} matrices, n={n}",
+                "group_ms_per_step": red[top]}
+    eff = nk * 16.0 / 3.0 * n ** 3 / (ph["tridiag"] / 1e3) / 1e12
+    reduction = {"method": "two-stage: dense -> band 8 (Householder panels, trailing updates as "
+                           "8-digit exact-slice products on tcgen05), band -> tridiagonal "
+                           "(bulge chase, FP64)",
+                 "groups_ms_per_step": red, "tridiag_phase_ms": ph["tridiag"],
+                 "one_stage_equivalent_tflops": eff,
+                 "one_stage_equivalent_frac_of_fp64_peak": eff / fp64_peak,
+                 "note": "(16/3) n^3 per k is the one-stage reduction's flop count; a value "
+                         "above the FP64 peak means the reduction no longer runs on the FP64 "
+                         "pipe, not that the FP64 pipe does more"}
+    return roofline, reduction
+
+
 def run_ours(args):
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -695,7 +760,7 @@ def run_ours(args):
     barrier = rep.barrier
 
     sampler = ClockSampler(device_bus_id(torch))
-    step_ms, phases = [], []
+    step_ms, phases, reds = [], [], []
     barrier()
     launches0 = bs.bs_launch_count()
     sampler.start()
@@ -710,6 +775,7 @@ def run_ours(args):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         phases.append(bs.bs_phase_times(h))
+        reds.append(bs.bs_reduction_times(h))
     t_wall = time.perf_counter() - t_wall
     barrier()
     clocks = sampler.stop()
@@ -724,7 +790,11 @@ def run_ours(args):
     # dominant kernel: the Householder tridiagonalisation
     ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
     peaks = device_peaks(torch, bs)
-    if prec == 0:
+    red = {k: statistics.mean(r[k] for r in reds) for k in reds[0]}
+    if prec == 0 and sum(red.values()) > 0:
+        roofline, reduction = band_roofline(red, n, nk, ph, peaks)
+    elif prec == 0:
+        reduction = None
         trid_flops = nk * 16.0 / 3.0 * n ** 3
         achieved = trid_flops / (ph["tridiag"] / 1e3) / 1e12
         fp64_peak = peaks["fp64_nominal_tflops"]
@@ -738,6 +808,7 @@ def run_ours(args):
                     "frac_of_probe": achieved / peaks["fp64_probe_tflops"],
                     "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}"}
     else:
+        reduction = None
         hbm_peak, _, note = measured_peaks()
         tri_bytes = nk * sum(m * (m + 1) // 2 for m in range(1, n)) * 16.0
         achieved = tri_bytes / (ph["tridiag"] / 1e3) / 1e9
@@ -822,6 +893,8 @@ def run_ours(args):
         "phases_ms": {k: round(v, 3) for k, v in ph.items() if v > 0},
         "wall_s_timed_region": t_wall, "clocks": clocks,
     }
+    if reduction is not None:
+        out["reduction"] = reduction
     if args.config == "mesh":
         out["paper_context"] = ("the paper's run of this workload (1000-element steel/epoxy mesh, "
                                 "M=5, 70 k, 18 branches) took 90 s on a Quadro K2000 desktop GPU, "
@@ -1381,12 +1454,18 @@ def run_3d(args):
     t_sol = statistics.mean(sol_ms)
     flops = nk * 16.0 / 3.0 * n ** 3
     achieved = flops / (t_sol / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "tridiag_step_kernel<double> (with the per-k builder "
-                                          "and bisection: bs_solve_k3 of one step)",
+    two_stage = n >= 400   # BS_REDUCE_AUTO: the two-stage reduction from n = 400 on
+    kern = ("bs_solve_k3 of one step: two-stage reduction (tcgen05 dense -> band, FP64 bulge "
+            "chase), per-k builder, bisection" if two_stage else
+            "tridiag_step_kernel<double> (with the per-k builder and bisection: bs_solve_k3 of "
+            "one step)")
+    roofline = {"bound": "alu", "kernel": kern,
                 "achieved": achieved, "peak": device_peaks(torch)["fp64_nominal_tflops"],
                 "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "nominal FP64: SMs (queried) x 2 FMA/clk x 2 flop x max SM clock",
-                "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}"}
+                "algorithmic": f"(16/3) n^3 real flops per k x {nk} k, n={n}" +
+                               ("; the one-stage reduction's flop count, so above 1.0 of the "
+                                "FP64 peak means the work left the FP64 pipe" if two_stage else "")}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hp, hl, hm, hr, hQ = (pin(cell.phase.astype(np.uint16)), pin(cell.lam), pin(cell.mu),

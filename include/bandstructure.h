@@ -270,6 +270,18 @@ int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps);
  * GB300); larger n use the one-stage reduction in every mode.
  * Errors: BS_EINVAL for any other mode.
  */
+/*
+ * bs_reduction_times - with profiling on (bs_set_profiling), the device time
+ * in ms of each kernel group of the last two-stage reduction of this cell's
+ * FP64 solve, summed over its panel steps: [0] panel Householder QR,
+ * [1] A22 V (digit planes of the trailing block and the tensor-core
+ * product), [2] the W formation, [3] the trailing rank-2nb update (tensor
+ * cores, FP64 epilogue), [4] the bulge chase to tridiagonal form.  All
+ * zeros when profiling is off or the last solve took the one-stage
+ * reduction.  A measurement aid (the paper has no counterpart).
+ */
+int bs_reduction_times(bs_cell* cell, double ms[5]);
+
 #define BS_REDUCE_AUTO     0
 #define BS_REDUCE_ONESTAGE 1
 #define BS_REDUCE_TWOSTAGE 2

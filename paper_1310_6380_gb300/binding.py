@@ -99,6 +99,7 @@ def _load():
         "bs_probe_fp64": [i32, i32, dp, vp],
         "bs_set_iteration_limits": [i32, i32],
         "bs_set_reduction": [i32],
+        "bs_reduction_times": [vp, dp],
         "bs_batch_set_tile": [vp, i32],
         "bs_stress_coefficients": [vp, dp, i32, i32, dp, dp, vp],
         "bs_mode_field": [vp, dp, i32, i32, dp, i32, dp, vp],
@@ -135,7 +136,7 @@ EXPORTED = ["bs_create_cell", "bs_assemble", "bs_solve_k", "bs_bands", "bs_form_
             "bs_mode_field", "bs_create_cell_mesh", "bs_set_stiffness", "bs_create_cell3",
             "bs_assemble3", "bs_solve_k3", "bs_form_factors3", "bs_reduced_matrix3",
             "bs_cell3_dims", "bs_destroy_cell3", "bs_set_iteration_limits", "bs_probe_fp64",
-            "bs_set_reduction"]
+            "bs_set_reduction", "bs_reduction_times"]
 BS_SOLVER_DENSE, BS_SOLVER_LOBPCG, BS_SOLVER_FP64 = 0, 1, 2
 BS_LOB_MAX_BANDS, BS_LOB_MAXIT = 12, 80
 BS_REDUCE_AUTO, BS_REDUCE_ONESTAGE, BS_REDUCE_TWOSTAGE = 0, 1, 2
@@ -474,6 +475,16 @@ def bs_phase_times(cell) -> dict:
     ms = np.zeros(8)
     _check(_lib.bs_phase_times(cell, ms.ctypes.data))
     return dict(zip(PHASES, ms.tolist()))
+
+
+REDUCTION_GROUPS = ("panel_qr", "a22_v", "w_form", "rank2_update", "bulge_chase")
+
+
+def bs_reduction_times(cell) -> dict:
+    """Device ms per kernel group of the last two-stage reduction (profiling on)."""
+    ms = np.zeros(5)
+    _check(_lib.bs_reduction_times(cell, ms.ctypes.data))
+    return dict(zip(REDUCTION_GROUPS, ms.tolist()))
 
 
 def bs_launch_count() -> int:

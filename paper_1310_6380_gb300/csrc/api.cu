@@ -757,10 +757,13 @@ static int solve_chunk(bs_cell* c, int kb, int nbands, cudaStream_t s) {
   if (bs_use_band(c->n)) {
     if (!c->band) c->band = new BandWs();
     TRY(bs_band_ws_alloc(c->band, c->n, c->kcap, BS_SLICES_BAND));
+    c->band->prof = c->prof;
     TRY(bs_launch_eig_band(c->d_C, c->n, kb, *c->band, c->d_de, c->d_info + 1, s));
+    c->band_used = true;
   } else {
     TRY(bs_launch_tridiag<double>(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
                                   c->d_beta, c->d_count, s));
+    c->band_used = false;
   }
   bs_phase_end(c, PH_TRID, s);
   bs_phase_begin(c, PH_BISECT, s);
@@ -1113,6 +1116,16 @@ extern "C" int bs_phase_times(bs_cell* c, double ms[8]) {
     ms[i] = t;
   }
   return BS_OK;
+}
+
+extern "C" int bs_reduction_times(bs_cell* c, double ms[5]) {
+  if (!c || !ms) {
+    bs_set_error("bs_reduction_times: NULL argument");
+    return BS_EINVAL;
+  }
+  for (int i = 0; i < 5; ++i) ms[i] = 0.0;
+  if (!c->prof || !c->band_used || !c->band) return BS_OK;
+  return bs_band_times(*c->band, ms);
 }
 
 // ------------------------------------------------------------------ diagnostics

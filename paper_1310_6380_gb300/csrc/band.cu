@@ -26,6 +26,7 @@
 // The unitary similarity keeps the eigenvalues; the tridiagonal is returned
 // as (d, |e|) for the Sturm multisection (bisect.cu).
 #include <algorithm>
+#include <atomic>
 
 #include "bs_internal.h"
 
@@ -219,95 +220,98 @@ __global__ void __launch_bounds__(QR_NT) panel_qr_kernel(zd* __restrict__ A, int
   }
 }
 
-// W = Y - (1/2) V (T^dagger Z), Y = X T, Z = V^dagger Y; one CTA per matrix
-// and dsc[i] = round((log2 max|W[:, i]| - log2 max|V[:, i]|) / 2), the
-// power of two that balances column i of V against column i of W in the
-// digit planes of the rank-2nb update
+// W = Y - (1/2) V (T^dagger Z) with Y = X T and Z = V^dagger Y = Z0 T,
+// Z0 = V^dagger X, in two launches over WCH row chunks per matrix (the
+// work is FP64 and one CTA per matrix would leave most SMs idle):
+// wz_kernel forms the chunk partials of Z0 and clears the exponent maxima,
+// wrow_kernel sums the partials, forms M2 = T^dagger Z0 T and the rows
+// W[r, :] = X[r, :] T - (1/2) V[r, :] M2 of its chunk, and records the
+// largest FP64 exponent of each column of V and of W (integer maxima of
+// the exponent fields), from which pack_rank2_kernel balances V against W.
+constexpr int WCH = 8;
+
 template <int NB>
-__global__ void __launch_bounds__(QR_NT) wform_kernel(const zd* __restrict__ X,
-                                                      const zd* __restrict__ V,
-                                                      const zd* __restrict__ T, int ld, long sv,
-                                                      int m, zd* __restrict__ W,
-                                                      int* __restrict__ dsc) {
-  constexpr int NP = NB * NB, NG = QR_NT / NP > 0 ? QR_NT / NP : 1;
-  __shared__ zd Ts[NB][NB];
+__global__ void __launch_bounds__(QR_NT) wz_kernel(const zd* __restrict__ X,
+                                                   const zd* __restrict__ V, int ld, long sv,
+                                                   int m, zd* __restrict__ zpart,
+                                                   int* __restrict__ emax) {
+  constexpr int NP = NB * NB, NG = QR_NT / NP;
   __shared__ zd Zp[NG][NP];
-  __shared__ zd M2[NB][NB];
-  __shared__ double cmax[2][NB][QR_NT / 32];
-  const int k = blockIdx.x, tid = threadIdx.x;
+  const int ch = blockIdx.x, k = blockIdx.y, tid = threadIdx.x;
+  const int rb = (int)((long)m * ch / WCH), re = (int)((long)m * (ch + 1) / WCH);
   const zd* xk = X + (size_t)k * sv;
   const zd* vk = V + (size_t)k * sv;
-  zd* wk = W + (size_t)k * sv;
-  for (int idx = tid; idx < NP; idx += QR_NT) Ts[idx % NB][idx / NB] = T[(size_t)k * NP + idx];
-  __syncthreads();
-  for (int idx = tid; idx < m * NB; idx += QR_NT) {
-    const int r = idx % m, c = idx / m;
-    zd y = zmake(0.0, 0.0);
-    for (int q = 0; q <= c; ++q) y = zfma(xk[(size_t)q * ld + r], Ts[q][c], y);
-    wk[(size_t)c * ld + r] = y;
-  }
-  __syncthreads();
-  {
-    const int p = tid % NP, g = tid / NP;
-    if (g < NG) {
-      const int a = p % NB, c = p / NB;
-      zd z = zmake(0.0, 0.0);
-      for (int r = g; r < m; r += NG) z = zfmac(wk[(size_t)c * ld + r], vk[(size_t)a * ld + r], z);
-      Zp[g][p] = z;
-    }
-  }
+  const int p = tid % NP, g = tid / NP, a = p % NB, c = p / NB;
+  zd z = zmake(0.0, 0.0);
+  for (int r = rb + g; r < re; r += NG) z = zfmac(xk[(size_t)c * ld + r], vk[(size_t)a * ld + r], z);
+  Zp[g][p] = z;
   __syncthreads();
   if (tid < NP) {
-    zd z = zmake(0.0, 0.0);
-    for (int g = 0; g < NG; ++g) z = zadd(z, Zp[g][tid]);
-    Zp[0][tid] = z;   // Z[a][c] at index a + c NB
+    zd t = zmake(0.0, 0.0);
+    for (int q = 0; q < NG; ++q) t = zadd(t, Zp[q][tid]);
+    zpart[((size_t)k * WCH + ch) * NP + tid] = t;   // Z0[a][c] at a + c NB
   }
+  if (ch == 0 && tid < 2 * NB) emax[(size_t)k * 2 * NB + tid] = 0;
+}
+
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(QR_NT) wrow_kernel(const zd* __restrict__ X,
+                                                     const zd* __restrict__ V,
+                                                     const zd* __restrict__ T, int ld, long sv,
+                                                     int m, const zd* __restrict__ zpart,
+                                                     zd* __restrict__ W, int* __restrict__ emax) {
+  constexpr int NP = NB * NB;
+  __shared__ zd Ts[NB][NB], Z0[NB][NB], Zt[NB][NB], M2[NB][NB];
+  __shared__ int ecol[2][NB];
+  const int ch = blockIdx.x, k = blockIdx.y, tid = threadIdx.x;
+  const int rb = (int)((long)m * ch / WCH), re = (int)((long)m * (ch + 1) / WCH);
+  for (int idx = tid; idx < NP; idx += QR_NT) {
+    Ts[idx % NB][idx / NB] = T[(size_t)k * NP + idx];
+    zd t = zmake(0.0, 0.0);
+    for (int q = 0; q < WCH; ++q) t = zadd(t, zpart[((size_t)k * WCH + q) * NP + idx]);
+    Z0[idx % NB][idx / NB] = t;
+  }
+  if (tid < 2 * NB) ecol[tid / NB][tid % NB] = 0;
   __syncthreads();
-  if (tid < NP) {
+  if (tid < NP) {   // Zt = Z0 T
     const int a = tid % NB, c = tid / NB;
     zd t = zmake(0.0, 0.0);
-    for (int d = 0; d <= a; ++d) t = zfma(zconj(Ts[d][a]), Zp[0][d + c * NB], t);
+    for (int q = 0; q <= c; ++q) t = zfma(Z0[a][q], Ts[q][c], t);
+    Zt[a][c] = t;
+  }
+  __syncthreads();
+  if (tid < NP) {   // M2 = T^dagger Zt
+    const int a = tid % NB, c = tid / NB;
+    zd t = zmake(0.0, 0.0);
+    for (int d = 0; d <= a; ++d) t = zfma(zconj(Ts[d][a]), Zt[d][c], t);
     M2[a][c] = t;
   }
   __syncthreads();
-  // thread -> (column c = tid % NB, rows r = tid / NB + i (QR_NT / NB)): the
-  // column maxima of V and W come out of the same pass
+  const zd* xk = X + (size_t)k * sv;
+  const zd* vk = V + (size_t)k * sv;
+  zd* wk = W + (size_t)k * sv;
   constexpr int RS = QR_NT / NB;
   const int c = tid % NB;
-  double mv = 0.0, mw = 0.0;
-  for (int r = tid / NB; r < m; r += RS) {
-    zd t = zmake(0.0, 0.0);
+  int ev = 0, ew = 0;
+  for (int r = rb + tid / NB; r < re; r += RS) {
+    zd y = zmake(0.0, 0.0), t = zmake(0.0, 0.0);
+    for (int q = 0; q <= c; ++q) y = zfma(xk[(size_t)q * ld + r], Ts[q][c], y);
     for (int q = 0; q < NB; ++q) t = zfma(vk[(size_t)q * ld + r], M2[q][c], t);
-    zd y = wk[(size_t)c * ld + r];
     y.x = fma(-0.5, t.x, y.x);
     y.y = fma(-0.5, t.y, y.y);
     wk[(size_t)c * ld + r] = y;
     const zd v = vk[(size_t)c * ld + r];
-    mv = fmax(mv, fmax(fabs(v.x), fabs(v.y)));
-    mw = fmax(mw, fmax(fabs(y.x), fabs(y.y)));
+    ev = max(ev, max(exp_field(v.x), exp_field(v.y)));
+    ew = max(ew, max(exp_field(y.x), exp_field(y.y)));
   }
-  // lanes l and l + NB, l + 2NB, ... of a warp share the column
-#pragma unroll
-  for (int o = NB; o < 32; o <<= 1) {
-    mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, o));
-    mw = fmax(mw, __shfl_xor_sync(0xffffffffu, mw, o));
-  }
-  if ((tid & 31) < NB) {
-    cmax[0][c][tid >> 5] = mv;
-    cmax[1][c][tid >> 5] = mw;
-  }
+  atomicMax(&ecol[0][c], ev);
+  atomicMax(&ecol[1][c], ew);
   __syncthreads();
-  if (tid < NB) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < QR_NT / 32; ++w) {
-      a = fmax(a, cmax[0][tid][w]);
-      b = fmax(b, cmax[1][tid][w]);
-    }
-    int ev = 0, ew = 0;
-    if (a > 0.0) frexp(a, &ev);
-    if (b > 0.0) frexp(b, &ew);
-    dsc[(size_t)k * NB + tid] = (a > 0.0 && b > 0.0) ? (ew - ev) / 2 : 0;
-  }
+  if (tid < 2 * NB) atomicMax(&emax[(size_t)k * 2 * NB + tid], ecol[tid / NB][tid % NB]);
 }
 
 // ---------------------------------------------------------------- stage 2
@@ -508,16 +512,36 @@ int max_optin_smem() {
   return v;
 }
 
+// the largest dynamic shared memory a kernel can take on this device: the
+// opt-in limit per block less the kernel's static shared memory
+int dyn_smem_limit(const void* fn) {
+  cudaFuncAttributes fa;
+  int st = 0;
+  if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) st = (int)fa.sharedSizeBytes;
+  else cudaGetLastError();
+  return max_optin_smem() - st;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
 bool bs_band_supported(int n) {
   // the panel QR keeps an m x NB panel in shared memory
-  return n >= 2 && (size_t)BS_BAND_NB * n * sizeof(zd) + 8192 <= (size_t)max_optin_smem();
+  return n >= 2 && (size_t)BS_BAND_NB * n * sizeof(zd) <=
+                    (size_t)dyn_smem_limit((const void*)panel_qr_kernel<BS_BAND_NB>);
+}
+
+static void band_events_free(BandWs* w) {
+  for (int i = 0; i < BS_BAND_GROUPS * 2 * w->evcap; ++i) cudaEventDestroy(w->ev[i]);
+  delete[] w->ev;
+  w->ev = nullptr;
+  w->evcap = 0;
 }
 
 void bs_band_ws_free(BandWs* w) {
-  void* p[] = {w->V, w->X, w->W, w->T, w->wA, w->wB, w->wD, w->eA, w->eB, w->band, w->dsc};
+  band_events_free(w);
+  void* p[] = {w->V, w->X, w->W, w->T, w->wA, w->wB, w->wD, w->eA, w->eB, w->band, w->dsc,
+               w->zpart};
   for (void* q : p) cudaFree(q);
   *w = BandWs();
 }
@@ -541,7 +565,8 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
       {(void**)&w->eA, nE * sizeof(int), "band exponents A"},
       {(void**)&w->eB, nE * sizeof(int), "band exponents B"},
       {(void**)&w->band, (size_t)kb * n * 2 * NB * sizeof(zd), "band storage"},
-      {(void**)&w->dsc, (size_t)kb * NB * sizeof(int), "band balance exponents"},
+      {(void**)&w->dsc, (size_t)kb * 2 * NB * sizeof(int), "band column exponents"},
+      {(void**)&w->zpart, (size_t)kb * WCH * NB * NB * sizeof(zd), "band Z0 partials"},
   };
   for (auto& it : items) {
     cudaError_t e = cudaMalloc(it.p, it.bytes);
@@ -569,34 +594,91 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
   BS_CHECK_LAUNCH("symmetrize_kernel");
   const int ld = std::max(n - NB, 1);
   const long sv = (long)ld * NB;
-  if (n - NB > 1) {
-    // the shared-memory opt-in is a per-device attribute of the kernel
-    cudaError_t e = cudaFuncSetAttribute(panel_qr_kernel<NB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)NB * (n - NB) * sizeof(zd)));
-    if (e != cudaSuccess) return bs_cuda_status(e, "panel QR smem");
+  {
+    // the shared-memory opt-ins are per-device attributes of the kernels,
+    // set once per device to the device's limit (not during a capture)
+    static std::atomic<bool> attr[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!attr[dev].load(std::memory_order_acquire)) {
+      cudaError_t e = cudaFuncSetAttribute(panel_qr_kernel<NB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           dyn_smem_limit((const void*)panel_qr_kernel<NB>));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(bulge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dyn_smem_limit((const void*)bulge_kernel));
+      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction smem");
+      attr[dev].store(true, std::memory_order_release);
+    }
   }
-  for (int j = 0; n - j - NB > 1; j += NB) {
+  // timing: event pairs per kernel group and step
+  const int steps = n - NB > 1 ? (n - NB - 2) / NB + 1 : 0;
+  if (w.prof && w.evcap < steps + 1) {
+    band_events_free(&w);
+    const int cap = steps + 1;
+    w.ev = new cudaEvent_t[BS_BAND_GROUPS * 2 * cap];
+    for (int i = 0; i < BS_BAND_GROUPS * 2 * cap; ++i) {
+      cudaError_t e = cudaEventCreate(&w.ev[i]);
+      if (e != cudaSuccess) {
+        for (int q = 0; q < i; ++q) cudaEventDestroy(w.ev[q]);
+        delete[] w.ev;
+        w.ev = nullptr;
+        return bs_cuda_status(e, "band reduction events");
+      }
+    }
+    w.evcap = cap;
+  }
+  auto mark = [&](int grp, int step, int end) {
+    if (w.prof) cudaEventRecord(w.ev[(grp * w.evcap + step) * 2 + end], s);
+  };
+  w.nsteps = steps;
+  int step = 0;
+  for (int j = 0; n - j - NB > 1; j += NB, ++step) {
     const int m = n - j - NB;
     const size_t smem = (size_t)NB * m * sizeof(zd);
+    mark(0, step, 0);
     panel_qr_kernel<NB><<<kb, QR_NT, smem, s>>>(A, n, j, w.V, ld, sv, w.T);
     BS_CHECK_LAUNCH("panel_qr_kernel");
+    mark(0, step, 1);
+    mark(1, step, 0);
     TRY_LAUNCH(bs_launch_band_av(A, n, j + NB, m, w.V, ld, sv, NB, kb, w.S, w.wA, w.wB, w.wD,
                                  w.eA, w.eB, w.X, ld, sv, err, s));
-    wform_kernel<NB><<<kb, QR_NT, 0, s>>>(w.X, w.V, w.T, ld, sv, m, w.W, w.dsc);
-    BS_CHECK_LAUNCH("wform_kernel");
+    mark(1, step, 1);
+    mark(2, step, 0);
+    wz_kernel<NB><<<dim3(WCH, kb), QR_NT, 0, s>>>(w.X, w.V, ld, sv, m, w.zpart, w.dsc);
+    BS_CHECK_LAUNCH("wz_kernel");
+    wrow_kernel<NB><<<dim3(WCH, kb), QR_NT, 0, s>>>(w.X, w.V, w.T, ld, sv, m, w.zpart, w.W,
+                                                    w.dsc);
+    BS_CHECK_LAUNCH("wrow_kernel");
+    mark(2, step, 1);
+    mark(3, step, 0);
     TRY_LAUNCH(bs_launch_band_rank2(w.V, w.W, ld, sv, w.dsc, m, NB, kb, w.S, w.wA, w.wB, w.eA, A,
                                     n, j + NB, err, s));
+    mark(3, step, 1);
   }
   static_assert(NB == CH_NB, "the bulge chase is written for a band half-width of 8");
-  const bool in_smem = bulge_smem(n, true) <= (size_t)max_optin_smem();
+  const bool in_smem = bulge_smem(n, true) <= (size_t)dyn_smem_limit((const void*)bulge_kernel);
   const size_t smem = bulge_smem(n, in_smem);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(bulge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return bs_cuda_status(e, "bulge chase smem");
-  }
+  mark(4, 0, 0);
   bulge_kernel<<<kb, CH_WARPS * 32, smem, s>>>(A, n, w.band, in_smem ? 1 : 0, de);
   BS_CHECK_LAUNCH("bulge_kernel");
+  mark(4, 0, 1);
+  return BS_OK;
+}
+
+int bs_band_times(BandWs& w, double ms[BS_BAND_GROUPS]) {
+  for (int g = 0; g < BS_BAND_GROUPS; ++g) ms[g] = 0.0;
+  if (!w.prof || !w.ev) return BS_OK;
+  cudaError_t e = cudaEventSynchronize(w.ev[(4 * w.evcap) * 2 + 1]);
+  if (e != cudaSuccess) return bs_cuda_status(e, "band reduction times");
+  for (int g = 0; g < BS_BAND_GROUPS; ++g) {
+    const int ns = g == 4 ? 1 : w.nsteps;
+    for (int st = 0; st < ns; ++st) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, w.ev[(g * w.evcap + st) * 2], w.ev[(g * w.evcap + st) * 2 + 1]);
+      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction times");
+      ms[g] += t;
+    }
+  }
   return BS_OK;
 }

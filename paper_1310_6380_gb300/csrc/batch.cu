@@ -159,6 +159,7 @@ struct BatchGroup {
   int* fbrow;
   zd* vec64;                  // FP64 solver: reduction vectors and partial sums
   zd* part64;
+  BandWs* band;               // FP64 solver: two-stage reduction workspace (large n)
   // [0] tensor-core pipeline timeout of a main-stream product, [1] a Gram
   // Cholesky failed, [2] a tensor-core timeout during a cell's assembly
   // (the workers' own flags are reset by every assembly, so each assembly's
@@ -211,6 +212,11 @@ static void prof_mark(bs_batch* B, cudaStream_t s) {
 }
 
 static void free_group(BatchGroup& g) {
+  if (g.band) {
+    bs_band_ws_free(g.band);
+    delete g.band;
+    g.band = nullptr;
+  }
   for (int w = 0; w < g.nworkers; ++w) {
     if (g.workers[w]) bs_destroy_cell(g.workers[w]);
     if (g.wstream[w]) cudaStreamDestroy(g.wstream[w]);
@@ -508,8 +514,11 @@ static int reduce_chunk_body(bs_batch* B, BatchGroup& g, int c0, int cn, int p, 
   prof_mark(B, s);   // assembly ends, reduction begins
   if (B->solver == BS_SOLVER_FP64) {
     // the plain FP64 dense path: Householder reduction and Sturm multisection
-    TRY_LAUNCH(bs_launch_tridiag<double>(g.C64, n, K, g.vec64, g.part64, g.de, g.tau, g.beta,
-                                         g.count, s));
+    if (g.band)
+      TRY_LAUNCH(bs_launch_eig_band(g.C64, n, K, *g.band, g.de, g.d_err, s));
+    else
+      TRY_LAUNCH(bs_launch_tridiag<double>(g.C64, n, K, g.vec64, g.part64, g.de, g.tau, g.beta,
+                                           g.count, s));
     prof_mark(B, s);
     TRY_LAUNCH(bs_launch_bisect(g.de, n, K, B->nbands, g.w, g.st, s));
     prof_mark(B, s);
@@ -848,6 +857,14 @@ extern "C" int bs_batch_set_solver(bs_batch* B, int solver) {
       if (!g.vec64) TRY_LAUNCH(balloc(&g.vec64, K * bs_tridiag_vec_elems(g.n), "batch FP64 vectors"));
       if (!g.part64)
         TRY_LAUNCH(balloc(&g.part64, K * bs_tridiag_part_elems(g.n), "batch FP64 partials"));
+      if (bs_use_band(g.n)) {
+        if (!g.band) g.band = new BandWs();
+        TRY_LAUNCH(bs_band_ws_alloc(g.band, g.n, (int)K, BS_SLICES_BAND));
+      } else if (g.band) {
+        bs_band_ws_free(g.band);
+        delete g.band;
+        g.band = nullptr;
+      }
     }
   }
   if (solver != B->solver) drop_graph(B);

@@ -202,6 +202,7 @@ struct bs_cell {
 
   // profiling: events around each phase of the last call
   struct BandWs* band;  // two-stage reduction workspace (allocated on first use)
+  bool band_used;       // the last FP64 solve took the two-stage reduction
 
   bool prof;
   bool prof_ready[PH_COUNT];
@@ -306,9 +307,19 @@ struct BandWs {
   int* eA = nullptr;
   int* eB = nullptr;
   zd* band = nullptr;       // kb x n x 2nb band storage (when it does not fit in shared memory)
-  int* dsc = nullptr;       // kb x nb power-of-two balance of V against W per column
+  int* dsc = nullptr;       // kb x 2 x nb largest FP64 exponent fields of V's and W's columns
+  zd* zpart = nullptr;      // kb x chunks x nb x nb partial sums of V^dagger X
+  // per-kernel-group timing of the last reduction (bs_reduction_times):
+  // event pairs [group][step] around the panel QR, A22 V, the W formation,
+  // the rank-2 update and the bulge chase
+  bool prof = false;
+  cudaEvent_t* ev = nullptr;
+  int evcap = 0;            // event pairs per group
+  int nsteps = 0;           // steps recorded by the last reduction
 };
 #define BS_BAND_AUTO_MIN 400   // BS_REDUCE_AUTO takes the two-stage reduction from this n on
+#define BS_BAND_GROUPS 5
+int bs_band_times(BandWs& w, double ms[BS_BAND_GROUPS]);
 bool bs_band_supported(int n);
 bool bs_use_band(int n);
 int bs_band_ws_alloc(BandWs* w, int n, int kb, int S);

@@ -54,6 +54,7 @@ struct bs_cell3 {
   double *d_de, *d_tau, *d_Q, *d_w;
   unsigned* d_count;
   int* d_stat;
+  BandWs* band;        // two-stage reduction workspace (allocated on first use)
 };
 
 namespace {
@@ -308,6 +309,11 @@ std::vector<double> monomial_coefficients() {
 }
 
 void free_ws3(bs_cell3* c) {
+  if (c->band) {
+    bs_band_ws_free(c->band);
+    delete c->band;
+    c->band = nullptr;
+  }
   cudaFree(c->d_C);
   cudaFree(c->d_vec);
   cudaFree(c->d_part);
@@ -608,8 +614,14 @@ extern "C" int bs_solve_k3(bs_cell3* c, const double* Q, int nk, int nbands, dou
       r = bs_cuda_status(e, "builder3_kernel");
       break;
     }
-    r = bs_launch_tridiag<double>(c->d_C, n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
-                                  c->d_beta, c->d_count, s);
+    if (bs_use_band(n)) {
+      if (!c->band) c->band = new BandWs();
+      r = bs_band_ws_alloc(c->band, n, c->kcap, BS_SLICES_BAND);
+      if (!r) r = bs_launch_eig_band(c->d_C, n, kb, *c->band, c->d_de, c->d_info + 1, s);
+    } else {
+      r = bs_launch_tridiag<double>(c->d_C, n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
+                                    c->d_beta, c->d_count, s);
+    }
     if (!r) r = bs_launch_bisect(c->d_de, n, kb, nbands, c->d_w, c->d_stat, s);
     if (r) break;
     e = cudaMemcpyAsync(omega_out + (size_t)k0 * nbands, c->d_w, (size_t)kb * nbands * 8,

@@ -129,6 +129,33 @@ __device__ __forceinline__ void put_digits(double x, int e, int S, uint16_t* out
   }
 }
 
+// put_digits with the digit count fixed at compile time (the shifts become
+// immediates); the same digits as put_digits(x, e, S, ...)
+template <int S>
+__device__ __forceinline__ void put_digits_t(double x, int e, uint16_t* out, ptrdiff_t plane) {
+  constexpr int B = 6 + 7 * (S - 1);
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long X = 0;
+  if (E != 0) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = 1075 - E - B + e;
+    if (sh <= 0) X = m << (-sh);
+    else if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
+    if (bits < 0) X = -X;
+  }
+  long long r = X;
+#pragma unroll
+  for (int sd = 0; sd < S; ++sd) {
+    const int sh = B - 6 - 7 * sd;
+    long long t;
+    if (sh > 0) t = (r + (1LL << (sh - 1))) >> sh;
+    else t = r;
+    r -= t << (sh > 0 ? sh : 0);
+    out[(ptrdiff_t)sd * plane] = bf16_bits(t);
+  }
+}
+
 // ---- assembly operands
 // A rows (f, p): grid (P, nf), block 128
 __global__ void pack_fields_kernel(const uint16_t* __restrict__ phase,
@@ -405,26 +432,31 @@ int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long
 namespace {
 
 // A rows r of [Re A22[r, :] | Im A22[r, :]], read as the conjugate of
-// column r; grid (m, kb), block 128
-__global__ void pack_trail_kernel(const zd* __restrict__ A, int n, int o, int m, int S, int Kp,
+// column r (eight digits); grid (m, kb), block 128
+__global__ void pack_trail_kernel(const zd* __restrict__ A, int n, int o, int m, int Kp,
                                   uint16_t* __restrict__ out, int* __restrict__ ex) {
+  constexpr int S = 8;
   __shared__ double sh[4];
-  const int r = blockIdx.x, k = blockIdx.y;
+  const int r = blockIdx.x, k = blockIdx.y, t = threadIdx.x;
   const zd* col = A + (size_t)k * n * n + (size_t)(o + r) * n + o;
   double mx = 0.0;
-  for (int c = threadIdx.x; c < m; c += 128) {
+  for (int c = t; c < m; c += 128) {
     const zd v = col[c];
     mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
   }
   const int e = row_exp(row_max(mx, sh));
   uint16_t* base = out + ((size_t)k * m + r) * S * Kp;
-  for (int c = threadIdx.x; c < Kp; c += 128) {
-    double x = 0.0;
-    if (c < m) x = col[c].x;
-    else if (c < 2 * m) x = -col[c - m].y;
-    put_digits(x, e, S, base + c, Kp);
+  for (int c = t; c < m; c += 128) {
+    const zd v = col[c];
+    put_digits_t<S>(v.x, e, base + c, Kp);
+    // Im A22[r, c] = -Im A22[c, r]: a sign flip of the bit pattern
+    put_digits_t<S>(__longlong_as_double(__double_as_longlong(v.y) ^ (1LL << 63)), e,
+                    base + m + c, Kp);
   }
-  if (threadIdx.x == 0) ex[(size_t)k * m + r] = e;
+  for (int c = 2 * m + t; c < Kp; c += 128)
+#pragma unroll
+    for (int sd = 0; sd < S; ++sd) base[(size_t)sd * Kp + c] = 0;
+  if (t == 0) ex[(size_t)k * m + r] = e;
 }
 
 // B rows (i, part) of the m x nb block V (leading dimension ldv, batch
@@ -473,10 +505,12 @@ __global__ void recombine_panel_kernel(const float* __restrict__ Dm, const Slice
 }
 
 // Operands of the rank-2nb update V W^dagger + W V^dagger = X Y^dagger with
-// X = [V D, W D^-1], Y = [W D^-1, V D] (m x 2nb), D = diag(2^dsc_i) a
+// X = [V D, W D^-1], Y = [W D^-1, V D] (m x 2nb), D = diag(2^d_i) a
 // power-of-two balance of column i of V (entries at most 1) against
-// column i of W (of the size of the matrix norm), so that one row scale
-// serves both halves of a row without starving V of digits:
+// column i of W (of the size of the matrix norm), d_i half the difference
+// of their largest exponents (ecol: kb x [V | W] x nb exponent fields), so
+// that one row scale serves both halves of a row without starving V of
+// digits:
 // A rows r = [Re X[r, :] | Im X[r, :]], B rows (c, 0) = [Re Y[c, :] | Im Y[c, :]],
 // (c, 1) = [-Im Y[c, :] | Re Y[c, :]], K = 4 nb <= 64 (one 64-column block).
 // Row r of X and of Y hold the same numbers, so one exponent serves both,
@@ -484,7 +518,7 @@ __global__ void recombine_panel_kernel(const float* __restrict__ Dm, const Slice
 // The scaling only shifts the digit exponents (no rounding); grid (m, kb),
 // block 64
 __global__ void pack_rank2_kernel(const zd* __restrict__ V, const zd* __restrict__ W, int ld,
-                                  long sv, const int* __restrict__ dsc, int m, int nb, int S,
+                                  long sv, const int* __restrict__ ecol, int m, int nb, int S,
                                   uint16_t* __restrict__ oa, uint16_t* __restrict__ ob,
                                   int* __restrict__ ex) {
   __shared__ double sh[2];
@@ -498,7 +532,8 @@ __global__ void pack_rank2_kernel(const zd* __restrict__ V, const zd* __restrict
   if (t < 2 * w2) {
     const int c = t < w2 ? t : t - w2;
     const int ci = c < nb ? c : c - nb;
-    const int d = dsc[(size_t)k * nb + ci];
+    const int ev = ecol[(size_t)k * 2 * nb + ci], ew = ecol[(size_t)k * 2 * nb + nb + ci];
+    const int d = (ev > 0 && ew > 0) ? (ew - ev) / 2 : 0;
     shx = c < nb ? d : -d;
     shy = -shx;
     const zd xv = c < nb ? vk[(size_t)c * ld + r] : wk[(size_t)(c - nb) * ld + r];
@@ -519,10 +554,10 @@ __global__ void pack_rank2_kernel(const zd* __restrict__ V, const zd* __restrict
   mx = fmax(sh[0], sh[1]);
   const int e = row_exp(mx);
   const size_t rowlen = (size_t)S * 64;
-  put_digits(a, e - shx, S, oa + ((size_t)k * m + r) * rowlen + t, 64);
+  put_digits_t<8>(a, e - shx, oa + ((size_t)k * m + r) * rowlen + t, 64);
   uint16_t* b0 = ob + ((size_t)k * 2 * m + 2 * (size_t)r) * rowlen + (size_t)(S - 1) * 64 + t;
-  put_digits(y0, e - shy, S, b0, -64);
-  put_digits(y1, e - shy, S, b0 + rowlen, -64);
+  put_digits_t<8>(y0, e - shy, b0, -64);
+  put_digits_t<8>(y1, e - shy, b0 + rowlen, -64);
   if (t == 0) ex[(size_t)k * m + r] = e;
 }
 
@@ -552,11 +587,11 @@ int bs_launch_band_av(const zd* A, int n, int o, int m, const zd* V, int ldv, lo
                       zd* X, int ldx, long sx, int* err, cudaStream_t s) {
   const int Kp = (2 * m + 63) / 64 * 64;
   SliceSlabs sl;
-  if (!bs_slice_slabs(S, Kp, m, 2 * nb, kb, &sl)) {
+  if (S != 8 || !bs_slice_slabs(S, Kp, m, 2 * nb, kb, &sl)) {
     bs_set_error("band reduction: m = %d gives too many digit slabs", m);
     return BS_EINVAL;
   }
-  pack_trail_kernel<<<dim3(m, kb), 128, 0, s>>>(A, n, o, m, S, Kp, wA, eA);
+  pack_trail_kernel<<<dim3(m, kb), 128, 0, s>>>(A, n, o, m, Kp, wA, eA);
   BS_CHECK_LAUNCH("pack_trail_kernel");
   pack_panel_kernel<<<dim3(nb, kb), 128, 0, s>>>(V, ldv, sv, m, nb, S, Kp, wB, eB);
   BS_CHECK_LAUNCH("pack_panel_kernel");

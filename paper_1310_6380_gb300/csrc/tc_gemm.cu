@@ -320,17 +320,29 @@ __global__ void __launch_bounds__(128, 2)
         : "memory");
   }
   __syncwarp();
+  // while TMA and the MMAs run, every thread fetches the FP64 entries of its
+  // row that the tile updates (the epilogue is otherwise bound by these
+  // loads' DRAM latency)
+  const int rl = warp * 32 + lane, r = m0 + rl;
+  const bool live = r < m;
+  zd* az = A + (size_t)z * n * n + (size_t)o * n + o;
+  zd old[CW];
+  int ec[CW];
+#pragma unroll
+  for (int cl = 0; cl < CW; ++cl) {
+    const int c = cc0 + cl;
+    const bool use = live && c < m && c <= r;
+    old[cl] = use ? az[(size_t)c * n + r] : zmake(0.0, 0.0);
+    ec[cl] = c < m ? ex[(size_t)z * m + c] : 0;
+  }
+  const int er = live ? ex[(size_t)z * m + r] : 0;
   const bool ok = __all_sync(0xffffffffu, mbar_wait(&done, 0u, err));
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // the A ring is free once every MMA has completed: it stages the tile
   // (BM x CW complex, row stride CW + 1) for the transposed stores
   zd* stage = reinterpret_cast<zd*>(sA);
-  const int rl = warp * 32 + lane, r = m0 + rl;
-  const bool live = r < m;
-  zd* az = A + (size_t)z * n * n + (size_t)o * n + o;
   if (ok) {
-    const int er = live ? ex[(size_t)z * m + r] : 0;
-#pragma unroll 1
+#pragma unroll
     for (int c0 = 0; c0 < BN; c0 += 16) {
       long long hi[16], lo[16];
 #pragma unroll
@@ -349,7 +361,10 @@ __global__ void __launch_bounds__(128, 2)
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const long long d = __float2int_rn(__uint_as_float(v[j]));
+          // the order sums are exact integers below 2^22: the FP32 add of
+          // 1.5 2^23 puts them in the low mantissa bits
+          const long long d =
+              (long long)(__float_as_int(__uint_as_float(v[j]) + 12582912.0f) - 0x4B400000);
           if (u < 4) hi[j] = hi[j] * 128 + d;
           else lo[j] = lo[j] * 128 + d;
         }
@@ -361,13 +376,11 @@ __global__ void __launch_bounds__(128, 2)
         if (live && c < m && c <= r) {
           const long long tr = hi[2 * jc] * 2097152 + (lo[2 * jc] >> 7);
           const long long ti = hi[2 * jc + 1] * 2097152 + (lo[2 * jc + 1] >> 7);
-          const int e = er + ex[(size_t)z * m + c] - 54;
-          const double w = __longlong_as_double((long long)(1023 + e) << 52);
-          zd* ap = az + (size_t)c * n + r;
-          val = *ap;
+          const double w = __longlong_as_double((long long)(1023 + er + ec[cl] - 54) << 52);
+          val = old[cl];
           val.x = fma(-(double)tr, w, val.x);
           val.y = r == c ? 0.0 : fma(-(double)ti, w, val.y);
-          *ap = val;
+          az[(size_t)c * n + r] = val;
         }
         stage[rl * (CW + 1) + cl] = val;
       }
