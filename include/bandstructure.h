@@ -276,11 +276,14 @@ int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps);
  * FP64 solve, summed over its panel steps: [0] panel Householder QR,
  * [1] A22 V (digit planes of the trailing block and the tensor-core
  * product), [2] the W formation, [3] the trailing rank-2nb update (tensor
- * cores, FP64 epilogue), [4] the bulge chase to tridiagonal form.  All
- * zeros when profiling is off or the last solve took the one-stage
- * reduction.  A measurement aid (the paper has no counterpart).
+ * cores, FP64 epilogue), [4] the bulge chase to tridiagonal form; [5] the
+ * number of matrices those launches processed.  The reduction runs the
+ * batch as two halves on two streams; the times bracket the first half's
+ * launches, which run beside the second half's.  All zeros when profiling
+ * is off or the last solve took the one-stage reduction.  A measurement aid
+ * (the paper has no counterpart).
  */
-int bs_reduction_times(bs_cell* cell, double ms[5]);
+int bs_reduction_times(bs_cell* cell, double ms[6]);
 
 #define BS_REDUCE_AUTO     0
 #define BS_REDUCE_ONESTAGE 1

@@ -477,12 +477,13 @@ def bs_phase_times(cell) -> dict:
     return dict(zip(PHASES, ms.tolist()))
 
 
-REDUCTION_GROUPS = ("panel_qr", "a22_v", "w_form", "rank2_update", "bulge_chase")
+REDUCTION_GROUPS = ("panel_qr", "a22_v", "w_form", "rank2_update", "bulge_chase", "matrices")
 
 
 def bs_reduction_times(cell) -> dict:
-    """Device ms per kernel group of the last two-stage reduction (profiling on)."""
-    ms = np.zeros(5)
+    """Device ms per kernel group of the last two-stage reduction (profiling on),
+    and the number of matrices the timed launches processed."""
+    ms = np.zeros(6)
     _check(_lib.bs_reduction_times(cell, ms.ctypes.data))
     return dict(zip(REDUCTION_GROUPS, ms.tolist()))
 

@@ -1118,14 +1118,16 @@ extern "C" int bs_phase_times(bs_cell* c, double ms[8]) {
   return BS_OK;
 }
 
-extern "C" int bs_reduction_times(bs_cell* c, double ms[5]) {
+extern "C" int bs_reduction_times(bs_cell* c, double ms[6]) {
   if (!c || !ms) {
     bs_set_error("bs_reduction_times: NULL argument");
     return BS_EINVAL;
   }
-  for (int i = 0; i < 5; ++i) ms[i] = 0.0;
+  for (int i = 0; i < 6; ++i) ms[i] = 0.0;
   if (!c->prof || !c->band_used || !c->band) return BS_OK;
-  return bs_band_times(*c->band, ms);
+  TRY(bs_band_times(*c->band, ms));
+  ms[5] = c->band->timed;
+  return BS_OK;
 }
 
 // ------------------------------------------------------------------ diagnostics

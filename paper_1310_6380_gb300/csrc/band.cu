@@ -32,7 +32,8 @@
 
 namespace {
 
-constexpr int QR_NT = 256;   // threads of the panel QR and W kernels
+constexpr int QR_NT = 256;   // threads of the W kernels
+constexpr int PQ_NT = 512;   // threads of the panel QR (16 warps hide the FP64 latency)
 constexpr int LAG = 3;       // blocks between consecutive sweeps
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -69,9 +70,9 @@ __global__ void symmetrize_kernel(zd* __restrict__ A, int n) {
 }
 
 // ---------------------------------------------------------------- panel QR
-// Block-wide sum of NV complex values held by every thread; the result is
-// left in out[0 .. NV).  sh: NV x (QR_NT/32) zd.
-template <int NV>
+// Block-wide sum of NV complex values held by every thread of an NT-thread
+// block; the result is left in out[0 .. NV).  sh: NV x (NT/32) zd.
+template <int NV, int NT>
 __device__ void block_zsum(zd (&v)[NV], zd* sh, zd* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -81,28 +82,28 @@ __device__ void block_zsum(zd (&v)[NV], zd* sh, zd* out) {
   }
   if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) sh[q * (QR_NT / 32) + warp] = v[q];
+    for (int q = 0; q < NV; ++q) sh[q * (NT / 32) + warp] = v[q];
   }
   __syncthreads();
   if (threadIdx.x < NV) {
     zd t = zmake(0.0, 0.0);
-    for (int w = 0; w < QR_NT / 32; ++w) t = zadd(t, sh[threadIdx.x * (QR_NT / 32) + w]);
+    for (int w = 0; w < NT / 32; ++w) t = zadd(t, sh[threadIdx.x * (NT / 32) + w]);
     out[threadIdx.x] = t;
   }
   __syncthreads();
 }
 
 // Householder QR of the panel A[j+NB : n, j : j+NB] (m x NB) of every
-// matrix of the batch, in shared memory.  Thread t owns rows t, t + QR_NT,
+// matrix of the batch, in shared memory.  Thread t owns rows t, t + PQ_NT,
 // ... of the panel throughout.  Writes R (upper triangle) and zeros below
 // it back into the panel, V (m x NB, unit lower trapezoidal, leading
 // dimension ldv) and T (NB x NB upper triangular, column-major).
 template <int NB>
-__global__ void __launch_bounds__(QR_NT) panel_qr_kernel(zd* __restrict__ A, int n, int j,
+__global__ void __launch_bounds__(PQ_NT) panel_qr_kernel(zd* __restrict__ A, int n, int j,
                                                          zd* __restrict__ V, int ldv, long sv,
                                                          zd* __restrict__ T) {
   extern __shared__ zd P[];   // [NB][m]
-  __shared__ zd red[NB * (QR_NT / 32)];
+  __shared__ zd red[NB * (PQ_NT / 32)];
   __shared__ zd dots[NB];
   __shared__ zd G[NB][NB];    // G[a][i] = v_a^dagger v_i, a < i
   __shared__ double tau_s[NB];
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(QR_NT) panel_qr_kernel(zd* __restrict__ A, int
   const int k = blockIdx.x, tid = threadIdx.x;
   const int m = n - j - NB;
   zd* a = A + (size_t)k * n * n;
-  for (int idx = tid; idx < NB * m; idx += QR_NT) {
+  for (int idx = tid; idx < NB * m; idx += PQ_NT) {
     const int i = idx / m, r = idx % m;
     P[idx] = a[(size_t)(j + i) * n + j + NB + r];
   }
@@ -121,12 +122,12 @@ __global__ void __launch_bounds__(QR_NT) panel_qr_kernel(zd* __restrict__ A, int
     zd* pi = P + (size_t)i * m;
     // ||x[1:]||^2 of x = P[i][i:]
     double s = 0.0;
-    for (int r = tid; r < m; r += QR_NT) {
+    for (int r = tid; r < m; r += PQ_NT) {
       if (r > i) s = fma(pi[r].x, pi[r].x, fma(pi[r].y, pi[r].y, s));
       if (r == i) alpha_s = pi[r];
     }
     zd sv1[1] = {zmake(s, 0.0)};
-    block_zsum<1>(sv1, red, dots);
+    block_zsum<1, PQ_NT>(sv1, red, dots);
     const zd alpha = alpha_s;
     const double aa = hypot(alpha.x, alpha.y);
     const double nu = sqrt(fma(aa, aa, dots[0].x));
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(QR_NT) panel_qr_kernel(zd* __restrict__ A, int
     zd acc[NB > 1 ? NB - 1 : 1];
 #pragma unroll
     for (int q = 0; q < NB - 1; ++q) acc[q] = zmake(0.0, 0.0);
-    for (int r = tid; r < m; r += QR_NT) {
+    for (int r = tid; r < m; r += PQ_NT) {
       if (r < i) continue;
       zd vr;
       if (r == i) {
@@ -165,28 +166,30 @@ __global__ void __launch_bounds__(QR_NT) panel_qr_kernel(zd* __restrict__ A, int
         }
       }
     }
-    block_zsum<(NB > 1 ? NB - 1 : 1)>(acc, red, dots);
+    block_zsum<(NB > 1 ? NB - 1 : 1), PQ_NT>(acc, red, dots);
     if (tid == 0) {
       tau_s[i] = tau;
       beta_s[i] = beta;
       for (int q = 0; q < i; ++q) G[q][i] = dots[q];
     }
     // P[c] -= tau v (v^dagger P[c]) for c > i
-    for (int r = tid; r < m; r += QR_NT) {
+    zd tz[NB > 1 ? NB - 1 : 1];
+#pragma unroll
+    for (int c = 1; c < NB; ++c) tz[c - 1] = zscale(dots[c - 1], tau);
+    for (int r = tid; r < m; r += PQ_NT) {
       if (r < i) continue;
       const zd vr = r == i ? zmake(1.0, 0.0) : pi[r];
 #pragma unroll
       for (int c = 1; c < NB; ++c) {
         if (c <= i) continue;
-        const zd z = zscale(dots[c - 1], tau);
-        P[(size_t)c * m + r] = zsub(P[(size_t)c * m + r], zmul(vr, z));
+        P[(size_t)c * m + r] = zfnma(vr, tz[c - 1], P[(size_t)c * m + r]);
       }
     }
     __syncthreads();
   }
   // write back: R and zeros into the panel, V, then T
   zd* vk = V + (size_t)k * sv;
-  for (int idx = tid; idx < NB * m; idx += QR_NT) {
+  for (int idx = tid; idx < NB * m; idx += PQ_NT) {
     const int i = idx / m, r = idx % m;
     zd out, vv;
     if (i < kk) {
@@ -395,6 +398,17 @@ __global__ void __launch_bounds__(CH_WARPS * 32, 1)
   __syncthreads();
   const int tend = tend_s;
   const int i = lane & 7;
+  // lower-triangle entries (row, column) of the 8 x 8 diagonal block that
+  // this lane updates: e = i + 8q in row-major order, 36 entries (-1: none)
+  int tr[5], tc[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int e = i + 8 * q;
+    int r = 0;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    tr[q] = e < 36 ? r : -1;
+    tc[q] = e < 36 ? e - r * (r + 1) / 2 : 0;
+  }
   int s = warp * 4 + (lane >> 3);   // this group's sweep
   zd vp = zmake(0.0, 0.0);          // previous reflector of the sweep (row i)
   double taup = 0.0;
@@ -454,7 +468,7 @@ __global__ void __launch_bounds__(CH_WARPS * 32, 1)
       const zd zi = rscatter8(P, i);
       const zd tv = zscale(v, tau);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) O[j] = zsub(O[j], zmul(tv, gshfl(zi, j)));
+      for (int j = 0; j < 8; ++j) O[j] = zfnma(tv, gshfl(zi, j), O[j]);
     }
     O[0] = i == 0 ? beta : zero;
 #pragma unroll
@@ -476,14 +490,19 @@ __global__ void __launch_bounds__(CH_WARPS * 32, 1)
     const zd q = zmul(zconj(v), p);
     const double vhp = gsum(q.x);   // v^dagger p is real
     const zd w = zsub(p, zscale(v, 0.5 * tau * vhp));
+    // D -= v w^dagger + w v^dagger on the 36 lower-triangle entries only,
+    // five per lane (entry e = i + 8q, (tr[q], tc[q]) precomputed)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      // every lane takes part in the shuffles; the lower triangle is stored
-      const zd wj = gshfl(w, j), vj = gshfl(v, j);
-      zd dv = zfnmac(v, wj, D[j]);
-      dv = zfnmac(w, vj, dv);
-      if (i == j) dv.y = 0.0;
-      if (j <= i && i < L) bd[(size_t)(r0 + j) * W2 + (i - j)] = dv;
+    for (int q = 0; q < 5; ++q) {
+      const int rr = tr[q], cc = tc[q];
+      const zd vr = gshfl(v, rr), wr = gshfl(w, rr), vc = gshfl(v, cc), wc = gshfl(w, cc);
+      if (rr >= 0 && rr < L) {
+        zd* dp = bd + (size_t)(r0 + cc) * W2 + (rr - cc);
+        zd dv = zfnmac(vr, wc, *dp);
+        dv = zfnmac(wr, vc, dv);
+        if (rr == cc) dv.y = 0.0;
+        *dp = dv;
+      }
     }
     vp = v;
     taup = tau;
@@ -540,10 +559,23 @@ static void band_events_free(BandWs* w) {
 
 void bs_band_ws_free(BandWs* w) {
   band_events_free(w);
+  if (w->fork) cudaEventDestroy(w->fork);
+  if (w->join) cudaEventDestroy(w->join);
+  if (w->s2) cudaStreamDestroy(w->s2);
   void* p[] = {w->V, w->X, w->W, w->T, w->wA, w->wB, w->wD, w->eA, w->eB, w->band, w->dsc,
                w->zpart};
   for (void* q : p) cudaFree(q);
   *w = BandWs();
+}
+
+// The batch runs as two halves on two streams (the caller's and one of the
+// workspace): the panel QR and W formation of one half are FP64-bound on
+// one CTA per matrix, and run beside the tensor-core and memory-bound
+// products of the other half.  The digit planes and sums have one region
+// per half.
+static void halves(int kb, int* k0, int* k1) {
+  *k0 = kb >= 2 ? kb / 2 : kb;
+  *k1 = kb - *k0;
 }
 
 int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
@@ -551,19 +583,25 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
   bs_band_ws_free(w);
   const int NB = BS_BAND_NB;
   const int m = std::max(n - NB, 1);
+  int k0 = 0, k1 = 0;
+  halves(kb, &k0, &k1);
   size_t nA = 0, nB = 0, nD = 0, nE = 0;
-  bs_band_tc_elems(n, NB, kb, S, &nA, &nB, &nD, &nE);
+  bs_band_tc_elems(n, NB, std::max(k0, k1), S, &nA, &nB, &nD, &nE);
+  w->hA = nA;
+  w->hB = nB;
+  w->hD = nD;
+  w->hE = nE;
   const size_t pv = (size_t)kb * m * NB;
   struct Item { void** p; size_t bytes; const char* what; } items[] = {
       {(void**)&w->V, pv * sizeof(zd), "band reflectors"},
       {(void**)&w->X, pv * sizeof(zd), "band A22 V"},
       {(void**)&w->W, pv * sizeof(zd), "band W"},
       {(void**)&w->T, (size_t)kb * NB * NB * sizeof(zd), "band T"},
-      {(void**)&w->wA, nA * sizeof(uint16_t), "band digit planes A"},
-      {(void**)&w->wB, nB * sizeof(uint16_t), "band digit planes B"},
-      {(void**)&w->wD, nD * sizeof(float), "band digit-order sums"},
-      {(void**)&w->eA, nE * sizeof(int), "band exponents A"},
-      {(void**)&w->eB, nE * sizeof(int), "band exponents B"},
+      {(void**)&w->wA, 2 * nA * sizeof(uint16_t), "band digit planes A"},
+      {(void**)&w->wB, 2 * nB * sizeof(uint16_t), "band digit planes B"},
+      {(void**)&w->wD, 2 * nD * sizeof(float), "band digit-order sums"},
+      {(void**)&w->eA, 2 * nE * sizeof(int), "band exponents A"},
+      {(void**)&w->eB, 2 * nE * sizeof(int), "band exponents B"},
       {(void**)&w->band, (size_t)kb * n * 2 * NB * sizeof(zd), "band storage"},
       {(void**)&w->dsc, (size_t)kb * 2 * NB * sizeof(int), "band column exponents"},
       {(void**)&w->zpart, (size_t)kb * WCH * NB * NB * sizeof(zd), "band Z0 partials"},
@@ -576,6 +614,13 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
       bs_set_error("out of device memory (%s, %zu bytes)", it.what, it.bytes);
       return BS_ENOMEM;
     }
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&w->s2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->join, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    bs_band_ws_free(w);
+    return bs_cuda_status(e, "band reduction stream");
   }
   w->n = n;
   w->kb = kb;
@@ -611,7 +656,7 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
       attr[dev].store(true, std::memory_order_release);
     }
   }
-  // timing: event pairs per kernel group and step
+  // timing: event pairs per kernel group and step, on the first half's stream
   const int steps = n - NB > 1 ? (n - NB - 2) / NB + 1 : 0;
   if (w.prof && w.evcap < steps + 1) {
     band_events_free(&w);
@@ -628,41 +673,77 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
     }
     w.evcap = cap;
   }
-  auto mark = [&](int grp, int step, int end) {
-    if (w.prof) cudaEventRecord(w.ev[(grp * w.evcap + step) * 2 + end], s);
-  };
+  int k0 = 0, k1 = 0;
+  halves(kb, &k0, &k1);
   w.nsteps = steps;
+  w.timed = k0;
+  cudaStream_t hs[2] = {s, w.s2};
+  const int hk[2] = {k0, k1}, off[2] = {0, k0};
+  if (k1 > 0) {
+    cudaError_t e = cudaEventRecord(w.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(w.s2, w.fork, 0);
+    if (e != cudaSuccess) return bs_cuda_status(e, "band reduction fork");
+  }
+  auto mark = [&](int h, int grp, int step, int end) {
+    if (w.prof && h == 0) cudaEventRecord(w.ev[(grp * w.evcap + step) * 2 + end], s);
+  };
   int step = 0;
   for (int j = 0; n - j - NB > 1; j += NB, ++step) {
     const int m = n - j - NB;
     const size_t smem = (size_t)NB * m * sizeof(zd);
-    mark(0, step, 0);
-    panel_qr_kernel<NB><<<kb, QR_NT, smem, s>>>(A, n, j, w.V, ld, sv, w.T);
-    BS_CHECK_LAUNCH("panel_qr_kernel");
-    mark(0, step, 1);
-    mark(1, step, 0);
-    TRY_LAUNCH(bs_launch_band_av(A, n, j + NB, m, w.V, ld, sv, NB, kb, w.S, w.wA, w.wB, w.wD,
-                                 w.eA, w.eB, w.X, ld, sv, err, s));
-    mark(1, step, 1);
-    mark(2, step, 0);
-    wz_kernel<NB><<<dim3(WCH, kb), QR_NT, 0, s>>>(w.X, w.V, ld, sv, m, w.zpart, w.dsc);
-    BS_CHECK_LAUNCH("wz_kernel");
-    wrow_kernel<NB><<<dim3(WCH, kb), QR_NT, 0, s>>>(w.X, w.V, w.T, ld, sv, m, w.zpart, w.W,
-                                                    w.dsc);
-    BS_CHECK_LAUNCH("wrow_kernel");
-    mark(2, step, 1);
-    mark(3, step, 0);
-    TRY_LAUNCH(bs_launch_band_rank2(w.V, w.W, ld, sv, w.dsc, m, NB, kb, w.S, w.wA, w.wB, w.eA, A,
-                                    n, j + NB, err, s));
-    mark(3, step, 1);
+    for (int h = 0; h < 2; ++h) {
+      const int kh = hk[h];
+      if (kh == 0) continue;
+      const cudaStream_t st = hs[h];
+      zd* Ah = A + (size_t)off[h] * n * n;
+      zd* Vh = w.V + (size_t)off[h] * sv;
+      zd* Xh = w.X + (size_t)off[h] * sv;
+      zd* Wh = w.W + (size_t)off[h] * sv;
+      zd* Th = w.T + (size_t)off[h] * NB * NB;
+      int* dh = w.dsc + (size_t)off[h] * 2 * NB;
+      zd* zh = w.zpart + (size_t)off[h] * WCH * NB * NB;
+      uint16_t* wAh = w.wA + h * w.hA;
+      uint16_t* wBh = w.wB + h * w.hB;
+      float* wDh = w.wD + h * w.hD;
+      int* eAh = w.eA + h * w.hE;
+      int* eBh = w.eB + h * w.hE;
+      mark(h, 0, step, 0);
+      panel_qr_kernel<NB><<<kh, PQ_NT, smem, st>>>(Ah, n, j, Vh, ld, sv, Th);
+      BS_CHECK_LAUNCH("panel_qr_kernel");
+      mark(h, 0, step, 1);
+      mark(h, 1, step, 0);
+      TRY_LAUNCH(bs_launch_band_av(Ah, n, j + NB, m, Vh, ld, sv, NB, kh, w.S, wAh, wBh, wDh, eAh,
+                                   eBh, Xh, ld, sv, err, st));
+      mark(h, 1, step, 1);
+      mark(h, 2, step, 0);
+      wz_kernel<NB><<<dim3(WCH, kh), QR_NT, 0, st>>>(Xh, Vh, ld, sv, m, zh, dh);
+      BS_CHECK_LAUNCH("wz_kernel");
+      wrow_kernel<NB><<<dim3(WCH, kh), QR_NT, 0, st>>>(Xh, Vh, Th, ld, sv, m, zh, Wh, dh);
+      BS_CHECK_LAUNCH("wrow_kernel");
+      mark(h, 2, step, 1);
+      mark(h, 3, step, 0);
+      TRY_LAUNCH(bs_launch_band_rank2(Vh, Wh, ld, sv, dh, m, NB, kh, w.S, wAh, wBh, eAh, Ah, n,
+                                      j + NB, err, st));
+      mark(h, 3, step, 1);
+    }
   }
   static_assert(NB == CH_NB, "the bulge chase is written for a band half-width of 8");
   const bool in_smem = bulge_smem(n, true) <= (size_t)dyn_smem_limit((const void*)bulge_kernel);
   const size_t smem = bulge_smem(n, in_smem);
-  mark(4, 0, 0);
-  bulge_kernel<<<kb, CH_WARPS * 32, smem, s>>>(A, n, w.band, in_smem ? 1 : 0, de);
-  BS_CHECK_LAUNCH("bulge_kernel");
-  mark(4, 0, 1);
+  for (int h = 0; h < 2; ++h) {
+    if (hk[h] == 0) continue;
+    mark(h, 4, 0, 0);
+    bulge_kernel<<<hk[h], CH_WARPS * 32, smem, hs[h]>>>(
+        A + (size_t)off[h] * n * n, n, w.band + (size_t)off[h] * n * 2 * NB, in_smem ? 1 : 0,
+        de + (size_t)off[h] * 2 * n);
+    BS_CHECK_LAUNCH("bulge_kernel");
+    mark(h, 4, 0, 1);
+  }
+  if (k1 > 0) {
+    cudaError_t e = cudaEventRecord(w.join, w.s2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join, 0);
+    if (e != cudaSuccess) return bs_cuda_status(e, "band reduction join");
+  }
   return BS_OK;
 }
 

@@ -37,6 +37,14 @@ __host__ __device__ __forceinline__ zd zfmac(zd a, zd b, zd acc) {
   acc.y = fma(-a.x, b.y, acc.y);
   return acc;
 }
+// acc - a * b
+__host__ __device__ __forceinline__ zd zfnma(zd a, zd b, zd acc) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
 // acc - a * conj(b)
 __host__ __device__ __forceinline__ zd zfnmac(zd a, zd b, zd acc) {
   acc.x = fma(-a.x, b.x, acc.x);
@@ -316,6 +324,12 @@ struct BandWs {
   cudaEvent_t* ev = nullptr;
   int evcap = 0;            // event pairs per group
   int nsteps = 0;           // steps recorded by the last reduction
+  int timed = 0;            // matrices of the half whose launches the events bracket
+  // the batch runs as two halves on two streams: the second stream, its
+  // fork and join events, and the per-half sizes of the digit buffers
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  size_t hA = 0, hB = 0, hD = 0, hE = 0;
 };
 #define BS_BAND_AUTO_MIN 400   // BS_REDUCE_AUTO takes the two-stage reduction from this n on
 #define BS_BAND_GROUPS 5

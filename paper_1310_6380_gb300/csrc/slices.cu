@@ -156,6 +156,33 @@ __device__ __forceinline__ void put_digits_t(double x, int e, uint16_t* out, ptr
   }
 }
 
+// Row scale by integer arithmetic: for non-negative doubles the bit
+// patterns order as the values do, so the largest |x| is the largest of
+// (bits & ~sign) as 64-bit integers, and frexp's exponent of it is the
+// exponent field less 1022 (0 for a zero row, as row_exp gives).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+// block-wide: blockDim.x == 32 * nw, sh holds nw entries
+__device__ int row_exp_bits(unsigned long long v, unsigned long long* sh, int nw) {
+  v = warp_umax(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long m = 0;
+  for (int w = 0; w < nw; ++w) m = sh[w] > m ? sh[w] : m;
+  __syncthreads();
+  const int E = (int)(m >> 52);
+  return m == 0 ? 0 : E - 1022;
+}
+
 // ---- assembly operands
 // A rows (f, p): grid (P, nf), block 128
 __global__ void pack_fields_kernel(const uint16_t* __restrict__ phase,
@@ -436,15 +463,17 @@ namespace {
 __global__ void pack_trail_kernel(const zd* __restrict__ A, int n, int o, int m, int Kp,
                                   uint16_t* __restrict__ out, int* __restrict__ ex) {
   constexpr int S = 8;
-  __shared__ double sh[4];
+  __shared__ unsigned long long sh[4];
   const int r = blockIdx.x, k = blockIdx.y, t = threadIdx.x;
   const zd* col = A + (size_t)k * n * n + (size_t)(o + r) * n + o;
-  double mx = 0.0;
+  unsigned long long mx = 0;
   for (int c = t; c < m; c += 128) {
     const zd v = col[c];
-    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
+    mx = a > mx ? a : mx;
+    mx = b > mx ? b : mx;
   }
-  const int e = row_exp(row_max(mx, sh));
+  const int e = row_exp_bits(mx, sh, 4);
   uint16_t* base = out + ((size_t)k * m + r) * S * Kp;
   for (int c = t; c < m; c += 128) {
     const zd v = col[c];

@@ -233,10 +233,10 @@ __global__ void __launch_bounds__(128, 2)
 // 2^62: sum_u 2^(-12-7u) o_u = 2^-54 T up to 2^-54 of the operands' scale,
 // the size of the digit truncation itself.  One conversion and one FMA per
 // real entry (GB300 issues 2 FP64 operations per clock per SM).
-constexpr int R2_S = 8, R2_STAGES = 4;
+constexpr int R2_S = 8;
 
-template <int BN>
-__global__ void __launch_bounds__(128, 2)
+template <int BN, int R2_STAGES, int MINB>
+__global__ void __launch_bounds__(128, MINB)
     rank2_update_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, const int* __restrict__ ex,
                         int m, zd* __restrict__ A, int n, int o, int* __restrict__ err) {
@@ -585,7 +585,9 @@ int bs_launch_slice_orders(const uint16_t* A, const uint16_t* B, float* D, int M
 // planes of pack_rank2_kernel; ex: row exponents (kb x m)
 int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex, int m, int kb,
                            zd* A, int n, int o, int* err, cudaStream_t s) {
-  constexpr int BN = 32;
+  // 128 x 16 tiles (8 complex columns), two A stages: 49 KB of shared memory
+  // and 128 TMEM columns per CTA, three CTAs per SM
+  constexpr int BN = 16, R2_STAGES = 2, MINB = 3;
   if (((uintptr_t)dA & 15) || ((uintptr_t)dB & 15) || m < 1 || kb < 1 || kb > 65535) {
     bs_set_error("rank-2 update: bad operands (m = %d, batch = %d)", m, kb);
     return BS_EINVAL;
@@ -602,13 +604,13 @@ int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
   if (!attr[dev].load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(rank2_update_kernel<BN>,
+    cudaError_t e = cudaFuncSetAttribute(rank2_update_kernel<BN, R2_STAGES, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return bs_cuda_status(e, "rank-2 update smem");
     attr[dev].store(true, std::memory_order_release);
   }
   dim3 grid((m + BM - 1) / BM, (2 * m + BN - 1) / BN, kb);
-  rank2_update_kernel<BN><<<grid, 128, smem, s>>>(ta, tb, ex, m, A, n, o, err);
+  rank2_update_kernel<BN, R2_STAGES, MINB><<<grid, 128, smem, s>>>(ta, tb, ex, m, A, n, o, err);
   BS_CHECK_LAUNCH("rank2_update_kernel");
   return BS_OK;
 }
