@@ -33,7 +33,7 @@
 namespace {
 
 constexpr int QR_NT = 256;   // threads of the W kernels
-constexpr int PQ_NT = 512;   // threads of the panel QR (16 warps hide the FP64 latency)
+constexpr int PQ_NT = 256;   // threads of the panel QR (512 measured 9 % slower)
 constexpr int LAG = 3;       // blocks between consecutive sweeps
 
 __device__ __forceinline__ double warp_sum_d(double v) {

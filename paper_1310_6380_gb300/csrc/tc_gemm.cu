@@ -585,9 +585,11 @@ int bs_launch_slice_orders(const uint16_t* A, const uint16_t* B, float* D, int M
 // planes of pack_rank2_kernel; ex: row exponents (kb x m)
 int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex, int m, int kb,
                            zd* A, int n, int o, int* err, cudaStream_t s) {
-  // 128 x 16 tiles (8 complex columns), two A stages: 49 KB of shared memory
-  // and 128 TMEM columns per CTA, three CTAs per SM
-  constexpr int BN = 16, R2_STAGES = 2, MINB = 3;
+  // 128 x 32 tiles (16 complex columns), four A stages: 97 KB of shared
+  // memory and 256 TMEM columns per CTA, two CTAs per SM (16-wide tiles at
+  // three CTAs per SM measured 11 % slower: each A tile then serves half the
+  // columns)
+  constexpr int BN = 32, R2_STAGES = 4, MINB = 2;
   if (((uintptr_t)dA & 15) || ((uintptr_t)dB & 15) || m < 1 || kb < 1 || kb > 65535) {
     bs_set_error("rank-2 update: bad operands (m = %d, batch = %d)", m, kb);
     return BS_EINVAL;
