@@ -643,8 +643,8 @@ BAND_NB = 8
 def band_roofline(red, n, nk_all, ph, peaks):
     """Roofline of the dominant kernel group of the two-stage reduction (live
     event times per group, summed over the panel steps of one solve; the
-    reduction runs the batch as two halves on two streams and the events
-    bracket the first half's launches, so the work counted is that half's)
+    reduction runs the batch in parts on concurrent streams and the events
+    bracket the first part's launches, so the work counted is that part's)
     and the reduction's rate on the one-stage flop count (16/3) n^3 per k."""
     hbm_peak, _, note = measured_peaks()
     red = dict(red)
@@ -697,7 +697,7 @@ def band_roofline(red, n, nk_all, ph, peaks):
     reduction = {"method": "two-stage: dense -> band 8 (Householder panels, trailing updates as "
                            "8-digit exact-slice products on tcgen05), band -> tridiagonal "
                            "(bulge chase, FP64)",
-                 "groups_ms_per_step": red, "timed_half_matrices": nk,
+                 "groups_ms_per_step": red, "timed_part_matrices": nk,
                  "tridiag_phase_ms": ph["tridiag"],
                  "one_stage_equivalent_tflops": eff,
                  "one_stage_equivalent_frac_of_fp64_peak": eff / fp64_peak,

@@ -278,8 +278,8 @@ int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps);
  * product), [2] the W formation, [3] the trailing rank-2nb update (tensor
  * cores, FP64 epilogue), [4] the bulge chase to tridiagonal form; [5] the
  * number of matrices those launches processed.  The reduction runs the
- * batch as two halves on two streams; the times bracket the first half's
- * launches, which run beside the second half's.  All zeros when profiling
+ * batch in parts on concurrent streams; the times bracket the first part's
+ * launches, which run beside the others'.  All zeros when profiling
  * is off or the last solve took the one-stage reduction.  A measurement aid
  * (the paper has no counterpart).
  */

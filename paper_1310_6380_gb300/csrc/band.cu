@@ -560,22 +560,25 @@ static void band_events_free(BandWs* w) {
 void bs_band_ws_free(BandWs* w) {
   band_events_free(w);
   if (w->fork) cudaEventDestroy(w->fork);
-  if (w->join) cudaEventDestroy(w->join);
-  if (w->s2) cudaStreamDestroy(w->s2);
+  for (int h = 1; h < BS_BAND_PARTS; ++h) {
+    if (w->join[h]) cudaEventDestroy(w->join[h]);
+    if (w->sp[h]) cudaStreamDestroy(w->sp[h]);
+  }
   void* p[] = {w->V, w->X, w->W, w->T, w->wA, w->wB, w->wD, w->eA, w->eB, w->band, w->dsc,
                w->zpart};
   for (void* q : p) cudaFree(q);
   *w = BandWs();
 }
 
-// The batch runs as two halves on two streams (the caller's and one of the
-// workspace): the panel QR and W formation of one half are FP64-bound on
-// one CTA per matrix, and run beside the tensor-core and memory-bound
-// products of the other half.  The digit planes and sums have one region
-// per half.
-static void halves(int kb, int* k0, int* k1) {
-  *k0 = kb >= 2 ? kb / 2 : kb;
-  *k1 = kb - *k0;
+// The batch runs in BAND_PARTS parts on as many streams (the caller's and
+// the workspace's own): the panel QR and W formation of one part are
+// FP64-bound on one CTA per matrix, and run beside the tensor-core and
+// memory-bound products of the others.  The digit planes and sums have one
+// region per part.
+constexpr int BAND_PARTS = BS_BAND_PARTS;
+static void parts(int kb, int* k) {
+  const int np = kb < BAND_PARTS ? kb : BAND_PARTS;
+  for (int h = 0; h < BAND_PARTS; ++h) k[h] = h < np ? kb / np + (h < kb % np ? 1 : 0) : 0;
 }
 
 int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
@@ -583,10 +586,10 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
   bs_band_ws_free(w);
   const int NB = BS_BAND_NB;
   const int m = std::max(n - NB, 1);
-  int k0 = 0, k1 = 0;
-  halves(kb, &k0, &k1);
+  int kp[BAND_PARTS];
+  parts(kb, kp);
   size_t nA = 0, nB = 0, nD = 0, nE = 0;
-  bs_band_tc_elems(n, NB, std::max(k0, k1), S, &nA, &nB, &nD, &nE);
+  bs_band_tc_elems(n, NB, kp[0], S, &nA, &nB, &nD, &nE);   // part 0 is the largest
   w->hA = nA;
   w->hB = nB;
   w->hD = nD;
@@ -597,11 +600,11 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
       {(void**)&w->X, pv * sizeof(zd), "band A22 V"},
       {(void**)&w->W, pv * sizeof(zd), "band W"},
       {(void**)&w->T, (size_t)kb * NB * NB * sizeof(zd), "band T"},
-      {(void**)&w->wA, 2 * nA * sizeof(uint16_t), "band digit planes A"},
-      {(void**)&w->wB, 2 * nB * sizeof(uint16_t), "band digit planes B"},
-      {(void**)&w->wD, 2 * nD * sizeof(float), "band digit-order sums"},
-      {(void**)&w->eA, 2 * nE * sizeof(int), "band exponents A"},
-      {(void**)&w->eB, 2 * nE * sizeof(int), "band exponents B"},
+      {(void**)&w->wA, BAND_PARTS * nA * sizeof(uint16_t), "band digit planes A"},
+      {(void**)&w->wB, BAND_PARTS * nB * sizeof(uint16_t), "band digit planes B"},
+      {(void**)&w->wD, BAND_PARTS * nD * sizeof(float), "band digit-order sums"},
+      {(void**)&w->eA, BAND_PARTS * nE * sizeof(int), "band exponents A"},
+      {(void**)&w->eB, BAND_PARTS * nE * sizeof(int), "band exponents B"},
       {(void**)&w->band, (size_t)kb * n * 2 * NB * sizeof(zd), "band storage"},
       {(void**)&w->dsc, (size_t)kb * 2 * NB * sizeof(int), "band column exponents"},
       {(void**)&w->zpart, (size_t)kb * WCH * NB * NB * sizeof(zd), "band Z0 partials"},
@@ -615,9 +618,11 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
       return BS_ENOMEM;
     }
   }
-  cudaError_t e = cudaStreamCreateWithFlags(&w->s2, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->join, cudaEventDisableTiming);
+  cudaError_t e = cudaEventCreateWithFlags(&w->fork, cudaEventDisableTiming);
+  for (int h = 1; e == cudaSuccess && h < BAND_PARTS; ++h) {
+    e = cudaStreamCreateWithFlags(&w->sp[h], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->join[h], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     bs_band_ws_free(w);
     return bs_cuda_status(e, "band reduction stream");
@@ -673,15 +678,19 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
     }
     w.evcap = cap;
   }
-  int k0 = 0, k1 = 0;
-  halves(kb, &k0, &k1);
+  int hk[BAND_PARTS], off[BAND_PARTS];
+  cudaStream_t hs[BAND_PARTS];
+  parts(kb, hk);
+  for (int h = 0; h < BAND_PARTS; ++h) {
+    off[h] = h == 0 ? 0 : off[h - 1] + hk[h - 1];
+    hs[h] = h == 0 ? s : w.sp[h];
+  }
   w.nsteps = steps;
-  w.timed = k0;
-  cudaStream_t hs[2] = {s, w.s2};
-  const int hk[2] = {k0, k1}, off[2] = {0, k0};
-  if (k1 > 0) {
+  w.timed = hk[0];
+  if (hk[1] > 0) {
     cudaError_t e = cudaEventRecord(w.fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(w.s2, w.fork, 0);
+    for (int h = 1; e == cudaSuccess && h < BAND_PARTS; ++h)
+      if (hk[h] > 0) e = cudaStreamWaitEvent(hs[h], w.fork, 0);
     if (e != cudaSuccess) return bs_cuda_status(e, "band reduction fork");
   }
   auto mark = [&](int h, int grp, int step, int end) {
@@ -691,7 +700,7 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
   for (int j = 0; n - j - NB > 1; j += NB, ++step) {
     const int m = n - j - NB;
     const size_t smem = (size_t)NB * m * sizeof(zd);
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < BAND_PARTS; ++h) {
       const int kh = hk[h];
       if (kh == 0) continue;
       const cudaStream_t st = hs[h];
@@ -730,7 +739,7 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
   static_assert(NB == CH_NB, "the bulge chase is written for a band half-width of 8");
   const bool in_smem = bulge_smem(n, true) <= (size_t)dyn_smem_limit((const void*)bulge_kernel);
   const size_t smem = bulge_smem(n, in_smem);
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < BAND_PARTS; ++h) {
     if (hk[h] == 0) continue;
     mark(h, 4, 0, 0);
     bulge_kernel<<<hk[h], CH_WARPS * 32, smem, hs[h]>>>(
@@ -739,9 +748,10 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
     BS_CHECK_LAUNCH("bulge_kernel");
     mark(h, 4, 0, 1);
   }
-  if (k1 > 0) {
-    cudaError_t e = cudaEventRecord(w.join, w.s2);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join, 0);
+  for (int h = 1; h < BAND_PARTS; ++h) {
+    if (hk[h] == 0) continue;
+    cudaError_t e = cudaEventRecord(w.join[h], hs[h]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join[h], 0);
     if (e != cudaSuccess) return bs_cuda_status(e, "band reduction join");
   }
   return BS_OK;

@@ -303,6 +303,7 @@ int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long
 // ---- two-stage reduction to tridiagonal form (band.cu)
 #define BS_BAND_NB 8        // half-width of the intermediate band
 #define BS_SLICES_BAND 8    // digit planes per operand in its contractions (~2^-53)
+#define BS_BAND_PARTS 4     // parts of the batch on concurrent streams (2: 178, 3: 172, 4: 170 ms on config 1)
 struct BandWs {
   int n = 0, kb = 0, S = 0;
   zd* V = nullptr;          // kb x (n - nb) x nb reflectors of the current panel
@@ -325,10 +326,11 @@ struct BandWs {
   int evcap = 0;            // event pairs per group
   int nsteps = 0;           // steps recorded by the last reduction
   int timed = 0;            // matrices of the half whose launches the events bracket
-  // the batch runs as two halves on two streams: the second stream, its
-  // fork and join events, and the per-half sizes of the digit buffers
-  cudaStream_t s2 = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  // the batch runs in BS_BAND_PARTS parts on as many streams: the extra
+  // streams, the fork and join events, and the per-part sizes of the digit
+  // buffers
+  cudaStream_t sp[BS_BAND_PARTS] = {};
+  cudaEvent_t fork = nullptr, join[BS_BAND_PARTS] = {};
   size_t hA = 0, hB = 0, hD = 0, hE = 0;
 };
 #define BS_BAND_AUTO_MIN 400   // BS_REDUCE_AUTO takes the two-stage reduction from this n on
