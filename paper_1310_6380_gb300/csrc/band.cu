@@ -661,7 +661,7 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
       attr[dev].store(true, std::memory_order_release);
     }
   }
-  // timing: event pairs per kernel group and step, on the first half's stream
+  // timing: event pairs per kernel group and step, on the first part's stream
   const int steps = n - NB > 1 ? (n - NB - 2) / NB + 1 : 0;
   if (w.prof && w.evcap < steps + 1) {
     band_events_free(&w);
