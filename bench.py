@@ -699,6 +699,8 @@ def band_roofline(red, n, nk_all, ph, peaks):
                            "(bulge chase, FP64)",
                  "groups_ms_per_step": red, "timed_part_matrices": nk,
                  "tridiag_phase_ms": ph["tridiag"],
+                 "tridiag_phase_includes": "the bisection (each part's runs right behind its "
+                                           "bulge chase, beside the other parts')",
                  "one_stage_equivalent_tflops": eff,
                  "one_stage_equivalent_frac_of_fp64_peak": eff / fp64_peak,
                  "note": "(16/3) n^3 per k is the one-stage reduction's flop count; a value "

@@ -758,13 +758,18 @@ static int solve_chunk(bs_cell* c, int kb, int nbands, cudaStream_t s) {
     if (!c->band) c->band = new BandWs();
     TRY(bs_band_ws_alloc(c->band, c->n, c->kcap, BS_SLICES_BAND));
     c->band->prof = c->prof;
-    TRY(bs_launch_eig_band(c->d_C, c->n, kb, *c->band, c->d_de, c->d_info + 1, s));
+    // the bisection of each part runs inside the reduction, behind its
+    // bulge chase (the bisect phase is then part of the tridiag phase)
+    BandBisect bis{nbands, c->d_w, c->d_stat};
+    TRY(bs_launch_eig_band(c->d_C, c->n, kb, *c->band, c->d_de, c->d_info + 1, s, &bis));
     c->band_used = true;
-  } else {
-    TRY(bs_launch_tridiag<double>(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
-                                  c->d_beta, c->d_count, s));
-    c->band_used = false;
+    bs_phase_end(c, PH_TRID, s);
+    c->prof_ready[PH_BISECT] = false;
+    return BS_OK;
   }
+  TRY(bs_launch_tridiag<double>(c->d_C, c->n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
+                                c->d_beta, c->d_count, s));
+  c->band_used = false;
   bs_phase_end(c, PH_TRID, s);
   bs_phase_begin(c, PH_BISECT, s);
   TRY(bs_launch_bisect(c->d_de, c->n, kb, nbands, c->d_w, c->d_stat, s));

@@ -633,7 +633,8 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
   return BS_OK;
 }
 
-int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cudaStream_t s) {
+int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cudaStream_t s,
+                       const BandBisect* bis) {
   constexpr int NB = BS_BAND_NB;
   if (w.n != n || w.kb < kb || !bs_band_supported(n)) {
     bs_set_error("band reduction: workspace for n = %d, %d matrices not set up", n, kb);
@@ -747,6 +748,12 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
         de + (size_t)off[h] * 2 * n);
     BS_CHECK_LAUNCH("bulge_kernel");
     mark(h, 4, 0, 1);
+    // the part's eigenvalues right behind its bulge chase, beside the
+    // other parts' chases
+    if (bis)
+      TRY_LAUNCH(bs_launch_bisect(de + (size_t)off[h] * 2 * n, n, hk[h], bis->nbands,
+                                  bis->omega + (size_t)off[h] * bis->nbands,
+                                  bis->stat ? bis->stat + off[h] : nullptr, hs[h]));
   }
   for (int h = 1; h < BAND_PARTS; ++h) {
     if (hk[h] == 0) continue;

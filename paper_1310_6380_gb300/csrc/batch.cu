@@ -514,13 +514,16 @@ static int reduce_chunk_body(bs_batch* B, BatchGroup& g, int c0, int cn, int p, 
   prof_mark(B, s);   // assembly ends, reduction begins
   if (B->solver == BS_SOLVER_FP64) {
     // the plain FP64 dense path: Householder reduction and Sturm multisection
-    if (g.band)
-      TRY_LAUNCH(bs_launch_eig_band(g.C64, n, K, *g.band, g.de, g.d_err, s));
-    else
+    if (g.band) {
+      BandBisect bis{B->nbands, g.w, g.st};
+      TRY_LAUNCH(bs_launch_eig_band(g.C64, n, K, *g.band, g.de, g.d_err, s, &bis));
+      prof_mark(B, s);
+    } else {
       TRY_LAUNCH(bs_launch_tridiag<double>(g.C64, n, K, g.vec64, g.part64, g.de, g.tau, g.beta,
                                            g.count, s));
-    prof_mark(B, s);
-    TRY_LAUNCH(bs_launch_bisect(g.de, n, K, B->nbands, g.w, g.st, s));
+      prof_mark(B, s);
+      TRY_LAUNCH(bs_launch_bisect(g.de, n, K, B->nbands, g.w, g.st, s));
+    }
     prof_mark(B, s);
     prof_mark(B, s);
   } else if (B->solver == BS_SOLVER_LOBPCG) {

@@ -340,7 +340,15 @@ bool bs_band_supported(int n);
 bool bs_use_band(int n);
 int bs_band_ws_alloc(BandWs* w, int n, int kb, int S);
 void bs_band_ws_free(BandWs* w);
-int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cudaStream_t s);
+// optional: the Sturm multisection of each part, run on the part's stream
+// right after its bulge chase (omega: kb x nbands, stat: kb)
+struct BandBisect {
+  int nbands;
+  double* omega;
+  int* stat;
+};
+int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cudaStream_t s,
+                       const BandBisect* bis = nullptr);
 void bs_band_tc_elems(int n, int nb, int kb, int S, size_t* nA, size_t* nB, size_t* nD,
                       size_t* nE);
 int bs_launch_band_av(const zd* A, int n, int o, int m, const zd* V, int ldv, long sv, int nb,

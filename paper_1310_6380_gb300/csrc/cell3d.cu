@@ -617,12 +617,13 @@ extern "C" int bs_solve_k3(bs_cell3* c, const double* Q, int nk, int nbands, dou
     if (bs_use_band(n)) {
       if (!c->band) c->band = new BandWs();
       r = bs_band_ws_alloc(c->band, n, c->kcap, BS_SLICES_BAND);
-      if (!r) r = bs_launch_eig_band(c->d_C, n, kb, *c->band, c->d_de, c->d_info + 1, s);
+      BandBisect bis{nbands, c->d_w, c->d_stat};
+      if (!r) r = bs_launch_eig_band(c->d_C, n, kb, *c->band, c->d_de, c->d_info + 1, s, &bis);
     } else {
       r = bs_launch_tridiag<double>(c->d_C, n, kb, c->d_vec, c->d_part, c->d_de, c->d_tau,
                                     c->d_beta, c->d_count, s);
+      if (!r) r = bs_launch_bisect(c->d_de, n, kb, nbands, c->d_w, c->d_stat, s);
     }
-    if (!r) r = bs_launch_bisect(c->d_de, n, kb, nbands, c->d_w, c->d_stat, s);
     if (r) break;
     e = cudaMemcpyAsync(omega_out + (size_t)k0 * nbands, c->d_w, (size_t)kb * nbands * 8,
                         w_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
