@@ -560,9 +560,13 @@ static void band_events_free(BandWs* w) {
 void bs_band_ws_free(BandWs* w) {
   band_events_free(w);
   if (w->fork) cudaEventDestroy(w->fork);
-  for (int h = 1; h < BS_BAND_PARTS; ++h) {
+  for (int h = 0; h < BS_BAND_PARTS; ++h) {
     if (w->join[h]) cudaEventDestroy(w->join[h]);
     if (w->sp[h]) cudaStreamDestroy(w->sp[h]);
+    if (w->sb[h]) cudaStreamDestroy(w->sb[h]);
+    if (w->epr[h]) cudaEventDestroy(w->epr[h]);
+    if (w->epan[h]) cudaEventDestroy(w->epan[h]);
+    if (w->ept[h]) cudaEventDestroy(w->ept[h]);
   }
   void* p[] = {w->V, w->X, w->W, w->T, w->wA, w->wB, w->wD, w->eA, w->eB, w->band, w->dsc,
                w->zpart};
@@ -622,6 +626,12 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
   for (int h = 1; e == cudaSuccess && h < BAND_PARTS; ++h) {
     e = cudaStreamCreateWithFlags(&w->sp[h], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->join[h], cudaEventDisableTiming);
+  }
+  for (int h = 0; e == cudaSuccess && h < BAND_PARTS; ++h) {
+    e = cudaStreamCreateWithFlags(&w->sb[h], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->epr[h], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->epan[h], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->ept[h], cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {
     bs_band_ws_free(w);
@@ -694,17 +704,26 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
       if (hk[h] > 0) e = cudaStreamWaitEvent(hs[h], w.fork, 0);
     if (e != cudaSuccess) return bs_cuda_status(e, "band reduction fork");
   }
-  auto mark = [&](int h, int grp, int step, int end) {
-    if (w.prof && h == 0) cudaEventRecord(w.ev[(grp * w.evcap + step) * 2 + end], s);
+  auto mark = [&](int h, int grp, int step, int end, cudaStream_t st) {
+    if (w.prof && h == 0) cudaEventRecord(w.ev[(grp * w.evcap + step) * 2 + end], st);
   };
+  // Per part, with look-ahead: after step j's operands of the rank-2
+  // update are packed, the update of the next panel's columns (the first
+  // column tile) runs first and the next panel's QR follows at once on the
+  // part's stream A, while the rest of the update and the next step's digit
+  // planes of A22 run on its stream B.  Events: epr (rank-2 operands
+  // packed), epan (next panel's columns updated), ept (next digit planes
+  // packed).  The panel QR reads and writes only the panel's columns, which
+  // stream B does not touch; B's pack of the next trailing block waits for
+  // the panel tile's writes (its mirror entries lie in that block).
   int step = 0;
   for (int j = 0; n - j - NB > 1; j += NB, ++step) {
     const int m = n - j - NB;
-    const size_t smem = (size_t)NB * m * sizeof(zd);
+    const bool next = n - (j + NB) - NB > 1;
     for (int h = 0; h < BAND_PARTS; ++h) {
       const int kh = hk[h];
       if (kh == 0) continue;
-      const cudaStream_t st = hs[h];
+      const cudaStream_t st = hs[h], sb = w.sb[h];
       zd* Ah = A + (size_t)off[h] * n * n;
       zd* Vh = w.V + (size_t)off[h] * sv;
       zd* Xh = w.X + (size_t)off[h] * sv;
@@ -717,24 +736,57 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
       float* wDh = w.wD + h * w.hD;
       int* eAh = w.eA + h * w.hE;
       int* eBh = w.eB + h * w.hE;
-      mark(h, 0, step, 0);
-      panel_qr_kernel<NB><<<kh, PQ_NT, smem, st>>>(Ah, n, j, Vh, ld, sv, Th);
-      BS_CHECK_LAUNCH("panel_qr_kernel");
-      mark(h, 0, step, 1);
-      mark(h, 1, step, 0);
-      TRY_LAUNCH(bs_launch_band_av(Ah, n, j + NB, m, Vh, ld, sv, NB, kh, w.S, wAh, wBh, wDh, eAh,
-                                   eBh, Xh, ld, sv, err, st));
-      mark(h, 1, step, 1);
-      mark(h, 2, step, 0);
+      if (step == 0) {
+        mark(h, 0, step, 0, st);
+        panel_qr_kernel<NB><<<kh, PQ_NT, (size_t)NB * m * sizeof(zd), st>>>(Ah, n, j, Vh, ld, sv,
+                                                                            Th);
+        BS_CHECK_LAUNCH("panel_qr_kernel");
+        mark(h, 0, step, 1, st);
+        mark(h, 1, step, 0, st);
+        TRY_LAUNCH(bs_launch_band_pack_trail(Ah, n, j + NB, m, kh, wAh, eAh, st));
+      } else {
+        cudaError_t e = cudaStreamWaitEvent(st, w.ept[h], 0);
+        if (e != cudaSuccess) return bs_cuda_status(e, "band reduction wait");
+        mark(h, 1, step, 0, st);
+      }
+      TRY_LAUNCH(bs_launch_band_av(m, Vh, ld, sv, NB, kh, w.S, wAh, wBh, wDh, eAh, eBh, Xh, ld, sv,
+                                   err, st));
+      mark(h, 1, step, 1, st);
+      mark(h, 2, step, 0, st);
       wz_kernel<NB><<<dim3(WCH, kh), QR_NT, 0, st>>>(Xh, Vh, ld, sv, m, zh, dh);
       BS_CHECK_LAUNCH("wz_kernel");
       wrow_kernel<NB><<<dim3(WCH, kh), QR_NT, 0, st>>>(Xh, Vh, Th, ld, sv, m, zh, Wh, dh);
       BS_CHECK_LAUNCH("wrow_kernel");
-      mark(h, 2, step, 1);
-      mark(h, 3, step, 0);
-      TRY_LAUNCH(bs_launch_band_rank2(Vh, Wh, ld, sv, dh, m, NB, kh, w.S, wAh, wBh, eAh, Ah, n,
-                                      j + NB, err, st));
-      mark(h, 3, step, 1);
+      mark(h, 2, step, 1, st);
+      TRY_LAUNCH(bs_launch_band_pack_rank2(Vh, Wh, ld, sv, dh, m, NB, kh, w.S, wAh, wBh, eAh, st));
+      if (!next) {
+        mark(h, 3, step, 0, st);
+        TRY_LAUNCH(bs_launch_rank2_update(wAh, wBh, eAh, m, kh, Ah, n, j + NB, 0, 0, err, st));
+        mark(h, 3, step, 1, st);
+        continue;
+      }
+      cudaError_t e = cudaEventRecord(w.epr[h], st);
+      // the next panel's columns (first column tile), then its QR
+      TRY_LAUNCH(bs_launch_rank2_update(wAh, wBh, eAh, m, kh, Ah, n, j + NB, 0, 1, err, st));
+      if (e == cudaSuccess) e = cudaEventRecord(w.epan[h], st);
+      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction events");
+      const int m2 = m - NB;
+      mark(h, 0, step + 1, 0, st);
+      panel_qr_kernel<NB><<<kh, PQ_NT, (size_t)NB * m2 * sizeof(zd), st>>>(Ah, n, j + NB, Vh,
+                                                                           ld, sv, Th);
+      BS_CHECK_LAUNCH("panel_qr_kernel");
+      mark(h, 0, step + 1, 1, st);
+      // stream B: the rest of the update, then the next trailing block's digits
+      e = cudaStreamWaitEvent(sb, w.epr[h], 0);
+      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction wait");
+      mark(h, 3, step, 0, sb);
+      TRY_LAUNCH(bs_launch_rank2_update(wAh, wBh, eAh, m, kh, Ah, n, j + NB, 1, 0, err, sb));
+      e = cudaStreamWaitEvent(sb, w.epan[h], 0);
+      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction wait");
+      TRY_LAUNCH(bs_launch_band_pack_trail(Ah, n, j + 2 * NB, m2, kh, wAh, eAh, sb));
+      mark(h, 3, step, 1, sb);
+      e = cudaEventRecord(w.ept[h], sb);
+      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction events");
     }
   }
   static_assert(NB == CH_NB, "the bulge chase is written for a band half-width of 8");
@@ -742,12 +794,12 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
   const size_t smem = bulge_smem(n, in_smem);
   for (int h = 0; h < BAND_PARTS; ++h) {
     if (hk[h] == 0) continue;
-    mark(h, 4, 0, 0);
+    mark(h, 4, 0, 0, hs[h]);
     bulge_kernel<<<hk[h], CH_WARPS * 32, smem, hs[h]>>>(
         A + (size_t)off[h] * n * n, n, w.band + (size_t)off[h] * n * 2 * NB, in_smem ? 1 : 0,
         de + (size_t)off[h] * 2 * n);
     BS_CHECK_LAUNCH("bulge_kernel");
-    mark(h, 4, 0, 1);
+    mark(h, 4, 0, 1, hs[h]);
     // the part's eigenvalues right behind its bulge chase, beside the
     // other parts' chases
     if (bis)

@@ -331,6 +331,10 @@ struct BandWs {
   // buffers
   cudaStream_t sp[BS_BAND_PARTS] = {};
   cudaEvent_t fork = nullptr, join[BS_BAND_PARTS] = {};
+  // look-ahead: per part a second stream for the bulk of the trailing update
+  // and the next step's digit planes, and the events that order the two
+  cudaStream_t sb[BS_BAND_PARTS] = {};
+  cudaEvent_t epr[BS_BAND_PARTS] = {}, epan[BS_BAND_PARTS] = {}, ept[BS_BAND_PARTS] = {};
   size_t hA = 0, hB = 0, hD = 0, hE = 0;
 };
 #define BS_BAND_AUTO_MIN 400   // BS_REDUCE_AUTO takes the two-stage reduction from this n on
@@ -351,14 +355,18 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
                        const BandBisect* bis = nullptr);
 void bs_band_tc_elems(int n, int nb, int kb, int S, size_t* nA, size_t* nB, size_t* nD,
                       size_t* nE);
-int bs_launch_band_av(const zd* A, int n, int o, int m, const zd* V, int ldv, long sv, int nb,
-                      int kb, int S, uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB,
-                      zd* X, int ldx, long sx, int* err, cudaStream_t s);
+int bs_launch_band_pack_trail(const zd* A, int n, int o, int m, int kb, uint16_t* wA, int* eA,
+                              cudaStream_t s);
+int bs_launch_band_av(int m, const zd* V, int ldv, long sv, int nb, int kb, int S, uint16_t* wA,
+                      uint16_t* wB, float* wD, int* eA, int* eB, zd* X, int ldx, long sx,
+                      int* err, cudaStream_t s);
+int bs_launch_band_pack_rank2(const zd* V, const zd* W, int ld, long sv, const int* dsc, int m,
+                              int nb, int kb, int S, uint16_t* wA, uint16_t* wB, int* ex,
+                              cudaStream_t s);
+int bs_rank2_column_tiles(int m);
 int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex, int m, int kb,
-                           zd* A, int n, int o, int* err, cudaStream_t s);
-int bs_launch_band_rank2(const zd* V, const zd* W, int ld, long sv, const int* dsc, int m, int nb,
-                         int kb, int S, uint16_t* wA, uint16_t* wB, int* ex, zd* A, int n, int o,
-                         int* err, cudaStream_t s);
+                           zd* A, int n, int o, int ct0, int nct, int* err, cudaStream_t s);
+
 
 int bs_launch_builder(const zd* Cm, int n, const double* Q, int nk, double q1x, double q1y,
                       double q2x, double q2y, zd* C, cudaStream_t s);

@@ -129,10 +129,17 @@ __device__ __forceinline__ void put_digits(double x, int e, int S, uint16_t* out
   }
 }
 
-// put_digits with the digit count fixed at compile time (the shifts become
-// immediates); the same digits as put_digits(x, e, S, ...)
+// The eight-digit split of the band reduction, in 32-bit integer arithmetic:
+// X = round(x 2^(55-e)) (as in put_digits, |X| <= 2^55) is cut into
+// X = Xh 2^28 + Xl with 0 <= Xl < 2^28; the four low digits are balanced
+// radix-128 digits of Xl from the bottom, d = ((v + 64) mod 128) - 64 in
+// [-64, 63], whose final carry (0 or 1) joins Xh, and three more come from
+// Xh the same way; the top digit is what remains (|t_0| <= 64).  The digits
+// represent X exactly, so every digit product stays an integer of at most
+// 2^12, as for put_digits.
 template <int S>
 __device__ __forceinline__ void put_digits_t(double x, int e, uint16_t* out, ptrdiff_t plane) {
+  static_assert(S == 8, "the 32-bit split is written for eight digits");
   constexpr int B = 6 + 7 * (S - 1);
   const long long bits = __double_as_longlong(x);
   const int E = (int)((bits >> 52) & 0x7FF);
@@ -144,16 +151,22 @@ __device__ __forceinline__ void put_digits_t(double x, int e, uint16_t* out, ptr
     else if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
     if (bits < 0) X = -X;
   }
-  long long r = X;
+  int u = (int)(X >> 28);
+  int v = (int)(X & 0xFFFFFFF);
 #pragma unroll
-  for (int sd = 0; sd < S; ++sd) {
-    const int sh = B - 6 - 7 * sd;
-    long long t;
-    if (sh > 0) t = (r + (1LL << (sh - 1))) >> sh;
-    else t = r;
-    r -= t << (sh > 0 ? sh : 0);
-    out[(ptrdiff_t)sd * plane] = bf16_bits(t);
+  for (int sd = S - 1; sd >= 4; --sd) {
+    const int d = ((v + 64) & 127) - 64;
+    v = (v - d) >> 7;
+    out[(ptrdiff_t)sd * plane] = bf16_bits(d);
   }
+  u += v;
+#pragma unroll
+  for (int sd = 3; sd >= 1; --sd) {
+    const int d = ((u + 64) & 127) - 64;
+    u = (u - d) >> 7;
+    out[(ptrdiff_t)sd * plane] = bf16_bits(d);
+  }
+  out[0] = bf16_bits(u);
 }
 
 // Row scale by integer arithmetic: for non-negative doubles the bit
@@ -611,17 +624,25 @@ void bs_band_tc_elems(int n, int nb, int kb, int S, size_t* nA, size_t* nB, size
   *nE = (size_t)kb * (m + 2 * nb);
 }
 
-int bs_launch_band_av(const zd* A, int n, int o, int m, const zd* V, int ldv, long sv, int nb,
-                      int kb, int S, uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB,
-                      zd* X, int ldx, long sx, int* err, cudaStream_t s) {
+// the digit planes of the trailing block (rows and columns from o on)
+int bs_launch_band_pack_trail(const zd* A, int n, int o, int m, int kb, uint16_t* wA, int* eA,
+                              cudaStream_t s) {
+  const int Kp = (2 * m + 63) / 64 * 64;
+  pack_trail_kernel<<<dim3(m, kb), 128, 0, s>>>(A, n, o, m, Kp, wA, eA);
+  BS_CHECK_LAUNCH("pack_trail_kernel");
+  return BS_OK;
+}
+
+// X = A22 V from the trailing block's digit planes (bs_launch_band_pack_trail)
+int bs_launch_band_av(int m, const zd* V, int ldv, long sv, int nb, int kb, int S, uint16_t* wA,
+                      uint16_t* wB, float* wD, int* eA, int* eB, zd* X, int ldx, long sx,
+                      int* err, cudaStream_t s) {
   const int Kp = (2 * m + 63) / 64 * 64;
   SliceSlabs sl;
   if (S != 8 || !bs_slice_slabs(S, Kp, m, 2 * nb, kb, &sl)) {
     bs_set_error("band reduction: m = %d gives too many digit slabs", m);
     return BS_EINVAL;
   }
-  pack_trail_kernel<<<dim3(m, kb), 128, 0, s>>>(A, n, o, m, Kp, wA, eA);
-  BS_CHECK_LAUNCH("pack_trail_kernel");
   pack_panel_kernel<<<dim3(nb, kb), 128, 0, s>>>(V, ldv, sv, m, nb, S, Kp, wB, eB);
   BS_CHECK_LAUNCH("pack_panel_kernel");
   TRY_LAUNCH(bs_launch_slice_orders(wA, wB, wD, m, 2 * nb, S, Kp, kb, err, s));
@@ -631,14 +652,15 @@ int bs_launch_band_av(const zd* A, int n, int o, int m, const zd* V, int ldv, lo
   return BS_OK;
 }
 
-int bs_launch_band_rank2(const zd* V, const zd* W, int ld, long sv, const int* dsc, int m, int nb,
-                         int kb, int S, uint16_t* wA, uint16_t* wB, int* ex, zd* A, int n, int o,
-                         int* err, cudaStream_t s) {
+// the digit planes of the rank-2nb update's operands [V D, W D^-1], [W D^-1, V D]
+int bs_launch_band_pack_rank2(const zd* V, const zd* W, int ld, long sv, const int* dsc, int m,
+                              int nb, int kb, int S, uint16_t* wA, uint16_t* wB, int* ex,
+                              cudaStream_t s) {
   if (S != 8 || 4 * nb > 64) {
     bs_set_error("band reduction: needs 8 digits and band width <= 16 (nb = %d)", nb);
     return BS_EINVAL;
   }
   pack_rank2_kernel<<<dim3(m, kb), 64, 0, s>>>(V, W, ld, sv, dsc, m, nb, S, wA, wB, ex);
   BS_CHECK_LAUNCH("pack_rank2_kernel");
-  return bs_launch_rank2_update(wA, wB, ex, m, kb, A, n, o, err, s);
+  return BS_OK;
 }

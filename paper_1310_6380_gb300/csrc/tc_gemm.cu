@@ -239,7 +239,8 @@ template <int BN, int R2_STAGES, int MINB>
 __global__ void __launch_bounds__(128, MINB)
     rank2_update_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, const int* __restrict__ ex,
-                        int m, zd* __restrict__ A, int n, int o, int* __restrict__ err) {
+                        int m, zd* __restrict__ A, int n, int o, int ct0,
+                        int* __restrict__ err) {
   constexpr int TILE_B = tile_b(BN);
   constexpr uint32_t IDESC = idesc(BN);
   constexpr int TCOLS = R2_S * BN;   // 256 or 512
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(128, MINB)
   __shared__ __align__(8) uint64_t full[R2_STAGES], empty[R2_STAGES], bfull, done;
   __shared__ uint32_t tmem_base;
   const int z = blockIdx.z;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, cc0 = n0 / 2;
+  const int m0 = blockIdx.x * BM, n0 = (blockIdx.y + ct0) * BN, cc0 = n0 / 2;
   if (cc0 > m0 + BM - 1) return;     // above the diagonal: the mirror tile writes it
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -342,35 +343,37 @@ __global__ void __launch_bounds__(128, MINB)
   // (BM x CW complex, row stride CW + 1) for the transposed stores
   zd* stage = reinterpret_cast<zd*>(sA);
   if (ok) {
+    // eight columns (four complex) at a time: the eight digit orders' loads
+    // are issued together and waited for once
 #pragma unroll
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      long long hi[16], lo[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+    for (int c0 = 0; c0 < BN; c0 += 8) {
+      uint32_t v[R2_S][8];
 #pragma unroll
       for (int u = 0; u < R2_S; ++u) {
-        uint32_t v[16];
         const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(u * BN + c0);
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-            "%10, %11, %12, %13, %14, %15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(v[u][0]), "=r"(v[u][1]), "=r"(v[u][2]), "=r"(v[u][3]), "=r"(v[u][4]),
+              "=r"(v[u][5]), "=r"(v[u][6]), "=r"(v[u][7])
             : "r"(ta));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      long long hi[8], lo[8];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+      for (int jj = 0; jj < 8; ++jj) {
+        hi[jj] = lo[jj] = 0;
+#pragma unroll
+        for (int u = 0; u < R2_S; ++u) {
           // the order sums are exact integers below 2^22: the FP32 add of
           // 1.5 2^23 puts them in the low mantissa bits
           const long long d =
-              (long long)(__float_as_int(__uint_as_float(v[j]) + 12582912.0f) - 0x4B400000);
-          if (u < 4) hi[j] = hi[j] * 128 + d;
-          else lo[j] = lo[j] * 128 + d;
+              (long long)(__float_as_int(__uint_as_float(v[u][jj]) + 12582912.0f) - 0x4B400000);
+          if (u < 4) hi[jj] = hi[jj] * 128 + d;
+          else lo[jj] = lo[jj] * 128 + d;
         }
       }
 #pragma unroll
-      for (int jc = 0; jc < 8; ++jc) {
+      for (int jc = 0; jc < 4; ++jc) {
         const int cl = c0 / 2 + jc, c = cc0 + cl;
         zd val = zmake(0.0, 0.0);
         if (live && c < m && c <= r) {
@@ -583,8 +586,11 @@ int bs_launch_slice_orders(const uint16_t* A, const uint16_t* B, float* D, int M
 
 // A22 (m x m at offset o of each n x n matrix) -= X Y^dagger from the digit
 // planes of pack_rank2_kernel; ex: row exponents (kb x m)
+int bs_rank2_column_tiles(int m) { return (2 * m + 31) / 32; }
+
+// column tiles ct0 .. ct0 + nct - 1 (16 complex columns each; nct <= 0: to the end)
 int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex, int m, int kb,
-                           zd* A, int n, int o, int* err, cudaStream_t s) {
+                           zd* A, int n, int o, int ct0, int nct, int* err, cudaStream_t s) {
   // 128 x 32 tiles (16 complex columns), four A stages: 97 KB of shared
   // memory and 256 TMEM columns per CTA, two CTAs per SM (16-wide tiles at
   // three CTAs per SM measured 11 % slower: each A tile then serves half the
@@ -611,8 +617,13 @@ int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex
     if (e != cudaSuccess) return bs_cuda_status(e, "rank-2 update smem");
     attr[dev].store(true, std::memory_order_release);
   }
-  dim3 grid((m + BM - 1) / BM, (2 * m + BN - 1) / BN, kb);
-  rank2_update_kernel<BN, R2_STAGES, MINB><<<grid, 128, smem, s>>>(ta, tb, ex, m, A, n, o, err);
+  static_assert(BN == 32, "bs_rank2_column_tiles assumes 32 real columns per tile");
+  const int tiles = (2 * m + BN - 1) / BN;
+  if (nct <= 0 || ct0 + nct > tiles) nct = tiles - ct0;
+  if (nct <= 0) return BS_OK;
+  dim3 grid((m + BM - 1) / BM, nct, kb);
+  rank2_update_kernel<BN, R2_STAGES, MINB><<<grid, 128, smem, s>>>(ta, tb, ex, m, A, n, o, ct0,
+                                                                    err);
   BS_CHECK_LAUNCH("rank2_update_kernel");
   return BS_OK;
 }
