@@ -27,7 +27,8 @@
 namespace {
 
 constexpr int L = 4;        // lanes per eigenvalue
-constexpr int NTB = 128;    // threads per block
+constexpr int NTB = 32;     // threads per block: one warp, EPC eigenvalues
+constexpr int EPC = NTB / L;  // eigenvalues per CTA (a matrix's bands spread over CTAs)
 
 __device__ __forceinline__ double rcp64(double q) {
   const double aq = fabs(q);
@@ -106,24 +107,33 @@ __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ 
     d32[k] = (float)d[k];
     e32[k] = (float)e2[k];
   }
-  __syncthreads();
-  if (tid == 0) {
-    double gl = d[0], gu = d[0], emax = 0.0;
-    for (int k = 0; k < n; ++k) {
+  __syncwarp();
+  {
+    // Gershgorin bounds and the largest e^2, reduced over the warp
+    double gl = INFINITY, gu = -INFINITY, emax = 0.0;
+    for (int k = tid; k < n; k += NTB) {
       const double el = k > 0 ? sqrt(e2[k - 1]) : 0.0, er = k + 1 < n ? sqrt(e2[k]) : 0.0;
       gl = fmin(gl, d[k] - el - er);
       gu = fmax(gu, d[k] + el + er);
       emax = fmax(emax, e2[k]);
     }
-    const double tnorm = fmax(fabs(gl), fabs(gu));
-    gl -= 2.0 * DBL_EPSILON * tnorm * n + DBL_MIN;
-    gu += 2.0 * DBL_EPSILON * tnorm * n + DBL_MIN;
-    red[0] = gl;
-    red[1] = gu;
-    red[2] = DBL_MIN * fmax(1.0, emax);
-    red[3] = tnorm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+      gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+      emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    }
+    if (tid == 0) {
+      const double tnorm = fmax(fabs(gl), fabs(gu));
+      gl -= 2.0 * DBL_EPSILON * tnorm * n + DBL_MIN;
+      gu += 2.0 * DBL_EPSILON * tnorm * n + DBL_MIN;
+      red[0] = gl;
+      red[1] = gu;
+      red[2] = DBL_MIN * fmax(1.0, emax);
+      red[3] = tnorm;
+    }
   }
-  __syncthreads();
+  __syncwarp();
   const double gl = red[0], gu = red[1], pivmin = red[2], tnorm = red[3];
   const double atol = fmax(4.0 * DBL_EPSILON, stop_rel) * tnorm;
   // FP32 counts need the matrix inside the FP32 range with headroom
@@ -136,7 +146,8 @@ __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ 
   auto c64 = [&](double x) { return count64(d, e2, n, x, pivmin); };
   auto c32 = [&](float x) { return count32(d32, e32, n, x, pivmin32); };
   int bad = 0;
-  for (int i = tid / L; i < nbands; i += NTB / L) {
+  const int iend = min(nbands, (int)(blockIdx.y + 1) * EPC);
+  for (int i = blockIdx.y * EPC + tid / L; i < iend; i += NTB / L) {
     double lo = gl, hi = gu;
     if (use32) {
       float flo = (float)gl, fhi = (float)gu;
@@ -165,22 +176,29 @@ __global__ void __launch_bounds__(NTB) bisect_kernel(const double* __restrict__ 
     if (!isfinite(lam) || !conv) bad = 1;   // sweep limit reached: not converged
     if (l == 0) omega[(size_t)b * nbands + i] = want_omega ? sqrt(fmax(lam, 0.0)) : lam;
   }
-  bad = __syncthreads_or(bad);
-  if (tid == 0 && stat) stat[b] = bad ? BS_ENOCONV : 0;
+  // the status of a matrix is zeroed before the launch; any CTA of it that
+  // ran out of sweeps marks it
+  bad = __any_sync(0xffffffffu, bad);
+  if (tid == 0 && stat && bad) atomicMin(stat + b, BS_ENOCONV);
 }
 
 }  // namespace
 
 int bs_launch_bisect(const double* de, int n, int batch, int nbands, double* omega, int* stat,
                      cudaStream_t s, bool want_omega, double stop_rel) {
+  if (batch < 1 || nbands < 1) return BS_OK;
   const size_t smem = 2 * (size_t)n * sizeof(double) + 2 * (size_t)n * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return bs_cuda_status(e, "bisect smem");
   }
-  bisect_kernel<<<batch, NTB, smem, s>>>(de, n, nbands, omega, stat, want_omega ? 1 : 0,
-                                         stop_rel, bs_bisect_sweeps());
+  if (stat) {
+    const cudaError_t e = cudaMemsetAsync(stat, 0, (size_t)batch * sizeof(int), s);
+    if (e != cudaSuccess) return bs_cuda_status(e, "bisect status");
+  }
+  bisect_kernel<<<dim3(batch, (nbands + EPC - 1) / EPC), NTB, smem, s>>>(
+      de, n, nbands, omega, stat, want_omega ? 1 : 0, stop_rel, bs_bisect_sweeps());
   BS_CHECK_LAUNCH("bisect_kernel");
   return BS_OK;
 }
