@@ -565,8 +565,7 @@ void bs_band_ws_free(BandWs* w) {
     if (w->sp[h]) cudaStreamDestroy(w->sp[h]);
     if (w->sb[h]) cudaStreamDestroy(w->sb[h]);
     if (w->epr[h]) cudaEventDestroy(w->epr[h]);
-    if (w->epan[h]) cudaEventDestroy(w->epan[h]);
-    if (w->ept[h]) cudaEventDestroy(w->ept[h]);
+    if (w->eru[h]) cudaEventDestroy(w->eru[h]);
   }
   void* p[] = {w->V, w->X, w->W, w->T, w->wA, w->wB, w->wD, w->eA, w->eB, w->band, w->dsc,
                w->zpart};
@@ -622,16 +621,18 @@ int bs_band_ws_alloc(BandWs* w, int n, int kb, int S) {
       return BS_ENOMEM;
     }
   }
-  cudaError_t e = cudaEventCreateWithFlags(&w->fork, cudaEventDisableTiming);
-  for (int h = 1; e == cudaSuccess && h < BAND_PARTS; ++h) {
-    e = cudaStreamCreateWithFlags(&w->sp[h], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->join[h], cudaEventDisableTiming);
-  }
+  // the chain of panel steps (QR, digit planes, A22 V, W, the next panel's
+  // columns) goes first whenever an SM frees up; the bulk of the trailing
+  // update fills the rest
+  int prio_lo = 0, prio_hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->fork, cudaEventDisableTiming);
   for (int h = 0; e == cudaSuccess && h < BAND_PARTS; ++h) {
-    e = cudaStreamCreateWithFlags(&w->sb[h], cudaStreamNonBlocking);
+    e = cudaStreamCreateWithPriority(&w->sp[h], cudaStreamNonBlocking, prio_hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->join[h], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&w->sb[h], cudaStreamNonBlocking, prio_lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->epr[h], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->epan[h], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->ept[h], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->eru[h], cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {
     bs_band_ws_free(w);
@@ -694,13 +695,13 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
   parts(kb, hk);
   for (int h = 0; h < BAND_PARTS; ++h) {
     off[h] = h == 0 ? 0 : off[h - 1] + hk[h - 1];
-    hs[h] = h == 0 ? s : w.sp[h];
+    hs[h] = w.sp[h];
   }
   w.nsteps = steps;
   w.timed = hk[0];
-  if (hk[1] > 0) {
+  {
     cudaError_t e = cudaEventRecord(w.fork, s);
-    for (int h = 1; e == cudaSuccess && h < BAND_PARTS; ++h)
+    for (int h = 0; e == cudaSuccess && h < BAND_PARTS; ++h)
       if (hk[h] > 0) e = cudaStreamWaitEvent(hs[h], w.fork, 0);
     if (e != cudaSuccess) return bs_cuda_status(e, "band reduction fork");
   }
@@ -710,12 +711,11 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
   // Per part, with look-ahead: after step j's operands of the rank-2
   // update are packed, the update of the next panel's columns (the first
   // column tile) runs first and the next panel's QR follows at once on the
-  // part's stream A, while the rest of the update and the next step's digit
-  // planes of A22 run on its stream B.  Events: epr (rank-2 operands
-  // packed), epan (next panel's columns updated), ept (next digit planes
-  // packed).  The panel QR reads and writes only the panel's columns, which
-  // stream B does not touch; B's pack of the next trailing block waits for
-  // the panel tile's writes (its mirror entries lie in that block).
+  // part's stream A, while the rest of the update runs on its stream B.
+  // Events: epr (rank-2 operands packed), eru (the rest of the update done).
+  // The panel QR reads and writes only the panel's columns, which stream B
+  // does not touch; the next step's digit planes of A22 (stream A) wait for
+  // the rest of the update, which also still reads this step's digit buffers.
   int step = 0;
   for (int j = 0; n - j - NB > 1; j += NB, ++step) {
     const int m = n - j - NB;
@@ -742,13 +742,12 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
                                                                             Th);
         BS_CHECK_LAUNCH("panel_qr_kernel");
         mark(h, 0, step, 1, st);
-        mark(h, 1, step, 0, st);
-        TRY_LAUNCH(bs_launch_band_pack_trail(Ah, n, j + NB, m, kh, wAh, eAh, st));
       } else {
-        cudaError_t e = cudaStreamWaitEvent(st, w.ept[h], 0);
+        cudaError_t e = cudaStreamWaitEvent(st, w.eru[h], 0);
         if (e != cudaSuccess) return bs_cuda_status(e, "band reduction wait");
-        mark(h, 1, step, 0, st);
       }
+      mark(h, 1, step, 0, st);
+      TRY_LAUNCH(bs_launch_band_pack_trail(Ah, n, j + NB, m, kh, wAh, eAh, st));
       TRY_LAUNCH(bs_launch_band_av(m, Vh, ld, sv, NB, kh, w.S, wAh, wBh, wDh, eAh, eBh, Xh, ld, sv,
                                    err, st));
       mark(h, 1, step, 1, st);
@@ -766,26 +765,22 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
         continue;
       }
       cudaError_t e = cudaEventRecord(w.epr[h], st);
+      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction events");
       // the next panel's columns (first column tile), then its QR
       TRY_LAUNCH(bs_launch_rank2_update(wAh, wBh, eAh, m, kh, Ah, n, j + NB, 0, 1, err, st));
-      if (e == cudaSuccess) e = cudaEventRecord(w.epan[h], st);
-      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction events");
       const int m2 = m - NB;
       mark(h, 0, step + 1, 0, st);
       panel_qr_kernel<NB><<<kh, PQ_NT, (size_t)NB * m2 * sizeof(zd), st>>>(Ah, n, j + NB, Vh,
                                                                            ld, sv, Th);
       BS_CHECK_LAUNCH("panel_qr_kernel");
       mark(h, 0, step + 1, 1, st);
-      // stream B: the rest of the update, then the next trailing block's digits
+      // stream B: the rest of the update
       e = cudaStreamWaitEvent(sb, w.epr[h], 0);
       if (e != cudaSuccess) return bs_cuda_status(e, "band reduction wait");
       mark(h, 3, step, 0, sb);
       TRY_LAUNCH(bs_launch_rank2_update(wAh, wBh, eAh, m, kh, Ah, n, j + NB, 1, 0, err, sb));
-      e = cudaStreamWaitEvent(sb, w.epan[h], 0);
-      if (e != cudaSuccess) return bs_cuda_status(e, "band reduction wait");
-      TRY_LAUNCH(bs_launch_band_pack_trail(Ah, n, j + 2 * NB, m2, kh, wAh, eAh, sb));
       mark(h, 3, step, 1, sb);
-      e = cudaEventRecord(w.ept[h], sb);
+      e = cudaEventRecord(w.eru[h], sb);
       if (e != cudaSuccess) return bs_cuda_status(e, "band reduction events");
     }
   }
@@ -807,7 +802,7 @@ int bs_launch_eig_band(zd* A, int n, int kb, BandWs& w, double* de, int* err, cu
                                   bis->omega + (size_t)off[h] * bis->nbands,
                                   bis->stat ? bis->stat + off[h] : nullptr, hs[h]));
   }
-  for (int h = 1; h < BAND_PARTS; ++h) {
+  for (int h = 0; h < BAND_PARTS; ++h) {
     if (hk[h] == 0) continue;
     cudaError_t e = cudaEventRecord(w.join[h], hs[h]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join[h], 0);

@@ -326,15 +326,15 @@ struct BandWs {
   int evcap = 0;            // event pairs per group
   int nsteps = 0;           // steps recorded by the last reduction
   int timed = 0;            // matrices of the half whose launches the events bracket
-  // the batch runs in BS_BAND_PARTS parts on as many streams: the extra
-  // streams, the fork and join events, and the per-part sizes of the digit
-  // buffers
+  // the batch runs in BS_BAND_PARTS parts, each on a high-priority stream
+  // (the chain of panel steps); the fork and join events, and the per-part
+  // sizes of the digit buffers
   cudaStream_t sp[BS_BAND_PARTS] = {};
   cudaEvent_t fork = nullptr, join[BS_BAND_PARTS] = {};
-  // look-ahead: per part a second stream for the bulk of the trailing update
-  // and the next step's digit planes, and the events that order the two
+  // look-ahead: per part a low-priority stream for the bulk of the trailing
+  // update, and the events that order the two (operands packed, update done)
   cudaStream_t sb[BS_BAND_PARTS] = {};
-  cudaEvent_t epr[BS_BAND_PARTS] = {}, epan[BS_BAND_PARTS] = {}, ept[BS_BAND_PARTS] = {};
+  cudaEvent_t epr[BS_BAND_PARTS] = {}, eru[BS_BAND_PARTS] = {};
   size_t hA = 0, hB = 0, hD = 0, hE = 0;
 };
 #define BS_BAND_AUTO_MIN 400   // BS_REDUCE_AUTO takes the two-stage reduction from this n on
