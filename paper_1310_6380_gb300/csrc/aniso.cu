@@ -12,9 +12,11 @@
 //   W0 = A_R [G1 Z1 + G2 Z3; G2 Z2 + G1 Z3]     (rows r of Z: Z_r, diag G scaling)
 // with A_R = L_R^-1 (V applied with the monomials; L_R^-1 I1 on a mesh), and
 //   C(k) = W W^dagger = sum over a <= b of k_a k_b (W_a W_b^dagger + h.c.),
-// the same six k-monomials as the isotropic path (k_0 = 1).  The products run
-// as FP64 complex GEMMs on the CUDA cores: 21 N^3 complex multiply-adds for
-// the W_i and 72 N^3 for the monomials, once per cell.
+// the same six k-monomials as the isotropic path (k_0 = 1).  The products
+// (18 N^3 complex multiply-adds for the W_i and 72 N^3 for the monomials,
+// once per cell) run as exact-slice tensor-core contractions, FP64-accurate
+// like the isotropic path's, while 6N <= 4096; beyond that as FP64 complex
+// GEMMs on the CUDA cores.
 #include "bs_internal.h"
 
 namespace {
@@ -37,9 +39,10 @@ __global__ void phi_build_kernel(const zd* __restrict__ T, int N, zd* __restrict
 }
 
 // Yw[t] (2N x 3N, column-major, ld 2N) = rows of H_t Z / (i V), Z = L^-dagger:
-// Z(r', c) = conj(L^-1(c, r'))
+// Z(r', c) = conj(L^-1(c, r')); with trans set, Yw[t]^dagger instead (3N x 2N,
+// ld 3N), the B operand of the tensor-core products
 __global__ void yw_kernel(const zd* __restrict__ LPhi, const double* __restrict__ G, int N,
-                          zd* __restrict__ Yw) {
+                          int trans, zd* __restrict__ Yw) {
   const size_t n2 = 2 * (size_t)N, n3 = 3 * (size_t)N;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n2 * n3) return;
@@ -58,7 +61,10 @@ __global__ void yw_kernel(const zd* __restrict__ LPhi, const double* __restrict_
     v = top ? zadd(zscale(Z(a), g1), zscale(Z(2 * N + a), g2))
             : zadd(zscale(Z(N + a), g2), zscale(Z(2 * N + a), g1));
   }
-  Yw[(size_t)t * n2 * n3 + i] = v;
+  if (trans)
+    Yw[(size_t)t * n2 * n3 + (size_t)c + (size_t)rho * n3] = zconj(v);
+  else
+    Yw[(size_t)t * n2 * n3 + i] = v;
 }
 
 // Cm[t] = V2 (P_ab + P_ab^dagger) (a < b) or V2 P_aa, monomials 1, k1, k2, k1^2, k1 k2, k2^2
@@ -137,18 +143,33 @@ int bs_launch_monomials_aniso(bs_cell* c, cudaStream_t s) {
                                   c->d_mA, c->d_mB, c->d_mD, c->d_meA, c->d_meB, err, s));
     AR = c->d_LinvR2;
   }
+  const bool tc = bs_zgemm_tc_fits(3 * N);
   yw_kernel<<<dim3((unsigned)((n2n3 + 255) / 256), 3), 256, 0, s>>>(c->d_LPhi, c->d_G, N,
-                                                                   c->d_Yw);
+                                                                   tc ? 1 : 0, c->d_Yw);
   BS_CHECK_LAUNCH("yw_kernel");
   // W_t = diag(A_R, A_R) Yw_t: the top and bottom halves as a batch of two
-  for (int t = 0; t < 3; ++t)
-    TRY_LAUNCH(bs_launch_zgemm(false, false, N, 3 * N, N, one, AR, N, 0, c->d_Yw + t * n2n3, n,
-                               N, nullptr, 0, c->d_Wk + t * n2n3, n, N, 2, c->mesh ? 0 : 1, s));
+  // (on the tensor cores B = Yw_t^dagger, halves 3N x N apart)
+  for (int t = 0; t < 3; ++t) {
+    if (tc)
+      TRY_LAUNCH(bs_launch_zgemm_tc_rect(AR, N, 0, nullptr, c->d_Yw + t * n2n3, 3 * N,
+                                         (long)(3 * NN), c->d_Wk + t * n2n3, n, N, N, 3 * N, N, 2,
+                                         c->d_mA, c->d_mB, c->d_mD, c->d_meA, c->d_meB, err, s));
+    else
+      TRY_LAUNCH(bs_launch_zgemm(false, false, N, 3 * N, N, one, AR, N, 0, c->d_Yw + t * n2n3, n,
+                                 N, nullptr, 0, c->d_Wk + t * n2n3, n, N, 2, c->mesh ? 0 : 1, s));
+  }
   const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
-  for (int t = 0; t < 6; ++t)
-    TRY_LAUNCH(bs_launch_zgemm(false, true, n, n, 3 * N, one, c->d_Wk + pa[t] * n2n3, n, 0,
-                               c->d_Wk + pb[t] * n2n3, n, 0, nullptr, 0, c->d_Pab + t * nn, n, 0,
-                               1, 0, s));
+  for (int t = 0; t < 6; ++t) {
+    if (tc)
+      TRY_LAUNCH(bs_launch_zgemm_tc_rect(c->d_Wk + pa[t] * n2n3, n, 0, nullptr,
+                                         c->d_Wk + pb[t] * n2n3, n, 0, c->d_Pab + t * nn, n, 0, n,
+                                         n, 3 * N, 1, c->d_mA, c->d_mB, c->d_mD, c->d_meA,
+                                         c->d_meB, err, s));
+    else
+      TRY_LAUNCH(bs_launch_zgemm(false, true, n, n, 3 * N, one, c->d_Wk + pa[t] * n2n3, n, 0,
+                                 c->d_Wk + pb[t] * n2n3, n, 0, nullptr, 0, c->d_Pab + t * nn, n,
+                                 0, 1, 0, s));
+  }
   const double V2 = c->mesh ? 1.0 : c->V * c->V;
   cm_aniso_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(c->d_Pab, n, V2, c->d_Cm);
   BS_CHECK_LAUNCH("cm_aniso_kernel");

@@ -526,6 +526,28 @@ static int realloc_fields(bs_cell* c, int nf) {
   if (!r) r = dalloc(&c->d_Yw, 18 * NN, "H_i Z");
   if (!r) r = dalloc(&c->d_Wk, 18 * NN, "W_i");
   if (!r) r = dalloc(&c->d_Pab, 24 * NN, "W_a W_b^dagger");
+  if (!r && nf == 7 && bs_zgemm_tc_fits(3 * c->N)) {
+    // the exact-slice workspace grows to the anisotropic products: W_t (N x 3N
+    // over K = N, two halves) and the monomials (2N x 2N over K = 3N)
+    size_t ma = 0, mb = 0, md = 0, a1 = 0, b1 = 0, d1 = 0;
+    bs_zgemm_tc_elems(c->N, 2, &ma, &mb, &md);
+    bs_zgemm_tc_rect_elems(c->N, 3 * c->N, c->N, 2, &a1, &b1, &d1);
+    ma = std::max(ma, a1), mb = std::max(mb, b1), md = std::max(md, d1);
+    bs_zgemm_tc_rect_elems(2 * c->N, 2 * c->N, 3 * c->N, 1, &a1, &b1, &d1);
+    ma = std::max(ma, a1), mb = std::max(mb, b1), md = std::max(md, d1);
+    cudaFree(c->d_mA);
+    cudaFree(c->d_mB);
+    cudaFree(c->d_mD);
+    cudaFree(c->d_meB);
+    c->d_mA = nullptr;
+    c->d_mB = nullptr;
+    c->d_mD = nullptr;
+    c->d_meB = nullptr;
+    r = dalloc(&c->d_mA, ma, "monomial digit planes A");
+    if (!r) r = dalloc(&c->d_mB, mb, "monomial digit planes B");
+    if (!r) r = dalloc(&c->d_mD, md, "monomial digit-pair products");
+    if (!r) r = dalloc(&c->d_meB, 6 * (size_t)c->N, "monomial exponents B");
+  }
   if (r) return r;
   CK(cudaMemcpy(c->d_table + (size_t)nf * np, raw.data(), raw.size() * 8, cudaMemcpyHostToDevice),
      "bs_set_stiffness raw");

@@ -298,6 +298,14 @@ void bs_zgemm_tc_elems(int N, int batch, size_t* nA, size_t* nB, size_t* nD);
 int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long sB, zd* C, long sC,
                        int N, int batch, uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB,
                        int* err, cudaStream_t s);
+// the same for column-major A (M x K, leading dimension lda), B (Nc x K) and
+// C (M x Nc); exponents eA: batch M, eB: batch Nc; needs 2K <= 4096
+bool bs_zgemm_tc_fits(int K);
+void bs_zgemm_tc_rect_elems(int M, int Nc, int K, int batch, size_t* nA, size_t* nB, size_t* nD);
+int bs_launch_zgemm_tc_rect(const zd* A, int lda, long sA, const double* sc, const zd* B, int ldb,
+                            long sB, zd* C, int ldc, long sC, int M, int Nc, int K, int batch,
+                            uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB, int* err,
+                            cudaStream_t s);
 
 // builder.cu
 // ---- two-stage reduction to tridiagonal form (band.cu)

@@ -17,6 +17,8 @@
 // coefficients are sums of the products P_X^{ab} = F_X^a F_X^b^dagger.
 #include <math.h>
 
+#include <algorithm>
+
 #include "bs_internal.h"
 
 namespace {
@@ -386,10 +388,67 @@ int bs_launch_cholesky(zd* A, int n, int batch, long stride, int* info, cudaStre
   return BS_OK;
 }
 
+namespace {
+// zero X strictly above the diagonal
+__global__ void zero_upper_kernel(zd* __restrict__ Xg, int n, long stride) {
+  zd* x = Xg + (size_t)blockIdx.y * stride;
+  const size_t nn = (size_t)n * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
+       e += (size_t)gridDim.x * blockDim.x)
+    if (e % n < e / n) x[e] = zmake(0.0, 0.0);
+}
+}  // namespace
+
+// X = L^-1 by doubling: with the NB x NB diagonal blocks inverted, each pair
+// of adjacent inverted diagonal blocks of size sz (sz = NB, 2 NB, 4 NB, ...)
+// gets the off-diagonal block of the inverse of [L11 0; L21 L22],
+//   X21 = -X22 L21 X11,
+// as two products: T^dagger = X11^dagger L21^dagger (kept in the pair's block
+// above the diagonal, which X does not use until the end), then
+// X21 = -X22 (T^dagger)^dagger.  The pairs of one size are a batch of
+// products whose operands lie 2 sz (n + 1) apart; a ragged last pair is its
+// own launch.  Every product has full 32 x 32 output tiles over a long inner
+// dimension: the work no longer waits on one CTA per block diagonal.
+static int trinv_doubling(const zd* L, zd* X, int n, int batch, long stride, cudaStream_t s) {
+  const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0);
+  for (int sz = NB; sz < n; sz *= 2) {
+    const int nfull = n / (2 * sz);
+    const int rem = n - nfull * 2 * sz;
+    const int s2r = rem > sz ? rem - sz : 0;
+    const long ps = 2L * sz * ((long)n + 1);
+    for (int b = 0; b < batch; ++b) {
+      const zd* Lb = L + (size_t)b * stride;
+      zd* Xb = X + (size_t)b * stride;
+      auto pair = [&](int i0, int s2, int np) -> int {
+        const zd* X11 = Xb + i0 + (size_t)i0 * n;
+        const zd* L21 = Lb + (i0 + sz) + (size_t)i0 * n;
+        zd* Tp = Xb + i0 + (size_t)(i0 + sz) * n;
+        zd* X21 = Xb + (i0 + sz) + (size_t)i0 * n;
+        const zd* X22 = Xb + (i0 + sz) + (size_t)(i0 + sz) * n;
+        TRY_LAUNCH(bs_launch_zgemm(true, true, sz, s2, sz, one, X11, n, ps, L21, n, ps, nullptr, 0,
+                                   Tp, n, ps, np, 4, s));
+        TRY_LAUNCH(bs_launch_zgemm(false, true, s2, sz, s2, mone, X22, n, ps, Tp, n, ps, nullptr,
+                                   0, X21, n, ps, np, 1, s));
+        return BS_OK;
+      };
+      if (nfull > 0) TRY_LAUNCH(pair(0, sz, nfull));
+      if (s2r > 0) TRY_LAUNCH(pair(nfull * 2 * sz, s2r, 1));
+    }
+  }
+  const size_t nn = (size_t)n * n;
+  const unsigned g = (unsigned)std::min<size_t>((nn + 255) / 256, 4096);
+  zero_upper_kernel<<<dim3(g, batch), 256, 0, s>>>(X, n, stride);
+  BS_CHECK_LAUNCH("zero_upper_kernel");
+  return BS_OK;
+}
+
 int bs_launch_trinv(const zd* L, zd* X, int n, int batch, long stride, cudaStream_t s) {
   const int nt = (n + NB - 1) / NB;
   trinv_diag_kernel<<<dim3(nt, batch), 256, 0, s>>>(L, X, n, stride);
   BS_CHECK_LAUNCH("trinv_diag_kernel");
+  // a few large factors (a cell's own): doubling; a batch of many small ones
+  // (a ragged batch's cells) keeps the SMs busy diagonal by diagonal
+  if (batch <= 4 && nt >= 16) return trinv_doubling(L, X, n, batch, stride, s);
   for (int d = 1; d < nt; ++d) {
     trinv_off_kernel<<<dim3(nt - d, batch), 256, 0, s>>>(L, X, n, stride, d);
     BS_CHECK_LAUNCH("trinv_off_kernel");

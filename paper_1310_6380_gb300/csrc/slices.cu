@@ -377,36 +377,39 @@ void bs_cx_tc_elems(int n, int b, int kb, size_t* nA, size_t* nB, size_t* nD) {
   *nD = bs_slice_planes(S, Kp, n, 2 * b, kb) * n * 2 * b;
 }
 
-// ---- complex N x N products C = A diag(sc) B^dagger (column-major, FP64)
+// ---- complex products C = A diag(sc) B^dagger (column-major, FP64): A is
+// M x K, B is Nc x K, C is M x Nc
 //   Re C = [Ar sc | Ai sc] [Br | Bi]^T,  Im C = [Ar sc | Ai sc] [-Bi | Br]^T
-// A rows r; B rows (c, part), digits reversed; K = 2N.
+// A rows r; B rows (c, part), digits reversed; the contraction runs over 2K.
 namespace {
 
-__global__ void pack_zrows_kernel(const zd* __restrict__ A, long sA, const double* __restrict__ sc,
-                                  int N, int S, int Kp, int parts, int reversed,
-                                  uint16_t* __restrict__ out, int* __restrict__ ex) {
-  // one CTA (128 threads) per row: the digit planes are written along K
+__global__ void pack_zrows_kernel(const zd* __restrict__ A, int ld, long sA,
+                                  const double* __restrict__ sc, int R, int K, int S, int Kp,
+                                  int parts, int reversed, uint16_t* __restrict__ out,
+                                  int* __restrict__ ex) {
+  // one CTA (128 threads) per row r < R of the operand: the digit planes are
+  // written along K
   __shared__ double sh[4];
   const int r = blockIdx.x, z = blockIdx.y;
   const zd* a = A + (size_t)z * sA;
   double m = 0.0;
-  for (int k = threadIdx.x; k < N; k += 128) {
-    zd v = a[r + (size_t)k * N];
+  for (int k = threadIdx.x; k < K; k += 128) {
+    zd v = a[r + (size_t)k * ld];
     if (sc) v = zscale(v, sc[k]);
     m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
   }
   const int e = row_exp(row_max(m, sh));
-  const size_t rows = (size_t)parts * N, rowlen = (size_t)S * Kp;
+  const size_t rows = (size_t)parts * R, rowlen = (size_t)S * Kp;
   uint16_t* base = out + ((size_t)z * rows + (size_t)r * parts) * rowlen +
                    (reversed ? (size_t)(S - 1) * Kp : 0);
   const ptrdiff_t plane = reversed ? -(ptrdiff_t)Kp : (ptrdiff_t)Kp;
   for (int k = threadIdx.x; k < Kp; k += 128) {
     double v0 = 0.0, v1 = 0.0;
-    if (k < 2 * N) {
-      const int kk = k < N ? k : k - N;
-      zd v = a[r + (size_t)kk * N];
+    if (k < 2 * K) {
+      const int kk = k < K ? k : k - K;
+      zd v = a[r + (size_t)kk * ld];
       if (sc) v = zscale(v, sc[kk]);
-      if (k < N) {          // part 0: [re | im], part 1: [-im | re]
+      if (k < K) {          // part 0: [re | im], part 1: [-im | re]
         v0 = v.x;
         v1 = -v.y;
       } else {
@@ -417,52 +420,68 @@ __global__ void pack_zrows_kernel(const zd* __restrict__ A, long sA, const doubl
     put_digits(v0, e, S, base + k, plane);
     if (parts == 2) put_digits(v1, e, S, base + rowlen + k, plane);
   }
-  if (threadIdx.x == 0) ex[(size_t)z * N + r] = e;
+  if (threadIdx.x == 0) ex[(size_t)z * R + r] = e;
 }
 
 __global__ void recombine_z_kernel(const float* __restrict__ Dm, const SliceSlabs sl,
-                                   const int* __restrict__ eA, const int* __restrict__ eB, int N,
-                                   zd* __restrict__ C, long sC) {
+                                   const int* __restrict__ eA, const int* __restrict__ eB, int M,
+                                   int Nc, zd* __restrict__ C, int ldc, long sC) {
   const int z = blockIdx.y;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= N * N) return;
-  const int r = idx % N, c = idx / N;
-  const size_t M = (size_t)N, Nn = 2 * (size_t)N;
-  const float* dz = Dm + (size_t)z * sl.nq * Nn * M;
+  if (idx >= M * Nc) return;
+  const int r = idx % M, c = idx / M;
+  const size_t Mz = (size_t)M, Nn = 2 * (size_t)Nc;
+  const float* dz = Dm + (size_t)z * sl.nq * Nn * Mz;
   double xr, xi;
-  order_sums(dz, Nn * M, (2 * (size_t)c) * M + r, (2 * (size_t)c + 1) * M + r, sl, &xr, &xi);
-  const int ex = eA[(size_t)z * N + r] + eB[(size_t)z * N + c];
-  C[(size_t)z * sC + idx] = zmake(ldexp(xr, ex), ldexp(xi, ex));
+  order_sums(dz, Nn * Mz, (2 * (size_t)c) * Mz + r, (2 * (size_t)c + 1) * Mz + r, sl, &xr, &xi);
+  const int ex = eA[(size_t)z * M + r] + eB[(size_t)z * Nc + c];
+  C[(size_t)z * sC + r + (size_t)c * ldc] = zmake(ldexp(xr, ex), ldexp(xi, ex));
 }
 
 }  // namespace
 
+bool bs_zgemm_tc_fits(int K) { return K >= 1 && 2 * K <= 4096; }
+
+void bs_zgemm_tc_rect_elems(int M, int Nc, int K, int batch, size_t* nA, size_t* nB,
+                            size_t* nD) {
+  const int S = BS_SLICES_ASM, Kp = (2 * K + 63) / 64 * 64;
+  *nA = (size_t)batch * M * S * Kp;
+  *nB = (size_t)batch * 2 * Nc * S * Kp;
+  *nD = bs_slice_planes(S, Kp, M, 2 * Nc, batch) * M * 2 * Nc;
+}
+
 void bs_zgemm_tc_elems(int N, int batch, size_t* nA, size_t* nB, size_t* nD) {
-  const int S = BS_SLICES_ASM, Kp = (2 * N + 63) / 64 * 64;
-  *nA = (size_t)batch * N * S * Kp;
-  *nB = (size_t)batch * 2 * N * S * Kp;
-  *nD = bs_slice_planes(S, Kp, N, 2 * N, batch) * N * 2 * N;
+  bs_zgemm_tc_rect_elems(N, N, N, batch, nA, nB, nD);
+}
+
+int bs_launch_zgemm_tc_rect(const zd* A, int lda, long sA, const double* sc, const zd* B, int ldb,
+                            long sB, zd* C, int ldc, long sC, int M, int Nc, int K, int batch,
+                            uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB, int* err,
+                            cudaStream_t s) {
+  const int S = BS_SLICES_ASM, Kp = (2 * K + 63) / 64 * 64;
+  SliceSlabs sl;
+  if (!bs_zgemm_tc_fits(K) || M < 1 || Nc < 1 || lda < M || ldb < Nc || ldc < M ||
+      !bs_slice_slabs(S, Kp, M, 2 * Nc, batch, &sl)) {
+    bs_set_error("complex product: 2K = %d exceeds the exact-slice limit 4096", 2 * K);
+    return BS_EINVAL;
+  }
+  pack_zrows_kernel<<<dim3(M, batch), 128, 0, s>>>(A, lda, sA, sc, M, K, S, Kp, 1, 0, wA, eA);
+  BS_CHECK_LAUNCH("pack_zrows_kernel A");
+  pack_zrows_kernel<<<dim3(Nc, batch), 128, 0, s>>>(B, ldb, sB, nullptr, Nc, K, S, Kp, 2, 1, wB,
+                                                    eB);
+  BS_CHECK_LAUNCH("pack_zrows_kernel B");
+  TRY_LAUNCH(bs_launch_slice_orders(wA, wB, wD, M, 2 * Nc, S, Kp, batch, err, s));
+  recombine_z_kernel<<<dim3((unsigned)(((size_t)M * Nc + 255) / 256), batch), 256, 0, s>>>(
+      wD, sl, eA, eB, M, Nc, C, ldc, sC);
+  BS_CHECK_LAUNCH("recombine_z_kernel");
+  return BS_OK;
 }
 
 int bs_launch_zgemm_tc(const zd* A, long sA, const double* sc, const zd* B, long sB, zd* C, long sC,
                        int N, int batch, uint16_t* wA, uint16_t* wB, float* wD, int* eA, int* eB,
                        int* err, cudaStream_t s) {
-  const int S = BS_SLICES_ASM, Kp = (2 * N + 63) / 64 * 64;
-  SliceSlabs sl;
-  if (2 * N > 4096 || !bs_slice_slabs(S, Kp, N, 2 * N, batch, &sl)) {
-    bs_set_error("complex product: 2N = %d exceeds the exact-slice limit 4096", 2 * N);
-    return BS_EINVAL;
-  }
-  const dim3 g(N, batch);
-  pack_zrows_kernel<<<g, 128, 0, s>>>(A, sA, sc, N, S, Kp, 1, 0, wA, eA);
-  BS_CHECK_LAUNCH("pack_zrows_kernel A");
-  pack_zrows_kernel<<<g, 128, 0, s>>>(B, sB, nullptr, N, S, Kp, 2, 1, wB, eB);
-  BS_CHECK_LAUNCH("pack_zrows_kernel B");
-  TRY_LAUNCH(bs_launch_slice_orders(wA, wB, wD, N, 2 * N, S, Kp, batch, err, s));
-  recombine_z_kernel<<<dim3((N * N + 255) / 256, batch), 256, 0, s>>>(
-      wD, sl, eA, eB, N, C, sC);
-  BS_CHECK_LAUNCH("recombine_z_kernel");
-  return BS_OK;
+  return bs_launch_zgemm_tc_rect(A, N, sA, sc, B, N, sB, C, N, sC, N, N, N, batch, wA, wB, wD, eA,
+                                 eB, err, s);
 }
 
 // ---- the two contractions of a dense-to-band reduction step

@@ -200,3 +200,44 @@ def test_aniso_argument_errors():
         assert np.isfinite(w).all()
     finally:
         bs.bs_destroy_cell(h)
+
+
+def test_aniso_c1_cell_full_size():
+    """The c1 cell with rotated orthotropic phases at M = 10 (n = 882), as the
+    benchmark solves it: the W and monomial products run on the exact-slice
+    tensor path (6N = 2646 <= 4096); sampled wavevectors against the oracle."""
+    cfg = cells.config1()
+    cell = cells.anisotropic_cell(cfg["cell"], seed=6380)
+    M, nb = cfg["M"], cfg["nbands"]
+    Q = cfg["Q"][[0, 37, 71]]
+    h = make(cell, M)
+    try:
+        w = np.empty((len(Q), nb))
+        st = np.empty(len(Q), np.int32)
+        bs.bs_solve_k(h, np.ascontiguousarray(Q), nb, w, st)
+        assert not st.any()
+    finally:
+        bs.bs_destroy_cell(h)
+    oc = mv.OracleCell(cell, M)
+    fl = omega_floor(cell)
+    for i, q in enumerate(Q):
+        assert omega_rel_err(w[i], oc.omega(q, nb), fl).max() <= 1e-8, i
+
+
+def test_aniso_products_beyond_the_exact_slice_limit():
+    """M = 13 (N = 729, 6N = 4374 > 4096): the W and monomial products fall
+    back to FP64 complex GEMMs on the CUDA cores; one wavevector against the
+    oracle."""
+    cell = cells.anisotropic_cell(cells.voronoi_cell(40, 8, seed=13), seed=11)
+    M, nb = 13, 8
+    q = np.array([[0.31, 0.12]])
+    h = make(cell, M)
+    try:
+        w = np.empty((1, nb))
+        st = np.empty(1, np.int32)
+        bs.bs_solve_k(h, q, nb, w, st)
+        assert not st.any()
+    finally:
+        bs.bs_destroy_cell(h)
+    ref = mv.OracleCell(cell, M).omega(q[0], nb)
+    assert omega_rel_err(w[0], ref, omega_floor(cell)).max() <= 1e-8

@@ -129,7 +129,13 @@ def test_batch_tile_edges_agree():
 def test_batch_fp64_solver_matches_single_cell_fp64():
     """BS_SOLVER_FP64 runs the plain FP64 path of bs_solve_k for every
     (cell, k) of a chunk at once: the same numbers as single-cell FP64 solves
-    and the oracle to 1e-8."""
+    to the rounding of two FP64 evaluation orders, and the oracle to 1e-8.
+
+    A single cell inverts its Gram factors by doubling, a batch of many cells
+    diagonal by diagonal; the two inverses differ by a few n eps, which moves
+    the eigenvalues by about n eps ||C||.  At the acoustic zero modes of Gamma
+    that is ~1e-13 ||C|| against the floor squared (||C|| / floor^2 ~ 60
+    here), hence 1e-10 on the floored relative error."""
     cfgs = [cells.config3_cell(i) for i in range(30, 36)]
     nk, nb = 4, 10
     Qs = np.ascontiguousarray(np.stack([c["Q"][::7][:nk] for c in cfgs]))
@@ -150,7 +156,7 @@ def test_batch_fp64_solver_matches_single_cell_fp64():
             bs.bs_solve_k(h, np.ascontiguousarray(Qs[i]), nb, ref)
         finally:
             bs.bs_destroy_cell(h)
-        assert omega_rel_err(w[i], ref, omega_floor(c["cell"])).max() <= 1e-12, i
+        assert omega_rel_err(w[i], ref, omega_floor(c["cell"])).max() <= 1e-10, i
     oc = mv.OracleCell(cfgs[0]["cell"], cfgs[0]["M"])
     ref = np.array([oc.omega(q, nb) for q in Qs[0]])
     assert omega_rel_err(w[0], ref, omega_floor(cfgs[0]["cell"])).max() <= 1e-8
