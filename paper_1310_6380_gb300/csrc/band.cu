@@ -98,6 +98,17 @@ __device__ void block_zsum(zd (&v)[NV], zd* sh, zd* out) {
 // ... of the panel throughout.  Writes R (upper triangle) and zeros below
 // it back into the panel, V (m x NB, unit lower trapezoidal, leading
 // dimension ldv) and T (NB x NB upper triangular, column-major).
+//
+// One block reduction per column i: with x = P[i][i:] and v = [1; x[i+1:] s]
+// (s = 1 / (x_i - beta)), every sum the step needs is a sum over the rows
+// below i of quantities known before beta,
+//   ||x[i+1:]||^2,  y_c = x[i+1:]^dagger P[c][i+1:] (c > i),
+//   g_q = v_q[i+1:]^dagger x[i+1:] (q < i),
+// and then v^dagger P[c] = P[c][i] + conj(s) y_c, v_q^dagger v = conj(v_q[i])
+// + s g_q.  The reflector scalars come from two reciprocal square roots and
+// one division, and the column of T of each reflector (T[0:i, i] =
+// -tau_i T[0:i, 0:i] G[0:i, i], G[q][i] = v_q^dagger v_i) is formed right
+// after its reduction by i threads at once.
 template <int NB>
 __global__ void __launch_bounds__(PQ_NT) panel_qr_kernel(zd* __restrict__ A, int n, int j,
                                                          zd* __restrict__ V, int ldv, long sv,
@@ -105,10 +116,9 @@ __global__ void __launch_bounds__(PQ_NT) panel_qr_kernel(zd* __restrict__ A, int
   extern __shared__ zd P[];   // [NB][m]
   __shared__ zd red[NB * (PQ_NT / 32)];
   __shared__ zd dots[NB];
-  __shared__ zd G[NB][NB];    // G[a][i] = v_a^dagger v_i, a < i
-  __shared__ double tau_s[NB];
+  __shared__ zd rowi[NB];     // row i of the panel, P[c][i]
+  __shared__ zd Ts[NB * NB];  // T, column-major
   __shared__ zd beta_s[NB];
-  __shared__ zd alpha_s;
   const int k = blockIdx.x, tid = threadIdx.x;
   const int m = n - j - NB;
   zd* a = A + (size_t)k * n * n;
@@ -116,73 +126,79 @@ __global__ void __launch_bounds__(PQ_NT) panel_qr_kernel(zd* __restrict__ A, int
     const int i = idx / m, r = idx % m;
     P[idx] = a[(size_t)(j + i) * n + j + NB + r];
   }
+  for (int idx = tid; idx < NB * NB; idx += PQ_NT) Ts[idx] = zmake(0.0, 0.0);
   __syncthreads();
   const int kk = min(NB, m - 1);   // reflectors of length >= 2
   for (int i = 0; i < kk; ++i) {
     zd* pi = P + (size_t)i * m;
-    // ||x[1:]||^2 of x = P[i][i:]
-    double s = 0.0;
-    for (int r = tid; r < m; r += PQ_NT) {
-      if (r > i) s = fma(pi[r].x, pi[r].x, fma(pi[r].y, pi[r].y, s));
-      if (r == i) alpha_s = pi[r];
-    }
-    zd sv1[1] = {zmake(s, 0.0)};
-    block_zsum<1, PQ_NT>(sv1, red, dots);
-    const zd alpha = alpha_s;
-    const double aa = hypot(alpha.x, alpha.y);
-    const double nu = sqrt(fma(aa, aa, dots[0].x));
-    double tau = 0.0;
-    zd beta = zmake(0.0, 0.0), scale = zmake(0.0, 0.0);
-    if (nu > 0.0) {
-      beta = aa > 0.0 ? zscale(alpha, -nu / aa) : zmake(-nu, 0.0);
-      tau = (aa + nu) / nu;
-      const zd den = zsub(alpha, beta);
-      const double d2 = den.x * den.x + den.y * den.y;
-      scale = zmake(den.x / d2, -den.y / d2);
-    }
-    // v = x / (x0 - beta) below the diagonal, and the dot products
-    // z_c = v^dagger P[c] (c > i) and G[a][i] = v_a^dagger v (a < i)
-    zd acc[NB > 1 ? NB - 1 : 1];
+    if (tid == i) {
 #pragma unroll
-    for (int q = 0; q < NB - 1; ++q) acc[q] = zmake(0.0, 0.0);
+      for (int c = 0; c < NB; ++c) rowi[c] = P[(size_t)c * m + i];
+    }
+    // acc[0]: ||x[i+1:]||^2; acc[q] (1 <= q <= i): g_{q-1}; acc[c] (c > i): y_c
+    zd acc[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) acc[q] = zmake(0.0, 0.0);
+    for (int r = tid; r < m; r += PQ_NT) {
+      if (r <= i) continue;
+      const zd x = pi[r];
+      acc[0].x = fma(x.x, x.x, fma(x.y, x.y, acc[0].x));
+#pragma unroll
+      for (int q = 1; q < NB; ++q) {
+        if (q <= i)
+          acc[q] = zfmac(x, P[(size_t)(q - 1) * m + r], acc[q]);   // conj(v_{q-1}[r]) x[r]
+        else
+          acc[q] = zfmac(P[(size_t)q * m + r], x, acc[q]);         // conj(x[r]) P[q][r]
+      }
+    }
+    block_zsum<NB, PQ_NT>(acc, red, dots);
+    const zd alpha = rowi[i];
+    const double a2 = fma(alpha.x, alpha.x, alpha.y * alpha.y), s2 = a2 + dots[0].x;
+    double tau = 0.0;
+    zd beta = zmake(0.0, 0.0), scl = zmake(0.0, 0.0);
+    if (s2 > 0.0) {
+      const double rn = rsqrt(s2), nu = s2 * rn;
+      if (a2 > 0.0) {
+        const double ra = rsqrt(a2), aa = a2 * ra;
+        beta = zscale(alpha, -nu * ra);
+        tau = (aa + nu) * rn;
+        // 1 / (alpha - beta) = conj(alpha) / (|alpha| (|alpha| + nu))
+        scl = zscale(zconj(alpha), ra / (aa + nu));
+      } else {
+        beta = zmake(-nu, 0.0);
+        tau = 1.0;
+        scl = zmake(rn, 0.0);
+      }
+    }
+    if (tid == 0) {
+      beta_s[i] = beta;
+      Ts[i + i * NB] = zmake(tau, 0.0);
+    }
+    if (tid < i) {
+      // T[tid][i] = -tau sum_{q = tid}^{i-1} T[tid][q] G[q][i]
+      zd t = zmake(0.0, 0.0);
+      for (int q = tid; q < i; ++q) {
+        const zd g = zfma(scl, dots[q + 1], zconj(rowi[q]));
+        t = zfma(Ts[tid + q * NB], g, t);
+      }
+      Ts[tid + i * NB] = zscale(t, -tau);
+    }
+    // P[c] -= tau v (v^dagger P[c]) for c > i, v stored below the diagonal
+    zd tz[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      tz[c] = c > i ? zscale(zfmac(dots[c], scl, rowi[c]), tau) : zmake(0.0, 0.0);
     for (int r = tid; r < m; r += PQ_NT) {
       if (r < i) continue;
-      zd vr;
-      if (r == i) {
-        vr = zmake(1.0, 0.0);
-      } else {
-        vr = zmul(pi[r], scale);
+      zd vr = zmake(1.0, 0.0);
+      if (r > i) {
+        vr = zmul(pi[r], scl);
         pi[r] = vr;
       }
 #pragma unroll
-      for (int q = 0; q < NB - 1; ++q) {
-        if (q < i) {
-          // G[q][i]: v_q[r] (v_q[q] = 1, stored below its diagonal)
-          const zd vq = P[(size_t)q * m + r];
-          acc[q] = zfmac(vr, vq, acc[q]);   // conj(v_q[r]) v[r]
-        } else {
-          const int c = q + 1;             // column c > i
-          if (c > i && c < NB) acc[q] = zfmac(P[(size_t)c * m + r], vr, acc[q]);
-        }
-      }
-    }
-    block_zsum<(NB > 1 ? NB - 1 : 1), PQ_NT>(acc, red, dots);
-    if (tid == 0) {
-      tau_s[i] = tau;
-      beta_s[i] = beta;
-      for (int q = 0; q < i; ++q) G[q][i] = dots[q];
-    }
-    // P[c] -= tau v (v^dagger P[c]) for c > i
-    zd tz[NB > 1 ? NB - 1 : 1];
-#pragma unroll
-    for (int c = 1; c < NB; ++c) tz[c - 1] = zscale(dots[c - 1], tau);
-    for (int r = tid; r < m; r += PQ_NT) {
-      if (r < i) continue;
-      const zd vr = r == i ? zmake(1.0, 0.0) : pi[r];
-#pragma unroll
       for (int c = 1; c < NB; ++c) {
         if (c <= i) continue;
-        P[(size_t)c * m + r] = zfnma(vr, tz[c - 1], P[(size_t)c * m + r]);
+        P[(size_t)c * m + r] = zfnma(vr, tz[c], P[(size_t)c * m + r]);
       }
     }
     __syncthreads();
@@ -202,25 +218,8 @@ __global__ void __launch_bounds__(PQ_NT) panel_qr_kernel(zd* __restrict__ A, int
     a[(size_t)(j + i) * n + j + NB + r] = out;
     vk[(size_t)i * ldv + r] = vv;
   }
-  if (tid == 0) {
-    // T (forward, columnwise): T[i][i] = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i];
-    // built in place of G's lower triangle and diagonal, column by column
-    zd* tk = T + (size_t)k * NB * NB;
-    for (int i = 0; i < NB; ++i) {
-      for (int r = 0; r < NB; ++r) {
-        zd t = zmake(0.0, 0.0);
-        if (i < kk) {
-          if (r == i) {
-            t = zmake(tau_s[i], 0.0);
-          } else if (r < i) {
-            for (int q = r; q < i; ++q) t = zfma(tk[r + q * NB], G[q][i], t);
-            t = zscale(t, -tau_s[i]);
-          }
-        }
-        tk[r + i * NB] = t;
-      }
-    }
-  }
+  zd* tk = T + (size_t)k * NB * NB;
+  for (int idx = tid; idx < NB * NB; idx += PQ_NT) tk[idx] = Ts[idx];
 }
 
 // W = Y - (1/2) V (T^dagger Z) with Y = X T and Z = V^dagger Y = Z0 T,
