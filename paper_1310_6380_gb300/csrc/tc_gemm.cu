@@ -361,16 +361,17 @@ __global__ void __launch_bounds__(128, MINB)
       long long hi[8], lo[8];
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        hi[jj] = lo[jj] = 0;
+        // the order sums are exact integers below 2^22: the FP32 add of
+        // 1.5 2^23 puts them in the low mantissa bits; pairs of orders
+        // o_u 2^7 + o_{u+1} stay below 2^29 and combine in 32 bits
+        int d[R2_S];
 #pragma unroll
-        for (int u = 0; u < R2_S; ++u) {
-          // the order sums are exact integers below 2^22: the FP32 add of
-          // 1.5 2^23 puts them in the low mantissa bits
-          const long long d =
-              (long long)(__float_as_int(__uint_as_float(v[u][jj]) + 12582912.0f) - 0x4B400000);
-          if (u < 4) hi[jj] = hi[jj] * 128 + d;
-          else lo[jj] = lo[jj] * 128 + d;
-        }
+        for (int u = 0; u < R2_S; ++u)
+          d[u] = __float_as_int(__uint_as_float(v[u][jj]) + 12582912.0f) - 0x4B400000;
+        const int p0 = d[0] * 128 + d[1], p1 = d[2] * 128 + d[3];
+        const int p2 = d[4] * 128 + d[5], p3 = d[6] * 128 + d[7];
+        hi[jj] = (long long)p0 * 16384 + p1;
+        lo[jj] = (long long)p2 * 16384 + p3;
       }
 #pragma unroll
       for (int jc = 0; jc < 4; ++jc) {
