@@ -235,8 +235,8 @@ __global__ void __launch_bounds__(128, 2)
 // real entry (GB300 issues 2 FP64 operations per clock per SM).
 constexpr int R2_S = 8;
 
-template <int BN, int R2_STAGES, int MINB>
-__global__ void __launch_bounds__(128, MINB)
+template <int BN, int R2_STAGES, int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB)
     rank2_update_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, const int* __restrict__ ex,
                         int m, zd* __restrict__ A, int n, int o, int ct0,
@@ -321,20 +321,24 @@ __global__ void __launch_bounds__(128, MINB)
         : "memory");
   }
   __syncwarp();
-  // while TMA and the MMAs run, every thread fetches the FP64 entries of its
-  // row that the tile updates (the epilogue is otherwise bound by these
-  // loads' DRAM latency)
-  const int rl = warp * 32 + lane, r = m0 + rl;
+  // The epilogue: warps w and w + 4 share the TMEM lanes (rows) of quadrant
+  // w % 4 and take half of the tile's columns each.  While TMA and the MMAs
+  // run, every thread fetches the FP64 entries of its row and columns that
+  // the tile updates (the epilogue is otherwise bound by these loads' DRAM
+  // latency).
+  constexpr int HALVES = NT / 128, CWH = CW / HALVES, BNH = BN / HALVES;
+  const int quad = warp & 3, half = warp >> 2;
+  const int rl = quad * 32 + lane, r = m0 + rl;
   const bool live = r < m;
   zd* az = A + (size_t)z * n * n + (size_t)o * n + o;
-  zd old[CW];
-  int ec[CW];
+  zd old[CWH];
+  int ec[CWH];
 #pragma unroll
-  for (int cl = 0; cl < CW; ++cl) {
-    const int c = cc0 + cl;
+  for (int h = 0; h < CWH; ++h) {
+    const int c = cc0 + half * CWH + h;
     const bool use = live && c < m && c <= r;
-    old[cl] = use ? az[(size_t)c * n + r] : zmake(0.0, 0.0);
-    ec[cl] = c < m ? ex[(size_t)z * m + c] : 0;
+    old[h] = use ? az[(size_t)c * n + r] : zmake(0.0, 0.0);
+    ec[h] = c < m ? ex[(size_t)z * m + c] : 0;
   }
   const int er = live ? ex[(size_t)z * m + r] : 0;
   const bool ok = __all_sync(0xffffffffu, mbar_wait(&done, 0u, err));
@@ -343,24 +347,23 @@ __global__ void __launch_bounds__(128, MINB)
   // (BM x CW complex, row stride CW + 1) for the transposed stores
   zd* stage = reinterpret_cast<zd*>(sA);
   if (ok) {
-    // eight columns (four complex) at a time: the eight digit orders' loads
+    // four columns (two complex) at a time: the eight digit orders' loads
     // are issued together and waited for once
 #pragma unroll
-    for (int c0 = 0; c0 < BN; c0 += 8) {
-      uint32_t v[R2_S][8];
+    for (int cq = 0; cq < BNH; cq += 4) {
+      const int c0 = half * BNH + cq;
+      uint32_t v[R2_S][4];
 #pragma unroll
       for (int u = 0; u < R2_S; ++u) {
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(u * BN + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(v[u][0]), "=r"(v[u][1]), "=r"(v[u][2]), "=r"(v[u][3]), "=r"(v[u][4]),
-              "=r"(v[u][5]), "=r"(v[u][6]), "=r"(v[u][7])
-            : "r"(ta));
+        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(u * BN + c0);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v[u][0]), "=r"(v[u][1]), "=r"(v[u][2]), "=r"(v[u][3])
+                     : "r"(ta));
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      long long hi[8], lo[8];
+      long long hi[4], lo[4];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
+      for (int jj = 0; jj < 4; ++jj) {
         // the order sums are exact integers below 2^22: the FP32 add of
         // 1.5 2^23 puts them in the low mantissa bits; pairs of orders
         // o_u 2^7 + o_{u+1} stay below 2^29 and combine in 32 bits
@@ -374,14 +377,14 @@ __global__ void __launch_bounds__(128, MINB)
         lo[jj] = (long long)p2 * 16384 + p3;
       }
 #pragma unroll
-      for (int jc = 0; jc < 4; ++jc) {
-        const int cl = c0 / 2 + jc, c = cc0 + cl;
+      for (int jc = 0; jc < 2; ++jc) {
+        const int h = cq / 2 + jc, cl = half * CWH + h, c = cc0 + cl;
         zd val = zmake(0.0, 0.0);
         if (live && c < m && c <= r) {
           const long long tr = hi[2 * jc] * 2097152 + (lo[2 * jc] >> 7);
           const long long ti = hi[2 * jc + 1] * 2097152 + (lo[2 * jc + 1] >> 7);
-          const double w = __longlong_as_double((long long)(1023 + er + ec[cl] - 54) << 52);
-          val = old[cl];
+          const double w = __longlong_as_double((long long)(1023 + er + ec[h] - 54) << 52);
+          val = old[h];
           val.x = fma(-(double)tr, w, val.x);
           val.y = r == c ? 0.0 : fma(-(double)ti, w, val.y);
           az[(size_t)c * n + r] = val;
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(128, MINB)
   }
   if (ok) {
     // A22[c, r] = conj(A22[r, c]) for r > c: CW consecutive c per row r
-    for (int idx = threadIdx.x; idx < BM * CW; idx += 128) {
+    for (int idx = threadIdx.x; idx < BM * CW; idx += NT) {
       const int rr = idx / CW, cl = idx % CW;
       const int rw = m0 + rr, c = cc0 + cl;
       if (rw < m && c < m && rw > c) az[(size_t)rw * n + c] = zconj(stage[rr * (CW + 1) + cl]);
@@ -596,7 +599,7 @@ int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex
   // memory and 256 TMEM columns per CTA, two CTAs per SM (16-wide tiles at
   // three CTAs per SM measured 11 % slower: each A tile then serves half the
   // columns)
-  constexpr int BN = 32, R2_STAGES = 4, MINB = 2;
+  constexpr int BN = 32, R2_STAGES = 4, MINB = 2, NT = 256;
   if (((uintptr_t)dA & 15) || ((uintptr_t)dB & 15) || m < 1 || kb < 1 || kb > 65535) {
     bs_set_error("rank-2 update: bad operands (m = %d, batch = %d)", m, kb);
     return BS_EINVAL;
@@ -613,7 +616,7 @@ int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
   if (!attr[dev].load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(rank2_update_kernel<BN, R2_STAGES, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(rank2_update_kernel<BN, R2_STAGES, MINB, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return bs_cuda_status(e, "rank-2 update smem");
     attr[dev].store(true, std::memory_order_release);
@@ -623,8 +626,8 @@ int bs_launch_rank2_update(const uint16_t* dA, const uint16_t* dB, const int* ex
   if (nct <= 0 || ct0 + nct > tiles) nct = tiles - ct0;
   if (nct <= 0) return BS_OK;
   dim3 grid((m + BM - 1) / BM, nct, kb);
-  rank2_update_kernel<BN, R2_STAGES, MINB><<<grid, 128, smem, s>>>(ta, tb, ex, m, A, n, o, ct0,
-                                                                    err);
+  rank2_update_kernel<BN, R2_STAGES, MINB, NT><<<grid, NT, smem, s>>>(ta, tb, ex, m, A, n, o,
+                                                                       ct0, err);
   BS_CHECK_LAUNCH("rank2_update_kernel");
   return BS_OK;
 }
