@@ -13,9 +13,8 @@
 // ||T|| of T), then widened by that margin, verified with FP64 counts and
 // finished in FP64 to 4 eps64 max(||T||, |lambda|).  In the FP64 pivot
 // recurrence q_k = (d_k - x) - e_k^2 / q_{k-1} the reciprocal of q is an
-// FP32 seed refined by two Newton-Raphson steps r <- r + r (1 - q r)
-// (relative error squares each step: ~2^-23 -> 2^-46 -> below 2^-53),
-// with an exact division when q lies outside the FP32 normal range.
+// FP32 seed refined by one cubic correction (rcp64 below), with an exact
+// division when q lies outside the FP32 normal range.
 // stop_rel > 4 eps ends the FP64 phase at stop_rel ||T||: the mixed path
 // needs the eigenvalues of its FP32-reduced T only as inverse-iteration
 // shifts, for which 1e-9 ||T|| is ample.
@@ -30,38 +29,64 @@ constexpr int L = 4;        // lanes per eigenvalue
 constexpr int NTB = 32;     // threads per block: one warp, EPC eigenvalues
 constexpr int EPC = NTB / L;  // eigenvalues per CTA (a matrix's bands spread over CTAs)
 
+// 1/q from the FP32 hardware approximation r0 (relative error e = 1 - q r0
+// below 2^-22) and the series 1/q = r0 / (1 - e) = r0 (1 + e + e^2 + ...),
+// cut after e^2 (what remains is below 2^-66); exact division when q lies
+// outside [2^-119, 2^120), where the FP32 approximation is not normal.  The
+// range test reads the exponent field, so no FP64 comparison lengthens the
+// recurrence's dependency chain.
 __device__ __forceinline__ double rcp64(double q) {
-  const double aq = fabs(q);
-  if (aq > 1e-36 && aq < 1e36) {
-    double r = (double)__frcp_rn((float)q);
-    r = fma(r, fma(-q, r, 1.0), r);
-    r = fma(r, fma(-q, r, 1.0), r);
-    return r;
+  const unsigned ex = ((unsigned)__double2hiint(q) >> 20) & 0x7ffu;
+  if (ex - 904u <= 238u) {
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)q));
+    const double r0 = (double)rf;
+    const double e = fma(-q, r0, 1.0);
+    return fma(fma(e, e, e), r0, r0);
   }
   return 1.0 / q;
 }
 
+__device__ __forceinline__ float rcp32(float q) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+  return r;
+}
+
+// |q| < pivmin as an integer comparison of the magnitude bits
+__device__ __forceinline__ bool tiny64(double q, long long pivbits) {
+  return (__double_as_longlong(q) & 0x7fffffffffffffffLL) < pivbits;
+}
+__device__ __forceinline__ bool tiny32(float q, int pivbits) {
+  return (__float_as_int(q) & 0x7fffffff) < pivbits;
+}
+
 __device__ int count64(const double* __restrict__ d, const double* __restrict__ e2, int n,
                        double x, double pivmin) {
+  const long long pb = __double_as_longlong(pivmin);
   double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
+  if (tiny64(q, pb)) q = -pivmin;
   int cnt = q <= 0.0;
   for (int k = 1; k < n; ++k) {
     q = fma(-e2[k - 1], rcp64(q), d[k] - x);
-    if (fabs(q) < pivmin) q = -pivmin;
+    if (tiny64(q, pb)) q = -pivmin;
     cnt += q <= 0.0;
   }
   return cnt;
 }
 
+// The FP32 pivots take e^2 / q as e^2 times the approximate reciprocal (a
+// few FP32 ulps of e^2: the count stays exact for a matrix within a few
+// eps32 ||T|| of T, the margin the FP32 phase allows for)
 __device__ int count32(const float* __restrict__ d, const float* __restrict__ e2, int n, float x,
                        float pivmin) {
+  const int pb = __float_as_int(pivmin);
   float q = d[0] - x;
-  if (fabsf(q) < pivmin) q = -pivmin;
+  if (tiny32(q, pb)) q = -pivmin;
   int cnt = q <= 0.0f;
   for (int k = 1; k < n; ++k) {
-    q = (d[k] - x) - e2[k - 1] / q;
-    if (fabsf(q) < pivmin) q = -pivmin;
+    q = fmaf(-e2[k - 1], rcp32(q), d[k] - x);
+    if (tiny32(q, pb)) q = -pivmin;
     cnt += q <= 0.0f;
   }
   return cnt;
