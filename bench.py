@@ -257,18 +257,18 @@ def device_peaks(torch, bs=None):
     return out
 
 
-def traffic_record(kernel):
-    """DRAM bytes per step of `kernel` from the committed ncu summary, if the
+def traffic_record(kernel, key="dram_bytes_per_step"):
+    """DRAM bytes (`key`) of `kernel` from the committed ncu summary, if the
     kernel's source is unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[kernel]
+        src = os.path.join(ROOT, "paper_1310_6380_gb300", "csrc", rec["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["sha256_16"]:
+            return None
+        return rec[key]
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_1310_6380_gb300", "csrc", rec["source"])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["sha256_16"]:
-        return None
-    return rec["dram_bytes_per_step"]
 
 
 def cpu_oracle_sample(cfg, nk_sample):
@@ -683,16 +683,40 @@ def band_roofline(red, n, nk_all, ph, peaks):
                    "unit": "TFLOP/s", "peak": fp64_peak, "peak_source": "nominal FP64",
                    "algorithmic": "2 m nb^2 complex multiply-adds per panel"},
     }
-    top = max(groups, key=lambda g: red[g])
+    # The dominant kernel is the bulge chase: the largest share of the
+    # reduction's launch list (serialised, one step of config 1) and the tail
+    # every part ends with.  Its events time it alone on its SMs; the other
+    # groups' events also count time queued behind the concurrent parts (the
+    # bulk of the rank-2 update runs on low-priority streams), so their rates
+    # below are lower bounds.
+    top = "bulge_chase"
     g = groups[top]
     t = red[top] / 1e3
     scale = 1e9 if g["unit"] == "GB/s" else 1e12
     achieved = g["work"] / t / scale
+    sms = peaks.get("sms") or 152
+    occ_peak = g["peak"] * min(nk, sms) / sms
+    # DRAM traffic of one bulge_kernel launch: the committed ncu capture's
+    # bytes per matrix (the band is read once into shared memory) times this
+    # launch's matrices, while band.cu is the file the counters were taken on
+    rec = traffic_record("bulge_kernel", "dram_bytes_per_matrix")
+    traffic = rec * nk if rec is not None and n == 882 else None
     roofline = {"bound": g["bound"], "kernel": g["kernel"], "achieved": achieved,
                 "peak": g["peak"], "unit": g["unit"], "frac": achieved / g["peak"],
-                "traffic": None, "peak_source": g["peak_source"],
+                "traffic": traffic, "peak_source": g["peak_source"],
                 "algorithmic": g["algorithmic"] + f"; {nk} matrices, n={n}",
-                "group_ms_per_step": red[top]}
+                "group_ms_per_step": red[top],
+                "occupied_sms": min(nk, sms),
+                "frac_of_occupied_sms": achieved / occ_peak,
+                "occupied_note": "one CTA per matrix (the band lives in its shared memory): a "
+                                 "launch can use at most as many SMs as it has matrices; "
+                                 "frac_of_occupied_sms compares with the FP64 peak of those SMs",
+                "group_rates": {k: groups[k]["work"] / (red[k] / 1e3) /
+                                (1e9 if groups[k]["unit"] == "GB/s" else 1e12)
+                                for k in groups if red.get(k)},
+                "group_rates_note": "work / event time per group (GB/s for rank2_update and "
+                                    "a22_v, TFLOP/s for the rest); the events of every group but "
+                                    "the bulge chase include time queued behind the other parts"}
     eff = nk_all * 16.0 / 3.0 * n ** 3 / (ph["tridiag"] / 1e3) / 1e12
     reduction = {"method": "two-stage: dense -> band 8 (Householder panels, trailing updates as "
                            "8-digit exact-slice products on tcgen05), band -> tridiagonal "
