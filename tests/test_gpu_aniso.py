@@ -241,3 +241,27 @@ def test_aniso_products_beyond_the_exact_slice_limit():
         bs.bs_destroy_cell(h)
     ref = mv.OracleCell(cell, M).omega(q[0], nb)
     assert omega_rel_err(w[0], ref, omega_floor(cell)).max() <= 1e-8
+
+
+def test_aniso_reduced_matrix_full_size():
+    """C(k) of the c1 cell with orthotropic phases at M = 10 (n = 882): the
+    3N = 1323 factor of Phi is inverted by doubling and the W_i and
+    monomial products run on the exact-slice tensor path; against the
+    oracle's literal pencil."""
+    cell = cells.anisotropic_cell(cells.config1()["cell"], seed=6380)
+    M = 10
+    h = make(cell, M)
+    N, n = bs.bs_cell_dims(h)
+    oc = mv.OracleCell(cell, M)
+    try:
+        Q = np.array([0.37, 0.11])
+        out = np.empty(n * n * 2)
+        bs.bs_reduced_matrix(h, Q, out)
+    finally:
+        bs.bs_destroy_cell(h)
+    got = out.view(np.complex128).reshape(n, n).T
+    A, Om = oc.pencil(Q)
+    Li = np.linalg.inv(np.linalg.cholesky(Om))
+    ref = Li @ A @ Li.conj().T
+    low = np.tril_indices(n)
+    assert np.abs(got[low] - ref[low]).max() <= 1e-11 * np.abs(ref).max()

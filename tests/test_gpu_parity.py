@@ -228,3 +228,25 @@ def test_c1_full_size_sampled():
         ref = oc.omega(cfg["Q"][i], cfg["nbands"])
         assert omega_rel_err(w[i], ref, fl).max() <= TOL_W, i
     assert np.all(np.diff(w, axis=1) >= 0)
+
+
+def test_reduced_matrix_doubling_inverse():
+    """M = 11 (N = 529): the three N x N Gram factors are inverted by
+    doubling (levels of batched products with a ragged last pair) instead of
+    diagonal by diagonal; C(k) against the oracle's literal pencil."""
+    cell = cells.voronoi_cell(64, 24, seed=29)
+    M = 11
+    g = GpuCell(cell, M)
+    oc = mv.OracleCell(cell, M)
+    try:
+        Q = np.array([0.29, 0.17])
+        out = np.empty(g.n * g.n * 2)
+        bs.bs_reduced_matrix(g.h, Q, out)
+    finally:
+        g.close()
+    got = out.view(np.complex128).reshape(g.n, g.n).T
+    A, Om = oc.pencil(Q)
+    Li = np.linalg.inv(np.linalg.cholesky(Om))
+    ref = Li @ A @ Li.conj().T
+    low = np.tril_indices(g.n)
+    assert np.abs(got[low] - ref[low]).max() <= 1e-11 * np.abs(ref).max()
