@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(QR_NT) wrow_kernel(const zd* __restrict__ X,
 // One sweep task works on an 8 x 8 block O (rows r0 .. r0+7 below the
 // columns C0 .. C0+7 of the previous reflector) and the diagonal block D
 // of rows r0 .. r0+7, on eight lanes, lane i holding row i of both, four
-// sweeps per warp.  Row sums are lane-local; column sums are a
-// reduce-scatter over the eight lanes (lane i ends with column i).  The
+// sweeps per warp.  Row sums are lane-local; for column sums the lanes pass
+// the block's entries round so that lane i forms column i's products.  The
 // scalars of the reflector come from FP64 reciprocal square roots and one
 // reciprocal; GB300 issues FP64 at 2 operations per clock per SM, so every
 // redundant FP64 operation across lanes counts.
@@ -335,21 +335,47 @@ constexpr int CH_SLOTS = CH_WARPS * 4;  // sweeps in flight per matrix
 __device__ __forceinline__ zd gshfl(zd v, int src) {
   return zmake(__shfl_sync(0xffffffffu, v.x, src, 8), __shfl_sync(0xffffffffu, v.y, src, 8));
 }
-__device__ __forceinline__ zd gxor(zd v, int o) {
-  return zmake(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
-}
 __device__ __forceinline__ zd sel(bool c, zd a, zd b) { return c ? a : b; }
 
-// sum over the eight lanes of a group of P[i] (lane i of the group): three
-// halving exchanges, 7 complex additions per lane
-__device__ __forceinline__ zd rscatter8(const zd (&P)[8], int i) {
-  const bool b2 = i & 4, b1 = i & 2, b0 = i & 1;
-  zd Q[4], R[2];
+// element k of a lane's eight complex values, k differing between lanes (a
+// select chain: integer work, which costs the chase nothing next to its
+// FP64 issue)
+__device__ __forceinline__ zd pick8(const zd (&O)[8], int k) {
+  zd r = O[0];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) Q[q] = zadd(sel(b2, P[q + 4], P[q]), gxor(sel(b2, P[q], P[q + 4]), 4));
+  for (int q = 1; q < 8; ++q) r = sel(k == q, O[q], r);
+  return r;
+}
+
+// z_i = sum_r conj(v_r) O[r][i] on lane i of the group (row r of O on lane
+// r): in round t lane r sends O[r][(r + t) mod 8] and lane i receives
+// O[(i - t) mod 8][i], so each lane forms the products of its own column
+// and no FP64 additions cross lanes (8 complex multiply-adds per lane,
+// against 8 products and 7 complex additions of a reduce-scatter)
+__device__ __forceinline__ zd colsum8(const zd (&O)[8], zd v, int i) {
+  zd z = zmake(0.0, 0.0);
 #pragma unroll
-  for (int q = 0; q < 2; ++q) R[q] = zadd(sel(b1, Q[q + 2], Q[q]), gxor(sel(b1, Q[q], Q[q + 2]), 2));
-  return zadd(sel(b0, R[1], R[0]), gxor(sel(b0, R[0], R[1]), 1));
+  for (int t = 0; t < 8; ++t) {
+    const int src = (i - t) & 7;
+    const zd got = gshfl(pick8(O, (i + t) & 7), src);
+    z = zfmac(got, gshfl(v, src), z);
+  }
+  return z;
+}
+
+// 1/x from the FP32 hardware approximation r0 and the series r0 (1 + e +
+// e^2), e = 1 - x r0 (below 2^-66 of it left out); exact division outside
+// the FP32 normal range
+__device__ __forceinline__ double rcp_d(double x) {
+  const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+  if (ex - 904u <= 238u) {
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)x));
+    const double r0 = (double)rf;
+    const double e = fma(-x, r0, 1.0);
+    return fma(fma(e, e, e), r0, r0);
+  }
+  return 1.0 / x;
 }
 
 __device__ __forceinline__ double gsum(double v) {
@@ -451,7 +477,7 @@ __global__ void __launch_bounds__(CH_WARPS * 32, 1)
         beta = zscale(al, -nu * ra);
         tau = (aa + nu) * rn;
         // 1 / (alpha - beta) = conj(alpha) ra / (|alpha| + nu)
-        scl = zscale(zconj(al), ra / (aa + nu));
+        scl = zscale(zconj(al), ra * rcp_d(aa + nu));
       } else {
         beta = zmake(-nu, 0.0);
         tau = 1.0;
@@ -461,10 +487,7 @@ __global__ void __launch_bounds__(CH_WARPS * 32, 1)
     const zd v = i == 0 ? zmake(1.0, 0.0) : ((i < L && tau != 0.0) ? zmul(x, scl) : zero);
     // O <- H O: z_j = sum_i conj(v_i) O[i][j], O[i][j] -= tau v_i z_j
     {
-      zd P[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) P[j] = zmul(zconj(v), O[j]);
-      const zd zi = rscatter8(P, i);
+      const zd zi = colsum8(O, v, i);
       const zd tv = zscale(v, tau);
 #pragma unroll
       for (int j = 0; j < 8; ++j) O[j] = zfnma(tv, gshfl(zi, j), O[j]);
