@@ -278,8 +278,11 @@ int bs_set_iteration_limits(int lobpcg_maxit, int bisect_sweeps);
  * product), [2] the W formation, [3] the trailing rank-2nb update (tensor
  * cores, FP64 epilogue), [4] the bulge chase to tridiagonal form; [5] the
  * number of matrices those launches processed.  The reduction runs the
- * batch in parts on concurrent streams; the times bracket the first part's
- * launches, which run beside the others'.  All zeros when profiling
+ * batch in parts on concurrent streams (per part, the chain of panel steps
+ * on a high-priority stream and the bulk of each rank-2nb update on a
+ * low-priority one); the times are event pairs around the first part's
+ * launches, which run beside the others', so every group but the bulge
+ * chase also counts time its launches waited for SMs.  All zeros when profiling
  * is off or the last solve took the one-stage reduction.  A measurement aid
  * (the paper has no counterpart).
  */
